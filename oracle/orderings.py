@@ -1,0 +1,186 @@
+"""ORACLE (test infrastructure only): the two vertex orderings of Section 3.2, in
+pure Python for small graphs.  Every function returns ``new_id`` with
+``new_id[old] = position of old vertex in the new order`` (the pi^-1 of
+Algorithm 1).
+
+Readings where the paper is silent (the product follows the same ones):
+
+* RCM (Section 3.2.1 names it only by citation): each connected component, taken
+  in order of its smallest vertex id, is started from a pseudo-peripheral vertex
+  found by the George-Liu iteration from that smallest id (repeat: BFS from x;
+  y = a vertex of minimum degree, smallest id on ties, in the last level; move to
+  y while its eccentricity is larger).  Cuthill-McKee visits the unvisited
+  neighbours of each dequeued vertex in ascending (degree, id).  The
+  concatenated order is reversed as a whole.
+* JaccardWithWindows (Algorithm 1): pop(Q) takes the smallest remaining id;
+  argmax ties go to the smallest id; J is compared as an exact rational
+  |N(j) & U| / |N(j) | U|, with 0/0 read as 0; the last window may be shorter
+  than w and gets ceil(L/sigma) clusters.
+* The pre-pass that Section 3.2 takes from Gorder is replaced by a documented
+  stand-in (Gorder itself is a third-party algorithm): a BFS visit order that
+  starts each component at the highest-degree unvisited vertex (smallest id on
+  ties) and scans neighbours in ascending id.  It groups the neighbours of the
+  same hub into the same window, which is what the pre-pass is there for.
+"""
+from __future__ import annotations
+
+from collections import deque
+from fractions import Fraction
+
+import numpy as np
+
+
+def _adj(n, row_ptr, col_idx):
+    rp = np.asarray(row_ptr, dtype=np.int64)
+    ci = np.asarray(col_idx, dtype=np.int64)
+    return [ci[rp[v]:rp[v + 1]].tolist() for v in range(n)]
+
+
+def _bfs_levels(adj, root):
+    lvl = {root: 0}
+    order = [root]
+    q = deque([root])
+    while q:
+        u = q.popleft()
+        for v in adj[u]:
+            if v not in lvl:
+                lvl[v] = lvl[u] + 1
+                order.append(v)
+                q.append(v)
+    return lvl
+
+
+def pseudo_peripheral(adj, start) -> int:
+    """George-Liu: from x, take y = min-degree (then min id) vertex of the last BFS
+    level; continue from y while its eccentricity grows."""
+    x = start
+    lx = _bfs_levels(adj, x)
+    ex = max(lx.values())
+    while True:
+        last = [v for v, d in lx.items() if d == ex]
+        y = min(last, key=lambda v: (len(adj[v]), v))
+        ly = _bfs_levels(adj, y)
+        ey = max(ly.values())
+        if ey > ex:
+            x, lx, ex = y, ly, ey
+        else:
+            return x
+
+
+def rcm(n: int, row_ptr, col_idx) -> np.ndarray:
+    """Reverse Cuthill-McKee, new_id[old]."""
+    adj = _adj(n, row_ptr, col_idx)
+    seen = [False] * n
+    order = []
+    for v0 in range(n):
+        if seen[v0]:
+            continue
+        r = pseudo_peripheral(adj, v0)
+        seen[r] = True
+        q = deque([r])
+        while q:
+            u = q.popleft()
+            order.append(u)
+            nb = sorted((v for v in adj[u] if not seen[v]), key=lambda v: (len(adj[v]), v))
+            for v in nb:
+                seen[v] = True
+                q.append(v)
+    new_id = np.empty(n, dtype=np.int32)
+    for pos, v in enumerate(order):
+        new_id[v] = n - 1 - pos
+    return new_id
+
+
+def hub_bfs_prepass(n: int, row_ptr, col_idx) -> np.ndarray:
+    """Stand-in pre-pass: BFS visit order, each component rooted at the
+    highest-degree unvisited vertex (smallest id on ties), neighbours in
+    ascending id.  new_id[old]."""
+    adj = _adj(n, row_ptr, col_idx)
+    cand = sorted(range(n), key=lambda v: (-len(adj[v]), v))
+    seen = [False] * n
+    order = []
+    for r in cand:
+        if seen[r]:
+            continue
+        seen[r] = True
+        q = deque([r])
+        while q:
+            u = q.popleft()
+            order.append(u)
+            for v in sorted(adj[u]):
+                if not seen[v]:
+                    seen[v] = True
+                    q.append(v)
+    new_id = np.empty(n, dtype=np.int32)
+    for pos, v in enumerate(order):
+        new_id[v] = pos
+    return new_id
+
+
+def jaccard_windows(n: int, row_ptr, col_idx, sigma: int = 8, w: int = 1 << 16) -> np.ndarray:
+    """Algorithm 1 (JaccardWithWindows) on the graph as labelled, new_id[old].
+    N(j) is column j of A, i.e. CSR row j for a symmetric graph."""
+    if w % sigma != 0 or w <= 0:
+        raise ValueError("w must be a positive multiple of sigma")
+    adj = [set(a) for a in _adj(n, row_ptr, col_idx)]
+    new_id = np.full(n, -1, dtype=np.int64)
+    for s_k in range(0, n, w):
+        e_k = min(s_k + w, n)
+        Q = list(range(s_k, e_k))            # kept sorted; pop(Q) = smallest id
+        L_k = e_k - s_k
+        M_k = (L_k + sigma - 1) // sigma
+        for ell in range(M_k):
+            j_star = Q.pop(0)
+            new_id[j_star] = s_k + ell * sigma
+            U = set(adj[j_star])
+            for r in range(1, sigma):
+                if not Q:
+                    break
+                best, best_j = None, None
+                for j in Q:                   # ascending id: strict > keeps the smallest on ties
+                    inter = len(adj[j] & U)
+                    union = len(adj[j] | U)
+                    J = Fraction(inter, union) if union else Fraction(0)
+                    if best is None or J > best:
+                        best, best_j = J, j
+                Q.remove(best_j)
+                new_id[best_j] = s_k + ell * sigma + r
+                U |= adj[best_j]
+    return new_id.astype(np.int32)
+
+
+def compose(first: np.ndarray, second: np.ndarray) -> np.ndarray:
+    """new_id of applying ``first`` then ``second`` (both new_id[old])."""
+    return np.asarray(second)[np.asarray(first)]
+
+
+def compress_order(n: int, row_ptr, col_idx, sigma: int = 8, w: int = 1 << 16) -> np.ndarray:
+    """The compression-oriented ordering: pre-pass, then Algorithm 1 on the
+    relabelled graph."""
+    p = hub_bfs_prepass(n, row_ptr, col_idx)
+    rp2, ci2 = relabel(n, row_ptr, col_idx, p)
+    return compose(p, jaccard_windows(n, rp2, ci2, sigma, w))
+
+
+def relabel(n: int, row_ptr, col_idx, new_id) -> tuple[np.ndarray, np.ndarray]:
+    """CSR of the graph with vertex v renamed new_id[v], rows sorted."""
+    rp = np.asarray(row_ptr, dtype=np.int64)
+    ci = np.asarray(col_idx, dtype=np.int64)
+    new_id = np.asarray(new_id, dtype=np.int64)
+    old_of = np.empty(n, dtype=np.int64)
+    old_of[new_id] = np.arange(n)
+    deg = np.diff(rp)[old_of]
+    rp2 = np.zeros(n + 1, dtype=np.int64)
+    rp2[1:] = np.cumsum(deg)
+    ci2 = np.empty(len(ci), dtype=np.int64)
+    for v_new in range(n):
+        v = old_of[v_new]
+        ci2[rp2[v_new]:rp2[v_new + 1]] = np.sort(new_id[ci[rp[v]:rp[v + 1]]])
+    return rp2.astype(np.int32), ci2.astype(np.int32)
+
+
+def bandwidth(n: int, row_ptr, col_idx) -> int:
+    rp = np.asarray(row_ptr, dtype=np.int64)
+    ci = np.asarray(col_idx, dtype=np.int64)
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(rp))
+    return int(np.abs(rows - ci).max()) if len(ci) else 0

@@ -1,0 +1,150 @@
+"""Pins for the oracle BVSS builder (Section 3.1): decode round trip, the
+Figure 1 caption example, placement rules and the Table 3 column relations."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import bvss as ob
+from oracle import model as om
+from paper_2512_21967_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "fig1_caption.json")
+
+
+def fig1_graph():
+    edges = []
+    edges += [(r, (r - 100) % 8) for r in range(100, 400)]
+    edges += [(r, 8 + (r - 400) % 8) for r in range(400, 450)]
+    edges += [(r, 16 + (r - 200) % 8) for r in range(200, 399)]
+    edges += [(3, 17), (3, 19), (3, 22)]
+    src = np.array([e[0] for e in edges], np.int32)
+    dst = np.array([e[1] for e in edges], np.int32)
+    return synth.csr_from_edges(512, src, dst)
+
+
+def decode(b: ob.BVSS):
+    """Adjacency (set of (row, col)) back from the BVSS arrays alone."""
+    out = set()
+    spt = 32 // b.sigma
+    for nu in range(b.num_vss):
+        s = int(b.virtual_to_real[nu])
+        for lane in range(32):
+            word = int(b.masks[32 * nu + lane])
+            for sub in range(spt):
+                m = (word >> (b.sigma * sub)) & ((1 << b.sigma) - 1)
+                u = int(b.row_ids[b.tau * nu + spt * lane + sub])
+                for j in range(b.sigma):
+                    if (m >> j) & 1:
+                        out.add((u, b.sigma * s + j))
+    return out
+
+
+def adjacency_pairs(g):
+    rows = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    return set(zip(rows.tolist(), g.col_idx.tolist()))
+
+
+def test_fig1_caption_example():
+    fx = json.load(open(GOLDEN))["facts"]
+    g = fig1_graph()
+    b = ob.build(g.n, g.row_ptr, g.col_idx)
+    rp = b.real_ptrs
+    assert list(range(rp[0], rp[1])) == fx["vss_of_slice_set_0"]
+    assert list(range(rp[2], rp[3])) == fx["vss_of_slice_set_2"]
+    tau = b.tau
+    for v in fx["full_vss"]:
+        assert b.vss_count[v] == tau
+    for v in fx["padded_vss"]:
+        assert b.vss_count[v] < tau
+    # row 3 in VSS 4: smallest row of slice set 2, so k = 0 -> lane 0, sub-slot 0
+    nu = fx["vss_of_slice_set_2"][0]
+    slices = ob.vss_slices(b, nu)
+    u, m = slices[0]
+    assert u == fx["row"]
+    cols_1based = [j + 1 for j in range(8) if (m >> j) & 1]
+    assert cols_1based == fx["row_mask_columns_1based"]
+    assert b.row_ids[tau * nu + 0] == fx["row"] and fx["row_handled_by_thread"] == 0
+    # frontier "11000000": first two columns of slice set 2
+    alpha = sum(1 << (c - 1) for c in fx["frontier_columns_1based"])
+    assert m & alpha != 0                                     # pull produces a hit
+    assert fx["row"] // 8 == fx["row_slice_set"]
+    assert fx["row"] // 32 == fx["row_next_frontier_word"]
+    assert fx["row"] % 32 + 1 == fx["row_next_frontier_bit_1based"]
+
+
+@pytest.mark.parametrize("scale,seed", [(7, 1), (8, 4), (9, 2)])
+def test_round_trip_rmat(scale, seed):
+    g = synth.rmat_graph(scale, 16, seed=seed)
+    b = ob.build(g.n, g.row_ptr, g.col_idx)
+    assert decode(b) == adjacency_pairs(g)
+
+
+def test_round_trip_ragged_n_and_isolated():
+    # n not a multiple of sigma, isolated vertices, an empty slice set
+    n = 45
+    edges = [(0, 44), (1, 2), (30, 31), (44, 3), (20, 21)]
+    src = np.array([e[0] for e in edges], np.int32)
+    dst = np.array([e[1] for e in edges], np.int32)
+    g = synth.csr_from_edges(n, src, dst)
+    b = ob.build(n, g.row_ptr, g.col_idx)
+    assert len(b.real_ptrs) == (n + 7) // 8 + 1
+    assert decode(b) == adjacency_pairs(g)
+    # slice set 1 (columns 8..15) has no edge: no VSS
+    assert b.real_ptrs[2] - b.real_ptrs[1] == 0
+
+
+def test_placement_rules():
+    g = synth.rmat_graph(10, 16, seed=7)
+    b = ob.build(g.n, g.row_ptr, g.col_idx)
+    tau = b.tau
+    for s in range(b.num_slice_sets):
+        vs = range(b.real_ptrs[s], b.real_ptrs[s + 1])
+        rows = []
+        for i, nu in enumerate(vs):
+            assert b.virtual_to_real[nu] == s
+            sl = ob.vss_slices(b, nu)
+            # only the last VSS of a slice set may be partial
+            if i + 1 < len(vs):
+                assert len(sl) == tau
+            assert all(m != 0 for _, m in sl)
+            rows += [u for u, _ in sl]
+            # padding: zero masks, last real row
+            for k in range(len(sl), tau):
+                lane, sub = k % 32, k // 32
+                assert (int(b.masks[32 * nu + lane]) >> (8 * sub)) & 0xFF == 0
+                assert b.row_ids[tau * nu + 4 * lane + sub] == sl[-1][0]
+        assert rows == sorted(rows) and len(set(rows)) == len(rows)
+
+
+def test_table3_relations():
+    """Relations between Table 3's columns that hold by construction: bits =
+    sigma x unpadded slices; compression = |E| / bits; #slices = tau x #VSS;
+    #VSS >= #non-empty slice sets; BVSS bytes = 5 B x #slices + 4 B x #VSS +
+    4 B x (#slice sets + 1).  Checked on Table 3's printed GAP-road row too."""
+    g = synth.rmat_graph(9, 16, seed=11)
+    b = ob.build(g.n, g.row_ptr, g.col_idx)
+    unp = ob.unpadded_slices(b)
+    assert len(b.row_ids) == b.tau * b.num_vss
+    assert b.num_vss >= int(np.count_nonzero(np.diff(b.real_ptrs)))
+    cr = om.compression_ratio(g.nnz, unp)
+    assert 1 / 8 <= cr <= 1.0
+    # printed GAP-road row: 48,228,067 unpadded slices x 8 = 385,824,536 bits;
+    # 2,993,419 VSS x 128 = 383,157,632 slices; 5 B/slice ~ 1.92 GB (printed 1.93)
+    assert 48_228_067 * 8 == 385_824_536
+    assert 2_993_419 * 128 == 383_157_632
+    assert abs(383_157_632 * 5 / 1e9 - 1.93) < 0.02
+    # vectorised per-slice-set slice counts agree with the slow builder
+    per_set = ob.slice_set_stats(g.n, g.row_ptr, g.col_idx)
+    assert int(per_set.sum()) == unp
+    assert np.array_equal((per_set + b.tau - 1) // b.tau, np.diff(b.real_ptrs))
+
+
+def test_planted_mistake_transposed_placement_fails():
+    """Swapping lane and sub-slot (a transposed placement) must break the decode."""
+    g = synth.rmat_graph(7, 16, seed=1)
+    b = ob.build(g.n, g.row_ptr, g.col_idx)
+    bad = ob.BVSS(b.n, b.sigma, b.real_ptrs, b.virtual_to_real,
+                  b.row_ids.reshape(-1, 32, 4).transpose(0, 2, 1).reshape(-1).copy(), b.masks, b.vss_count)
+    assert decode(bad) != adjacency_pairs(g)
