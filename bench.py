@@ -1,0 +1,431 @@
+#!/usr/bin/env python
+"""GTEPS benchmark of the GB300 BVSS breadth-first search.
+
+Default workload: single-source BFS on an R-MAT graph of scale 23 (8,388,608
+vertices, edgefactor 16, quadrant probabilities (0.57, 0.19, 0.19, 0.05),
+seeded relabel, symmetrised, self-loops and duplicates dropped), reordered
+with the compression-oriented ordering, 64 seeded sources from vertices of
+degree > 0 timed one at a time.  One step = the 64 traversals.
+
+GTEPS = undirected edges in the reached component / device traversal time
+(Graph500 convention); reordering and the BVSS build are timed separately.
+The L2 is flushed (a 256 MiB write) before every traversal, outside its CUDA
+event pair.
+
+Arms:
+  --impl ours       (default) the CUDA path through the C ABI.
+  --impl reference  the CPU oracle (plain queue BFS, one thread) on the same
+                    workload, a bounded sample of sources per step.
+Multi-GPU (torchrun, N > 1): every rank runs the whole step on its own GPU on
+its own copy of the graph ("replicas only"; single-source BFS has no sharding
+without a per-level exchange), value = all ranks' edges / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GTEPS (1 GB300, bit-exact levels), single vs batched multi-source; % HBM roofline"
+
+WORKLOADS = {
+    # name: (kind, size, sources, order, seed_graph, seed_src, msbfs_k)
+    "rmat23": ("rmat", 23, 64, "compress", 2, 1002, 0),
+    "rmat16": ("rmat", 16, 64, "compress", 1, 1001, 0),
+    "grid4096": ("grid", 4096, 64, "bandwidth", 3, 1003, 0),
+    "rmat22-ms64": ("rmat", 22, 64, "compress", 4, 1004, 64),
+    "rmat22-ms256": ("rmat", 22, 256, "compress", 4, 1004, 256),
+    "rmat22-single": ("rmat", 22, 64, "compress", 4, 1004, 0),
+}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def build_workload(name, window):
+    from paper_2512_21967_gb300 import synth
+    kind, size, nsrc, order, sg, ss, k = WORKLOADS[name]
+    t0 = time.time()
+    if kind == "rmat":
+        g, srcs = synth.rmat_workload(size, nsrc, seed_graph=sg, seed_src=ss)
+    else:
+        g, srcs = synth.grid_workload(size, nsrc, seed_graph=sg, seed_src=ss)
+    return g, srcs, order, k, time.time() - t0
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid=None):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if device_uuid:
+            cmd += ["-i", device_uuid]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": float(max(power)) if power else None}
+
+
+# ------------------------------------------------------------- byte model
+
+def byte_model(h, g, n):
+    """Per-slice-set algorithmic bytes of one stage-1 visit: every VSS of the
+    set costs 5 B per unpadded slice (4 B row id + 1 B mask) + 8 B to read its
+    queue entry + 8 B to write it one level earlier."""
+    import paper_2512_21967_gb300 as blest
+    rp = blest.blest_export(h, blest.BLEST_ARRAY_REAL_PTRS).astype(np.int64)
+    cnt = blest.blest_export(h, blest.BLEST_ARRAY_VSS_COUNT).astype(np.int64)
+    per_vss = 5 * cnt + 16
+    pref = np.zeros(len(per_vss) + 1, np.int64)
+    pref[1:] = np.cumsum(per_vss)
+    w_s = pref[rp[1:]] - pref[rp[:-1]]
+    new_id = blest.blest_export(h, blest.BLEST_ARRAY_NEW_ID).astype(np.int64)
+    return w_s, new_id
+
+
+def traversal_bytes(levels_t, new_id_t, w_s_t, nss, n, lazy, torch):
+    """Algorithmic bytes of one traversal from its (device) level array."""
+    reached = levels_t >= 0
+    nreached = int(reached.sum().item())
+    lv = levels_t[reached].long()
+    s = new_id_t[reached] >> 3
+    key = torch.unique(lv * nss + s)
+    stage1 = int(w_s_t[key % nss].sum().item())
+    nlevels = int(lv.max().item()) + 1          # levels 1..max+1 are processed
+    nwords = (n + 31) // 32
+    sweeps = (nlevels + 1) if lazy else 1       # level 0 plus one per lazy level
+    sweep = sweeps * nwords * 8
+    return stage1 + sweep + 4 * nreached + 12 * n, nreached
+
+
+# ------------------------------------------------------------------ ours
+
+def run_ours(args):
+    import torch
+
+    import paper_2512_21967_gb300 as blest
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    g, srcs, order_name, msk, t_gen = build_workload(args.workload, args.window)
+    order = {"compress": blest.BLEST_ORDER_COMPRESS, "bandwidth": blest.BLEST_ORDER_BANDWIDTH,
+             "none": blest.BLEST_ORDER_NONE}[order_name]
+    t0 = time.time()
+    h = blest.blest_graph_create_ex(g.n, g.row_ptr, g.col_idx, order, window=args.window)
+    t_create = time.time() - t0
+    st = blest.blest_get_stats(h)
+    if args.update != "auto":
+        blest.blest_set_option(h, blest.BLEST_OPT_UPDATE,
+                               blest.BLEST_UPDATE_EAGER if args.update == "eager" else blest.BLEST_UPDATE_LAZY)
+    if args.pull == "mma":
+        blest.blest_set_option(h, blest.BLEST_OPT_PULL, blest.BLEST_PULL_MMA)
+    if args.blocks_per_sm:
+        blest.blest_set_option(h, blest.BLEST_OPT_BLOCKS_PER_SM, args.blocks_per_sm)
+    blest.blest_set_option(h, blest.BLEST_OPT_UNROLL, args.unroll)
+    n = g.n
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    deg_t = torch.from_numpy(g.degrees()).to(dev)
+    w_s, new_id = byte_model(h, g, n)
+    w_s_t = torch.from_numpy(w_s).to(dev)
+    new_id_t = torch.from_numpy(new_id).to(dev)
+    nss = (n + 7) // 8
+
+    if msk:
+        return run_ours_msbfs(args, torch, blest, h, g, srcs, msk, dev, stream, flush, st, t_gen, t_create,
+                              rank, world)
+
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    edges = np.zeros(len(srcs), np.int64)
+    abytes = np.zeros(len(srcs), np.int64)
+    lazy = None
+
+    def one_step(timed_events=None):
+        for i, s in enumerate(srcs):
+            flush.fill_(i & 0xFF)
+            if timed_events is not None:
+                timed_events[i][0].record(stream)
+            blest.blest_bfs_device(h, int(s), out, stream=stream)
+            if timed_events is not None:
+                timed_events[i][1].record(stream)
+
+    # warm-up; the first pass also measures edges and bytes per source
+    for w in range(args.warmup):
+        if w == 0:
+            for i, s in enumerate(srcs):
+                blest.blest_bfs_device(h, int(s), out, stream=stream)
+                blest.blest_sync(h)
+                edges[i] = int((deg_t[out >= 0]).sum().item()) // 2
+                if lazy is None:
+                    info, _ = blest.blest_get_run_info(h)
+                    lazy = info["update"] == blest.BLEST_UPDATE_LAZY
+                abytes[i], _ = traversal_bytes(out, new_id_t, w_s_t, nss, n, lazy, torch)
+        else:
+            one_step()
+    blest.blest_sync(h)
+    torch.cuda.synchronize(dev)
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid) if rank == 0 else None
+    events = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in srcs]
+              for _ in range(args.steps)]
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        one_step(events[k])
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    blest.blest_sync(h)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    per = np.array([[e[0].elapsed_time(e[1]) for e in step] for step in events])  # ms
+    bfs_ms = float(per.sum())
+    wall_ms = t_start.elapsed_time(t_end)
+    tot_edges = float(edges.sum()) * args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([bfs_ms, tot_edges], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        bfs_ms_max, edges_all = float(mx[0]), float(sm[1])
+    else:
+        bfs_ms_max, edges_all = bfs_ms, tot_edges
+    value = edges_all / (bfs_ms_max / 1e3) / 1e9
+    avg_launch_ms = float(per.mean())
+    avg_bytes = float(abytes.mean())
+    hbm, peak_kind = peaks()
+    achieved = avg_bytes / (avg_launch_ms / 1e3) / 1e9
+
+    # end to end through the host-buffer C call
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        host = np.empty(n, np.int32)
+        t0 = time.perf_counter()
+        for s in srcs:
+            blest.blest_bfs(h, int(s), host)
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": float(edges.sum()) / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": 0,
+               "d2h_bytes_per_step": int(len(srcs) * n * 4),
+               "what": "blest_bfs(handle, src, host levels) for the 64 sources, levels copied to host memory"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(g, srcs, args.cpu_sources, edges_of=None)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(bfs_ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"single-source BFS, {g.name}, {len(srcs)} seeded sources, {order_name} order",
+                       "n": g.n, "directed_edges": g.nnz, "sources_per_step": len(srcs),
+                       "order": order_name, "window": args.window,
+                       "update": "lazy" if lazy else "eager", "pull": args.pull, "unroll": args.unroll,
+                       "l2": "flushed by a 256 MiB write before every traversal, outside its event pair",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(achieved / hbm, 4), "peak_kind": peak_kind, "traffic": None,
+                         "kernel": "bfs_kernel (fused persistent traversal)",
+                         "bytes_per_launch": avg_bytes, "avg_launch_ms": round(avg_launch_ms, 5)},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(args.steps * len(srcs)),
+            "clocks": clocks,
+            "ms_per_step_wall": round(wall_ms / args.steps, 4),
+            "bvss": {k: st[k] for k in ("num_slice_sets", "num_vss", "num_slices", "unpadded_slices",
+                                        "connectivity_bits", "update_divergence", "compression_ratio",
+                                        "bvss_bytes")},
+            "preprocess_s": {"generate": round(t_gen, 2), "create_total": round(t_create, 2),
+                             "order": round(st["order_seconds"], 2), "build": round(st["build_seconds"], 2)},
+            "gteps_per_source_ms": {"min": round(float(per.min()), 4), "median": round(float(np.median(per)), 4),
+                                    "max": round(float(per.max()), 4)},
+        }
+        print(json.dumps(line), flush=True)
+    blest.blest_destroy(h)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_ours_msbfs(args, torch, blest, h, g, srcs, k, dev, stream, flush, st, t_gen, t_create, rank, world):
+    n = g.n
+    out = torch.empty((k, n), dtype=torch.int32, device=dev)
+    deg_t = torch.from_numpy(g.degrees()).to(dev)
+    for _ in range(args.warmup):
+        blest.blest_msbfs_device(h, srcs[:k], out, stream=stream)
+    blest.blest_sync(h)
+    edges = int(((out >= 0).to(torch.int64) * deg_t[None, :]).sum().item()) // 2
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler() if rank == 0 else None
+    evs = [[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        evs[i][0].record(stream)
+        blest.blest_msbfs_device(h, srcs[:k], out, stream=stream)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    blest.blest_sync(h)
+    clocks = sampler.stop() if sampler else None
+    ms = float(sum(e[0].elapsed_time(e[1]) for e in evs))
+    value = edges * args.steps / (ms / 1e3) / 1e9
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": {"workload": f"multi-source BFS k={k}, {g.name}", "n": n, "directed_edges": g.nnz,
+                           "k": k, "source_bfs_per_s": round(k * args.steps / (ms / 1e3), 2)},
+                "gpu_launches": args.steps, "clocks": clocks,
+                "bvss": {kk: st[kk] for kk in ("num_vss", "unpadded_slices", "compression_ratio")},
+                "preprocess_s": {"generate": round(t_gen, 2), "create_total": round(t_create, 2)}}
+        print(json.dumps(line), flush=True)
+    blest.blest_destroy(h)
+
+
+# ------------------------------------------------------------- CPU oracle
+
+def cpu_baseline(g, srcs, nsrc, edges_of=None):
+    """The oracle (plain single-threaded queue BFS) timed on the host on the
+    first ``nsrc`` sources of the same workload."""
+    import oracle
+    sample = [int(s) for s in srcs[:nsrc]]
+    tot_e, tot_t = 0, 0.0
+    for s in sample:
+        t0 = time.perf_counter()
+        lv = oracle.bfs_levels(g.n, g.row_ptr, g.col_idx, s)
+        tot_t += time.perf_counter() - t0
+        tot_e += oracle.reached_edges(g.row_ptr, lv)
+    return {"value": round(tot_e / tot_t / 1e9, 5), "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"{len(sample)} of the {len(srcs)} sources, one thread, nproc={os.cpu_count()}",
+            "seconds": round(tot_t, 2)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    g, srcs, order_name, k, t_gen = build_workload(args.workload, args.window)
+    import oracle
+    per_step = max(1, args.ref_sources)
+    for w in range(args.warmup):
+        s = int(srcs[w % len(srcs)])
+        oracle.bfs_levels(g.n, g.row_ptr, g.col_idx, s)
+    tot_e, tot_t = 0, 0.0
+    for k_ in range(args.steps):
+        for j in range(per_step):
+            s = int(srcs[(k_ * per_step + j) % len(srcs)])
+            t0 = time.perf_counter()
+            lv = oracle.bfs_levels(g.n, g.row_ptr, g.col_idx, s)
+            tot_t += time.perf_counter() - t0
+            tot_e += oracle.reached_edges(g.row_ptr, lv)
+    value = tot_e / tot_t / 1e9
+    line = {"metric": METRIC, "value": round(value, 5), "unit": "GTEPS", "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_t / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": f"single-source BFS, {g.name}, {len(srcs)} seeded sources", "n": g.n,
+                       "directed_edges": g.nnz, "sources_per_step": per_step},
+            "cpu_baseline": {"value": round(value, 5), "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} source(s) per step, one thread, nproc={os.cpu_count()}"},
+            "e2e": {"value": round(value, 5), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat23")
+    ap.add_argument("--window", type=int, default=4096)
+    ap.add_argument("--update", choices=["auto", "eager", "lazy"], default="auto")
+    ap.add_argument("--pull", choices=["popc", "mma"], default="popc")
+    ap.add_argument("--unroll", type=int, default=2)
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--cpu-sources", type=int, default=4)
+    ap.add_argument("--ref-sources", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 1:
+        args.warmup = 1
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,250 @@
+/*
+ * blest.h -- C ABI of a GB300 (sm_103a) breadth-first search built on Binarised
+ * Virtual Slice Sets (BVSS), after "BLEST: Blazingly Efficient BFS using Tensor
+ * Cores" (Elbek and Kaya).
+ *
+ * Problem (Section 2, Background and Notation): for a graph G = (V, E) and a
+ * source s, compute level[v] = length of a shortest s -> v path.  The search is
+ * pull-only: with A the adjacency matrix of the transposed graph and x the
+ * current frontier bit-vector, the next frontier is the Boolean SpMSpV
+ * y = A (AND, OR) x, repeated until y = 0.  Several sources stack their frontiers
+ * into a bit-matrix and the step becomes a Boolean SpMM.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every call returns a blest_status; nothing aborts the process and no kernel
+ *   traps.  blest_last_error() gives a human-readable message for the calling
+ *   thread's last failure.
+ * - Vertex ids are int32 in [0, n).  Levels are int32: 0 for a source, -1 for a
+ *   vertex that no source reaches.  All outputs use the caller's ORIGINAL vertex
+ *   ids; the internal reordering is undone on the device.
+ * - Host pointers stay owned by the caller; the library copies what it keeps.
+ *   Device pointers (the *_device calls) must be CUDA device memory of the
+ *   current device, also caller-owned.
+ * - A handle owns its device memory and one CUDA stream.  A handle is not
+ *   re-entrant: calls on the same handle must not overlap in time.  Distinct
+ *   handles may be used from distinct threads.
+ * - The graph must be symmetric (u in N(v) iff v in N(u)).  Self-loops and
+ *   duplicate entries are accepted and ignored; they do not change levels.
+ *   Rows need not be sorted.
+ */
+#ifndef BLEST_H
+#define BLEST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct blest_graph* blest_handle;
+
+typedef enum {
+    BLEST_OK = 0,
+    BLEST_ERR_INVALID_ARG = 1,   /* bad pointer, size, id or option */
+    BLEST_ERR_NOT_SYMMETRIC = 2, /* some edge (u, v) has no (v, u) */
+    BLEST_ERR_TOO_LARGE = 3,     /* nnz >= 2^31, or more virtual slice sets than int32 holds */
+    BLEST_ERR_OOM = 4,           /* device or host allocation failed */
+    BLEST_ERR_CUDA = 5,          /* a CUDA runtime call failed (message in blest_last_error) */
+    BLEST_ERR_TIMEOUT = 6,       /* a grid barrier gave up after the configured limit */
+    BLEST_ERR_INTERNAL = 7       /* a device-side consistency check failed (e.g. queue overflow) */
+} blest_status;
+
+/* Vertex reordering applied before the BVSS build (Section 3.2). */
+typedef enum {
+    BLEST_ORDER_NONE = 0,       /* keep the input order */
+    BLEST_ORDER_COMPRESS = 1,   /* pre-pass + JaccardWithWindows (Algorithm 1), for social-like graphs */
+    BLEST_ORDER_BANDWIDTH = 2,  /* Reverse Cuthill-McKee, for non-social graphs (Section 3.2.1) */
+    BLEST_ORDER_AUTO = 3        /* COMPRESS if social-like, else BANDWIDTH (Section 3.2.1 classifier) */
+} blest_order;
+
+/* Level-update scheme (Section 4.2). */
+typedef enum {
+    BLEST_UPDATE_AUTO = 0,      /* lazy iff the update divergence exceeds 25,000 (Section 5) */
+    BLEST_UPDATE_EAGER = 1,     /* Algorithm 2: level write + returning atomicOr at each hit */
+    BLEST_UPDATE_LAZY = 2       /* Algorithm 3: returnless mark, then a coalesced finalisation sweep */
+} blest_update;
+
+/* How a virtual slice set is pulled against its frontier word (Section 4.1). */
+typedef enum {
+    BLEST_PULL_POPC = 0,        /* CUDA cores: AND of each 8-bit mask with the frontier byte */
+    BLEST_PULL_MMA = 1          /* two m8n8k128 b1 AND+POPC tensor-core MMAs per VSS (Figure 2c) */
+} blest_pull;
+
+/* Keys for blest_set_option.  Options apply to later traversals. */
+typedef enum {
+    BLEST_OPT_UPDATE = 0,            /* blest_update value */
+    BLEST_OPT_PULL = 1,              /* blest_pull value */
+    BLEST_OPT_BLOCKS_PER_SM = 2,     /* persistent-grid blocks per SM; 0 = as many as fit */
+    BLEST_OPT_BARRIER_TIMEOUT_US = 3,/* grid-barrier wait limit in microseconds (default 2,000,000) */
+    BLEST_OPT_RECORD_LEVELS = 4,     /* 1 = record the per-level queue sizes (blest_get_run_info) */
+    BLEST_OPT_UNROLL = 5,            /* virtual slice sets a warp loads at once: 1, 2 or 4 (default 2) */
+    BLEST_OPT_TEST_PHANTOM_BLOCK = 6 /* testing: 1 = every barrier waits for one block that does not
+                                        exist, so the next traversal must end in BLEST_ERR_TIMEOUT */
+} blest_option;
+
+/* Creation parameters; pass NULL to blest_graph_create_ex for the defaults. */
+typedef struct {
+    int32_t window;          /* JaccardWithWindows window w, a multiple of 8 (default 65536, Section 5) */
+    int32_t threads;         /* host threads for reordering and cleaning; 0 = all cores */
+    int32_t skip_symmetry_check; /* 1 = trust the caller that the input is symmetric */
+} blest_create_params;
+
+/* Table 3 columns plus timings of the preprocessing, filled by blest_get_stats. */
+typedef struct {
+    int64_t n;                   /* vertices */
+    int64_t nnz;                 /* directed entries after dropping self-loops and duplicates */
+    int64_t num_slice_sets;      /* ceil(n / 8) */
+    int64_t num_vss;             /* virtual slice sets */
+    int64_t num_slices;          /* padded slices = 128 * num_vss */
+    int64_t unpadded_slices;     /* non-empty slices */
+    int64_t connectivity_bits;   /* 8 * unpadded_slices */
+    double  update_divergence;   /* U_div (Section 3.2.1) */
+    double  compression_ratio;   /* nnz / connectivity_bits (Section 3.2) */
+    int64_t bvss_bytes;          /* device bytes of the four static arrays */
+    int64_t state_bytes;         /* device bytes of queues, bitmaps and levels */
+    int32_t order;               /* blest_order actually used */
+    int32_t update;              /* blest_update the AUTO rule picks for this graph */
+    double  order_seconds;       /* host reordering time */
+    double  build_seconds;       /* everything else in create (cleaning, upload, device BVSS build) */
+} blest_stats;
+
+/* What the last traversal on a handle did, filled by blest_get_run_info. */
+typedef struct {
+    int32_t levels;              /* BFS levels processed (the last one finds nothing new) */
+    int32_t update;              /* blest_update used */
+    int32_t pull;                /* blest_pull used */
+    int32_t grid_blocks;         /* persistent-grid blocks */
+    int32_t threads_per_block;
+    int32_t recorded;            /* entries of the queue-size record below that are valid */
+} blest_run_info;
+
+/* ---------------------------------------------------------------- graphs */
+
+/* Build a handle for the symmetric CSR graph (row_ptr[n+1], col_idx[row_ptr[n]],
+ * host memory, int32, row_ptr[0] = 0, non-decreasing).  Steps: clean (sort rows,
+ * drop self-loops and duplicates), check symmetry, reorder (Section 3.2),
+ * upload, build BVSS on the device (Section 3.1: slice sets of sigma = 8 columns,
+ * virtual slice sets of tau = 128 slices, slices sorted by row and placed
+ * lane-major, the last VSS of a slice set padded with zero masks), compute the
+ * Table 3 statistics.  On failure *out is NULL.  n = 0 gives an empty handle.
+ * Errors: INVALID_ARG (NULL pointer, n < 0, malformed row_ptr, id out of range),
+ * NOT_SYMMETRIC, TOO_LARGE, OOM, CUDA. */
+blest_status blest_graph_create(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                                blest_order order, blest_handle* out);
+
+/* Same, with explicit parameters (NULL = defaults). */
+blest_status blest_graph_create_ex(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                                   blest_order order, const blest_create_params* params,
+                                   blest_handle* out);
+
+/* Build one handle over the disjoint union of num_graphs graphs, for batched
+ * traversal of many graphs in one persistent launch.  Graph g has n_each[g]
+ * vertices and CSR (row_ptrs[g], col_idxs[g]) in its own local ids, and is
+ * reordered with orders[g] inside its own id range; in the union, graph g's
+ * vertices follow those of graphs 0..g-1.  Errors as blest_graph_create. */
+blest_status blest_batch_create(int32_t num_graphs, const int32_t* n_each,
+                                const int32_t* const* row_ptrs, const int32_t* const* col_idxs,
+                                const int32_t* orders, const blest_create_params* params,
+                                blest_handle* out);
+
+/* Release the handle and all its device memory.  NULL is ignored. */
+void blest_destroy(blest_handle h);
+
+blest_status blest_set_option(blest_handle h, int32_t key, int64_t value);
+
+blest_status blest_get_stats(blest_handle h, blest_stats* out);
+
+/* --------------------------------------------------------------- traversal */
+
+/* Single-source BFS (Algorithms 2 and 3, fused into one persistent kernel per
+ * traversal, Section 4.3).  levels: host memory of n int32, caller-owned,
+ * written in original ids.  Blocks until done.
+ * Errors: INVALID_ARG (NULL handle/levels, src outside [0, n)), TIMEOUT, INTERNAL, CUDA. */
+blest_status blest_bfs(blest_handle h, int32_t src, int32_t* levels);
+
+/* k independent BFS runs from srcs[0..k) (host array), as one Boolean SpMM per
+ * level over an n x k frontier bit-matrix (Section 2, multi-source form).
+ * levels: host memory of k*n int32, row-major by source: levels[i*n + v] is the
+ * level of v from srcs[i].  Duplicate sources are allowed.  k = 0 does nothing.
+ * Errors: as blest_bfs. */
+blest_status blest_msbfs(blest_handle h, const int32_t* srcs, int32_t k, int32_t* levels);
+
+/* One BFS whose level-0 frontier is the whole set srcs[0..k) (host array):
+ * levels[v] = distance from v to the nearest source.  On a batch handle, with
+ * one source per graph, this is an independent BFS in every graph.
+ * levels: host memory of n int32. */
+blest_status blest_bfs_multiroot(blest_handle h, const int32_t* srcs, int32_t k, int32_t* levels);
+
+/* Batch handle: one source per graph, srcs_local[g] in graph g's local ids;
+ * levels: host memory of sum(n_each) int32, graph g's levels at the offset of g. */
+blest_status blest_batch_bfs(blest_handle h, const int32_t* srcs_local, int32_t* levels);
+
+/* Device-memory forms.  They enqueue the traversal on `stream` (a cudaStream_t;
+ * NULL = the handle's own stream) and return without waiting; sources are host
+ * arrays read before the call returns.  d_levels is device memory of n (or k*n)
+ * int32.  The status of the traversal (TIMEOUT, INTERNAL) is reported by the
+ * next blest_sync on the handle; a launch failure is reported at once. */
+blest_status blest_bfs_device(blest_handle h, int32_t src, int32_t* d_levels, void* stream);
+blest_status blest_msbfs_device(blest_handle h, const int32_t* srcs, int32_t k, int32_t* d_levels,
+                                void* stream);
+blest_status blest_bfs_multiroot_device(blest_handle h, const int32_t* srcs, int32_t k,
+                                        int32_t* d_levels, void* stream);
+
+/* Wait for every traversal enqueued on the handle and return the first device
+ * status they reported (BLEST_OK if none failed). */
+blest_status blest_sync(blest_handle h);
+
+/* Per-level queue sizes of the last traversal (recorded when
+ * BLEST_OPT_RECORD_LEVELS = 1): queue_sizes[l-1] = virtual slice sets processed
+ * at level l, up to cap entries.  Waits for the handle's work first. */
+blest_status blest_get_run_info(blest_handle h, blest_run_info* info, int32_t* queue_sizes, int32_t cap);
+
+/* ----------------------------------------------------------------- export */
+
+/* Copy an internal array to host memory (bytes must equal the array's size,
+ * which blest_export_size reports).  For tests and statistics. */
+typedef enum {
+    BLEST_ARRAY_REAL_PTRS = 0,       /* int32[num_slice_sets + 1] */
+    BLEST_ARRAY_VIRTUAL_TO_REAL = 1, /* int32[num_vss] */
+    BLEST_ARRAY_ROW_IDS = 2,         /* int32[128 * num_vss] */
+    BLEST_ARRAY_MASKS = 3,           /* uint32[32 * num_vss] */
+    BLEST_ARRAY_NEW_ID = 4,          /* int32[n]: new_id[original id] */
+    BLEST_ARRAY_VSS_COUNT = 5        /* int32[num_vss]: unpadded slices per VSS */
+} blest_array;
+
+int64_t blest_export_size(blest_handle h, int32_t which);
+blest_status blest_export(blest_handle h, int32_t which, void* host_out, int64_t bytes);
+
+/* ---------------------------------------------------------- host-only calls */
+
+/* The vertex order blest_graph_create would use, without any GPU: new_id[v] =
+ * position of v in the new order (the pi^-1 of Algorithm 1).  Same input rules
+ * as blest_graph_create; new_id is host memory of n int32. */
+blest_status blest_compute_order(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                                 blest_order order, const blest_create_params* params,
+                                 int32_t* new_id);
+
+/* 1 if the Section 3.2.1 classifier calls the graph social-like, else 0;
+ * negative blest_status on bad input. */
+int32_t blest_is_social(int32_t n, const int32_t* row_ptr, const int32_t* col_idx);
+
+/* ---------------------------------------------------------------- testing */
+
+/* The stage-1 pull of one virtual slice set, on the device, for every tile:
+ * hits[i] bit q (q = 0..3) is set iff sub-slot q of masks[i] (bits 8q..8q+7)
+ * ANDed with alpha[i / 32] is nonzero -- Eq. 1's threshold of the AND/POPC
+ * product.  masks: device uint32[32 * tiles]; alpha: device uint8[tiles];
+ * hits: device uint8[32 * tiles].  pull selects the CUDA-core or the tensor-core
+ * path.  Synchronous. */
+blest_status blest_debug_pull(const uint32_t* d_masks, const uint8_t* d_alpha, int32_t tiles,
+                              int32_t pull, uint8_t* d_hits);
+
+const char* blest_status_string(blest_status s);
+const char* blest_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BLEST_H */

@@ -184,3 +184,31 @@ def bandwidth(n: int, row_ptr, col_idx) -> int:
     ci = np.asarray(col_idx, dtype=np.int64)
     rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(rp))
     return int(np.abs(rows - ci).max()) if len(ci) else 0
+
+
+def is_social_like(n: int, row_ptr, col_idx) -> bool:
+    """Section 3.2.1 classifier.  Heavy-tail sharing: the top 1% of vertices by
+    degree (ceil(n/100) of them) hold more than 5% of the edges and the top 10%
+    (ceil(n/10)) more than 40%.  Power law (the paper gives no numbers; this
+    reading's band): a least-squares line through (log d, log #vertices of degree
+    d) over degrees d >= 1 with at least 5 points has slope in [-3.5, -1.5] and
+    R^2 >= 0.8.  Social-like = either property."""
+    deg = np.diff(np.asarray(row_ptr, dtype=np.int64))
+    total = int(deg.sum())
+    if n == 0 or total == 0:
+        return False
+    srt = np.sort(deg)[::-1]
+    k1, k10 = max(1, -(-n // 100)), max(1, -(-n // 10))
+    if srt[:k1].sum() > 0.05 * total and srt[:k10].sum() > 0.40 * total:
+        return True
+    ds, cnt = np.unique(deg[deg >= 1], return_counts=True)
+    if len(ds) < 5:
+        return False
+    x, y = np.log(ds.astype(np.float64)), np.log(cnt.astype(np.float64))
+    vx = ((x - x.mean()) ** 2).sum()
+    vy = ((y - y.mean()) ** 2).sum()
+    cxy = ((x - x.mean()) * (y - y.mean())).sum()
+    if vx <= 0 or vy <= 0:
+        return False
+    slope, r2 = cxy / vx, cxy * cxy / (vx * vy)
+    return bool(-3.5 <= slope <= -1.5 and r2 >= 0.8)

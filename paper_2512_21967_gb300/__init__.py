@@ -1,0 +1,362 @@
+"""GB300-native BLEST breadth-first search: thin Python binding of ``libblest.so``.
+
+Every function below has the name of the C entry point it marshals (declared in
+``include/blest.h``); none of them computes any part of the traversal.  Arrays
+are numpy int32 on the host; the ``*_device`` calls take CUDA int32 tensors (or
+raw device pointers) and an optional CUDA stream.  A non-OK status raises
+:class:`BlestError`.  If the compiled library is missing it is built in-tree;
+if it cannot be built or loaded the import of any entry point fails loudly --
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "BlestError", "Stats", "RunInfo",
+    "BLEST_ORDER_NONE", "BLEST_ORDER_COMPRESS", "BLEST_ORDER_BANDWIDTH", "BLEST_ORDER_AUTO",
+    "BLEST_UPDATE_AUTO", "BLEST_UPDATE_EAGER", "BLEST_UPDATE_LAZY", "BLEST_PULL_POPC", "BLEST_PULL_MMA",
+    "blest_graph_create", "blest_graph_create_ex", "blest_batch_create", "blest_destroy", "blest_set_option",
+    "blest_get_stats", "blest_bfs", "blest_msbfs", "blest_bfs_multiroot", "blest_batch_bfs", "blest_bfs_device",
+    "blest_msbfs_device", "blest_bfs_multiroot_device", "blest_sync", "blest_get_run_info", "blest_export",
+    "blest_export_size", "blest_compute_order", "blest_is_social", "blest_debug_pull", "lib", "EXPORTED_SYMBOLS",
+]
+
+BLEST_OK = 0
+STATUS_NAMES = {0: "BLEST_OK", 1: "BLEST_ERR_INVALID_ARG", 2: "BLEST_ERR_NOT_SYMMETRIC", 3: "BLEST_ERR_TOO_LARGE",
+                4: "BLEST_ERR_OOM", 5: "BLEST_ERR_CUDA", 6: "BLEST_ERR_TIMEOUT", 7: "BLEST_ERR_INTERNAL"}
+BLEST_ORDER_NONE, BLEST_ORDER_COMPRESS, BLEST_ORDER_BANDWIDTH, BLEST_ORDER_AUTO = 0, 1, 2, 3
+BLEST_UPDATE_AUTO, BLEST_UPDATE_EAGER, BLEST_UPDATE_LAZY = 0, 1, 2
+BLEST_PULL_POPC, BLEST_PULL_MMA = 0, 1
+BLEST_OPT_UPDATE, BLEST_OPT_PULL, BLEST_OPT_BLOCKS_PER_SM, BLEST_OPT_BARRIER_TIMEOUT_US = 0, 1, 2, 3
+BLEST_OPT_RECORD_LEVELS, BLEST_OPT_UNROLL, BLEST_OPT_TEST_PHANTOM_BLOCK = 4, 5, 6
+BLEST_ARRAY_REAL_PTRS, BLEST_ARRAY_VIRTUAL_TO_REAL, BLEST_ARRAY_ROW_IDS = 0, 1, 2
+BLEST_ARRAY_MASKS, BLEST_ARRAY_NEW_ID, BLEST_ARRAY_VSS_COUNT = 3, 4, 5
+
+EXPORTED_SYMBOLS = [
+    "blest_graph_create", "blest_graph_create_ex", "blest_batch_create", "blest_destroy", "blest_set_option",
+    "blest_get_stats", "blest_bfs", "blest_msbfs", "blest_bfs_multiroot", "blest_batch_bfs", "blest_bfs_device",
+    "blest_msbfs_device", "blest_bfs_multiroot_device", "blest_sync", "blest_get_run_info", "blest_export_size",
+    "blest_export", "blest_compute_order", "blest_is_social", "blest_debug_pull", "blest_status_string",
+    "blest_last_error",
+]
+
+
+class BlestError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        self.name = STATUS_NAMES.get(status, f"status {status}")
+        super().__init__(f"{where}: {self.name}: {message}")
+
+
+class CreateParams(ctypes.Structure):
+    _fields_ = [("window", ctypes.c_int32), ("threads", ctypes.c_int32), ("skip_symmetry_check", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("num_slice_sets", ctypes.c_int64),
+                ("num_vss", ctypes.c_int64), ("num_slices", ctypes.c_int64), ("unpadded_slices", ctypes.c_int64),
+                ("connectivity_bits", ctypes.c_int64), ("update_divergence", ctypes.c_double),
+                ("compression_ratio", ctypes.c_double), ("bvss_bytes", ctypes.c_int64),
+                ("state_bytes", ctypes.c_int64), ("order", ctypes.c_int32), ("update", ctypes.c_int32),
+                ("order_seconds", ctypes.c_double), ("build_seconds", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class RunInfo(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("update", ctypes.c_int32), ("pull", ctypes.c_int32),
+                ("grid_blocks", ctypes.c_int32), ("threads_per_block", ctypes.c_int32), ("recorded", ctypes.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_vp = ctypes.c_void_p
+
+
+def lib():
+    """Load (building in-tree if needed) ``libblest.so`` and declare its ABI."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        sig = {
+            "blest_graph_create": (ctypes.c_int, [ctypes.c_int32, _i32p, _i32p, ctypes.c_int, ctypes.POINTER(_vp)]),
+            "blest_graph_create_ex": (ctypes.c_int, [ctypes.c_int32, _i32p, _i32p, ctypes.c_int,
+                                                     ctypes.POINTER(CreateParams), ctypes.POINTER(_vp)]),
+            "blest_batch_create": (ctypes.c_int, [ctypes.c_int32, _i32p, ctypes.POINTER(_i32p), ctypes.POINTER(_i32p),
+                                                  _i32p, ctypes.POINTER(CreateParams), ctypes.POINTER(_vp)]),
+            "blest_destroy": (None, [_vp]),
+            "blest_set_option": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int64]),
+            "blest_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(Stats)]),
+            "blest_bfs": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p]),
+            "blest_msbfs": (ctypes.c_int, [_vp, _i32p, ctypes.c_int32, _i32p]),
+            "blest_bfs_multiroot": (ctypes.c_int, [_vp, _i32p, ctypes.c_int32, _i32p]),
+            "blest_batch_bfs": (ctypes.c_int, [_vp, _i32p, _i32p]),
+            "blest_bfs_device": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp]),
+            "blest_msbfs_device": (ctypes.c_int, [_vp, _i32p, ctypes.c_int32, _vp, _vp]),
+            "blest_bfs_multiroot_device": (ctypes.c_int, [_vp, _i32p, ctypes.c_int32, _vp, _vp]),
+            "blest_sync": (ctypes.c_int, [_vp]),
+            "blest_get_run_info": (ctypes.c_int, [_vp, ctypes.POINTER(RunInfo), _i32p, ctypes.c_int32]),
+            "blest_export_size": (ctypes.c_int64, [_vp, ctypes.c_int32]),
+            "blest_export": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.c_int64]),
+            "blest_compute_order": (ctypes.c_int, [ctypes.c_int32, _i32p, _i32p, ctypes.c_int,
+                                                   ctypes.POINTER(CreateParams), _i32p]),
+            "blest_is_social": (ctypes.c_int32, [ctypes.c_int32, _i32p, _i32p]),
+            "blest_debug_pull": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp]),
+            "blest_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "blest_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+        return L
+
+
+def _check(status: int, where: str) -> None:
+    if status != BLEST_OK:
+        msg = lib().blest_last_error()
+        raise BlestError(status, where, msg.decode() if msg else "")
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_i32p)
+
+
+def _params(window=None, threads=None, skip_symmetry_check=False):
+    if window is None and threads is None and not skip_symmetry_check:
+        return None
+    return CreateParams(int(window or 0), int(threads or 0), 1 if skip_symmetry_check else 0)
+
+
+def _dev_ptr(x) -> int:
+    """Device address of a CUDA tensor (or an int already holding one)."""
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        if not x.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return int(x.data_ptr())
+    raise TypeError("expected a CUDA tensor or a device pointer")
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+# ------------------------------------------------------------------- graphs
+
+def blest_graph_create(n: int, row_ptr, col_idx, order: int = BLEST_ORDER_NONE) -> int:
+    rp, ci = _i32(row_ptr), _i32(col_idx)
+    h = _vp()
+    _check(lib().blest_graph_create(int(n), _ptr(rp), _ptr(ci), int(order), ctypes.byref(h)), "blest_graph_create")
+    return h.value
+
+
+def blest_graph_create_ex(n: int, row_ptr, col_idx, order: int = BLEST_ORDER_NONE, window=None, threads=None,
+                          skip_symmetry_check=False) -> int:
+    rp, ci = _i32(row_ptr), _i32(col_idx)
+    h = _vp()
+    p = _params(window, threads, skip_symmetry_check)
+    _check(lib().blest_graph_create_ex(int(n), _ptr(rp), _ptr(ci), int(order), ctypes.byref(p) if p else None,
+                                       ctypes.byref(h)), "blest_graph_create_ex")
+    return h.value
+
+
+def blest_batch_create(graphs, orders, window=None, threads=None) -> int:
+    """graphs: sequence of (n, row_ptr, col_idx) in local ids."""
+    G = len(graphs)
+    ns = _i32([g[0] for g in graphs])
+    keep = [(_i32(g[1]), _i32(g[2])) for g in graphs]
+    rps = (_i32p * max(G, 1))(*[_ptr(k[0]) for k in keep])
+    cis = (_i32p * max(G, 1))(*[_ptr(k[1]) for k in keep])
+    od = _i32(orders)
+    h = _vp()
+    p = _params(window, threads)
+    _check(lib().blest_batch_create(G, _ptr(ns), rps, cis, _ptr(od), ctypes.byref(p) if p else None,
+                                    ctypes.byref(h)), "blest_batch_create")
+    return h.value
+
+
+def blest_destroy(h: int | None) -> None:
+    if h:
+        lib().blest_destroy(h)
+
+
+def blest_set_option(h: int, key: int, value: int) -> None:
+    _check(lib().blest_set_option(h, int(key), int(value)), "blest_set_option")
+
+
+def blest_get_stats(h: int) -> dict:
+    s = Stats()
+    _check(lib().blest_get_stats(h, ctypes.byref(s)), "blest_get_stats")
+    return s.as_dict()
+
+
+# --------------------------------------------------------------- traversal
+
+def _n_of(h: int) -> int:
+    return int(blest_get_stats(h)["n"])
+
+
+def blest_bfs(h: int, src: int, levels: np.ndarray | None = None) -> np.ndarray:
+    n = _n_of(h)
+    out = np.empty(n, np.int32) if levels is None else levels
+    if out.dtype != np.int32 or not out.flags.c_contiguous or out.size != n:
+        raise ValueError("levels must be a contiguous int32 array of n entries")
+    _check(lib().blest_bfs(h, int(src), _ptr(out)), "blest_bfs")
+    return out
+
+
+def blest_msbfs(h: int, srcs, levels: np.ndarray | None = None) -> np.ndarray:
+    s = _i32(srcs)
+    n = _n_of(h)
+    out = np.empty((len(s), n), np.int32) if levels is None else levels
+    if out.dtype != np.int32 or not out.flags.c_contiguous or out.size != len(s) * n:
+        raise ValueError("levels must be a contiguous int32 array of k*n entries")
+    _check(lib().blest_msbfs(h, _ptr(s), len(s), _ptr(out)), "blest_msbfs")
+    return out
+
+
+def blest_bfs_multiroot(h: int, srcs, levels: np.ndarray | None = None) -> np.ndarray:
+    s = _i32(srcs)
+    n = _n_of(h)
+    out = np.empty(n, np.int32) if levels is None else levels
+    _check(lib().blest_bfs_multiroot(h, _ptr(s), len(s), _ptr(out)), "blest_bfs_multiroot")
+    return out
+
+
+def blest_batch_bfs(h: int, srcs_local, levels: np.ndarray | None = None) -> np.ndarray:
+    s = _i32(srcs_local)
+    n = _n_of(h)
+    out = np.empty(n, np.int32) if levels is None else levels
+    _check(lib().blest_batch_bfs(h, _ptr(s), _ptr(out)), "blest_batch_bfs")
+    return out
+
+
+def blest_bfs_device(h: int, src: int, d_levels, stream=None) -> None:
+    _check(lib().blest_bfs_device(h, int(src), _dev_ptr(d_levels), _stream_ptr(stream)), "blest_bfs_device")
+
+
+def blest_msbfs_device(h: int, srcs, d_levels, stream=None) -> None:
+    s = _i32(srcs)
+    _check(lib().blest_msbfs_device(h, _ptr(s), len(s), _dev_ptr(d_levels), _stream_ptr(stream)),
+           "blest_msbfs_device")
+
+
+def blest_bfs_multiroot_device(h: int, srcs, d_levels, stream=None) -> None:
+    s = _i32(srcs)
+    _check(lib().blest_bfs_multiroot_device(h, _ptr(s), len(s), _dev_ptr(d_levels), _stream_ptr(stream)),
+           "blest_bfs_multiroot_device")
+
+
+def blest_sync(h: int) -> None:
+    _check(lib().blest_sync(h), "blest_sync")
+
+
+def blest_get_run_info(h: int, cap: int = 0) -> tuple[dict, np.ndarray]:
+    info = RunInfo()
+    buf = np.zeros(max(cap, 1), np.int32)
+    _check(lib().blest_get_run_info(h, ctypes.byref(info), _ptr(buf), int(cap)), "blest_get_run_info")
+    d = {f: getattr(info, f) for f, _ in info._fields_}
+    return d, buf[:max(0, min(cap, d["recorded"]))].copy()
+
+
+# ------------------------------------------------------------------ export
+
+_EXPORT_DTYPES = {BLEST_ARRAY_MASKS: np.uint32}
+
+
+def blest_export_size(h: int, which: int) -> int:
+    return int(lib().blest_export_size(h, int(which)))
+
+
+def blest_export(h: int, which: int) -> np.ndarray:
+    nbytes = blest_export_size(h, which)
+    if nbytes < 0:
+        raise BlestError(1, "blest_export", "unknown array")
+    out = np.empty(nbytes // 4, _EXPORT_DTYPES.get(which, np.int32))
+    _check(lib().blest_export(h, int(which), out.ctypes.data_as(_vp), nbytes), "blest_export")
+    return out
+
+
+# --------------------------------------------------------------- host only
+
+def blest_compute_order(n: int, row_ptr, col_idx, order: int, window=None, threads=None) -> np.ndarray:
+    rp, ci = _i32(row_ptr), _i32(col_idx)
+    out = np.empty(max(n, 1), np.int32)
+    p = _params(window, threads)
+    _check(lib().blest_compute_order(int(n), _ptr(rp), _ptr(ci), int(order), ctypes.byref(p) if p else None,
+                                     _ptr(out)), "blest_compute_order")
+    return out[:n]
+
+
+def blest_is_social(n: int, row_ptr, col_idx) -> bool:
+    rp, ci = _i32(row_ptr), _i32(col_idx)
+    r = lib().blest_is_social(int(n), _ptr(rp), _ptr(ci))
+    if r < 0:
+        _check(-r, "blest_is_social")
+    return bool(r)
+
+
+def blest_debug_pull(d_masks, d_alpha, tiles: int, pull: int, d_hits) -> None:
+    _check(lib().blest_debug_pull(_dev_ptr(d_masks), _dev_ptr(d_alpha), int(tiles), int(pull), _dev_ptr(d_hits)),
+           "blest_debug_pull")
+
+
+class BlestGraph:
+    """Owning wrapper: ``with BlestGraph(n, rp, ci, order) as g: g.bfs(src)``."""
+
+    def __init__(self, n, row_ptr, col_idx, order=BLEST_ORDER_NONE, **kw):
+        self.h = blest_graph_create_ex(n, row_ptr, col_idx, order, **kw) if kw else \
+            blest_graph_create(n, row_ptr, col_idx, order)
+
+    def close(self):
+        blest_destroy(self.h)
+        self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                self.close()
+        except Exception:
+            pass
+
+    def bfs(self, src):
+        return blest_bfs(self.h, src)
+
+    def msbfs(self, srcs):
+        return blest_msbfs(self.h, srcs)
+
+    def stats(self):
+        return blest_get_stats(self.h)
+
+    def set_option(self, key, value):
+        blest_set_option(self.h, key, value)

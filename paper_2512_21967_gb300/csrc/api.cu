@@ -1,0 +1,675 @@
+// C ABI of the BLEST traversal library (declared in include/blest.h).  Host
+// code: argument checks, the create pipeline (clean -> symmetry check ->
+// reorder -> upload -> device BVSS build -> statistics), traversal launches and
+// array export.  Every step of a traversal runs in the device kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/blest.h"
+#include "bfs_launch.h"
+#include "host_graph.h"
+#include "msbfs_launch.h"
+
+using blest::Csr;
+
+namespace {
+thread_local std::string g_last_error;
+
+blest_status fail(blest_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+blest_status cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? BLEST_ERR_OOM : BLEST_ERR_CUDA;
+}
+
+constexpr int kLevelRecordCap = 1 << 16;
+constexpr int32_t kMaxVertices = 1 << 29;
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+}  // namespace
+
+struct blest_graph {
+    int32_t n = 0;
+    int64_t nnz = 0;
+    blest::DeviceBvss bvss;
+    std::vector<int32_t> h_new_id;       // empty = identity
+    int32_t* d_new_id = nullptr;
+    int32_t* d_L = nullptr;              // internal levels (BVSS ids)
+    int32_t* d_out = nullptr;            // staging for host-output calls (original ids)
+    uint32_t* d_vcur = nullptr;
+    uint32_t* d_vnext = nullptr;
+    uint32_t* d_F = nullptr;             // 3 * nwords
+    unsigned long long* d_Q = nullptr;   // 3 * qcap
+    unsigned int qcap = 0;
+    unsigned int* d_ctrl = nullptr;      // 64-byte control block + sticky error word at [16]
+    int32_t* d_level_sizes = nullptr;
+    int32_t* d_roots = nullptr;
+    int64_t roots_cap = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t last_stream = nullptr;
+    int sms = 0;
+    // options
+    int update_opt = BLEST_UPDATE_AUTO;
+    int pull = BLEST_PULL_POPC;
+    int blocks_per_sm = 0;
+    int64_t timeout_us = 2000000;
+    int record = 0;
+    int unroll = 2;
+    int phantom = 0;
+    // results
+    blest_stats stats{};
+    blest_run_info info{};
+    std::vector<int64_t> offsets;        // batch handles: graph g owns [offsets[g], offsets[g+1])
+    blest::MsbfsState ms;
+
+    int nwords() const { return (n + 31) / 32; }
+    int resolved_update() const {
+        if (update_opt == BLEST_UPDATE_EAGER || update_opt == BLEST_UPDATE_LAZY) return update_opt;
+        return stats.update;
+    }
+};
+
+namespace {
+
+void free_handle(blest_graph* h) {
+    if (!h) return;
+    blest::free_bvss_device(h->bvss);
+    blest::free_msbfs_state(h->ms);
+    cudaFree(h->d_new_id);
+    cudaFree(h->d_L);
+    cudaFree(h->d_out);
+    cudaFree(h->d_vcur);
+    cudaFree(h->d_vnext);
+    cudaFree(h->d_F);
+    cudaFree(h->d_Q);
+    cudaFree(h->d_ctrl);
+    cudaFree(h->d_level_sizes);
+    cudaFree(h->d_roots);
+    if (h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+// Device part of create: upload the relabelled CSR, build BVSS, allocate state.
+blest_status finish_create(blest_graph* h, const Csr& g, const std::vector<int32_t>& new_id, double t_order) {
+    double t0 = now_s();
+    cudaError_t e;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if ((e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return cuda_fail(e, "cudaDeviceGetAttribute");
+    if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "cudaStreamCreate");
+    h->n = g.n;
+    h->nnz = g.nnz();
+    int32_t *d_rp = nullptr, *d_ci = nullptr;
+    if ((e = cudaMalloc(&d_rp, sizeof(int32_t) * ((size_t)g.n + 1))) != cudaSuccess) return cuda_fail(e, "cudaMalloc(row_ptr)");
+    if ((e = cudaMalloc(&d_ci, sizeof(int32_t) * (size_t)std::max<int64_t>(h->nnz, 1))) != cudaSuccess) {
+        cudaFree(d_rp);
+        return cuda_fail(e, "cudaMalloc(col_idx)");
+    }
+    cudaMemcpyAsync(d_rp, g.rp.data(), sizeof(int32_t) * ((size_t)g.n + 1), cudaMemcpyHostToDevice, h->stream);
+    if (h->nnz) cudaMemcpyAsync(d_ci, g.ci.data(), sizeof(int32_t) * (size_t)h->nnz, cudaMemcpyHostToDevice, h->stream);
+    const char* err = nullptr;
+    int rc = blest::build_bvss_device(d_rp, d_ci, g.n, h->nnz, h->stream, h->bvss, &err);
+    cudaFree(d_rp);
+    cudaFree(d_ci);
+    if (rc) return fail((blest_status)rc, std::string("BVSS build: ") + (err ? err : "?"));
+    if (h->bvss.nvss >= (int64_t)1 << 31) return fail(BLEST_ERR_TOO_LARGE, "more than 2^31 virtual slice sets");
+    double udiv = 0.0;
+    rc = blest::update_divergence_device(h->bvss, h->stream, &udiv, &err);
+    if (rc) return fail((blest_status)rc, std::string("update divergence: ") + (err ? err : "?"));
+
+    // traversal state
+    const size_t nw = (size_t)h->nwords();
+    h->qcap = (unsigned int)std::max<int64_t>(h->bvss.nvss, 1);
+#define BLEST_ALLOC(ptr, bytes, what) \
+    if ((e = cudaMalloc(&(ptr), (bytes))) != cudaSuccess) return cuda_fail(e, what);
+    BLEST_ALLOC(h->d_L, sizeof(int32_t) * std::max<size_t>(g.n, 1), "cudaMalloc(levels)");
+    BLEST_ALLOC(h->d_out, sizeof(int32_t) * std::max<size_t>(g.n, 1), "cudaMalloc(out)");
+    BLEST_ALLOC(h->d_vcur, sizeof(uint32_t) * std::max<size_t>(nw, 1), "cudaMalloc(vcur)");
+    BLEST_ALLOC(h->d_vnext, sizeof(uint32_t) * std::max<size_t>(nw, 1), "cudaMalloc(vnext)");
+    BLEST_ALLOC(h->d_F, sizeof(uint32_t) * 3 * std::max<size_t>(nw, 1), "cudaMalloc(frontier)");
+    BLEST_ALLOC(h->d_Q, sizeof(unsigned long long) * 3 * (size_t)h->qcap, "cudaMalloc(queues)");
+    BLEST_ALLOC(h->d_ctrl, 128, "cudaMalloc(ctrl)");
+    BLEST_ALLOC(h->d_level_sizes, sizeof(int32_t) * kLevelRecordCap, "cudaMalloc(level record)");
+#undef BLEST_ALLOC
+    cudaMemsetAsync(h->d_ctrl, 0, 128, h->stream);
+    if (!new_id.empty()) {
+        h->h_new_id = new_id;
+        if ((e = cudaMalloc(&h->d_new_id, sizeof(int32_t) * (size_t)g.n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(new_id)");
+        cudaMemcpyAsync(h->d_new_id, new_id.data(), sizeof(int32_t) * (size_t)g.n, cudaMemcpyHostToDevice, h->stream);
+    }
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(e, "create");
+
+    blest_stats& s = h->stats;
+    s.n = g.n;
+    s.nnz = h->nnz;
+    s.num_slice_sets = h->bvss.nss;
+    s.num_vss = h->bvss.nvss;
+    s.num_slices = 128 * h->bvss.nvss;
+    s.unpadded_slices = h->bvss.unpadded;
+    s.connectivity_bits = 8 * h->bvss.unpadded;
+    s.update_divergence = udiv;
+    s.compression_ratio = h->bvss.unpadded ? (double)h->nnz / (double)(8 * h->bvss.unpadded) : 0.0;
+    s.bvss_bytes = (int64_t)h->bvss.nvss * (128 * 4 + 32 * 4 + 4 + 4) + ((int64_t)h->bvss.nss + 1) * 4;
+    s.state_bytes = (int64_t)g.n * 8 + (int64_t)nw * 4 * 5 + (int64_t)h->qcap * 24 + 128 + kLevelRecordCap * 4;
+    s.update = udiv > 25000.0 ? BLEST_UPDATE_LAZY : BLEST_UPDATE_EAGER;
+    s.order_seconds = t_order;
+    s.build_seconds += now_s() - t0;
+    return BLEST_OK;
+}
+
+blest_status prepare_graph(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, blest_order order,
+                           const blest_create_params* params, int threads, Csr& clean, std::vector<int32_t>& new_id,
+                           int32_t* order_used, double* t_order, double* t_clean) {
+    if (order < BLEST_ORDER_NONE || order > BLEST_ORDER_AUTO) return fail(BLEST_ERR_INVALID_ARG, "unknown order");
+    if (n < 0) return fail(BLEST_ERR_INVALID_ARG, "n must be >= 0");
+    if (n > kMaxVertices) return fail(BLEST_ERR_TOO_LARGE, "more than 2^29 vertices");
+    int32_t window = params && params->window > 0 ? params->window : 65536;
+    if (window % 8 != 0) return fail(BLEST_ERR_INVALID_ARG, "window must be a multiple of 8");
+    double t0 = now_s();
+    std::string err;
+    int rc = blest::clean_csr(n, row_ptr, col_idx, threads, clean, err);
+    if (rc) return fail((blest_status)rc, err);
+    if (!(params && params->skip_symmetry_check)) {
+        int64_t bu = -1, bv = -1;
+        if (!blest::is_symmetric(clean, threads, &bu, &bv))
+            return fail(BLEST_ERR_NOT_SYMMETRIC, "edge (" + std::to_string(bu) + ", " + std::to_string(bv) +
+                                                     ") has no reverse edge");
+    }
+    *t_clean = now_s() - t0;
+    t0 = now_s();
+    int32_t ord = order;
+    if (ord == BLEST_ORDER_AUTO) ord = blest::is_social_like(clean) ? BLEST_ORDER_COMPRESS : BLEST_ORDER_BANDWIDTH;
+    new_id.clear();
+    if (ord == BLEST_ORDER_COMPRESS) blest::order_compress(clean, 8, window, threads, new_id);
+    else if (ord == BLEST_ORDER_BANDWIDTH) blest::order_rcm(clean, new_id);
+    *order_used = ord;
+    *t_order = now_s() - t0;
+    return BLEST_OK;
+}
+
+int pick_grid(blest_graph* h, int update, int pull, int unroll) {
+    int maxb = blest::bfs_max_blocks_per_sm(update, pull, unroll);
+    if (maxb <= 0) return 0;
+    int b = h->blocks_per_sm > 0 ? std::min(h->blocks_per_sm, maxb) : maxb;
+    return b * h->sms;
+}
+
+// Enqueue one single-frontier traversal from the (BVSS-order) roots, writing
+// levels in original ids into d_out (device, n int32).
+blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots, int32_t* d_out, cudaStream_t st) {
+    if (h->n == 0) return BLEST_OK;
+    cudaError_t e;
+    blest::BfsLaunch L;
+    L.update = h->resolved_update() == BLEST_UPDATE_EAGER ? 1 : 2;
+    L.pull = h->pull;
+    L.unroll = h->unroll;
+    L.grid = pick_grid(h, L.update, L.pull, L.unroll);
+    if (L.grid <= 0) return fail(BLEST_ERR_CUDA, "no co-resident grid for the traversal kernel");
+    L.n = h->n;
+    L.qcap = h->qcap;
+    L.real_ptrs = h->bvss.real_ptrs;
+    L.row_ids = h->bvss.row_ids;
+    L.masks = h->bvss.masks;
+    L.new_id = h->d_new_id;
+    L.levels_internal = h->d_new_id ? h->d_L : d_out;
+    L.vcur = h->d_vcur;
+    L.vnext = h->d_vnext;
+    const size_t nw = (size_t)h->nwords();
+    for (int i = 0; i < 3; ++i) {
+        L.F[i] = h->d_F + i * nw;
+        L.Q[i] = h->d_Q + i * (size_t)h->qcap;
+    }
+    L.ctrl = h->d_ctrl;
+    L.level_sizes = h->record ? h->d_level_sizes : nullptr;
+    L.level_cap = kLevelRecordCap;
+    L.nroots = (int32_t)roots.size();
+    if (roots.size() > (size_t)blest::kInlineRoots) {
+        if ((int64_t)roots.size() > h->roots_cap) {
+            cudaFree(h->d_roots);
+            h->d_roots = nullptr;
+            h->roots_cap = 0;
+            if ((e = cudaMalloc(&h->d_roots, sizeof(int32_t) * roots.size())) != cudaSuccess) return cuda_fail(e, "cudaMalloc(roots)");
+            h->roots_cap = (int64_t)roots.size();
+        }
+        if ((e = cudaMemcpyAsync(h->d_roots, roots.data(), sizeof(int32_t) * roots.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_fail(e, "copy roots");
+        L.roots_device = h->d_roots;
+    } else {
+        for (size_t i = 0; i < roots.size(); ++i) L.roots_host[i] = roots[i];
+    }
+    L.out = d_out;
+    L.timeout_ns = (uint64_t)h->timeout_us * 1000ull;
+    L.phantom = h->phantom ? 1u : 0u;
+    cudaMemsetAsync(h->d_ctrl, 0, 64, st);
+    cudaMemsetAsync(L.levels_internal, 0xFF, sizeof(int32_t) * (size_t)h->n, st);
+    cudaMemsetAsync(h->d_vcur, 0, sizeof(uint32_t) * nw, st);
+    cudaMemsetAsync(h->d_vnext, 0, sizeof(uint32_t) * nw, st);
+    if (L.update == 1) cudaMemsetAsync(h->d_F, 0, sizeof(uint32_t) * 3 * nw, st);
+    if ((e = blest::launch_bfs_kernel(L, st)) != cudaSuccess) return cuda_fail(e, "traversal launch");
+    h->last_stream = st;
+    h->info.update = L.update == 1 ? BLEST_UPDATE_EAGER : BLEST_UPDATE_LAZY;
+    h->info.pull = L.pull;
+    h->info.grid_blocks = L.grid;
+    h->info.threads_per_block = blest::bfs_threads_per_block();
+    h->info.recorded = -1;  // resolved in blest_get_run_info
+    return BLEST_OK;
+}
+
+blest_status map_sources(blest_graph* h, const int32_t* srcs, int32_t k, std::vector<int32_t>& roots) {
+    roots.resize((size_t)k);
+    for (int32_t i = 0; i < k; ++i) {
+        int32_t s = srcs[i];
+        if (s < 0 || s >= h->n) return fail(BLEST_ERR_INVALID_ARG, "source " + std::to_string(s) + " outside [0, n)");
+        roots[i] = h->h_new_id.empty() ? s : h->h_new_id[s];
+    }
+    return BLEST_OK;
+}
+
+blest_status sync_status(blest_graph* h) {
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    if (h->last_stream && h->last_stream != h->stream)
+        if ((e = cudaStreamSynchronize(h->last_stream)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    if (!h->d_ctrl) return BLEST_OK;
+    unsigned int sticky = 0;
+    if ((e = cudaMemcpy(&sticky, h->d_ctrl + 16, sizeof(unsigned int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "read status");
+    if (sticky) {
+        cudaMemset(h->d_ctrl + 16, 0, sizeof(unsigned int));
+        if (sticky == BLEST_ERR_TIMEOUT) return fail(BLEST_ERR_TIMEOUT, "a grid barrier timed out");
+        if (sticky == BLEST_ERR_INTERNAL) return fail(BLEST_ERR_INTERNAL, "device-side consistency check failed");
+        return fail((blest_status)sticky, "device error");
+    }
+    return BLEST_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* blest_status_string(blest_status s) {
+    switch (s) {
+        case BLEST_OK: return "BLEST_OK";
+        case BLEST_ERR_INVALID_ARG: return "BLEST_ERR_INVALID_ARG";
+        case BLEST_ERR_NOT_SYMMETRIC: return "BLEST_ERR_NOT_SYMMETRIC";
+        case BLEST_ERR_TOO_LARGE: return "BLEST_ERR_TOO_LARGE";
+        case BLEST_ERR_OOM: return "BLEST_ERR_OOM";
+        case BLEST_ERR_CUDA: return "BLEST_ERR_CUDA";
+        case BLEST_ERR_TIMEOUT: return "BLEST_ERR_TIMEOUT";
+        case BLEST_ERR_INTERNAL: return "BLEST_ERR_INTERNAL";
+    }
+    return "BLEST_ERR_UNKNOWN";
+}
+
+const char* blest_last_error(void) { return g_last_error.c_str(); }
+
+blest_status blest_graph_create_ex(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, blest_order order,
+                                   const blest_create_params* params, blest_handle* out) {
+    if (!out) return fail(BLEST_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    const int threads = blest::host_threads(params ? params->threads : 0);
+    Csr clean;
+    std::vector<int32_t> new_id;
+    int32_t used = order;
+    double t_order = 0, t_clean = 0;
+    blest_status s = prepare_graph(n, row_ptr, col_idx, order, params, threads, clean, new_id, &used, &t_order, &t_clean);
+    if (s) return s;
+    std::unique_ptr<blest_graph, void (*)(blest_graph*)> h(new blest_graph(), free_handle);
+    Csr relabelled;
+    const Csr* g = &clean;
+    if (!new_id.empty()) {
+        double t0 = now_s();
+        blest::relabel_csr(clean, new_id, threads, relabelled);
+        t_clean += now_s() - t0;
+        g = &relabelled;
+    }
+    h->stats.build_seconds = t_clean;
+    s = finish_create(h.get(), *g, new_id, t_order);
+    if (s) return s;
+    h->stats.order = used;
+    *out = h.release();
+    return BLEST_OK;
+}
+
+blest_status blest_graph_create(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, blest_order order,
+                                blest_handle* out) {
+    return blest_graph_create_ex(n, row_ptr, col_idx, order, nullptr, out);
+}
+
+blest_status blest_batch_create(int32_t num_graphs, const int32_t* n_each, const int32_t* const* row_ptrs,
+                                const int32_t* const* col_idxs, const int32_t* orders,
+                                const blest_create_params* params, blest_handle* out) {
+    if (!out) return fail(BLEST_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (num_graphs < 0 || (num_graphs > 0 && (!n_each || !row_ptrs || !col_idxs || !orders)))
+        return fail(BLEST_ERR_INVALID_ARG, "bad batch description");
+    const int threads = blest::host_threads(params ? params->threads : 0);
+    std::vector<int64_t> offsets(1, 0);
+    for (int32_t g = 0; g < num_graphs; ++g) {
+        if (n_each[g] < 0) return fail(BLEST_ERR_INVALID_ARG, "graph with n < 0");
+        offsets.push_back(offsets.back() + n_each[g]);
+    }
+    if (offsets.back() > kMaxVertices) return fail(BLEST_ERR_TOO_LARGE, "more than 2^29 vertices in the batch");
+    const int32_t N = (int32_t)offsets.back();
+    Csr uni;
+    uni.n = N;
+    uni.rp.assign((size_t)N + 1, 0);
+    std::vector<int32_t> new_id((size_t)N);
+    double t_order = 0, t_clean = 0;
+    std::vector<Csr> parts((size_t)num_graphs);
+    std::vector<std::vector<int32_t>> ids((size_t)num_graphs);
+    int64_t total = 0;
+    for (int32_t g = 0; g < num_graphs; ++g) {
+        int32_t used = 0;
+        double to = 0, tc = 0;
+        Csr clean;
+        blest_status s = prepare_graph(n_each[g], row_ptrs[g], col_idxs[g], (blest_order)orders[g], params, threads, clean,
+                                       ids[g], &used, &to, &tc);
+        if (s) return fail(s, "graph " + std::to_string(g) + ": " + g_last_error);
+        t_order += to;
+        t_clean += tc;
+        if (!ids[g].empty()) blest::relabel_csr(clean, ids[g], threads, parts[g]);
+        else parts[g] = std::move(clean);
+        total += parts[g].nnz();
+        if (total >= ((int64_t)1 << 31)) return fail(BLEST_ERR_TOO_LARGE, "batch has 2^31 or more entries");
+    }
+    uni.ci.resize((size_t)total);
+    int64_t pos = 0;
+    for (int32_t g = 0; g < num_graphs; ++g) {
+        const int64_t off = offsets[g];
+        const Csr& p = parts[g];
+        for (int32_t v = 0; v < p.n; ++v) {
+            uni.rp[off + v + 1] = uni.rp[off + v] + (p.rp[v + 1] - p.rp[v]);
+            new_id[off + v] = (int32_t)(off + (ids[g].empty() ? v : ids[g][v]));
+        }
+        for (int64_t e = 0; e < p.nnz(); ++e) uni.ci[pos++] = (int32_t)(p.ci[e] + off);
+        parts[g] = Csr();
+    }
+    std::unique_ptr<blest_graph, void (*)(blest_graph*)> h(new blest_graph(), free_handle);
+    h->stats.build_seconds = t_clean;
+    blest_status s = finish_create(h.get(), uni, new_id, t_order);
+    if (s) return s;
+    h->stats.order = num_graphs > 0 ? orders[0] : BLEST_ORDER_NONE;
+    h->offsets = offsets;
+    *out = h.release();
+    return BLEST_OK;
+}
+
+void blest_destroy(blest_handle h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->last_stream && h->last_stream != h->stream) cudaStreamSynchronize(h->last_stream);
+    free_handle(h);
+}
+
+blest_status blest_set_option(blest_handle h, int32_t key, int64_t value) {
+    if (!h) return fail(BLEST_ERR_INVALID_ARG, "NULL handle");
+    switch (key) {
+        case BLEST_OPT_UPDATE:
+            if (value < BLEST_UPDATE_AUTO || value > BLEST_UPDATE_LAZY) break;
+            h->update_opt = (int)value;
+            return BLEST_OK;
+        case BLEST_OPT_PULL:
+            if (value != BLEST_PULL_POPC && value != BLEST_PULL_MMA) break;
+            h->pull = (int)value;
+            return BLEST_OK;
+        case BLEST_OPT_BLOCKS_PER_SM:
+            if (value < 0 || value > 64) break;
+            h->blocks_per_sm = (int)value;
+            return BLEST_OK;
+        case BLEST_OPT_BARRIER_TIMEOUT_US:
+            if (value < 1 || value > 600000000) break;
+            h->timeout_us = value;
+            return BLEST_OK;
+        case BLEST_OPT_RECORD_LEVELS:
+            if (value != 0 && value != 1) break;
+            h->record = (int)value;
+            return BLEST_OK;
+        case BLEST_OPT_UNROLL:
+            if (value != 1 && value != 2 && value != 4) break;
+            h->unroll = (int)value;
+            return BLEST_OK;
+        case BLEST_OPT_TEST_PHANTOM_BLOCK:
+            if (value != 0 && value != 1) break;
+            h->phantom = (int)value;
+            return BLEST_OK;
+        default:
+            return fail(BLEST_ERR_INVALID_ARG, "unknown option key");
+    }
+    return fail(BLEST_ERR_INVALID_ARG, "option value out of range");
+}
+
+blest_status blest_get_stats(blest_handle h, blest_stats* out) {
+    if (!h || !out) return fail(BLEST_ERR_INVALID_ARG, "NULL argument");
+    *out = h->stats;
+    return BLEST_OK;
+}
+
+blest_status blest_bfs_device(blest_handle h, int32_t src, int32_t* d_levels, void* stream) {
+    if (!h) return fail(BLEST_ERR_INVALID_ARG, "NULL handle");
+    if (h->n == 0 || src < 0 || src >= h->n) return fail(BLEST_ERR_INVALID_ARG, "source outside [0, n)");
+    if (!d_levels) return fail(BLEST_ERR_INVALID_ARG, "levels is NULL");
+    std::vector<int32_t> roots;
+    blest_status s = map_sources(h, &src, 1, roots);
+    if (s) return s;
+    return enqueue_traversal(h, roots, d_levels, stream ? (cudaStream_t)stream : h->stream);
+}
+
+blest_status blest_bfs_multiroot_device(blest_handle h, const int32_t* srcs, int32_t k, int32_t* d_levels, void* stream) {
+    if (!h) return fail(BLEST_ERR_INVALID_ARG, "NULL handle");
+    if (k < 0 || (k > 0 && !srcs)) return fail(BLEST_ERR_INVALID_ARG, "bad source list");
+    if (h->n > 0 && !d_levels) return fail(BLEST_ERR_INVALID_ARG, "levels is NULL");
+    std::vector<int32_t> roots;
+    blest_status s = map_sources(h, srcs, k, roots);
+    if (s) return s;
+    cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
+    if (k == 0) {
+        if (h->n > 0) cudaMemsetAsync(d_levels, 0xFF, sizeof(int32_t) * (size_t)h->n, st);
+        return BLEST_OK;
+    }
+    return enqueue_traversal(h, roots, d_levels, st);
+}
+
+blest_status blest_sync(blest_handle h) {
+    if (!h) return fail(BLEST_ERR_INVALID_ARG, "NULL handle");
+    return sync_status(h);
+}
+
+blest_status blest_bfs(blest_handle h, int32_t src, int32_t* levels) {
+    if (!h) return fail(BLEST_ERR_INVALID_ARG, "NULL handle");
+    if (!levels) return fail(BLEST_ERR_INVALID_ARG, "levels is NULL");
+    blest_status s = blest_bfs_device(h, src, h->d_out, h->stream);
+    if (s) return s;
+    cudaError_t e = cudaMemcpyAsync(levels, h->d_out, sizeof(int32_t) * (size_t)h->n, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copy levels");
+    return sync_status(h);
+}
+
+blest_status blest_bfs_multiroot(blest_handle h, const int32_t* srcs, int32_t k, int32_t* levels) {
+    if (!h) return fail(BLEST_ERR_INVALID_ARG, "NULL handle");
+    if (h->n > 0 && !levels) return fail(BLEST_ERR_INVALID_ARG, "levels is NULL");
+    blest_status s = blest_bfs_multiroot_device(h, srcs, k, h->d_out, h->stream);
+    if (s) return s;
+    if (h->n > 0) {
+        cudaError_t e = cudaMemcpyAsync(levels, h->d_out, sizeof(int32_t) * (size_t)h->n, cudaMemcpyDeviceToHost, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "copy levels");
+    }
+    return sync_status(h);
+}
+
+blest_status blest_batch_bfs(blest_handle h, const int32_t* srcs_local, int32_t* levels) {
+    if (!h) return fail(BLEST_ERR_INVALID_ARG, "NULL handle");
+    if (h->offsets.empty()) return fail(BLEST_ERR_INVALID_ARG, "not a batch handle");
+    const int32_t G = (int32_t)h->offsets.size() - 1;
+    if (G > 0 && !srcs_local) return fail(BLEST_ERR_INVALID_ARG, "srcs is NULL");
+    std::vector<int32_t> glob;
+    for (int32_t g = 0; g < G; ++g) {
+        const int64_t ng = h->offsets[g + 1] - h->offsets[g];
+        if (ng == 0) continue;   // an empty graph has no source
+        if (srcs_local[g] < 0 || srcs_local[g] >= ng) return fail(BLEST_ERR_INVALID_ARG, "source outside its graph");
+        glob.push_back((int32_t)(h->offsets[g] + srcs_local[g]));
+    }
+    return blest_bfs_multiroot(h, glob.data(), (int32_t)glob.size(), levels);
+}
+
+blest_status blest_msbfs_device(blest_handle h, const int32_t* srcs, int32_t k, int32_t* d_levels, void* stream) {
+    if (!h) return fail(BLEST_ERR_INVALID_ARG, "NULL handle");
+    if (k < 0 || (k > 0 && !srcs)) return fail(BLEST_ERR_INVALID_ARG, "bad source list");
+    if (k == 0) return BLEST_OK;
+    if (!d_levels) return fail(BLEST_ERR_INVALID_ARG, "levels is NULL");
+    std::vector<int32_t> roots;
+    blest_status s = map_sources(h, srcs, k, roots);
+    if (s) return s;
+    cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
+    blest::MsbfsLaunchCommon c;
+    c.n = h->n;
+    c.nss = h->bvss.nss;
+    c.nvss = h->bvss.nvss;
+    c.real_ptrs = h->bvss.real_ptrs;
+    c.row_ids = h->bvss.row_ids;
+    c.masks = h->bvss.masks;
+    c.new_id = h->d_new_id;
+    c.ctrl = h->d_ctrl;
+    c.sms = h->sms;
+    c.blocks_per_sm = h->blocks_per_sm;
+    c.timeout_ns = (uint64_t)h->timeout_us * 1000ull;
+    c.phantom = h->phantom ? 1u : 0u;
+    c.level_sizes = h->record ? h->d_level_sizes : nullptr;
+    c.level_cap = kLevelRecordCap;
+    const char* err = nullptr;
+    int rc = blest::run_msbfs(h->ms, c, roots, d_levels, st, &err);
+    if (rc) return fail((blest_status)rc, std::string("msbfs: ") + (err ? err : "?"));
+    h->last_stream = st;
+    h->info.update = BLEST_UPDATE_LAZY;
+    h->info.pull = BLEST_PULL_POPC;
+    h->info.recorded = -1;
+    return BLEST_OK;
+}
+
+blest_status blest_msbfs(blest_handle h, const int32_t* srcs, int32_t k, int32_t* levels) {
+    if (!h) return fail(BLEST_ERR_INVALID_ARG, "NULL handle");
+    if (k < 0 || (k > 0 && (!srcs || !levels))) return fail(BLEST_ERR_INVALID_ARG, "bad arguments");
+    if (k == 0) return BLEST_OK;
+    int32_t* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(int32_t) * (size_t)k * (size_t)std::max(h->n, 1));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(msbfs levels)");
+    blest_status s = blest_msbfs_device(h, srcs, k, d, h->stream);
+    if (!s) {
+        e = cudaMemcpyAsync(levels, d, sizeof(int32_t) * (size_t)k * (size_t)h->n, cudaMemcpyDeviceToHost, h->stream);
+        if (e != cudaSuccess) s = cuda_fail(e, "copy levels");
+    }
+    blest_status s2 = sync_status(h);
+    cudaFree(d);
+    return s ? s : s2;
+}
+
+blest_status blest_get_run_info(blest_handle h, blest_run_info* info, int32_t* queue_sizes, int32_t cap) {
+    if (!h || !info) return fail(BLEST_ERR_INVALID_ARG, "NULL argument");
+    blest_status s = sync_status(h);
+    if (s) return s;
+    unsigned int ctrl[16];
+    cudaError_t e = cudaMemcpy(ctrl, h->d_ctrl, 64, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read run info");
+    h->info.levels = (int32_t)ctrl[6];
+    h->info.recorded = h->record ? std::min<int32_t>(h->info.levels, kLevelRecordCap) : 0;
+    *info = h->info;
+    if (queue_sizes && cap > 0 && h->info.recorded > 0) {
+        int32_t m = std::min(cap, h->info.recorded);
+        e = cudaMemcpy(queue_sizes, h->d_level_sizes, sizeof(int32_t) * (size_t)m, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "read level record");
+    }
+    return BLEST_OK;
+}
+
+int64_t blest_export_size(blest_handle h, int32_t which) {
+    if (!h) return -1;
+    switch (which) {
+        case BLEST_ARRAY_REAL_PTRS: return 4 * ((int64_t)h->bvss.nss + 1);
+        case BLEST_ARRAY_VIRTUAL_TO_REAL: return 4 * h->bvss.nvss;
+        case BLEST_ARRAY_ROW_IDS: return 4 * 128 * h->bvss.nvss;
+        case BLEST_ARRAY_MASKS: return 4 * 32 * h->bvss.nvss;
+        case BLEST_ARRAY_NEW_ID: return 4 * (int64_t)h->n;
+        case BLEST_ARRAY_VSS_COUNT: return 4 * h->bvss.nvss;
+    }
+    return -1;
+}
+
+blest_status blest_export(blest_handle h, int32_t which, void* host_out, int64_t bytes) {
+    if (!h || (!host_out && bytes > 0)) return fail(BLEST_ERR_INVALID_ARG, "NULL argument");
+    int64_t need = blest_export_size(h, which);
+    if (need < 0) return fail(BLEST_ERR_INVALID_ARG, "unknown array");
+    if (bytes != need) return fail(BLEST_ERR_INVALID_ARG, "byte count does not match the array size");
+    if (need == 0) return BLEST_OK;
+    const void* src = nullptr;
+    switch (which) {
+        case BLEST_ARRAY_REAL_PTRS: src = h->bvss.real_ptrs; break;
+        case BLEST_ARRAY_VIRTUAL_TO_REAL: src = h->bvss.v2r; break;
+        case BLEST_ARRAY_ROW_IDS: src = h->bvss.row_ids; break;
+        case BLEST_ARRAY_MASKS: src = h->bvss.masks; break;
+        case BLEST_ARRAY_VSS_COUNT: src = h->bvss.vss_count; break;
+        case BLEST_ARRAY_NEW_ID:
+            if (h->h_new_id.empty()) {
+                int32_t* o = (int32_t*)host_out;
+                for (int32_t v = 0; v < h->n; ++v) o[v] = v;
+            } else {
+                std::memcpy(host_out, h->h_new_id.data(), (size_t)need);
+            }
+            return BLEST_OK;
+    }
+    blest_status s = sync_status(h);
+    if (s) return s;
+    cudaError_t e = cudaMemcpy(host_out, src, (size_t)need, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "export");
+    return BLEST_OK;
+}
+
+blest_status blest_compute_order(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, blest_order order,
+                                 const blest_create_params* params, int32_t* new_id) {
+    if (n > 0 && !new_id) return fail(BLEST_ERR_INVALID_ARG, "new_id is NULL");
+    const int threads = blest::host_threads(params ? params->threads : 0);
+    Csr clean;
+    std::vector<int32_t> ids;
+    int32_t used = 0;
+    double to = 0, tc = 0;
+    blest_status s = prepare_graph(n, row_ptr, col_idx, order, params, threads, clean, ids, &used, &to, &tc);
+    if (s) return s;
+    for (int32_t v = 0; v < n; ++v) new_id[v] = ids.empty() ? v : ids[v];
+    return BLEST_OK;
+}
+
+int32_t blest_is_social(int32_t n, const int32_t* row_ptr, const int32_t* col_idx) {
+    Csr clean;
+    std::string err;
+    int rc = blest::clean_csr(n, row_ptr, col_idx, blest::host_threads(0), clean, err);
+    if (rc) {
+        g_last_error = err;
+        return -rc;
+    }
+    return blest::is_social_like(clean) ? 1 : 0;
+}
+
+blest_status blest_debug_pull(const uint32_t* d_masks, const uint8_t* d_alpha, int32_t tiles, int32_t pull,
+                              uint8_t* d_hits) {
+    if (tiles < 0 || (tiles > 0 && (!d_masks || !d_alpha || !d_hits))) return fail(BLEST_ERR_INVALID_ARG, "bad arguments");
+    if (pull != BLEST_PULL_POPC && pull != BLEST_PULL_MMA) return fail(BLEST_ERR_INVALID_ARG, "unknown pull");
+    if (tiles == 0) return BLEST_OK;
+    cudaError_t e = blest::launch_debug_pull(d_masks, d_alpha, tiles, pull, d_hits, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "debug pull");
+    return BLEST_OK;
+}
+
+}  // extern "C"

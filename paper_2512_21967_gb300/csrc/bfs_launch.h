@@ -1,0 +1,68 @@
+// Host-side launch descriptions of the traversal kernels (no device code here).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace blest {
+
+constexpr int kInlineRoots = 16;
+
+// One fused single-frontier traversal (bfs_kernel.cu).
+struct BfsLaunch {
+    int update = 2;            // 1 eager, 2 lazy
+    int pull = 0;              // 0 CUDA cores, 1 b1 MMA
+    int unroll = 2;            // 1, 2, 4
+    int grid = 0;              // blocks (co-resident)
+    int32_t n = 0;
+    unsigned int qcap = 0;     // entries per queue buffer
+    const int32_t* real_ptrs = nullptr;
+    const int32_t* row_ids = nullptr;
+    const uint32_t* masks = nullptr;
+    const int32_t* new_id = nullptr;
+    int32_t* levels_internal = nullptr;
+    uint32_t* vcur = nullptr;
+    uint32_t* vnext = nullptr;
+    uint32_t* F[3] = {nullptr, nullptr, nullptr};
+    unsigned long long* Q[3] = {nullptr, nullptr, nullptr};
+    void* ctrl = nullptr;      // 64-byte control block
+    int32_t* level_sizes = nullptr;
+    int32_t level_cap = 0;
+    const int32_t* roots_device = nullptr;
+    int32_t roots_host[kInlineRoots] = {0};
+    int32_t nroots = 0;
+    int32_t* out = nullptr;
+    uint64_t timeout_ns = 2000000000ull;
+    unsigned int phantom = 0;
+};
+
+int bfs_max_blocks_per_sm(int update, int pull, int unroll);
+int bfs_threads_per_block();
+cudaError_t launch_bfs_kernel(const BfsLaunch& L, cudaStream_t stream);
+
+// Device BVSS arrays (bvss_build.cu).
+struct DeviceBvss {
+    int32_t n = 0;
+    int32_t nss = 0;
+    int64_t nvss = 0;
+    int64_t unpadded = 0;
+    int32_t* real_ptrs = nullptr;   // nss + 1
+    int32_t* v2r = nullptr;         // nvss
+    int32_t* row_ids = nullptr;     // 128 * nvss
+    uint32_t* masks = nullptr;      // 32 * nvss
+    int32_t* vss_count = nullptr;   // nvss
+};
+
+// Builds the BVSS of the (sorted, symmetric) device CSR.  Allocates the arrays
+// of `out` with cudaMalloc.  Returns a blest_status code; err gets a message.
+int build_bvss_device(const int32_t* d_rp, const int32_t* d_ci, int32_t n, int64_t nnz, cudaStream_t st,
+                      DeviceBvss& out, const char** err);
+void free_bvss_device(DeviceBvss& b);
+// Update divergence of the BVSS (mean over VSSs of the mean column std-dev).
+int update_divergence_device(const DeviceBvss& b, cudaStream_t st, double* out, const char** err);
+
+// Tile-level pull used by blest_debug_pull.
+cudaError_t launch_debug_pull(const uint32_t* d_masks, const uint8_t* d_alpha, int32_t tiles, int pull,
+                              uint8_t* d_hits, cudaStream_t st);
+
+}  // namespace blest

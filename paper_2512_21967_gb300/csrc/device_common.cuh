@@ -1,0 +1,149 @@
+// Device helpers shared by the BLEST kernels: a bounded grid barrier for
+// persistent cooperative kernels, global-timer reads, L1-bypassing loads of
+// state that other SMs write during a launch, and warp scans.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace blest {
+
+constexpr int kWarp = 32;
+
+// Control block (device memory, zeroed before every traversal).
+struct Ctrl {
+    unsigned int barrier;      // monotonically increasing arrival counter
+    unsigned int error;        // first blest_status raised on the device (0 = none)
+    unsigned int qcount[4];    // queue sizes, index = level & 3
+    unsigned int levels;       // levels processed
+    unsigned int pad[9];
+};
+static_assert(sizeof(Ctrl) == 64, "Ctrl is one 64-byte block");
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned int ld_volatile_u32(const unsigned int* p) {
+    return *(const volatile unsigned int*)p;
+}
+
+// Loads of data written by other blocks in the same launch: cache at L2 only.
+template <class T>
+__device__ __forceinline__ T ld_cg(const T* p) { return __ldcg(p); }
+
+// Grid barrier for a cooperative launch (all blocks co-resident).  Thread 0 of
+// each block arrives with a release (fence + atomic add) and spins with acquire
+// loads until every block of this generation has arrived.  The wait is bounded:
+// after timeout_ns it records BLEST_ERR_TIMEOUT (6) in ctrl->error and returns
+// false, as it does when another block already recorded an error.  `extra`
+// adds phantom participants (test hook: a barrier that can never complete).
+// `gen` is this block's barrier count, kept in a register by the caller.
+__device__ __forceinline__ bool grid_barrier(Ctrl* ctrl, unsigned int nblocks, unsigned int extra,
+                                             unsigned int& gen, uint64_t timeout_ns) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        gen += 1;
+        const unsigned int target = gen * (nblocks + extra);
+        __threadfence();
+        atomicAdd(&ctrl->barrier, 1u);
+        int ok = 1;
+        const uint64_t t0 = global_timer_ns();
+        unsigned int spins = 0;
+        for (;;) {
+            unsigned int v = ld_acquire_gpu(&ctrl->barrier);
+            if ((int)(v - target) >= 0) break;
+            if (ld_volatile_u32(&ctrl->error) != 0) { ok = 0; break; }
+            if ((++spins & 31u) == 0 && global_timer_ns() - t0 > timeout_ns) {
+                atomicCAS(&ctrl->error, 0u, 6u);
+                ok = 0;
+                break;
+            }
+            __nanosleep(20);
+        }
+        __threadfence();
+        if (ld_volatile_u32(&ctrl->error) != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ void raise_error(Ctrl* ctrl, unsigned int code) {
+    atomicCAS(&ctrl->error, 0u, code);
+}
+
+__device__ __forceinline__ unsigned int warp_inclusive_scan(unsigned int v, int lane) {
+#pragma unroll
+    for (int d = 1; d < kWarp; d <<= 1) {
+        unsigned int t = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += t;
+    }
+    return v;
+}
+
+// Every block folds the traversal's status into the sticky word (ctrl + 64 B),
+// which the host reads at synchronisation; the first failure wins.
+__device__ __forceinline__ void fold_status(Ctrl* ctrl) {
+    if (threadIdx.x == 0) {
+        const unsigned int e = ld_volatile_u32(&ctrl->error);
+        if (e) atomicCAS(reinterpret_cast<unsigned int*>(ctrl) + 16, 0u, e);
+    }
+}
+
+// Warp-aggregated queue append (Section 4.2): lane i appends the VSS ranges
+// [st[q], st[q] + ln[q]) of up to NS slice sets, payload pay[q] in the upper
+// 32 bits of each entry.  One atomicAdd on the queue size per warp; lanes with
+// long ranges (hub slice sets) are written by the whole warp together.
+// Raises BLEST_ERR_INTERNAL (7) instead of writing past qcap.
+template <int NS>
+__device__ __forceinline__ void warp_enqueue(unsigned int qcap, Ctrl* ctrl, unsigned long long* Qout,
+                                             unsigned int* qcount, const int (&st)[NS], const int (&ln)[NS],
+                                             const uint32_t (&pay)[NS], int lane) {
+    unsigned int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < NS; ++q) cnt += (unsigned int)ln[q];
+    const unsigned int incl = warp_inclusive_scan(cnt, lane);
+    const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) return;
+    unsigned int base = 0;
+    if (lane == 31) base = atomicAdd(qcount, total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    if (base + total > qcap || base + total < base) {
+        if (lane == 0) raise_error(ctrl, 7u);
+        return;
+    }
+    unsigned int pos = base + incl - cnt;
+    const bool big = cnt > 64;
+    if (!big) {
+#pragma unroll
+        for (int q = 0; q < NS; ++q)
+            for (int i = 0; i < ln[q]; ++i)
+                Qout[pos++] = (unsigned long long)(unsigned int)(st[q] + i) | ((unsigned long long)pay[q] << 32);
+    }
+    unsigned int bigmask = __ballot_sync(0xffffffffu, big);
+    while (bigmask) {
+        const int src = __ffs(bigmask) - 1;
+        bigmask &= bigmask - 1;
+        unsigned int p = __shfl_sync(0xffffffffu, pos, src);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            const int s0 = __shfl_sync(0xffffffffu, st[q], src);
+            const int l0 = __shfl_sync(0xffffffffu, ln[q], src);
+            const uint32_t p0 = __shfl_sync(0xffffffffu, pay[q], src);
+            for (int i = lane; i < l0; i += kWarp)
+                Qout[p + i] = (unsigned long long)(unsigned int)(s0 + i) | ((unsigned long long)p0 << 32);
+            p += (unsigned int)l0;
+        }
+    }
+}
+
+}  // namespace blest

@@ -1,0 +1,424 @@
+// Host-side graph preprocessing (see host_graph.h).
+#include "host_graph.h"
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <thread>
+
+#include "../../include/blest.h"
+
+namespace blest {
+
+int host_threads(int requested) {
+    if (requested > 0) return std::min(requested, 256);
+    unsigned hc = std::thread::hardware_concurrency();
+    return hc ? (int)std::min(hc, 256u) : 1;
+}
+
+// Run fn(lo, hi) over [0, n) in chunks handed out dynamically to `threads` workers.
+template <class F>
+static void parallel_chunks(int threads, int64_t n, int64_t chunk, F fn) {
+    if (threads <= 1 || n <= chunk) {
+        for (int64_t lo = 0; lo < n; lo += chunk) fn(lo, std::min(n, lo + chunk));
+        return;
+    }
+    std::atomic<int64_t> next(0);
+    auto worker = [&]() {
+        for (;;) {
+            int64_t lo = next.fetch_add(chunk);
+            if (lo >= n) break;
+            fn(lo, std::min(n, lo + chunk));
+        }
+    };
+    std::vector<std::thread> pool;
+    int nt = (int)std::min<int64_t>(threads, (n + chunk - 1) / chunk);
+    for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
+}
+
+// ------------------------------------------------------------------ cleaning
+
+int clean_csr(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int threads, Csr& out,
+              std::string& err) {
+    if (n < 0) { err = "n must be >= 0"; return BLEST_ERR_INVALID_ARG; }
+    if (!row_ptr) { err = "row_ptr is NULL"; return BLEST_ERR_INVALID_ARG; }
+    if (row_ptr[0] != 0) { err = "row_ptr[0] must be 0"; return BLEST_ERR_INVALID_ARG; }
+    for (int64_t u = 0; u < n; ++u)
+        if (row_ptr[u + 1] < row_ptr[u]) { err = "row_ptr must be non-decreasing"; return BLEST_ERR_INVALID_ARG; }
+    int64_t m = row_ptr[n];
+    if (m > 0 && !col_idx) { err = "col_idx is NULL"; return BLEST_ERR_INVALID_ARG; }
+    std::atomic<int64_t> bad(-1);
+    parallel_chunks(threads, m, 1 << 20, [&](int64_t lo, int64_t hi) {
+        for (int64_t e = lo; e < hi; ++e)
+            if (col_idx[e] < 0 || col_idx[e] >= n) { bad.store(e); return; }
+    });
+    if (bad.load() >= 0) { err = "col_idx entry out of range [0, n)"; return BLEST_ERR_INVALID_ARG; }
+
+    out.n = n;
+    out.rp.assign((size_t)n + 1, 0);
+    std::vector<int32_t> tmp((size_t)std::max<int64_t>(m, 1));
+    std::vector<int32_t> newdeg((size_t)n + 1, 0);
+    parallel_chunks(threads, n, 4096, [&](int64_t lo, int64_t hi) {
+        for (int64_t u = lo; u < hi; ++u) {
+            int32_t* a = tmp.data() + row_ptr[u];
+            int64_t len = row_ptr[u + 1] - row_ptr[u];
+            std::memcpy(a, col_idx + row_ptr[u], (size_t)len * sizeof(int32_t));
+            std::sort(a, a + len);
+            int64_t w = 0;
+            for (int64_t i = 0; i < len; ++i)
+                if (a[i] != (int32_t)u && (w == 0 || a[w - 1] != a[i])) a[w++] = a[i];
+            newdeg[u] = (int32_t)w;
+        }
+    });
+    for (int64_t u = 0; u < n; ++u) out.rp[u + 1] = out.rp[u] + newdeg[u];
+    out.ci.resize((size_t)out.rp[n]);
+    parallel_chunks(threads, n, 4096, [&](int64_t lo, int64_t hi) {
+        for (int64_t u = lo; u < hi; ++u)
+            std::memcpy(out.ci.data() + out.rp[u], tmp.data() + row_ptr[u], (size_t)newdeg[u] * sizeof(int32_t));
+    });
+    return BLEST_OK;
+}
+
+bool is_symmetric(const Csr& g, int threads, int64_t* bad_u, int64_t* bad_v) {
+    std::atomic<int64_t> found(-1);
+    std::atomic<int64_t> found_v(-1);
+    parallel_chunks(threads, g.n, 4096, [&](int64_t lo, int64_t hi) {
+        for (int64_t u = lo; u < hi && found.load(std::memory_order_relaxed) < 0; ++u)
+            for (int64_t e = g.rp[u]; e < g.rp[u + 1]; ++e) {
+                int32_t v = g.ci[e];
+                const int32_t* b = g.ci.data() + g.rp[v];
+                const int32_t* en = g.ci.data() + g.rp[v + 1];
+                if (!std::binary_search(b, en, (int32_t)u)) { found.store(u); found_v.store(v); break; }
+            }
+    });
+    if (found.load() >= 0) {
+        if (bad_u) *bad_u = found.load();
+        if (bad_v) *bad_v = found_v.load();
+        return false;
+    }
+    return true;
+}
+
+void relabel_csr(const Csr& g, const std::vector<int32_t>& new_id, int threads, Csr& out) {
+    int32_t n = g.n;
+    std::vector<int32_t> old_of((size_t)n);
+    for (int32_t v = 0; v < n; ++v) old_of[new_id[v]] = v;
+    out.n = n;
+    out.rp.assign((size_t)n + 1, 0);
+    for (int32_t w = 0; w < n; ++w) {
+        int32_t v = old_of[w];
+        out.rp[w + 1] = out.rp[w] + (g.rp[v + 1] - g.rp[v]);
+    }
+    out.ci.resize((size_t)out.rp[n]);
+    parallel_chunks(threads, n, 4096, [&](int64_t lo, int64_t hi) {
+        for (int64_t w = lo; w < hi; ++w) {
+            int32_t v = old_of[w];
+            int32_t* dst = out.ci.data() + out.rp[w];
+            int64_t len = g.rp[v + 1] - g.rp[v];
+            for (int64_t i = 0; i < len; ++i) dst[i] = new_id[g.ci[g.rp[v] + i]];
+            std::sort(dst, dst + len);
+        }
+    });
+}
+
+// -------------------------------------------------------------------- RCM
+// Section 3.2.1 uses RCM as a bandwidth-reducing order.  Each component (in
+// order of its smallest id) starts at a George-Liu pseudo-peripheral vertex;
+// unvisited neighbours are queued in ascending (degree, id); the whole
+// Cuthill-McKee sequence is reversed at the end.
+
+namespace {
+struct LevelBfs {
+    std::vector<int32_t> stamp, level, queue;
+    int32_t cur = 0;
+    explicit LevelBfs(int32_t n) : stamp((size_t)n, 0), level((size_t)n, 0), queue((size_t)std::max(n, 1)) {}
+    // BFS from root over its component; returns eccentricity; queue[0..count) holds the visit order.
+    int32_t run(const Csr& g, int32_t root, int64_t& count) {
+        ++cur;
+        int64_t head = 0, tail = 0;
+        stamp[root] = cur; level[root] = 0; queue[tail++] = root;
+        int32_t ecc = 0;
+        while (head < tail) {
+            int32_t u = queue[head++];
+            for (int32_t e = g.rp[u]; e < g.rp[u + 1]; ++e) {
+                int32_t v = g.ci[e];
+                if (stamp[v] != cur) {
+                    stamp[v] = cur; level[v] = level[u] + 1; queue[tail++] = v;
+                    if (level[v] > ecc) ecc = level[v];
+                }
+            }
+        }
+        count = tail;
+        return ecc;
+    }
+};
+}  // namespace
+
+static int32_t pseudo_peripheral(const Csr& g, LevelBfs& bfs, int32_t start) {
+    int32_t x = start;
+    int64_t cnt = 0;
+    int32_t ex = bfs.run(g, x, cnt);
+    for (;;) {
+        int32_t y = -1;
+        for (int64_t i = 0; i < cnt; ++i) {
+            int32_t v = bfs.queue[i];
+            if (bfs.level[v] != ex) continue;
+            if (y < 0) { y = v; continue; }
+            int32_t dv = g.rp[v + 1] - g.rp[v], dy = g.rp[y + 1] - g.rp[y];
+            if (dv < dy || (dv == dy && v < y)) y = v;
+        }
+        int64_t cy = 0;
+        int32_t ey = bfs.run(g, y, cy);
+        if (ey > ex) {
+            x = y; ex = ey; cnt = cy;
+        } else {
+            return x;
+        }
+    }
+}
+
+void order_rcm(const Csr& g, std::vector<int32_t>& new_id) {
+    int32_t n = g.n;
+    new_id.assign((size_t)n, 0);
+    if (n == 0) return;
+    LevelBfs bfs(n);
+    std::vector<uint8_t> seen((size_t)n, 0);
+    std::vector<int32_t> order;
+    order.reserve((size_t)n);
+    std::vector<int32_t> nb;
+    for (int32_t v0 = 0; v0 < n; ++v0) {
+        if (seen[v0]) continue;
+        int32_t r = pseudo_peripheral(g, bfs, v0);
+        size_t head = order.size();
+        seen[r] = 1;
+        order.push_back(r);
+        while (head < order.size()) {
+            int32_t u = order[head++];
+            nb.clear();
+            for (int32_t e = g.rp[u]; e < g.rp[u + 1]; ++e)
+                if (!seen[g.ci[e]]) nb.push_back(g.ci[e]);
+            std::sort(nb.begin(), nb.end(), [&](int32_t a, int32_t b) {
+                int32_t da = g.rp[a + 1] - g.rp[a], db = g.rp[b + 1] - g.rp[b];
+                return da != db ? da < db : a < b;
+            });
+            for (int32_t v : nb) { seen[v] = 1; order.push_back(v); }
+        }
+    }
+    for (int64_t pos = 0; pos < n; ++pos) new_id[order[pos]] = (int32_t)(n - 1 - pos);
+}
+
+// ------------------------------------------------------------ hub pre-pass
+// Stand-in for the Gorder pre-pass of Section 3.2: BFS visit order, every
+// component rooted at the highest-degree unvisited vertex (smallest id on
+// ties), neighbours scanned in ascending id.  Neighbours of the same hub land
+// in the same window of Algorithm 1.
+
+void order_hub_prepass(const Csr& g, std::vector<int32_t>& new_id) {
+    int32_t n = g.n;
+    new_id.assign((size_t)n, 0);
+    std::vector<int32_t> cand((size_t)n);
+    for (int32_t v = 0; v < n; ++v) cand[v] = v;
+    std::sort(cand.begin(), cand.end(), [&](int32_t a, int32_t b) {
+        int32_t da = g.rp[a + 1] - g.rp[a], db = g.rp[b + 1] - g.rp[b];
+        return da != db ? da > db : a < b;
+    });
+    std::vector<uint8_t> seen((size_t)n, 0);
+    std::vector<int32_t> order;
+    order.reserve((size_t)n);
+    for (int32_t r : cand) {
+        if (seen[r]) continue;
+        size_t head = order.size();
+        seen[r] = 1;
+        order.push_back(r);
+        while (head < order.size()) {
+            int32_t u = order[head++];
+            for (int32_t e = g.rp[u]; e < g.rp[u + 1]; ++e) {
+                int32_t v = g.ci[e];
+                if (!seen[v]) { seen[v] = 1; order.push_back(v); }
+            }
+        }
+    }
+    for (int32_t pos = 0; pos < n; ++pos) new_id[order[pos]] = pos;
+}
+
+// ------------------------------------------------------- JaccardWithWindows
+// Algorithm 1.  Windows [s_k, e_k) of at most w ids are independent and run in
+// parallel.  Inside a window: M_k = ceil(L_k / sigma) clusters; each starts at
+// the smallest remaining id (pop(Q)), then sigma-1 times adds the remaining
+// vertex j maximising J = |N(j) & U| / |N(j) | U| (exact rational comparison,
+// smallest id on ties), U growing by N(j).
+//
+// The counts c[j] = |N(j) & U| are kept incrementally: when a vertex x joins U,
+// every window member adjacent to x gets c[j] + 1 (a window-local reverse
+// index x -> {j in window : x in N(j)} makes that a list walk).  Members with
+// c[j] = 0 all have J = 0, so when no member has c[j] > 0 the smallest
+// remaining id is chosen, as the argmax tie rule says.
+
+namespace {
+struct JaccardWorker {
+    const Csr& g;
+    int sigma;
+    std::vector<int32_t> ustamp;   // per vertex: stamp of the cluster whose U contains it
+    std::vector<int32_t> c, cstamp;
+    std::vector<uint8_t> inq;
+    std::vector<int32_t> touched;
+    std::vector<uint64_t> pairs;
+    std::vector<int32_t> revx, revptr, revj;
+    int32_t stamp = 0;
+
+    JaccardWorker(const Csr& gr, int s) : g(gr), sigma(s), ustamp((size_t)gr.n, 0) {}
+
+    void window(int32_t s_k, int32_t e_k, int32_t* new_id) {
+        int32_t L = e_k - s_k;
+        c.assign((size_t)L, 0);
+        cstamp.assign((size_t)L, 0);
+        inq.assign((size_t)L, 1);
+        // reverse index
+        pairs.clear();
+        for (int32_t jl = 0; jl < L; ++jl) {
+            int32_t j = s_k + jl;
+            for (int32_t e = g.rp[j]; e < g.rp[j + 1]; ++e)
+                pairs.push_back(((uint64_t)(uint32_t)g.ci[e] << 32) | (uint32_t)jl);
+        }
+        std::sort(pairs.begin(), pairs.end());
+        revx.clear(); revptr.clear(); revj.resize(pairs.size());
+        for (size_t i = 0; i < pairs.size(); ++i) {
+            int32_t x = (int32_t)(pairs[i] >> 32);
+            if (revx.empty() || revx.back() != x) { revx.push_back(x); revptr.push_back((int32_t)i); }
+            revj[i] = (int32_t)(pairs[i] & 0xffffffffu);
+        }
+        revptr.push_back((int32_t)pairs.size());
+
+        int32_t qptr = 0, remaining = L;
+        int32_t M = (L + sigma - 1) / sigma;
+        for (int32_t ell = 0; ell < M; ++ell) {
+            while (!inq[qptr]) ++qptr;
+            int32_t js = qptr;
+            inq[js] = 0; --remaining;
+            new_id[s_k + js] = s_k + ell * sigma;
+            ++stamp;
+            if (stamp == 0x7fffffff) {  // stamp wrap: reset the marks
+                std::fill(ustamp.begin(), ustamp.end(), 0);
+                std::fill(cstamp.begin(), cstamp.end(), 0);
+                stamp = 1;
+            }
+            int64_t usize = 0;
+            touched.clear();
+            add_to_u(s_k + js, usize);
+            for (int r = 1; r < sigma; ++r) {
+                if (remaining == 0) break;
+                int32_t best = -1;
+                int64_t bnum = 0, bden = 1;
+                for (int32_t jl : touched) {
+                    if (!inq[jl]) continue;
+                    int64_t num = c[jl];
+                    int64_t den = (int64_t)(g.rp[s_k + jl + 1] - g.rp[s_k + jl]) + usize - num;
+                    // num > 0 here, so den >= 1
+                    bool better = best < 0 || num * bden > bnum * den || (num * bden == bnum * den && jl < best);
+                    if (better) { best = jl; bnum = num; bden = den; }
+                }
+                if (best < 0) {
+                    while (!inq[qptr]) ++qptr;
+                    best = qptr;
+                }
+                inq[best] = 0; --remaining;
+                new_id[s_k + best] = s_k + ell * sigma + r;
+                add_to_u(s_k + best, usize);
+            }
+        }
+    }
+
+    void add_to_u(int32_t j, int64_t& usize) {
+        for (int32_t e = g.rp[j]; e < g.rp[j + 1]; ++e) {
+            int32_t x = g.ci[e];
+            if (ustamp[x] == stamp) continue;
+            ustamp[x] = stamp;
+            ++usize;
+            auto it = std::lower_bound(revx.begin(), revx.end(), x);
+            if (it == revx.end() || *it != x) continue;
+            size_t k = (size_t)(it - revx.begin());
+            for (int32_t i = revptr[k]; i < revptr[k + 1]; ++i) {
+                int32_t jl = revj[i];
+                if (!inq[jl]) continue;
+                if (cstamp[jl] != stamp) { cstamp[jl] = stamp; c[jl] = 0; touched.push_back(jl); }
+                ++c[jl];
+            }
+        }
+    }
+};
+}  // namespace
+
+void order_jaccard_windows(const Csr& g, int sigma, int32_t window, int threads, std::vector<int32_t>& new_id) {
+    int32_t n = g.n;
+    new_id.assign((size_t)n, 0);
+    if (n == 0) return;
+    int64_t nwin = ((int64_t)n + window - 1) / window;
+    int nt = (int)std::min<int64_t>(threads, nwin);
+    if (nt < 1) nt = 1;
+    std::atomic<int64_t> next(0);
+    auto work = [&]() {
+        JaccardWorker wk(g, sigma);
+        for (;;) {
+            int64_t k = next.fetch_add(1);
+            if (k >= nwin) break;
+            int32_t s_k = (int32_t)(k * window);
+            int32_t e_k = (int32_t)std::min<int64_t>((int64_t)s_k + window, n);
+            wk.window(s_k, e_k, new_id.data());
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+    work();
+    for (auto& th : pool) th.join();
+}
+
+void order_compress(const Csr& g, int sigma, int32_t window, int threads, std::vector<int32_t>& new_id) {
+    std::vector<int32_t> pre;
+    order_hub_prepass(g, pre);
+    Csr g2;
+    relabel_csr(g, pre, threads, g2);
+    std::vector<int32_t> jw;
+    order_jaccard_windows(g2, sigma, window, threads, jw);
+    new_id.resize((size_t)g.n);
+    for (int32_t v = 0; v < g.n; ++v) new_id[v] = jw[pre[v]];
+}
+
+// ------------------------------------------------------------ classifier
+
+bool is_social_like(const Csr& g) {
+    int32_t n = g.n;
+    if (n == 0) return false;
+    std::vector<int64_t> deg((size_t)n);
+    int64_t total = 0;
+    for (int32_t v = 0; v < n; ++v) { deg[v] = g.rp[v + 1] - g.rp[v]; total += deg[v]; }
+    if (total == 0) return false;
+    std::vector<int64_t> sorted = deg;
+    std::sort(sorted.begin(), sorted.end(), std::greater<int64_t>());
+    int64_t k1 = std::max<int64_t>(1, (n + 99) / 100), k10 = std::max<int64_t>(1, (n + 9) / 10);
+    int64_t s1 = 0, s10 = 0;
+    for (int64_t i = 0; i < k10; ++i) { if (i < k1) s1 += sorted[i]; s10 += sorted[i]; }
+    bool heavy = (double)s1 > 0.05 * (double)total && (double)s10 > 0.40 * (double)total;
+    if (heavy) return true;
+    // log-log degree histogram, least-squares line over degrees >= 1
+    int64_t dmax = sorted[0];
+    std::vector<int64_t> hist((size_t)dmax + 1, 0);
+    for (int64_t d : deg) hist[d]++;
+    double sx = 0, sy = 0, sxx = 0, sxy = 0, syy = 0;
+    int pts = 0;
+    for (int64_t d = 1; d <= dmax; ++d) {
+        if (!hist[d]) continue;
+        double x = std::log((double)d), y = std::log((double)hist[d]);
+        sx += x; sy += y; sxx += x * x; sxy += x * y; syy += y * y; ++pts;
+    }
+    if (pts < 5) return false;
+    double vx = sxx - sx * sx / pts, vy = syy - sy * sy / pts, cxy = sxy - sx * sy / pts;
+    if (vx <= 0 || vy <= 0) return false;
+    double slope = cxy / vx;
+    double r2 = cxy * cxy / (vx * vy);
+    return slope >= -3.5 && slope <= -1.5 && r2 >= 0.8;
+}
+
+}  // namespace blest

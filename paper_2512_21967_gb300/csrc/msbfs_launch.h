@@ -1,0 +1,48 @@
+// Host-side description of the multi-source traversal (msbfs_kernel.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+namespace blest {
+
+// Device buffers of a multi-source traversal, grown on demand and kept with
+// the handle between calls.
+struct MsbfsState {
+    int64_t words_cap = 0;             // u64 words per bitmap (n * W)
+    unsigned long long* vcur = nullptr;
+    unsigned long long* vnext = nullptr;
+    unsigned long long* front = nullptr;
+    int64_t qcap = 0;
+    unsigned long long* Q = nullptr;   // 3 * qcap
+    int64_t lint_cap = 0;              // int32 entries of the internal level buffer
+    int32_t* lint = nullptr;
+    int64_t roots_cap = 0;
+    int32_t* roots = nullptr;
+};
+
+struct MsbfsLaunchCommon {
+    int32_t n = 0, nss = 0;
+    int64_t nvss = 0;
+    const int32_t* real_ptrs = nullptr;
+    const int32_t* row_ids = nullptr;
+    const uint32_t* masks = nullptr;
+    const int32_t* new_id = nullptr;    // NULL = identity
+    unsigned int* ctrl = nullptr;       // 64-byte control block + sticky word at [16]
+    int sms = 0;
+    int blocks_per_sm = 0;
+    uint64_t timeout_ns = 2000000000ull;
+    unsigned int phantom = 0;
+    int32_t* level_sizes = nullptr;
+    int32_t level_cap = 0;
+};
+
+// Runs k = roots.size() traversals (sources already in BVSS ids) in batches of
+// at most 256 sources, writing out[i*n + v] in original ids.  Returns a
+// blest_status code (device-side status is folded into the sticky word).
+int run_msbfs(MsbfsState& s, const MsbfsLaunchCommon& c, const std::vector<int32_t>& roots, int32_t* d_out,
+              cudaStream_t st, const char** err);
+void free_msbfs_state(MsbfsState& s);
+
+}  // namespace blest

@@ -1,0 +1,127 @@
+"""The C-ABI library without a GPU: it loads, exports every symbol declared in
+include/blest.h, and its host-only entry points (input checks, the two vertex
+orderings, the social-like classifier) agree with the oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2512_21967_gb300 as blest
+from oracle import orderings as oo
+from paper_2512_21967_gb300 import synth
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "blest.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(blest_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = blest.lib()
+    names = declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in blest.h but not exported"
+    assert sorted(blest.EXPORTED_SYMBOLS) == names
+
+
+def csr(n, edges):
+    src = np.array([e[0] for e in edges], np.int32)
+    dst = np.array([e[1] for e in edges], np.int32)
+    return synth.csr_from_edges(n, src, dst)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_rcm_matches_oracle(seed):
+    g, _ = synth.grid_graph(14 + seed, p=0.85, seed=seed)
+    got = blest.blest_compute_order(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_BANDWIDTH)
+    assert np.array_equal(got, oo.rcm(g.n, g.row_ptr, g.col_idx))
+
+
+def test_rcm_matches_oracle_rmat_with_isolated():
+    g = synth.rmat_graph(9, 4, seed=8)
+    got = blest.blest_compute_order(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_BANDWIDTH)
+    assert np.array_equal(got, oo.rcm(g.n, g.row_ptr, g.col_idx))
+
+
+@pytest.mark.parametrize("scale,w", [(8, 16), (9, 64), (10, 1024)])
+def test_compress_order_matches_oracle(scale, w):
+    g = synth.rmat_graph(scale, 16, seed=scale)
+    got = blest.blest_compute_order(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_COMPRESS, window=w, threads=3)
+    assert np.array_equal(got, oo.compress_order(g.n, g.row_ptr, g.col_idx, sigma=8, w=w))
+
+
+def test_compress_order_ragged_last_window():
+    g = synth.rmat_graph(7, 8, seed=4)
+    # n = 128, w = 48: windows of 48, 48, 32
+    got = blest.blest_compute_order(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_COMPRESS, window=48)
+    assert np.array_equal(got, oo.compress_order(g.n, g.row_ptr, g.col_idx, sigma=8, w=48))
+
+
+def test_none_order_is_identity_and_auto_classifies():
+    g = synth.rmat_graph(10, 16, seed=1)
+    assert np.array_equal(blest.blest_compute_order(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_NONE),
+                          np.arange(g.n))
+    gg, _ = synth.grid_graph(40, 0.9, seed=2)
+    for graph, social in ((g, True), (gg, False)):
+        assert blest.blest_is_social(graph.n, graph.row_ptr, graph.col_idx) == social
+        assert oo.is_social_like(graph.n, graph.row_ptr, graph.col_idx) == social
+    auto = blest.blest_compute_order(gg.n, gg.row_ptr, gg.col_idx, blest.BLEST_ORDER_AUTO)
+    assert np.array_equal(auto, oo.rcm(gg.n, gg.row_ptr, gg.col_idx))
+
+
+def test_classifier_agrees_with_oracle_on_mixed_graphs():
+    for seed in range(4):
+        g = synth.rmat_graph(9, 2 + 4 * seed, seed=seed)
+        assert blest.blest_is_social(g.n, g.row_ptr, g.col_idx) == oo.is_social_like(g.n, g.row_ptr, g.col_idx)
+    path = csr(50, [(i, i + 1) for i in range(49)])
+    assert not blest.blest_is_social(path.n, path.row_ptr, path.col_idx)
+
+
+def test_unsorted_rows_duplicates_and_loops_are_cleaned():
+    g = synth.rmat_graph(8, 8, seed=3)
+    rng = np.random.default_rng(0)
+    rows = []
+    for u in range(g.n):
+        r = list(g.col_idx[g.row_ptr[u]:g.row_ptr[u + 1]])
+        r += r[:1] + [u]            # a duplicate and a self-loop
+        rng.shuffle(r)
+        rows.append(r)
+    rp = np.zeros(g.n + 1, np.int32)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    ci = np.array([x for r in rows for x in r], np.int32)
+    a = blest.blest_compute_order(g.n, rp, ci, blest.BLEST_ORDER_BANDWIDTH)
+    assert np.array_equal(a, oo.rcm(g.n, g.row_ptr, g.col_idx))
+
+
+def test_input_errors():
+    g = csr(4, [(0, 1), (1, 2)])
+    with pytest.raises(blest.BlestError) as e:
+        blest.blest_compute_order(4, g.row_ptr, np.array([0, 1, 1, 9], np.int32), blest.BLEST_ORDER_NONE)
+    assert e.value.name == "BLEST_ERR_INVALID_ARG"
+    asym_rp = np.array([0, 1, 1, 1, 1], np.int32)
+    with pytest.raises(blest.BlestError) as e:
+        blest.blest_compute_order(4, asym_rp, np.array([2], np.int32), blest.BLEST_ORDER_NONE)
+    assert e.value.name == "BLEST_ERR_NOT_SYMMETRIC"
+    with pytest.raises(blest.BlestError) as e:
+        blest.blest_compute_order(4, np.array([0, 2, 1, 2, 2], np.int32), g.col_idx, blest.BLEST_ORDER_NONE)
+    assert e.value.name == "BLEST_ERR_INVALID_ARG"
+    with pytest.raises(blest.BlestError) as e:
+        blest.blest_compute_order(g.n, g.row_ptr, g.col_idx, 7)
+    assert e.value.name == "BLEST_ERR_INVALID_ARG"
+    with pytest.raises(blest.BlestError):
+        blest.blest_compute_order(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_COMPRESS, window=12)
+    # n = 0 is a valid, empty graph
+    assert blest.blest_compute_order(0, np.zeros(1, np.int32), np.zeros(0, np.int32), blest.BLEST_ORDER_AUTO).size == 0
+
+
+def test_null_handle_calls_fail_cleanly():
+    lib = blest.lib()
+    assert lib.blest_bfs(None, 0, None) == 1
+    assert lib.blest_sync(None) == 1
+    lib.blest_destroy(None)
+    assert blest.blest_export_size(None, 0) == -1

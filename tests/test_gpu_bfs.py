@@ -1,0 +1,300 @@
+"""GPU parity of the BLEST kernels against the oracle, through the C ABI.
+Levels and BVSS arrays are integer results: every comparison is bit-exact."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2512_21967_gb300 as blest
+from oracle import bvss as ob
+from oracle import model as om
+from oracle import orderings as oo
+from paper_2512_21967_gb300 import synth
+
+from gpu_helpers import ORDERS, assert_bvss_equal, check_levels, csr, export_bvss, oracle_bvss, oracle_order
+
+pytestmark = pytest.mark.gpu
+
+MODES = [(u, p) for u in (blest.BLEST_UPDATE_EAGER, blest.BLEST_UPDATE_LAZY)
+         for p in (blest.BLEST_PULL_POPC, blest.BLEST_PULL_MMA)]
+
+
+@pytest.fixture(scope="module")
+def torch_cuda(gpu):
+    import torch
+    torch.cuda.init()
+    return torch
+
+
+# ------------------------------------------------------------ pull tiles
+
+@pytest.mark.parametrize("pull", [blest.BLEST_PULL_POPC, blest.BLEST_PULL_MMA])
+def test_pull_tile_exhaustive(torch_cuda, pull):
+    """Every (8-bit mask, alpha) pair in every one of the 4 sub-slots (Figure 2c's
+    fragment contract): hit iff popc(mask & alpha) > 0 (Eq. 1)."""
+    torch = torch_cuda
+    alphas = np.repeat(np.arange(256, dtype=np.uint8), 8)          # 8 tiles per alpha
+    tiles = len(alphas)
+    j = np.tile(np.arange(8), 256)[:, None, None]
+    lane = np.arange(32)[None, :, None]
+    q = np.arange(4)[None, None, :]
+    byte = (j * 32 + lane + 64 * q) % 256                           # all 256 values per sub-slot
+    masks = (byte.astype(np.uint32) << (8 * q).astype(np.uint32)).sum(axis=2).astype(np.uint32)
+    exp = np.zeros((tiles, 32), np.uint8)
+    for qq in range(4):
+        hit = (byte[:, :, qq] & alphas[:, None]) != 0
+        exp |= (hit.astype(np.uint8) << qq)
+    d_m = torch.from_numpy(masks.view(np.int32).reshape(-1)).cuda()
+    d_a = torch.from_numpy(alphas).cuda()
+    d_h = torch.zeros(tiles * 32, dtype=torch.uint8, device="cuda")
+    blest.blest_debug_pull(d_m, d_a, tiles, pull, d_h)
+    assert np.array_equal(d_h.cpu().numpy().reshape(tiles, 32), exp)
+
+
+# ------------------------------------------------------------- BVSS build
+
+@pytest.mark.parametrize("order", ["none", "bandwidth", "compress"])
+@pytest.mark.parametrize("scale", [7, 10])
+def test_bvss_build_matches_oracle(gpu, order, scale):
+    g = synth.rmat_graph(scale, 16, seed=scale + 1)
+    o = ORDERS[order]
+    h = blest.blest_graph_create_ex(g.n, g.row_ptr, g.col_idx, o, window=256)
+    try:
+        got = export_bvss(h)
+        ref_id = oracle_order(g, o, window=256)
+        assert np.array_equal(got["new_id"], ref_id)
+        assert_bvss_equal(got, oracle_bvss(g, ref_id))
+        st = blest.blest_get_stats(h)
+        b = oracle_bvss(g, ref_id)
+        assert st["unpadded_slices"] == ob.unpadded_slices(b)
+        assert abs(st["compression_ratio"] - om.compression_ratio(g.nnz, ob.unpadded_slices(b))) < 1e-12
+        assert abs(st["update_divergence"] - om.update_divergence(b)) <= 1e-9 * max(1.0, om.update_divergence(b))
+    finally:
+        blest.blest_destroy(h)
+
+
+def test_bvss_build_edge_shapes(gpu):
+    from test_oracle_bvss import fig1_graph
+    cases = [fig1_graph(),
+             csr(45, [(0, 44), (1, 2), (30, 31), (44, 3), (20, 21)]),          # ragged n, empty slice set
+             csr(300, [(0, i) for i in range(1, 300)]),                          # hub: 3 VSSs in slice set 0
+             csr(1, []), csr(9, [])]
+    for g in cases:
+        h = blest.blest_graph_create(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_NONE)
+        try:
+            assert_bvss_equal(export_bvss(h), ob.build(g.n, g.row_ptr, g.col_idx))
+        finally:
+            blest.blest_destroy(h)
+
+
+# ------------------------------------------------------------- traversals
+
+@pytest.fixture(scope="module")
+def cfg1(gpu):
+    """R-MAT scale 16, edgefactor 16, 64 seeded degree>0 sources."""
+    g, srcs = synth.rmat_workload(16, 64, seed_graph=1, seed_src=1001)
+    exp = oracle.msbfs_levels(g.n, g.row_ptr, g.col_idx, srcs, threads=8)
+    return g, srcs, exp
+
+
+@pytest.mark.parametrize("order", ["none", "compress", "bandwidth"])
+def test_rmat16_all_sources_all_modes(cfg1, order):
+    g, srcs, exp = cfg1
+    h = blest.blest_graph_create_ex(g.n, g.row_ptr, g.col_idx, ORDERS[order], window=4096)
+    try:
+        for upd, pull in MODES:
+            blest.blest_set_option(h, blest.BLEST_OPT_UPDATE, upd)
+            blest.blest_set_option(h, blest.BLEST_OPT_PULL, pull)
+            for unroll in (1, 4) if (upd, pull) == MODES[0] else (2,):
+                blest.blest_set_option(h, blest.BLEST_OPT_UNROLL, unroll)
+                for i, s in enumerate(srcs):
+                    got = blest.blest_bfs(h, int(s))
+                    assert np.array_equal(got, exp[i]), f"mode {(upd, pull, unroll)} source {s}"
+    finally:
+        blest.blest_destroy(h)
+
+
+def test_queue_sizes_match_replay(cfg1):
+    """Per-level VSS counts equal the oracle replay: only slice sets with a
+    column in the previous frontier are processed (Section 3.1.1), once each."""
+    g, srcs, exp = cfg1
+    h = blest.blest_graph_create(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_NONE)
+    try:
+        b = ob.build(g.n, g.row_ptr, g.col_idx)
+        blest.blest_set_option(h, blest.BLEST_OPT_RECORD_LEVELS, 1)
+        for upd in (blest.BLEST_UPDATE_EAGER, blest.BLEST_UPDATE_LAZY):
+            blest.blest_set_option(h, blest.BLEST_OPT_UPDATE, upd)
+            for i in range(4):
+                blest.blest_bfs(h, int(srcs[i]))
+                info, sizes = blest.blest_get_run_info(h, 4096)
+                ref = om.queue_sizes(b, exp[i])
+                assert info["levels"] == len(ref)
+                assert sizes.tolist() == ref
+    finally:
+        blest.blest_destroy(h)
+
+
+@pytest.mark.parametrize("upd", [blest.BLEST_UPDATE_EAGER, blest.BLEST_UPDATE_LAZY])
+def test_grid_high_diameter(gpu, upd):
+    g, srcs = synth.grid_workload(192, 6, seed_graph=3, seed_src=1003)
+    h = blest.blest_graph_create(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_BANDWIDTH)
+    try:
+        blest.blest_set_option(h, blest.BLEST_OPT_UPDATE, upd)
+        check_levels(g, h, srcs)
+    finally:
+        blest.blest_destroy(h)
+
+
+def test_small_graphs_closed_forms(gpu):
+    cases = []
+    n = 77
+    cases.append((csr(n, [(i, i + 1) for i in range(n - 1)]), [0, 38, 76]))                 # path: |i - c|
+    cases.append((csr(40, [(0, i) for i in range(1, 40)]), [0, 13]))                        # star
+    cases.append((csr(33, [(i, (i + 1) % 33) for i in range(33)]), [5]))                    # cycle
+    cases.append((csr(12, [(i, j) for i in range(6) for j in range(i + 1, 6)]), [1, 9]))    # K6 + isolated
+    cases.append((csr(1, []), [0]))                                                          # single vertex
+    cases.append((csr(50, [(1, 2)]), [49, 1]))                                               # isolated source
+    for g, srcs in cases:
+        for order in ORDERS.values():
+            h = blest.blest_graph_create(g.n, g.row_ptr, g.col_idx, order)
+            try:
+                for upd, pull in MODES:
+                    blest.blest_set_option(h, blest.BLEST_OPT_UPDATE, upd)
+                    blest.blest_set_option(h, blest.BLEST_OPT_PULL, pull)
+                    check_levels(g, h, srcs)
+            finally:
+                blest.blest_destroy(h)
+
+
+def test_invalid_sources_and_empty_graph(gpu):
+    g = csr(10, [(0, 1)])
+    h = blest.blest_graph_create(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_NONE)
+    try:
+        for bad in (-1, 10):
+            with pytest.raises(blest.BlestError) as e:
+                blest.blest_bfs(h, bad)
+            assert e.value.name == "BLEST_ERR_INVALID_ARG"
+        with pytest.raises(blest.BlestError):
+            blest.blest_msbfs(h, [0, 11])
+        assert blest.blest_bfs(h, 0)[1] == 1          # handle still usable
+    finally:
+        blest.blest_destroy(h)
+    h0 = blest.blest_graph_create(0, np.zeros(1, np.int32), np.zeros(0, np.int32), blest.BLEST_ORDER_NONE)
+    try:
+        with pytest.raises(blest.BlestError):
+            blest.blest_bfs(h0, 0)
+        assert blest.blest_msbfs(h0, []).size == 0
+    finally:
+        blest.blest_destroy(h0)
+
+
+def test_barrier_timeout_is_reported_and_recoverable(gpu):
+    """A barrier that waits for a block that does not exist gives up after the
+    configured limit with BLEST_ERR_TIMEOUT; the handle keeps working."""
+    g = synth.rmat_graph(10, 16, seed=3)
+    h = blest.blest_graph_create(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_NONE)
+    try:
+        blest.blest_set_option(h, blest.BLEST_OPT_BARRIER_TIMEOUT_US, 20000)
+        blest.blest_set_option(h, blest.BLEST_OPT_TEST_PHANTOM_BLOCK, 1)
+        with pytest.raises(blest.BlestError) as e:
+            blest.blest_bfs(h, 0)
+        assert e.value.name == "BLEST_ERR_TIMEOUT"
+        with pytest.raises(blest.BlestError) as e:
+            blest.blest_msbfs(h, [0, 1])
+        assert e.value.name == "BLEST_ERR_TIMEOUT"
+        blest.blest_set_option(h, blest.BLEST_OPT_TEST_PHANTOM_BLOCK, 0)
+        blest.blest_set_option(h, blest.BLEST_OPT_BARRIER_TIMEOUT_US, 2000000)
+        assert np.array_equal(blest.blest_bfs(h, 0), oracle.bfs_levels(g.n, g.row_ptr, g.col_idx, 0))
+    finally:
+        blest.blest_destroy(h)
+
+
+# ---------------------------------------------------------- multi-source
+
+@pytest.mark.parametrize("k", [1, 7, 64, 65, 130, 256, 300])
+def test_msbfs_matches_k_oracle_runs(gpu, k):
+    g = synth.rmat_graph(12, 16, seed=5)
+    srcs = synth.pick_sources(g, k, seed=77)
+    srcs[-1] = srcs[0]                                   # a duplicate source
+    exp = oracle.msbfs_levels(g.n, g.row_ptr, g.col_idx, srcs, threads=8)
+    for order in (blest.BLEST_ORDER_NONE, blest.BLEST_ORDER_COMPRESS):
+        h = blest.blest_graph_create(g.n, g.row_ptr, g.col_idx, order)
+        try:
+            assert np.array_equal(blest.blest_msbfs(h, srcs), exp)
+        finally:
+            blest.blest_destroy(h)
+
+
+def test_msbfs_grid_and_isolated(gpu):
+    g, srcs = synth.grid_workload(96, 20, seed_graph=4, seed_src=9)
+    srcs = np.concatenate([srcs, [int(np.argmin(g.degrees()))]]).astype(np.int32)
+    exp = oracle.msbfs_levels(g.n, g.row_ptr, g.col_idx, srcs, threads=8)
+    h = blest.blest_graph_create(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_BANDWIDTH)
+    try:
+        assert np.array_equal(blest.blest_msbfs(h, srcs), exp)
+    finally:
+        blest.blest_destroy(h)
+
+
+def min_over_sources(g, srcs):
+    per = oracle.msbfs_levels(g.n, g.row_ptr, g.col_idx, srcs, threads=8).astype(np.int64)
+    per = np.where(per < 0, np.iinfo(np.int64).max, per).min(axis=0)
+    return np.where(per == np.iinfo(np.int64).max, -1, per).astype(np.int32)
+
+
+def test_multiroot_is_min_over_sources(gpu):
+    g = synth.rmat_graph(11, 8, seed=6)
+    srcs = synth.pick_sources(g, 40, seed=3)
+    h = blest.blest_graph_create(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_COMPRESS)
+    try:
+        for upd in (blest.BLEST_UPDATE_EAGER, blest.BLEST_UPDATE_LAZY):
+            blest.blest_set_option(h, blest.BLEST_OPT_UPDATE, upd)
+            assert np.array_equal(blest.blest_bfs_multiroot(h, srcs), min_over_sources(g, srcs))
+            assert np.array_equal(blest.blest_bfs_multiroot(h, srcs[:3]), min_over_sources(g, srcs[:3]))
+    finally:
+        blest.blest_destroy(h)
+
+
+def test_batch_of_uneven_graphs(gpu):
+    rng = np.random.default_rng(5)
+    graphs, srcs, orders = [], [], []
+    for i in range(12):
+        if i % 2 == 0:
+            g = synth.rmat_graph(int(rng.integers(6, 12)), 16, seed=100 + i)
+            orders.append(blest.BLEST_ORDER_COMPRESS)
+        else:
+            g, _ = synth.grid_graph(int(rng.integers(8, 60)), 0.9, seed=200 + i)
+            orders.append(blest.BLEST_ORDER_BANDWIDTH)
+        graphs.append(g)
+        srcs.append(int(synth.pick_sources(g, 1, seed=300 + i)[0]))
+    h = blest.blest_batch_create([(g.n, g.row_ptr, g.col_idx) for g in graphs], orders)
+    try:
+        for upd in (blest.BLEST_UPDATE_EAGER, blest.BLEST_UPDATE_LAZY):
+            blest.blest_set_option(h, blest.BLEST_OPT_UPDATE, upd)
+            got = blest.blest_batch_bfs(h, srcs)
+            off = 0
+            for g, s in zip(graphs, srcs):
+                assert np.array_equal(got[off:off + g.n], oracle.bfs_levels(g.n, g.row_ptr, g.col_idx, s))
+                off += g.n
+    finally:
+        blest.blest_destroy(h)
+
+
+def test_device_api_with_torch_stream(torch_cuda):
+    torch = torch_cuda
+    g = synth.rmat_graph(13, 16, seed=9)
+    srcs = synth.pick_sources(g, 5, seed=1)
+    exp = oracle.msbfs_levels(g.n, g.row_ptr, g.col_idx, srcs)
+    h = blest.blest_graph_create(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_COMPRESS)
+    try:
+        s = torch.cuda.Stream()
+        out = torch.empty((len(srcs), g.n), dtype=torch.int32, device="cuda")
+        for i, src in enumerate(srcs):
+            blest.blest_bfs_device(h, int(src), out[i], stream=s)
+        blest.blest_sync(h)
+        assert np.array_equal(out.cpu().numpy(), exp)
+        out2 = torch.empty((len(srcs), g.n), dtype=torch.int32, device="cuda")
+        blest.blest_msbfs_device(h, srcs, out2, stream=s)
+        blest.blest_sync(h)
+        assert np.array_equal(out2.cpu().numpy(), exp)
+    finally:
+        blest.blest_destroy(h)
