@@ -182,7 +182,8 @@ def run_ours(args):
         blest.blest_set_option(h, blest.BLEST_OPT_BLOCKS_PER_SM, args.blocks_per_sm)
     blest.blest_set_option(h, blest.BLEST_OPT_UNROLL, args.unroll)
     n = g.n
-    stream = torch.cuda.current_stream(dev)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)      # flushes, events and traversals all on this stream
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     deg_t = torch.from_numpy(g.degrees()).to(dev)
     w_s, new_id = byte_model(h, g, n)

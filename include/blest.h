@@ -78,9 +78,11 @@ typedef enum {
     BLEST_OPT_BLOCKS_PER_SM = 2,     /* persistent-grid blocks per SM; 0 = as many as fit */
     BLEST_OPT_BARRIER_TIMEOUT_US = 3,/* grid-barrier wait limit in microseconds (default 2,000,000) */
     BLEST_OPT_RECORD_LEVELS = 4,     /* 1 = record the per-level queue sizes (blest_get_run_info) */
-    BLEST_OPT_UNROLL = 5,            /* virtual slice sets a warp loads at once: 1, 2 or 4 (default 2) */
-    BLEST_OPT_TEST_PHANTOM_BLOCK = 6 /* testing: 1 = every barrier waits for one block that does not
+    BLEST_OPT_UNROLL = 5,            /* virtual slice sets a warp loads at once: 1 or 2 (default 2) */
+    BLEST_OPT_TEST_PHANTOM_BLOCK = 6,/* testing: 1 = every barrier waits for one block that does not
                                         exist, so the next traversal must end in BLEST_ERR_TIMEOUT */
+    BLEST_OPT_VISITED_FILTER = 7,    /* 1 (default) = test a visited bitmap before marking a row */
+    BLEST_OPT_MIN_BLOCKS = 8         /* kernel variant compiled for 2 (default) or 3 blocks per SM */
 } blest_option;
 
 /* Creation parameters; pass NULL to blest_graph_create_ex for the defaults. */
@@ -181,7 +183,8 @@ blest_status blest_bfs_multiroot(blest_handle h, const int32_t* srcs, int32_t k,
 blest_status blest_batch_bfs(blest_handle h, const int32_t* srcs_local, int32_t* levels);
 
 /* Device-memory forms.  They enqueue the traversal on `stream` (a cudaStream_t;
- * NULL = the handle's own stream) and return without waiting; sources are host
+ * NULL = the handle's own stream; pass cudaStreamLegacy for the legacy default
+ * stream) and return without waiting; sources are host
  * arrays read before the call returns.  d_levels is device memory of n (or k*n)
  * int32.  The status of the traversal (TIMEOUT, INTERNAL) is reported by the
  * next blest_sync on the handle; a launch failure is reported at once. */
@@ -199,6 +202,28 @@ blest_status blest_sync(blest_handle h);
  * BLEST_OPT_RECORD_LEVELS = 1): queue_sizes[l-1] = virtual slice sets processed
  * at level l, up to cap entries.  Waits for the handle's work first. */
 blest_status blest_get_run_info(blest_handle h, blest_run_info* info, int32_t* queue_sizes, int32_t cap);
+
+/* ---------------------------------------------------------------- autotune */
+
+/* Result of blest_autotune: the options it kept and what they measured. */
+typedef struct {
+    int32_t update;              /* blest_update kept (EAGER or LAZY) */
+    int32_t pull;                /* blest_pull kept */
+    int32_t unroll;
+    int32_t min_blocks;
+    int32_t visited_filter;
+    int32_t blocks_per_sm;       /* 0 = as many as fit */
+    int32_t candidates;          /* variants timed */
+    double  best_ms;             /* mean device time per traversal of the kept variant */
+    double  rule_ms;             /* same for the Section 5 rule (lazy iff U_div > 25,000), CUDA-core pull */
+} blest_tune_result;
+
+/* Time every single-source traversal variant (update scheme, pull back-end,
+ * unroll, occupancy variant, visited filter, blocks per SM) on the k host
+ * sources srcs[0..k) with CUDA events, each variant after one untimed pass,
+ * and keep the fastest as the handle's options.  out may be NULL.
+ * Errors: INVALID_ARG (k < 1, bad source), TIMEOUT, INTERNAL, CUDA. */
+blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, blest_tune_result* out);
 
 /* ----------------------------------------------------------------- export */
 

@@ -24,7 +24,7 @@ __all__ = [
     "blest_graph_create", "blest_graph_create_ex", "blest_batch_create", "blest_destroy", "blest_set_option",
     "blest_get_stats", "blest_bfs", "blest_msbfs", "blest_bfs_multiroot", "blest_batch_bfs", "blest_bfs_device",
     "blest_msbfs_device", "blest_bfs_multiroot_device", "blest_sync", "blest_get_run_info", "blest_export",
-    "blest_export_size", "blest_compute_order", "blest_is_social", "blest_debug_pull", "lib", "EXPORTED_SYMBOLS",
+    "blest_autotune", "blest_export_size", "blest_compute_order", "blest_is_social", "blest_debug_pull", "lib", "EXPORTED_SYMBOLS",
 ]
 
 BLEST_OK = 0
@@ -35,15 +35,16 @@ BLEST_UPDATE_AUTO, BLEST_UPDATE_EAGER, BLEST_UPDATE_LAZY = 0, 1, 2
 BLEST_PULL_POPC, BLEST_PULL_MMA = 0, 1
 BLEST_OPT_UPDATE, BLEST_OPT_PULL, BLEST_OPT_BLOCKS_PER_SM, BLEST_OPT_BARRIER_TIMEOUT_US = 0, 1, 2, 3
 BLEST_OPT_RECORD_LEVELS, BLEST_OPT_UNROLL, BLEST_OPT_TEST_PHANTOM_BLOCK = 4, 5, 6
+BLEST_OPT_VISITED_FILTER, BLEST_OPT_MIN_BLOCKS = 7, 8
 BLEST_ARRAY_REAL_PTRS, BLEST_ARRAY_VIRTUAL_TO_REAL, BLEST_ARRAY_ROW_IDS = 0, 1, 2
 BLEST_ARRAY_MASKS, BLEST_ARRAY_NEW_ID, BLEST_ARRAY_VSS_COUNT = 3, 4, 5
 
 EXPORTED_SYMBOLS = [
     "blest_graph_create", "blest_graph_create_ex", "blest_batch_create", "blest_destroy", "blest_set_option",
     "blest_get_stats", "blest_bfs", "blest_msbfs", "blest_bfs_multiroot", "blest_batch_bfs", "blest_bfs_device",
-    "blest_msbfs_device", "blest_bfs_multiroot_device", "blest_sync", "blest_get_run_info", "blest_export_size",
-    "blest_export", "blest_compute_order", "blest_is_social", "blest_debug_pull", "blest_status_string",
-    "blest_last_error",
+    "blest_msbfs_device", "blest_bfs_multiroot_device", "blest_sync", "blest_get_run_info", "blest_autotune",
+    "blest_export_size", "blest_export", "blest_compute_order", "blest_is_social", "blest_debug_pull",
+    "blest_status_string", "blest_last_error",
 ]
 
 
@@ -68,6 +69,12 @@ class Stats(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("update", ctypes.c_int32), ("pull", ctypes.c_int32), ("unroll", ctypes.c_int32),
+                ("min_blocks", ctypes.c_int32), ("visited_filter", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_double), ("rule_ms", ctypes.c_double)]
 
 
 class RunInfo(ctypes.Structure):
@@ -107,6 +114,7 @@ def lib():
             "blest_bfs_multiroot_device": (ctypes.c_int, [_vp, _i32p, ctypes.c_int32, _vp, _vp]),
             "blest_sync": (ctypes.c_int, [_vp]),
             "blest_get_run_info": (ctypes.c_int, [_vp, ctypes.POINTER(RunInfo), _i32p, ctypes.c_int32]),
+            "blest_autotune": (ctypes.c_int, [_vp, _i32p, ctypes.c_int32, ctypes.POINTER(TuneResult)]),
             "blest_export_size": (ctypes.c_int64, [_vp, ctypes.c_int32]),
             "blest_export": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.c_int64]),
             "blest_compute_order": (ctypes.c_int, [ctypes.c_int32, _i32p, _i32p, ctypes.c_int,
@@ -157,12 +165,19 @@ def _dev_ptr(x) -> int:
     raise TypeError("expected a CUDA tensor or a device pointer")
 
 
+CUDA_STREAM_LEGACY = 1   # cudaStreamLegacy
+
+
 def _stream_ptr(stream) -> int | None:
+    """cudaStream_t of a torch stream.  torch's default stream is the legacy
+    NULL stream; NULL means "the handle's own stream" to the C ABI, so it is
+    passed as cudaStreamLegacy instead."""
     if stream is None:
         return None
     if isinstance(stream, int):
         return stream
-    return int(stream.cuda_stream)
+    p = int(stream.cuda_stream)
+    return p if p != 0 else CUDA_STREAM_LEGACY
 
 
 # ------------------------------------------------------------------- graphs
@@ -281,6 +296,13 @@ def blest_get_run_info(h: int, cap: int = 0) -> tuple[dict, np.ndarray]:
     _check(lib().blest_get_run_info(h, ctypes.byref(info), _ptr(buf), int(cap)), "blest_get_run_info")
     d = {f: getattr(info, f) for f, _ in info._fields_}
     return d, buf[:max(0, min(cap, d["recorded"]))].copy()
+
+
+def blest_autotune(h: int, srcs) -> dict:
+    s = _i32(srcs)
+    r = TuneResult()
+    _check(lib().blest_autotune(h, _ptr(s), len(s), ctypes.byref(r)), "blest_autotune")
+    return {f: getattr(r, f) for f, _ in r._fields_}
 
 
 # ------------------------------------------------------------------ export

@@ -16,6 +16,15 @@
 #include "host_graph.h"
 #include "msbfs_launch.h"
 
+namespace blest {
+constexpr int kCtrlBytes = 256;        // layout in device_common.cuh
+constexpr int kCtrlClearBytes = 192;
+constexpr int kStickyWord = 48;
+}  // namespace blest
+using blest::kCtrlBytes;
+using blest::kCtrlClearBytes;
+using blest::kStickyWord;
+
 using blest::Csr;
 
 namespace {
@@ -52,7 +61,7 @@ struct blest_graph {
     uint32_t* d_F = nullptr;             // 3 * nwords
     unsigned long long* d_Q = nullptr;   // 3 * qcap
     unsigned int qcap = 0;
-    unsigned int* d_ctrl = nullptr;      // 64-byte control block + sticky error word at [16]
+    unsigned int* d_ctrl = nullptr;      // 256-byte control block (device_common.cuh layout)
     int32_t* d_level_sizes = nullptr;
     int32_t* d_roots = nullptr;
     int64_t roots_cap = 0;
@@ -66,6 +75,8 @@ struct blest_graph {
     int64_t timeout_us = 2000000;
     int record = 0;
     int unroll = 2;
+    int minb = 2;
+    int filter = 1;
     int phantom = 0;
     // results
     blest_stats stats{};
@@ -141,10 +152,10 @@ blest_status finish_create(blest_graph* h, const Csr& g, const std::vector<int32
     BLEST_ALLOC(h->d_vnext, sizeof(uint32_t) * std::max<size_t>(nw, 1), "cudaMalloc(vnext)");
     BLEST_ALLOC(h->d_F, sizeof(uint32_t) * 3 * std::max<size_t>(nw, 1), "cudaMalloc(frontier)");
     BLEST_ALLOC(h->d_Q, sizeof(unsigned long long) * 3 * (size_t)h->qcap, "cudaMalloc(queues)");
-    BLEST_ALLOC(h->d_ctrl, 128, "cudaMalloc(ctrl)");
+    BLEST_ALLOC(h->d_ctrl, kCtrlBytes, "cudaMalloc(ctrl)");
     BLEST_ALLOC(h->d_level_sizes, sizeof(int32_t) * kLevelRecordCap, "cudaMalloc(level record)");
 #undef BLEST_ALLOC
-    cudaMemsetAsync(h->d_ctrl, 0, 128, h->stream);
+    cudaMemsetAsync(h->d_ctrl, 0, kCtrlBytes, h->stream);
     if (!new_id.empty()) {
         h->h_new_id = new_id;
         if ((e = cudaMalloc(&h->d_new_id, sizeof(int32_t) * (size_t)g.n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(new_id)");
@@ -200,8 +211,8 @@ blest_status prepare_graph(int32_t n, const int32_t* row_ptr, const int32_t* col
     return BLEST_OK;
 }
 
-int pick_grid(blest_graph* h, int update, int pull, int unroll) {
-    int maxb = blest::bfs_max_blocks_per_sm(update, pull, unroll);
+int pick_grid(blest_graph* h, int update, int pull, int unroll, int minb) {
+    int maxb = blest::bfs_max_blocks_per_sm(update, pull, unroll, minb);
     if (maxb <= 0) return 0;
     int b = h->blocks_per_sm > 0 ? std::min(h->blocks_per_sm, maxb) : maxb;
     return b * h->sms;
@@ -216,7 +227,9 @@ blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots
     L.update = h->resolved_update() == BLEST_UPDATE_EAGER ? 1 : 2;
     L.pull = h->pull;
     L.unroll = h->unroll;
-    L.grid = pick_grid(h, L.update, L.pull, L.unroll);
+    L.minb = h->minb;
+    L.filter = h->filter;
+    L.grid = pick_grid(h, L.update, L.pull, L.unroll, L.minb);
     if (L.grid <= 0) return fail(BLEST_ERR_CUDA, "no co-resident grid for the traversal kernel");
     L.n = h->n;
     L.qcap = h->qcap;
@@ -253,7 +266,7 @@ blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots
     L.out = d_out;
     L.timeout_ns = (uint64_t)h->timeout_us * 1000ull;
     L.phantom = h->phantom ? 1u : 0u;
-    cudaMemsetAsync(h->d_ctrl, 0, 64, st);
+    cudaMemsetAsync(h->d_ctrl, 0, kCtrlClearBytes, st);
     cudaMemsetAsync(L.levels_internal, 0xFF, sizeof(int32_t) * (size_t)h->n, st);
     cudaMemsetAsync(h->d_vcur, 0, sizeof(uint32_t) * nw, st);
     cudaMemsetAsync(h->d_vnext, 0, sizeof(uint32_t) * nw, st);
@@ -285,10 +298,10 @@ blest_status sync_status(blest_graph* h) {
         if ((e = cudaStreamSynchronize(h->last_stream)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
     if (!h->d_ctrl) return BLEST_OK;
     unsigned int sticky = 0;
-    if ((e = cudaMemcpy(&sticky, h->d_ctrl + 16, sizeof(unsigned int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    if ((e = cudaMemcpy(&sticky, h->d_ctrl + kStickyWord, sizeof(unsigned int), cudaMemcpyDeviceToHost)) != cudaSuccess)
         return cuda_fail(e, "read status");
     if (sticky) {
-        cudaMemset(h->d_ctrl + 16, 0, sizeof(unsigned int));
+        cudaMemset(h->d_ctrl + kStickyWord, 0, sizeof(unsigned int));
         if (sticky == BLEST_ERR_TIMEOUT) return fail(BLEST_ERR_TIMEOUT, "a grid barrier timed out");
         if (sticky == BLEST_ERR_INTERNAL) return fail(BLEST_ERR_INTERNAL, "device-side consistency check failed");
         return fail((blest_status)sticky, "device error");
@@ -439,8 +452,16 @@ blest_status blest_set_option(blest_handle h, int32_t key, int64_t value) {
             h->record = (int)value;
             return BLEST_OK;
         case BLEST_OPT_UNROLL:
-            if (value != 1 && value != 2 && value != 4) break;
+            if (value != 1 && value != 2) break;
             h->unroll = (int)value;
+            return BLEST_OK;
+        case BLEST_OPT_VISITED_FILTER:
+            if (value != 0 && value != 1) break;
+            h->filter = (int)value;
+            return BLEST_OK;
+        case BLEST_OPT_MIN_BLOCKS:
+            if (value != 2 && value != 3) break;
+            h->minb = (int)value;
             return BLEST_OK;
         case BLEST_OPT_TEST_PHANTOM_BLOCK:
             if (value != 0 && value != 1) break;
@@ -581,7 +602,7 @@ blest_status blest_get_run_info(blest_handle h, blest_run_info* info, int32_t* q
     blest_status s = sync_status(h);
     if (s) return s;
     unsigned int ctrl[16];
-    cudaError_t e = cudaMemcpy(ctrl, h->d_ctrl, 64, cudaMemcpyDeviceToHost);
+    cudaError_t e = cudaMemcpy(ctrl, h->d_ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "read run info");
     h->info.levels = (int32_t)ctrl[6];
     h->info.recorded = h->record ? std::min<int32_t>(h->info.levels, kLevelRecordCap) : 0;
@@ -590,6 +611,67 @@ blest_status blest_get_run_info(blest_handle h, blest_run_info* info, int32_t* q
         int32_t m = std::min(cap, h->info.recorded);
         e = cudaMemcpy(queue_sizes, h->d_level_sizes, sizeof(int32_t) * (size_t)m, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "read level record");
+    }
+    return BLEST_OK;
+}
+
+blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, blest_tune_result* out) {
+    if (!h) return fail(BLEST_ERR_INVALID_ARG, "NULL handle");
+    if (k < 1 || !srcs) return fail(BLEST_ERR_INVALID_ARG, "autotune needs at least one source");
+    if (h->n == 0) return fail(BLEST_ERR_INVALID_ARG, "empty graph");
+    std::vector<int32_t> roots;
+    blest_status s = map_sources(h, srcs, k, roots);
+    if (s) return s;
+    struct Cand { int update, pull, unroll, minb, filter, bps; };
+    std::vector<Cand> cands;
+    for (int u : {BLEST_UPDATE_EAGER, BLEST_UPDATE_LAZY})
+        for (int p : {BLEST_PULL_POPC, BLEST_PULL_MMA})
+            for (int r : {1, 2})
+                for (int m : {2, 3})
+                    for (int f : {0, 1})
+                        for (int b : {0, 1}) cands.push_back({u, p, r, m, f, b});
+    struct Opts { int update_opt, pull, unroll, minb, filter, blocks_per_sm; };
+    const Opts saved{h->update_opt, h->pull, h->unroll, h->minb, h->filter, h->blocks_per_sm};
+    cudaEvent_t e0, e1;
+    cudaError_t e;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(e, "cudaEventCreate"); }
+    double best = 1e300, rule = -1.0;
+    Cand bestc = cands[0];
+    const int rule_update = h->stats.update;
+    for (const Cand& c : cands) {
+        h->update_opt = c.update; h->pull = c.pull; h->unroll = c.unroll; h->minb = c.minb;
+        h->filter = c.filter; h->blocks_per_sm = c.bps;
+        std::vector<int32_t> one(1);
+        for (int pass = 0; pass < 2 && !s; ++pass) {
+            if (pass == 1) cudaEventRecord(e0, h->stream);
+            for (int32_t i = 0; i < k && !s; ++i) {
+                one[0] = roots[i];
+                s = enqueue_traversal(h, one, h->d_out, h->stream);
+            }
+        }
+        if (s) break;
+        cudaEventRecord(e1, h->stream);
+        if ((s = sync_status(h)) != BLEST_OK) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = (double)ms / k;
+        if (per < best) { best = per; bestc = c; }
+        if (c.update == rule_update && c.pull == BLEST_PULL_POPC && c.unroll == saved.unroll && c.minb == saved.minb &&
+            c.filter == 0 && c.bps == 0)
+            rule = per;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->update_opt = saved.update_opt; h->pull = saved.pull; h->unroll = saved.unroll; h->minb = saved.minb;
+    h->filter = saved.filter; h->blocks_per_sm = saved.blocks_per_sm;
+    if (s) return s;
+    h->update_opt = bestc.update; h->pull = bestc.pull; h->unroll = bestc.unroll; h->minb = bestc.minb;
+    h->filter = bestc.filter; h->blocks_per_sm = bestc.bps;
+    if (out) {
+        out->update = bestc.update; out->pull = bestc.pull; out->unroll = bestc.unroll; out->min_blocks = bestc.minb;
+        out->visited_filter = bestc.filter; out->blocks_per_sm = bestc.bps; out->candidates = (int32_t)cands.size();
+        out->best_ms = best; out->rule_ms = rule;
     }
     return BLEST_OK;
 }

@@ -57,6 +57,7 @@ struct BfsArgs {
     int32_t* out;                         // output in original ids (unused when new_id is NULL)
     uint64_t timeout_ns;
     unsigned int phantom;
+    int filter;                           // 1 = skip rows already set in the V bitmap
 };
 
 // ------------------------------------------------------------------- pull
@@ -154,11 +155,11 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
     }
     if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns)) return;
     sweep<UPDATE>(a, 0, a.Q[1], &ctrl->qcount[1], a.F[1]);
-    if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns)) return;
+    unsigned int qn = 0, qprev = 0;
+    if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns, &ctrl->qcount[1], &qn)) return;
 
     int lvl = 1;
     for (;; ++lvl) {
-        unsigned int qn = ld_cg(&ctrl->qcount[lvl & 3]);
         if (qn > a.qcap) qn = a.qcap;   // only after an overflow, which already raised an error
         if (gtid == 0) {
             ctrl->qcount[(lvl + 2) & 3] = 0;
@@ -167,8 +168,6 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
         const unsigned long long* Qin = a.Q[lvl % 3];
         if (UPDATE == 1) {
             // clear the frontier bytes of level lvl-1 (read last level, rewritten at lvl+1)
-            unsigned int qprev = ld_cg(&ctrl->qcount[(lvl + 3) & 3]);
-            if (qprev > a.qcap) qprev = a.qcap;
             const unsigned long long* Qp = a.Q[(lvl + 2) % 3];
             unsigned char* Fold = reinterpret_cast<unsigned char*>(a.F[(lvl + 2) % 3]);
             for (unsigned int i = (unsigned int)gtid; i < qprev; i += (unsigned int)nthreads)
@@ -205,8 +204,15 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
                     const unsigned int h = pull_hits<PULL>(msk[i], alpha, lane);
                     const int r4[4] = {rows[i].x, rows[i].y, rows[i].z, rows[i].w};
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (h & (1u << q)) atomicOr(&a.vnext[r4[q] >> 5], 1u << (r4[q] & 31));
+                    for (int q = 0; q < 4; ++q) {
+                        if (!(h & (1u << q))) continue;
+                        const int u = r4[q];
+                        const uint32_t bit = 1u << (u & 31);
+                        // visited filter: V_curr only gains bits during a traversal, so a
+                        // stale (older) word can only let through a redundant mark
+                        if (a.filter && (a.vcur[u >> 5] & bit)) continue;
+                        atomicOr(&a.vnext[u >> 5], bit);
+                    }
                 }
             } else {
                 int st[4 * UNROLL], ln[4 * UNROLL];
@@ -225,17 +231,20 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
                     for (int q = 0; q < 4; ++q) {
                         const int k = 4 * i + q;
                         st[k] = 0; ln[k] = 0; pay[k] = 0;
-                        if (h & (1u << q)) {
-                            const int u = r4[q];
-                            if (ld_cg(&a.L[u]) < 0) {
-                                a.L[u] = lvl;
-                                const uint32_t old = atomicOr(&Fnext[u >> 5], 1u << (u & 31));
-                                if (((old >> (u & 24)) & 0xFFu) == 0) {
-                                    const int s2 = u >> 3;
-                                    st[k] = __ldg(&a.real_ptrs[s2]);
-                                    ln[k] = __ldg(&a.real_ptrs[s2 + 1]) - st[k];
-                                    pay[k] = (uint32_t)s2;
-                                }
+                        if (!(h & (1u << q))) continue;
+                        const int u = r4[q];
+                        const uint32_t bit = 1u << (u & 31);
+                        // visited filter on the V bitmap (a subset of the visited set, see lazy)
+                        if (a.filter && (a.vcur[u >> 5] & bit)) continue;
+                        if (ld_cg(&a.L[u]) < 0) {
+                            a.L[u] = lvl;
+                            if (a.filter) atomicOr(&a.vcur[u >> 5], bit);
+                            const uint32_t old = atomicOr(&Fnext[u >> 5], bit);
+                            if (((old >> (u & 24)) & 0xFFu) == 0) {
+                                const int s2 = u >> 3;
+                                st[k] = __ldg(&a.real_ptrs[s2]);
+                                ln[k] = __ldg(&a.real_ptrs[s2 + 1]) - st[k];
+                                pay[k] = (uint32_t)s2;
                             }
                         }
                     }
@@ -243,12 +252,15 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
                 warp_enqueue<4 * UNROLL>(a.qcap, ctrl, Qout, qcount_next, st, ln, pay, lane);
             }
         }
-        if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns)) return;
         if (UPDATE == 2) {
-            sweep<UPDATE>(a, lvl, Qout, qcount_next, nullptr);
             if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns)) return;
+            sweep<UPDATE>(a, lvl, Qout, qcount_next, nullptr);
         }
-        if (ld_cg(qcount_next) == 0) break;
+        unsigned int qnext = 0;
+        if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns, qcount_next, &qnext)) return;
+        if (qnext == 0) break;
+        qprev = qn;
+        qn = qnext;
     }
     if (gtid == 0) ctrl->levels = (unsigned int)lvl;
     // undo the reordering: out[v] = L[new_id[v]]
@@ -257,8 +269,8 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
     }
 }
 
-template <int UPDATE, int PULL, int UNROLL>
-__global__ void __launch_bounds__(kBfsBlock) bfs_kernel(BfsArgs a) {
+template <int UPDATE, int PULL, int UNROLL, int MINB>
+__global__ void __launch_bounds__(kBfsBlock, MINB) bfs_kernel(BfsArgs a) {
     bfs_body<UPDATE, PULL, UNROLL>(a);
     fold_status(a.ctrl);
 }
@@ -278,24 +290,24 @@ __global__ void debug_pull_kernel(const uint32_t* __restrict__ masks, const uint
 
 // ---------------------------------------------------------------- launching
 
-template <int UPDATE, int PULL, int UNROLL>
+template <int UPDATE, int PULL, int UNROLL, int MINB>
 static void* kernel_ptr() {
-    return reinterpret_cast<void*>(&bfs_kernel<UPDATE, PULL, UNROLL>);
+    return reinterpret_cast<void*>(&bfs_kernel<UPDATE, PULL, UNROLL, MINB>);
 }
 
-static void* pick_kernel(int update, int pull, int unroll) {
-#define BLEST_PICK(U, P, R) \
-    if (update == U && pull == P && unroll == R) return kernel_ptr<U, P, R>();
-    BLEST_PICK(1, 0, 1) BLEST_PICK(1, 0, 2) BLEST_PICK(1, 0, 4)
-    BLEST_PICK(1, 1, 1) BLEST_PICK(1, 1, 2) BLEST_PICK(1, 1, 4)
-    BLEST_PICK(2, 0, 1) BLEST_PICK(2, 0, 2) BLEST_PICK(2, 0, 4)
-    BLEST_PICK(2, 1, 1) BLEST_PICK(2, 1, 2) BLEST_PICK(2, 1, 4)
+static void* pick_kernel(int update, int pull, int unroll, int minb) {
+#define BLEST_PICK(U, P, R, M) \
+    if (update == U && pull == P && unroll == R && minb == M) return kernel_ptr<U, P, R, M>();
+#define BLEST_PICK_M(U, P, R) BLEST_PICK(U, P, R, 2) BLEST_PICK(U, P, R, 3)
+    BLEST_PICK_M(1, 0, 1) BLEST_PICK_M(1, 0, 2) BLEST_PICK_M(1, 1, 1) BLEST_PICK_M(1, 1, 2)
+    BLEST_PICK_M(2, 0, 1) BLEST_PICK_M(2, 0, 2) BLEST_PICK_M(2, 1, 1) BLEST_PICK_M(2, 1, 2)
+#undef BLEST_PICK_M
 #undef BLEST_PICK
     return nullptr;
 }
 
-int bfs_max_blocks_per_sm(int update, int pull, int unroll) {
-    void* k = pick_kernel(update, pull, unroll);
+int bfs_max_blocks_per_sm(int update, int pull, int unroll, int minb) {
+    void* k = pick_kernel(update, pull, unroll, minb);
     if (!k) return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBfsBlock, 0) != cudaSuccess) return 0;
@@ -313,7 +325,7 @@ cudaError_t launch_debug_pull(const uint32_t* d_masks, const uint8_t* d_alpha, i
 }
 
 cudaError_t launch_bfs_kernel(const BfsLaunch& L, cudaStream_t stream) {
-    void* k = pick_kernel(L.update, L.pull, L.unroll);
+    void* k = pick_kernel(L.update, L.pull, L.unroll, L.minb);
     if (!k) return cudaErrorInvalidValue;
     BfsArgs a;
     a.n = L.n;
@@ -336,6 +348,7 @@ cudaError_t launch_bfs_kernel(const BfsLaunch& L, cudaStream_t stream) {
     a.out = L.out;
     a.timeout_ns = L.timeout_ns;
     a.phantom = L.phantom;
+    a.filter = L.filter;
     void* args[] = {&a};
     return cudaLaunchCooperativeKernel(k, dim3((unsigned)L.grid), dim3(kBfsBlock), args, 0, stream);
 }

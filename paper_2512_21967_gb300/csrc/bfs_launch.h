@@ -12,7 +12,9 @@ constexpr int kInlineRoots = 16;
 struct BfsLaunch {
     int update = 2;            // 1 eager, 2 lazy
     int pull = 0;              // 0 CUDA cores, 1 b1 MMA
-    int unroll = 2;            // 1, 2, 4
+    int unroll = 2;            // 1, 2
+    int minb = 2;              // __launch_bounds__ minimum blocks per SM: 2 or 3
+    int filter = 1;            // skip marks of rows already in the V bitmap
     int grid = 0;              // blocks (co-resident)
     int32_t n = 0;
     unsigned int qcap = 0;     // entries per queue buffer
@@ -36,7 +38,7 @@ struct BfsLaunch {
     unsigned int phantom = 0;
 };
 
-int bfs_max_blocks_per_sm(int update, int pull, int unroll);
+int bfs_max_blocks_per_sm(int update, int pull, int unroll, int minb);
 int bfs_threads_per_block();
 cudaError_t launch_bfs_kernel(const BfsLaunch& L, cudaStream_t stream);
 

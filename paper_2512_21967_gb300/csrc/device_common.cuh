@@ -39,41 +39,77 @@ __device__ __forceinline__ unsigned int ld_volatile_u32(const unsigned int* p) {
 template <class T>
 __device__ __forceinline__ T ld_cg(const T* p) { return __ldcg(p); }
 
+// Control words live in one 256-byte device block: the Ctrl struct at byte 0,
+// the barrier release flag alone on the cache line at byte 128, and the sticky
+// status word at byte 192.  Bytes [0, 192) are cleared before every traversal.
+constexpr int kCtrlBytes = 256;
+constexpr int kCtrlClearBytes = 192;
+constexpr int kFlagWord = 32;     // unsigned-int index of the 64-bit release flag
+constexpr int kStickyWord = 48;   // unsigned-int index of the sticky status
+
+__device__ __forceinline__ unsigned long long ld_acquire_gpu_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_gpu_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 // Grid barrier for a cooperative launch (all blocks co-resident).  Thread 0 of
-// each block arrives with a release (fence + atomic add) and spins with acquire
-// loads until every block of this generation has arrived.  The wait is bounded:
-// after timeout_ns it records BLEST_ERR_TIMEOUT (6) in ctrl->error and returns
-// false, as it does when another block already recorded an error.  `extra`
-// adds phantom participants (test hook: a barrier that can never complete).
-// `gen` is this block's barrier count, kept in a register by the caller.
+// each block arrives with a release (fence + atomic add on the arrival
+// counter).  The block that arrives last reads *pub (after an acquire fence, so
+// it sees every block's writes) and releases the others by storing
+// (generation << 32 | *pub) into a flag on its own cache line; the waiting
+// blocks spin on that flag with acquire loads.  Every block returns the
+// published word through *published (the next queue size, so the level loop
+// needs no separate read of it).
+// The wait is bounded: after timeout_ns it records BLEST_ERR_TIMEOUT (6) in
+// ctrl->error and returns false, as it does when another block has already
+// recorded an error.  `extra` adds phantom participants (test hook: a barrier
+// that can never complete).  `gen` is this block's barrier count.
 __device__ __forceinline__ bool grid_barrier(Ctrl* ctrl, unsigned int nblocks, unsigned int extra,
-                                             unsigned int& gen, uint64_t timeout_ns) {
+                                             unsigned int& gen, uint64_t timeout_ns,
+                                             const unsigned int* pub = nullptr,
+                                             unsigned int* published = nullptr) {
     __shared__ int s_ok;
+    __shared__ unsigned int s_pub;
     __syncthreads();
     if (threadIdx.x == 0) {
         gen += 1;
+        unsigned long long* flag = reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned int*>(ctrl) + kFlagWord);
         const unsigned int target = gen * (nblocks + extra);
         __threadfence();
-        atomicAdd(&ctrl->barrier, 1u);
+        const unsigned int old = atomicAdd(&ctrl->barrier, 1u);
         int ok = 1;
-        const uint64_t t0 = global_timer_ns();
-        unsigned int spins = 0;
-        for (;;) {
-            unsigned int v = ld_acquire_gpu(&ctrl->barrier);
-            if ((int)(v - target) >= 0) break;
-            if (ld_volatile_u32(&ctrl->error) != 0) { ok = 0; break; }
-            if ((++spins & 31u) == 0 && global_timer_ns() - t0 > timeout_ns) {
-                atomicCAS(&ctrl->error, 0u, 6u);
-                ok = 0;
-                break;
+        unsigned int value = 0;
+        if (old + 1u == target) {
+            __threadfence();
+            value = pub ? atomicOr(const_cast<unsigned int*>(pub), 0u) : 0u;   // coherent read at L2
+            st_release_gpu_u64(flag, ((unsigned long long)gen << 32) | value);
+        } else {
+            const uint64_t t0 = global_timer_ns();
+            unsigned int spins = 0;
+            for (;;) {
+                const unsigned long long f = ld_acquire_gpu_u64(flag);
+                if ((unsigned int)(f >> 32) >= gen) { value = (unsigned int)f; break; }
+                if (ld_volatile_u32(&ctrl->error) != 0) { ok = 0; break; }
+                if ((++spins & 31u) == 0 && global_timer_ns() - t0 > timeout_ns) {
+                    atomicCAS(&ctrl->error, 0u, 6u);
+                    ok = 0;
+                    break;
+                }
+                if (spins > 64) __nanosleep(32);
             }
-            __nanosleep(20);
         }
         __threadfence();
         if (ld_volatile_u32(&ctrl->error) != 0) ok = 0;
         s_ok = ok;
+        s_pub = value;
     }
     __syncthreads();
+    if (published) *published = s_pub;
     return s_ok != 0;
 }
 
@@ -90,12 +126,12 @@ __device__ __forceinline__ unsigned int warp_inclusive_scan(unsigned int v, int 
     return v;
 }
 
-// Every block folds the traversal's status into the sticky word (ctrl + 64 B),
+// Every block folds the traversal's status into the sticky word (byte 192),
 // which the host reads at synchronisation; the first failure wins.
 __device__ __forceinline__ void fold_status(Ctrl* ctrl) {
     if (threadIdx.x == 0) {
         const unsigned int e = ld_volatile_u32(&ctrl->error);
-        if (e) atomicCAS(reinterpret_cast<unsigned int*>(ctrl) + 16, 0u, e);
+        if (e) atomicCAS(reinterpret_cast<unsigned int*>(ctrl) + kStickyWord, 0u, e);
     }
 }
 

@@ -107,11 +107,11 @@ __device__ __forceinline__ void ms_body(const MsArgs& a) {
     }
     if (!grid_barrier(ctrl, gridDim.x, a.phantom, gen, a.timeout_ns)) return;
     ms_sweep<W>(a, 0, a.Q[1], &ctrl->qcount[1]);
-    if (!grid_barrier(ctrl, gridDim.x, a.phantom, gen, a.timeout_ns)) return;
+    unsigned int qn = 0;
+    if (!grid_barrier(ctrl, gridDim.x, a.phantom, gen, a.timeout_ns, &ctrl->qcount[1], &qn)) return;
 
     int lvl = 1;
     for (;; ++lvl) {
-        unsigned int qn = ld_cg(&ctrl->qcount[lvl & 3]);
         if (qn > a.qcap) qn = a.qcap;   // only after an overflow, which already raised an error
         if (gtid == 0) {
             ctrl->qcount[(lvl + 2) & 3] = 0;
@@ -158,13 +158,20 @@ __device__ __forceinline__ void ms_body(const MsArgs& a) {
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
-                for (int w = 0; w < W; ++w)
-                    if (y[q][w]) atomicOr(&a.vnext[(size_t)r4[q] * W + w], y[q][w]);
+                for (int w = 0; w < W; ++w) {
+                    if (!y[q][w]) continue;
+                    // sources that already reached the row need no mark; V_curr only gains
+                    // bits during a traversal, so a stale word can only let a mark through
+                    const unsigned long long fresh = y[q][w] & ~a.vcur[(size_t)r4[q] * W + w];
+                    if (fresh) atomicOr(&a.vnext[(size_t)r4[q] * W + w], fresh);
+                }
         }
         if (!grid_barrier(ctrl, gridDim.x, a.phantom, gen, a.timeout_ns)) return;
         ms_sweep<W>(a, lvl, Qout, qcount_next);
-        if (!grid_barrier(ctrl, gridDim.x, a.phantom, gen, a.timeout_ns)) return;
-        if (ld_cg(qcount_next) == 0) break;
+        unsigned int qnext = 0;
+        if (!grid_barrier(ctrl, gridDim.x, a.phantom, gen, a.timeout_ns, qcount_next, &qnext)) return;
+        if (qnext == 0) break;
+        qn = qnext;
     }
     if (gtid == 0) ctrl->levels = (unsigned int)lvl;
     // out[i*n + v] = level of v from source i (original ids), -1 if unreached
@@ -225,7 +232,7 @@ int run_msbfs(MsbfsState& s, const MsbfsLaunchCommon& c, const std::vector<int32
         if (c.new_id && (e = grow(s.lint, s.lint_cap, (int64_t)k * c.n)) != cudaSuccess) break;
         if ((e = grow(s.roots, s.roots_cap, k)) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(s.roots, roots.data() + i0, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
-        cudaMemsetAsync(c.ctrl, 0, 64, st);
+        cudaMemsetAsync(c.ctrl, 0, kCtrlClearBytes, st);
         cudaMemsetAsync(s.vcur, 0, sizeof(unsigned long long) * (size_t)words, st);
         cudaMemsetAsync(s.vnext, 0, sizeof(unsigned long long) * (size_t)words, st);
         MsArgs a;

@@ -104,11 +104,13 @@ def test_rmat16_all_sources_all_modes(cfg1, order):
         for upd, pull in MODES:
             blest.blest_set_option(h, blest.BLEST_OPT_UPDATE, upd)
             blest.blest_set_option(h, blest.BLEST_OPT_PULL, pull)
-            for unroll in (1, 4) if (upd, pull) == MODES[0] else (2,):
+            for unroll, minb, filt in ((2, 2, 1), (1, 3, 0), (2, 3, 1), (1, 2, 0)):
                 blest.blest_set_option(h, blest.BLEST_OPT_UNROLL, unroll)
+                blest.blest_set_option(h, blest.BLEST_OPT_MIN_BLOCKS, minb)
+                blest.blest_set_option(h, blest.BLEST_OPT_VISITED_FILTER, filt)
                 for i, s in enumerate(srcs):
                     got = blest.blest_bfs(h, int(s))
-                    assert np.array_equal(got, exp[i]), f"mode {(upd, pull, unroll)} source {s}"
+                    assert np.array_equal(got, exp[i]), f"mode {(upd, pull, unroll, minb, filt)} source {s}"
     finally:
         blest.blest_destroy(h)
 
