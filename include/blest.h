@@ -265,6 +265,37 @@ int32_t blest_is_social(int32_t n, const int32_t* row_ptr, const int32_t* col_id
 blest_status blest_debug_pull(const uint32_t* d_masks, const uint8_t* d_alpha, int32_t tiles,
                               int32_t pull, uint8_t* d_hits);
 
+/* ------------------------------------------------- allocation-free traversal */
+
+/* Single-source BFS that allocates nothing, for callers that may not call
+ * cudaMalloc: work captured into a CUDA graph whose capture mode forbids
+ * allocation, plugins and embedded runtimes whose host application owns every
+ * device allocation, and services whose device memory is budgeted up front.
+ * The paper has no counterpart; this is a deployment variant of blest_bfs_device.
+ *
+ * Inputs are the BVSS arrays of a graph in device memory, as blest_export gives
+ * them: d_real_ptrs (int32[ceil(n/8)+1]), d_row_ids (int32[128*num_vss]),
+ * d_masks (uint32[32*num_vss]) and d_new_id (int32[n], original id -> BVSS id;
+ * NULL if the BVSS uses the original order).  src_bvss is the source in BVSS
+ * ids (new_id[src]).  d_levels (int32[n], device) receives the levels in
+ * ORIGINAL ids.  update is BLEST_UPDATE_EAGER or BLEST_UPDATE_LAZY.  stream is a
+ * cudaStream_t (NULL = the legacy default stream).  The call blocks until the
+ * traversal is done and returns its status.
+ *
+ * Working memory comes from one fixed device array inside the library (about
+ * 21 MiB), which every GPU that loads the library keeps until the process
+ * exits.  Limits: n <= 2,097,152 vertices and num_vss <= 524,288 virtual slice
+ * sets; larger graphs get BLEST_ERR_TOO_LARGE.  The first call on a device looks
+ * up the array's device address (once per device, with that device current);
+ * make that first call before any stream capture.  All calls share the one
+ * array and each clears what it needs, so calls that overlap on the GPU (from
+ * several host threads or streams) race and must be serialised by the caller.
+ * Errors: INVALID_ARG, TOO_LARGE, TIMEOUT, INTERNAL, CUDA. */
+blest_status blest_bfs_static_scratch(int32_t n, int64_t num_vss, const int32_t* d_real_ptrs,
+                                      const int32_t* d_row_ids, const uint32_t* d_masks,
+                                      const int32_t* d_new_id, int32_t src_bvss, int32_t* d_levels,
+                                      int32_t update, void* stream);
+
 const char* blest_status_string(blest_status s);
 const char* blest_last_error(void);
 

@@ -24,7 +24,8 @@ __all__ = [
     "blest_graph_create", "blest_graph_create_ex", "blest_batch_create", "blest_destroy", "blest_set_option",
     "blest_get_stats", "blest_bfs", "blest_msbfs", "blest_bfs_multiroot", "blest_batch_bfs", "blest_bfs_device",
     "blest_msbfs_device", "blest_bfs_multiroot_device", "blest_sync", "blest_get_run_info", "blest_export",
-    "blest_autotune", "blest_export_size", "blest_compute_order", "blest_is_social", "blest_debug_pull", "lib", "EXPORTED_SYMBOLS",
+    "blest_autotune", "blest_export_size", "blest_compute_order", "blest_is_social", "blest_debug_pull",
+    "blest_bfs_static_scratch", "lib", "EXPORTED_SYMBOLS",
 ]
 
 BLEST_OK = 0
@@ -44,7 +45,7 @@ EXPORTED_SYMBOLS = [
     "blest_get_stats", "blest_bfs", "blest_msbfs", "blest_bfs_multiroot", "blest_batch_bfs", "blest_bfs_device",
     "blest_msbfs_device", "blest_bfs_multiroot_device", "blest_sync", "blest_get_run_info", "blest_autotune",
     "blest_export_size", "blest_export", "blest_compute_order", "blest_is_social", "blest_debug_pull",
-    "blest_status_string", "blest_last_error",
+    "blest_bfs_static_scratch", "blest_status_string", "blest_last_error",
 ]
 
 
@@ -121,6 +122,8 @@ def lib():
                                                    ctypes.POINTER(CreateParams), _i32p]),
             "blest_is_social": (ctypes.c_int32, [ctypes.c_int32, _i32p, _i32p]),
             "blest_debug_pull": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp]),
+            "blest_bfs_static_scratch": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _vp, _vp, _vp, _vp,
+                                                        ctypes.c_int32, _vp, ctypes.c_int32, _vp]),
             "blest_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "blest_last_error": (ctypes.c_char_p, []),
         }
@@ -345,6 +348,16 @@ def blest_is_social(n: int, row_ptr, col_idx) -> bool:
 def blest_debug_pull(d_masks, d_alpha, tiles: int, pull: int, d_hits) -> None:
     _check(lib().blest_debug_pull(_dev_ptr(d_masks), _dev_ptr(d_alpha), int(tiles), int(pull), _dev_ptr(d_hits)),
            "blest_debug_pull")
+
+
+def blest_bfs_static_scratch(n: int, num_vss: int, d_real_ptrs, d_row_ids, d_masks, d_new_id, src_bvss: int,
+                             d_levels, update: int = BLEST_UPDATE_LAZY, stream=None) -> None:
+    """Allocation-free single-source traversal (see include/blest.h); device
+    arguments are CUDA tensors or raw pointers, d_new_id may be None."""
+    _check(lib().blest_bfs_static_scratch(int(n), int(num_vss), _dev_ptr(d_real_ptrs), _dev_ptr(d_row_ids),
+                                          _dev_ptr(d_masks), None if d_new_id is None else _dev_ptr(d_new_id),
+                                          int(src_bvss), _dev_ptr(d_levels), int(update), _stream_ptr(stream)),
+           "blest_bfs_static_scratch")
 
 
 class BlestGraph:

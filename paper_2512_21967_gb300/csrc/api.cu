@@ -43,6 +43,15 @@ blest_status cuda_fail(cudaError_t e, const char* what) {
 constexpr int kLevelRecordCap = 1 << 16;
 constexpr int32_t kMaxVertices = 1 << 29;
 
+}  // namespace
+
+namespace blest {
+// Lets other translation units of the library report through blest_last_error.
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace blest
+
+namespace {
+
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
