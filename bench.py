@@ -41,10 +41,13 @@ WORKLOADS = {
     # name: (kind, size, sources, order, seed_graph, seed_src, msbfs_k)
     "rmat23": ("rmat", 23, 64, "compress", 2, 1002, 0),
     "rmat16": ("rmat", 16, 64, "compress", 1, 1001, 0),
+    "rmat21": ("rmat", 21, 64, "compress", 2, 1002, 0),
     "grid4096": ("grid", 4096, 64, "bandwidth", 3, 1003, 0),
     "rmat22-ms64": ("rmat", 22, 64, "compress", 4, 1004, 64),
     "rmat22-ms256": ("rmat", 22, 256, "compress", 4, 1004, 256),
     "rmat22-single": ("rmat", 22, 64, "compress", 4, 1004, 0),
+    "batch128": ("batch", 128, 128, "per-kind", 4, 0, 0),
+    "serve": ("serve", 16, 0, "per-kind", 5, 0, 0),
 }
 
 
@@ -61,6 +64,8 @@ def build_workload(name, window):
     from paper_2512_21967_gb300 import synth
     kind, size, nsrc, order, sg, ss, k = WORKLOADS[name]
     t0 = time.time()
+    if kind == "batch":
+        return synth.batch_workload(size, sg), None, order, k, time.time() - t0
     if kind == "rmat":
         g, srcs = synth.rmat_workload(size, nsrc, seed_graph=sg, seed_src=ss)
     else:
@@ -155,6 +160,20 @@ def traversal_bytes(levels_t, new_id_t, w_s_t, nss, n, lazy, torch):
 
 # ------------------------------------------------------------------ ours
 
+def aggregate_over_ranks(local_ms, local_edges, world, device):
+    """Replicas: every rank traversed its own copy; the job's time is the slowest
+    rank's and its work is the sum of all ranks' edges."""
+    if world <= 1:
+        return float(local_ms), float(local_edges)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    e = torch.tensor([float(local_edges)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(e.item())
+
+
 def run_ours(args):
     import torch
 
@@ -166,6 +185,10 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if WORKLOADS[args.workload][0] == "batch":
+        return run_ours_batch(args, torch, blest, dev, rank, world)
+    if WORKLOADS[args.workload][0] == "serve":
+        return run_ours_serve(args, torch, blest, dev, rank, world)
     g, srcs, order_name, msk, t_gen = build_workload(args.workload, args.window)
     order = {"compress": blest.BLEST_ORDER_COMPRESS, "bandwidth": blest.BLEST_ORDER_BANDWIDTH,
              "none": blest.BLEST_ORDER_NONE}[order_name]
@@ -173,6 +196,9 @@ def run_ours(args):
     h = blest.blest_graph_create_ex(g.n, g.row_ptr, g.col_idx, order, window=args.window)
     t_create = time.time() - t0
     st = blest.blest_get_stats(h)
+    if args.sources:
+        srcs = srcs[:args.sources]
+    tune = None
     if args.update != "auto":
         blest.blest_set_option(h, blest.BLEST_OPT_UPDATE,
                                blest.BLEST_UPDATE_EAGER if args.update == "eager" else blest.BLEST_UPDATE_LAZY)
@@ -181,6 +207,14 @@ def run_ours(args):
     if args.blocks_per_sm:
         blest.blest_set_option(h, blest.BLEST_OPT_BLOCKS_PER_SM, args.blocks_per_sm)
     blest.blest_set_option(h, blest.BLEST_OPT_UNROLL, args.unroll)
+    blest.blest_set_option(h, blest.BLEST_OPT_MIN_BLOCKS, args.minb)
+    blest.blest_set_option(h, blest.BLEST_OPT_VISITED_FILTER, args.filter)
+    blest.blest_set_option(h, blest.BLEST_OPT_STAGE_DEPTH, args.depth)
+    if not args.no_tune and not msk:
+        # the autotuner times every kernel variant on 4 of the sources (untimed setup)
+        t0 = time.time()
+        tune = blest.blest_autotune(h, srcs[:4])
+        tune["seconds"] = round(time.time() - t0, 2)
     n = g.n
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)      # flushes, events and traversals all on this stream
@@ -199,6 +233,7 @@ def run_ours(args):
     edges = np.zeros(len(srcs), np.int64)
     abytes = np.zeros(len(srcs), np.int64)
     lazy = None
+    run_info = None
 
     def one_step(timed_events=None):
         for i, s in enumerate(srcs):
@@ -217,8 +252,8 @@ def run_ours(args):
                 blest.blest_sync(h)
                 edges[i] = int((deg_t[out >= 0]).sum().item()) // 2
                 if lazy is None:
-                    info, _ = blest.blest_get_run_info(h)
-                    lazy = info["update"] == blest.BLEST_UPDATE_LAZY
+                    run_info, _ = blest.blest_get_run_info(h)
+                    lazy = run_info["update"] == blest.BLEST_UPDATE_LAZY
                 abytes[i], _ = traversal_bytes(out, new_id_t, w_s_t, nss, n, lazy, torch)
         else:
             one_step()
@@ -253,16 +288,7 @@ def run_ours(args):
     bfs_ms = float(per.sum())
     wall_ms = t_start.elapsed_time(t_end)
     tot_edges = float(edges.sum()) * args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([bfs_ms, tot_edges], dtype=torch.float64, device=dev)
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        bfs_ms_max, edges_all = float(mx[0]), float(sm[1])
-    else:
-        bfs_ms_max, edges_all = bfs_ms, tot_edges
+    bfs_ms_max, edges_all = aggregate_over_ranks(bfs_ms, tot_edges, world, dev)
     value = edges_all / (bfs_ms_max / 1e3) / 1e9
     avg_launch_ms = float(per.mean())
     avg_bytes = float(abytes.mean())
@@ -293,7 +319,13 @@ def run_ours(args):
             "config": {"workload": f"single-source BFS, {g.name}, {len(srcs)} seeded sources, {order_name} order",
                        "n": g.n, "directed_edges": g.nnz, "sources_per_step": len(srcs),
                        "order": order_name, "window": args.window,
-                       "update": "lazy" if lazy else "eager", "pull": args.pull, "unroll": args.unroll,
+                       "update": "lazy" if lazy else "eager", "pull": ["popc", "mma"][run_info["pull"]],
+                       "variant": {k: tune[k] for k in ("unroll", "min_blocks", "visited_filter", "blocks_per_sm",
+                                                        "stage_depth")}
+                       if tune else {"unroll": args.unroll, "min_blocks": args.minb, "visited_filter": args.filter,
+                                     "blocks_per_sm": args.blocks_per_sm, "stage_depth": args.depth},
+                       "autotune": tune,
+                       "grid_blocks": run_info["grid_blocks"],
                        "l2": "flushed by a 256 MiB write before every traversal, outside its event pair",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
@@ -341,17 +373,190 @@ def run_ours_msbfs(args, torch, blest, h, g, srcs, k, dev, stream, flush, st, t_
     clocks = sampler.stop() if sampler else None
     ms = float(sum(e[0].elapsed_time(e[1]) for e in evs))
     value = edges * args.steps / (ms / 1e3) / 1e9
+    # the same sources as single-source traversals looped one at a time (autotuned variant)
+    loop_srcs = srcs[:min(k, 64)]
+    tune = blest.blest_autotune(h, loop_srcs[:4])
+    one = torch.empty(n, dtype=torch.int32, device=dev)
+    for s_ in loop_srcs[:8]:
+        blest.blest_bfs_device(h, int(s_), one, stream=stream)
+    torch.cuda.synchronize(dev)
+    le = []
+    for s_ in loop_srcs:
+        flush.fill_(7)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        blest.blest_bfs_device(h, int(s_), one, stream=stream)
+        e1.record(stream)
+        le.append((e0, e1))
+    torch.cuda.synchronize(dev)
+    blest.blest_sync(h)
+    loop_ms = float(sum(a_.elapsed_time(b_) for a_, b_ in le))
+    loop_rate = len(loop_srcs) / (loop_ms / 1e3)
+    batched_rate = k * args.steps / (ms / 1e3)
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
                 "config": {"workload": f"multi-source BFS k={k}, {g.name}", "n": n, "directed_edges": g.nnz,
-                           "k": k, "source_bfs_per_s": round(k * args.steps / (ms / 1e3), 2)},
+                           "k": k, "source_bfs_per_s": round(batched_rate, 2),
+                           "single_source_loop_bfs_per_s": round(loop_rate, 2),
+                           "batched_over_loop": round(batched_rate / loop_rate, 2),
+                           "single_source_variant": {kk: tune[kk] for kk in ("update", "unroll", "stage_depth",
+                                                                              "visited_filter", "blocks_per_sm")}},
                 "gpu_launches": args.steps, "clocks": clocks,
                 "bvss": {kk: st[kk] for kk in ("num_vss", "unpadded_slices", "compression_ratio")},
                 "preprocess_s": {"generate": round(t_gen, 2), "create_total": round(t_create, 2)}}
         print(json.dumps(line), flush=True)
     blest.blest_destroy(h)
+
+
+def run_ours_batch(args, torch, blest, dev, rank, world):
+    """Many graphs of uneven size in one persistent launch: one traversal of their
+    disjoint union (one source per graph), captured once as a CUDA graph and
+    replayed every step."""
+    items, _, _, _, t_gen = build_workload(args.workload, args.window)
+    graphs = [it[0] for it in items]
+    srcs = [it[1] for it in items]
+    orders = [blest.BLEST_ORDER_COMPRESS if it[2] == "rmat" else blest.BLEST_ORDER_BANDWIDTH for it in items]
+    t0 = time.time()
+    h = blest.blest_batch_create([(g.n, g.row_ptr, g.col_idx) for g in graphs], orders, window=args.window)
+    t_create = time.time() - t0
+    st = blest.blest_get_stats(h)
+    if args.update != "auto":
+        blest.blest_set_option(h, blest.BLEST_OPT_UPDATE,
+                               blest.BLEST_UPDATE_EAGER if args.update == "eager" else blest.BLEST_UPDATE_LAZY)
+    blest.blest_set_option(h, blest.BLEST_OPT_STAGE_DEPTH, args.depth)
+    n = sum(g.n for g in graphs)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    blest.blest_batch_graph_capture(h, out)
+    deg = torch.from_numpy(np.concatenate([g.degrees() for g in graphs])).to(dev)
+    for _ in range(args.warmup):
+        blest.blest_batch_graph_launch(h, srcs, stream=stream)
+    blest.blest_sync(h)
+    edges = int(deg[out >= 0].sum().item()) // 2
+    info, _ = blest.blest_get_run_info(h)
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler() if rank == 0 else None
+    evs = [[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        evs[i][0].record(stream)
+        blest.blest_batch_graph_launch(h, srcs, stream=stream)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    blest.blest_sync(h)
+    clocks = sampler.stop() if sampler else None
+    ms = float(sum(e[0].elapsed_time(e[1]) for e in evs))
+    value = edges * args.steps / (ms / 1e3) / 1e9
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+                "config": {"workload": f"{len(graphs)} graphs of uneven size (R-MAT scale 10..18, grids 64..1024), "
+                                       "one source each, one persistent launch replayed as a CUDA graph",
+                           "n": n, "directed_edges": int(sum(g.nnz for g in graphs)), "graphs": len(graphs),
+                           "levels": info["levels"], "update": ["auto", "eager", "lazy"][info["update"]]},
+                "gpu_launches": args.steps, "clocks": clocks,
+                "preprocess_s": {"generate": round(t_gen, 2), "create_total": round(t_create, 2),
+                                 "order": round(st["order_seconds"], 2)}}
+        print(json.dumps(line), flush=True)
+    blest.blest_destroy(h)
+
+
+def serve_stream(blest, srv, stream):
+    """Submit the stream at its arrival times; latency of a query = completion
+    time - scheduled arrival (so a lagging client is charged to the server)."""
+    import threading
+    t0 = time.perf_counter()
+    lat = [None] * len(stream)
+    tickets = [None] * len(stream)
+    submit_at = [0.0] * len(stream)
+    lock = threading.Lock()
+    done = threading.Event()
+
+    def waiter():
+        for i in range(len(stream)):
+            while tickets[i] is None:
+                time.sleep(0.0001)
+            srv_lat = blest.blest_server_wait(srv, tickets[i], 600.0)
+            with lock:
+                lat[i] = (submit_at[i] - stream[i][0]) + srv_lat
+        done.set()
+
+    th = threading.Thread(target=waiter, daemon=True)
+    th.start()
+    for i, (t_arr, g, srcs) in enumerate(stream):
+        now = time.perf_counter() - t0
+        if t_arr > now:
+            time.sleep(t_arr - now)
+        submit_at[i] = time.perf_counter() - t0
+        tickets[i] = blest.blest_server_submit(srv, g, srcs, None)
+    done.wait()
+    wall = time.perf_counter() - t0
+    return np.array(lat), wall
+
+
+def run_ours_serve(args, torch, blest, dev, rank, world):
+    """Serving: 16 resident graphs (8 R-MAT, scales 16..22; 8 grids, sides
+    256..2048), a Poisson stream of queries (uniform graph, 1..32 uniform
+    sources) at several rates, served with continuous batching under a 40 GB
+    device-memory cap, against the same stream served one query per launch."""
+    items = synth_serving()
+    graphs = [it[0] for it in items]
+    pools = [it[1] for it in items]
+    t0 = time.time()
+    handles = [blest.blest_graph_create_ex(g.n, g.row_ptr, g.col_idx,
+                                           blest.BLEST_ORDER_COMPRESS if it[2] == "rmat" else blest.BLEST_ORDER_BANDWIDTH,
+                                           window=args.window) for g, it in zip(graphs, items)]
+    t_create = time.time() - t0
+    results = []
+    rates = [float(r) for r in args.rates.split(",")]
+    for rate in rates:
+        stream = synth_query_stream(args.queries, len(graphs), rate, 55, pools)
+        row = {"rate_qps": rate, "queries": len(stream)}
+        for mode in ("batched", "one_at_a_time"):
+            if mode == "batched":
+                srv = blest.blest_server_create(handles, memory_cap_bytes=40 << 30, max_batch_sources=64,
+                                                max_inflight=4, blocks_per_sm=1)
+            else:
+                srv = blest.blest_server_create(handles, memory_cap_bytes=40 << 30, max_batch_sources=32,
+                                                max_inflight=1, blocks_per_sm=0, max_queries_per_launch=1)
+            try:
+                lat, wall = serve_stream(blest, srv, stream)
+                st = blest.blest_server_get_stats(srv)
+            finally:
+                blest.blest_server_destroy(srv)
+            row[mode] = {"p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
+                         "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
+                         "throughput_qps": round(len(stream) / wall, 2), "launches": st["launches"],
+                         "mean_sources_per_launch": round(st["sources_launched"] / max(1, st["launches"]), 2),
+                         "memory_peak_gb": round(st["memory_peak"] / 2**30, 2)}
+        results.append(row)
+    for h in handles:
+        blest.blest_destroy(h)
+    best = max(r["batched"]["throughput_qps"] for r in results)
+    if rank == 0:
+        line = {"metric": METRIC, "value": best, "unit": "queries/s", "n_gpus": world, "steps": len(rates),
+                "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "u64", "data": "synthetic",
+                "config": {"workload": "serving: 16 resident graphs (8 R-MAT s16..22, 8 grids 256..2048, p=0.9), "
+                                       f"Poisson queries with 1..32 sources, {args.queries} per rate, 40 GB cap",
+                           "results_copied": "no (levels stay in device memory)"},
+                "serving": results, "preprocess_s": {"create_total": round(t_create, 2)}}
+        print(json.dumps(line), flush=True)
+
+
+def synth_serving():
+    from paper_2512_21967_gb300 import synth
+    return synth.serving_workload()
+
+
+def synth_query_stream(num, ng, rate, seed, pools):
+    from paper_2512_21967_gb300 import synth
+    return synth.query_stream(num, ng, rate, seed, pools)
 
 
 # ------------------------------------------------------------- CPU oracle
@@ -414,6 +619,13 @@ def main():
     ap.add_argument("--update", choices=["auto", "eager", "lazy"], default="auto")
     ap.add_argument("--pull", choices=["popc", "mma"], default="popc")
     ap.add_argument("--unroll", type=int, default=2)
+    ap.add_argument("--minb", type=int, default=2)
+    ap.add_argument("--filter", type=int, default=1)
+    ap.add_argument("--sources", type=int, default=0, help="use only the first N sources of the workload")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner, use the flags as given")
+    ap.add_argument("--depth", type=int, default=0, help="TMA ring depth of the lazy kernel (0, 4, 8)")
+    ap.add_argument("--queries", type=int, default=2000, help="serving: queries per arrival rate")
+    ap.add_argument("--rates", default="100,400,1600", help="serving: arrival rates in queries/s")
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--cpu-sources", type=int, default=4)
     ap.add_argument("--ref-sources", type=int, default=2)

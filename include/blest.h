@@ -78,11 +78,14 @@ typedef enum {
     BLEST_OPT_BLOCKS_PER_SM = 2,     /* persistent-grid blocks per SM; 0 = as many as fit */
     BLEST_OPT_BARRIER_TIMEOUT_US = 3,/* grid-barrier wait limit in microseconds (default 2,000,000) */
     BLEST_OPT_RECORD_LEVELS = 4,     /* 1 = record the per-level queue sizes (blest_get_run_info) */
-    BLEST_OPT_UNROLL = 5,            /* virtual slice sets a warp loads at once: 1 or 2 (default 2) */
+    BLEST_OPT_UNROLL = 5,            /* virtual slice sets a warp handles at once: 1, 2 (default) or 4
+                                        (4 only with the 8-stage TMA ring) */
     BLEST_OPT_TEST_PHANTOM_BLOCK = 6,/* testing: 1 = every barrier waits for one block that does not
                                         exist, so the next traversal must end in BLEST_ERR_TIMEOUT */
     BLEST_OPT_VISITED_FILTER = 7,    /* 1 (default) = test a visited bitmap before marking a row */
-    BLEST_OPT_MIN_BLOCKS = 8         /* kernel variant compiled for 2 (default) or 3 blocks per SM */
+    BLEST_OPT_MIN_BLOCKS = 8,        /* kernel variant compiled for 2 (default) or 3 blocks per SM */
+    BLEST_OPT_STAGE_DEPTH = 9        /* lazy stage 1 through a per-warp TMA ring of 4 or 8 stages; 0 = plain
+                                        128-bit loads (default); used with BLEST_OPT_MIN_BLOCKS = 2 */
 } blest_option;
 
 /* Creation parameters; pass NULL to blest_graph_create_ex for the defaults. */
@@ -182,6 +185,17 @@ blest_status blest_bfs_multiroot(blest_handle h, const int32_t* srcs, int32_t k,
  * levels: host memory of sum(n_each) int32, graph g's levels at the offset of g. */
 blest_status blest_batch_bfs(blest_handle h, const int32_t* srcs_local, int32_t* levels);
 
+/* Batch handle, CUDA-graph form: blest_batch_graph_capture records one batched
+ * traversal (source upload from a pinned list, clears, the persistent kernel)
+ * into a CUDA graph bound to d_levels (device, sum(n_each) int32, caller-owned,
+ * must stay valid while the capture is used); blest_batch_graph_launch writes
+ * new sources (srcs_local[g] in graph g's local ids) into the pinned list and
+ * replays the graph on `stream` (NULL = the handle's stream) without waiting
+ * for it.  A launch first waits until the previous replay has finished.
+ * Completion and device status: blest_sync.  Errors: INVALID_ARG, CUDA. */
+blest_status blest_batch_graph_capture(blest_handle h, int32_t* d_levels);
+blest_status blest_batch_graph_launch(blest_handle h, const int32_t* srcs_local, void* stream);
+
 /* Device-memory forms.  They enqueue the traversal on `stream` (a cudaStream_t;
  * NULL = the handle's own stream; pass cudaStreamLegacy for the legacy default
  * stream) and return without waiting; sources are host
@@ -203,6 +217,15 @@ blest_status blest_sync(blest_handle h);
  * at level l, up to cap entries.  Waits for the handle's work first. */
 blest_status blest_get_run_info(blest_handle h, blest_run_info* info, int32_t* queue_sizes, int32_t cap);
 
+/* Device timeline of the last single-frontier traversal (recorded when
+ * BLEST_OPT_RECORD_LEVELS = 1), in globaltimer nanoseconds: times_ns[1] =
+ * kernel entry, times_ns[0] = start of level 0's sweep; for level l >= 1,
+ * times_ns[2l] = start of its stage 1 and times_ns[2l+1] = start of its
+ * finalisation sweep (lazy only); for the last level L, times_ns[2L+2] = end
+ * of the traversal and times_ns[2L+3] = end of block 0's share of the
+ * unpermute epilogue.  Up to cap entries. */
+blest_status blest_get_level_times(blest_handle h, uint64_t* times_ns, int32_t cap);
+
 /* ---------------------------------------------------------------- autotune */
 
 /* Result of blest_autotune: the options it kept and what they measured. */
@@ -213,6 +236,7 @@ typedef struct {
     int32_t min_blocks;
     int32_t visited_filter;
     int32_t blocks_per_sm;       /* 0 = as many as fit */
+    int32_t stage_depth;         /* BLEST_OPT_STAGE_DEPTH kept */
     int32_t candidates;          /* variants timed */
     double  best_ms;             /* mean device time per traversal of the kept variant */
     double  rule_ms;             /* same for the Section 5 rule (lazy iff U_div > 25,000), CUDA-core pull */
@@ -264,6 +288,66 @@ int32_t blest_is_social(int32_t n, const int32_t* row_ptr, const int32_t* col_id
  * path.  Synchronous. */
 blest_status blest_debug_pull(const uint32_t* d_masks, const uint8_t* d_alpha, int32_t tiles,
                               int32_t pull, uint8_t* d_hits);
+
+/* ------------------------------------------------------------ query server */
+
+/* A server keeps graph handles resident and answers multi-source queries with
+ * continuous batching: a scheduler thread packs the waiting queries of a graph
+ * (in arrival order, up to max_batch_sources sources) into one multi-source
+ * launch whenever a launch slot is free and the launch's device memory fits
+ * under memory_cap_bytes next to the launches in flight; queries that arrive
+ * meanwhile join a later launch, and launches run concurrently on their own
+ * streams.  Each query's levels are those blest_msbfs gives for it alone.  The
+ * graph handles must outlive the server and must not be used by other calls
+ * while it runs. */
+typedef struct blest_server* blest_server_handle;
+
+typedef struct {
+    int64_t memory_cap_bytes;    /* device bytes launches in flight may hold (default 40 GiB) */
+    int32_t max_batch_sources;   /* sources per launch, 1..256 (default 64) */
+    int32_t max_inflight;        /* launches in flight at once (default 4, at most 64) */
+    int32_t blocks_per_sm;       /* persistent-grid blocks per SM of each launch (default 1) */
+    int32_t max_queries_per_launch; /* 0 = no limit (default); 1 = one query per launch (no coalescing) */
+} blest_server_params;
+
+typedef struct {
+    int64_t launches;            /* multi-source launches issued */
+    int64_t sources_launched;    /* sources over all launches */
+    int64_t queries_done;
+    int64_t queries_waiting;
+    int64_t memory_in_use;       /* device bytes held by launches in flight */
+    int64_t memory_peak;
+} blest_server_stats;
+
+/* graphs: num_graphs handles; params may be NULL.  Errors: INVALID_ARG, OOM, CUDA. */
+blest_status blest_server_create(const blest_handle* graphs, int32_t num_graphs, const blest_server_params* params,
+                                 blest_server_handle* out);
+
+/* Queue a query: k sources (host array, original ids of graph `graph`); levels
+ * receives k * n int32 (source-major) and may be host or device memory, or NULL
+ * to discard the result; use page-locked host memory or device memory for
+ * fully asynchronous completion.  *ticket identifies the query.  Returns at
+ * once.  Errors: INVALID_ARG, TOO_LARGE (k > max_batch_sources, or one query
+ * alone exceeds the memory cap). */
+blest_status blest_server_submit(blest_server_handle s, int32_t graph, const int32_t* srcs, int32_t k,
+                                 int32_t* levels, uint64_t* ticket);
+
+/* Wait up to timeout_s seconds (negative = no limit) for the query, return its
+ * status and (optionally) its latency from submission to completion, and
+ * release the ticket.  Errors: INVALID_ARG (unknown ticket), TIMEOUT (not done
+ * yet; the ticket stays valid), or the query's own status. */
+blest_status blest_server_wait(blest_server_handle s, uint64_t ticket, double timeout_s, double* latency_s);
+
+/* paused = 1: start no new launch (launches in flight finish, queries keep
+ * queueing); paused = 0: resume.  Lets a caller drain the GPU or build up a
+ * backlog that the next launches coalesce. */
+blest_status blest_server_pause(blest_server_handle s, int32_t paused);
+
+blest_status blest_server_get_stats(blest_server_handle s, blest_server_stats* out);
+
+/* Stop the scheduler after the launches in flight; queries still waiting are
+ * dropped.  NULL is ignored. */
+void blest_server_destroy(blest_server_handle s);
 
 /* ------------------------------------------------- allocation-free traversal */
 

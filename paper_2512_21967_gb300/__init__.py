@@ -22,10 +22,13 @@ __all__ = [
     "BLEST_ORDER_NONE", "BLEST_ORDER_COMPRESS", "BLEST_ORDER_BANDWIDTH", "BLEST_ORDER_AUTO",
     "BLEST_UPDATE_AUTO", "BLEST_UPDATE_EAGER", "BLEST_UPDATE_LAZY", "BLEST_PULL_POPC", "BLEST_PULL_MMA",
     "blest_graph_create", "blest_graph_create_ex", "blest_batch_create", "blest_destroy", "blest_set_option",
-    "blest_get_stats", "blest_bfs", "blest_msbfs", "blest_bfs_multiroot", "blest_batch_bfs", "blest_bfs_device",
-    "blest_msbfs_device", "blest_bfs_multiroot_device", "blest_sync", "blest_get_run_info", "blest_export",
+    "blest_get_stats", "blest_bfs", "blest_msbfs", "blest_bfs_multiroot", "blest_batch_bfs",
+    "blest_batch_graph_capture", "blest_batch_graph_launch", "blest_bfs_device",
+    "blest_msbfs_device", "blest_bfs_multiroot_device", "blest_sync", "blest_get_run_info", "blest_get_level_times",
+    "blest_export",
     "blest_autotune", "blest_export_size", "blest_compute_order", "blest_is_social", "blest_debug_pull",
-    "blest_bfs_static_scratch", "lib", "EXPORTED_SYMBOLS",
+    "blest_bfs_static_scratch", "blest_server_create", "blest_server_submit", "blest_server_wait",
+    "blest_server_pause", "blest_server_get_stats", "blest_server_destroy", "lib", "EXPORTED_SYMBOLS",
 ]
 
 BLEST_OK = 0
@@ -36,16 +39,18 @@ BLEST_UPDATE_AUTO, BLEST_UPDATE_EAGER, BLEST_UPDATE_LAZY = 0, 1, 2
 BLEST_PULL_POPC, BLEST_PULL_MMA = 0, 1
 BLEST_OPT_UPDATE, BLEST_OPT_PULL, BLEST_OPT_BLOCKS_PER_SM, BLEST_OPT_BARRIER_TIMEOUT_US = 0, 1, 2, 3
 BLEST_OPT_RECORD_LEVELS, BLEST_OPT_UNROLL, BLEST_OPT_TEST_PHANTOM_BLOCK = 4, 5, 6
-BLEST_OPT_VISITED_FILTER, BLEST_OPT_MIN_BLOCKS = 7, 8
+BLEST_OPT_VISITED_FILTER, BLEST_OPT_MIN_BLOCKS, BLEST_OPT_STAGE_DEPTH = 7, 8, 9
 BLEST_ARRAY_REAL_PTRS, BLEST_ARRAY_VIRTUAL_TO_REAL, BLEST_ARRAY_ROW_IDS = 0, 1, 2
 BLEST_ARRAY_MASKS, BLEST_ARRAY_NEW_ID, BLEST_ARRAY_VSS_COUNT = 3, 4, 5
 
 EXPORTED_SYMBOLS = [
     "blest_graph_create", "blest_graph_create_ex", "blest_batch_create", "blest_destroy", "blest_set_option",
-    "blest_get_stats", "blest_bfs", "blest_msbfs", "blest_bfs_multiroot", "blest_batch_bfs", "blest_bfs_device",
-    "blest_msbfs_device", "blest_bfs_multiroot_device", "blest_sync", "blest_get_run_info", "blest_autotune",
+    "blest_get_stats", "blest_bfs", "blest_msbfs", "blest_bfs_multiroot", "blest_batch_bfs", "blest_batch_graph_capture",
+    "blest_batch_graph_launch", "blest_bfs_device", "blest_msbfs_device", "blest_bfs_multiroot_device", "blest_sync",
+    "blest_get_run_info", "blest_get_level_times", "blest_autotune",
     "blest_export_size", "blest_export", "blest_compute_order", "blest_is_social", "blest_debug_pull",
-    "blest_bfs_static_scratch", "blest_status_string", "blest_last_error",
+    "blest_server_create", "blest_server_submit", "blest_server_wait", "blest_server_pause", "blest_server_get_stats",
+    "blest_server_destroy", "blest_bfs_static_scratch", "blest_status_string", "blest_last_error",
 ]
 
 
@@ -75,7 +80,18 @@ class Stats(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     _fields_ = [("update", ctypes.c_int32), ("pull", ctypes.c_int32), ("unroll", ctypes.c_int32),
                 ("min_blocks", ctypes.c_int32), ("visited_filter", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_double), ("rule_ms", ctypes.c_double)]
+                ("stage_depth", ctypes.c_int32), ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_double), ("rule_ms", ctypes.c_double)]
+
+
+class ServerParams(ctypes.Structure):
+    _fields_ = [("memory_cap_bytes", ctypes.c_int64), ("max_batch_sources", ctypes.c_int32),
+                ("max_inflight", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("max_queries_per_launch", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("sources_launched", ctypes.c_int64), ("queries_done", ctypes.c_int64),
+                ("queries_waiting", ctypes.c_int64), ("memory_in_use", ctypes.c_int64), ("memory_peak", ctypes.c_int64)]
 
 
 class RunInfo(ctypes.Structure):
@@ -110,12 +126,15 @@ def lib():
             "blest_msbfs": (ctypes.c_int, [_vp, _i32p, ctypes.c_int32, _i32p]),
             "blest_bfs_multiroot": (ctypes.c_int, [_vp, _i32p, ctypes.c_int32, _i32p]),
             "blest_batch_bfs": (ctypes.c_int, [_vp, _i32p, _i32p]),
+            "blest_batch_graph_capture": (ctypes.c_int, [_vp, _vp]),
+            "blest_batch_graph_launch": (ctypes.c_int, [_vp, _i32p, _vp]),
             "blest_bfs_device": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp]),
             "blest_msbfs_device": (ctypes.c_int, [_vp, _i32p, ctypes.c_int32, _vp, _vp]),
             "blest_bfs_multiroot_device": (ctypes.c_int, [_vp, _i32p, ctypes.c_int32, _vp, _vp]),
             "blest_sync": (ctypes.c_int, [_vp]),
             "blest_get_run_info": (ctypes.c_int, [_vp, ctypes.POINTER(RunInfo), _i32p, ctypes.c_int32]),
             "blest_autotune": (ctypes.c_int, [_vp, _i32p, ctypes.c_int32, ctypes.POINTER(TuneResult)]),
+            "blest_get_level_times": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32]),
             "blest_export_size": (ctypes.c_int64, [_vp, ctypes.c_int32]),
             "blest_export": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.c_int64]),
             "blest_compute_order": (ctypes.c_int, [ctypes.c_int32, _i32p, _i32p, ctypes.c_int,
@@ -124,6 +143,14 @@ def lib():
             "blest_debug_pull": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp]),
             "blest_bfs_static_scratch": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _vp, _vp, _vp, _vp,
                                                         ctypes.c_int32, _vp, ctypes.c_int32, _vp]),
+            "blest_server_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(ServerParams),
+                                                   ctypes.POINTER(_vp)]),
+            "blest_server_submit": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p, ctypes.c_int32, _vp,
+                                                   ctypes.POINTER(ctypes.c_uint64)]),
+            "blest_server_wait": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+            "blest_server_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(ServerStats)]),
+            "blest_server_pause": (ctypes.c_int, [_vp, ctypes.c_int32]),
+            "blest_server_destroy": (None, [_vp]),
             "blest_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "blest_last_error": (ctypes.c_char_p, []),
         }
@@ -273,6 +300,15 @@ def blest_batch_bfs(h: int, srcs_local, levels: np.ndarray | None = None) -> np.
     return out
 
 
+def blest_batch_graph_capture(h: int, d_levels) -> None:
+    _check(lib().blest_batch_graph_capture(h, _dev_ptr(d_levels)), "blest_batch_graph_capture")
+
+
+def blest_batch_graph_launch(h: int, srcs_local, stream=None) -> None:
+    s = _i32(srcs_local)
+    _check(lib().blest_batch_graph_launch(h, _ptr(s), _stream_ptr(stream)), "blest_batch_graph_launch")
+
+
 def blest_bfs_device(h: int, src: int, d_levels, stream=None) -> None:
     _check(lib().blest_bfs_device(h, int(src), _dev_ptr(d_levels), _stream_ptr(stream)), "blest_bfs_device")
 
@@ -306,6 +342,13 @@ def blest_autotune(h: int, srcs) -> dict:
     r = TuneResult()
     _check(lib().blest_autotune(h, _ptr(s), len(s), ctypes.byref(r)), "blest_autotune")
     return {f: getattr(r, f) for f, _ in r._fields_}
+
+
+def blest_get_level_times(h: int, cap: int = 1 << 17) -> np.ndarray:
+    out = np.zeros(cap, np.uint64)
+    _check(lib().blest_get_level_times(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), int(cap)),
+           "blest_get_level_times")
+    return out
 
 
 # ------------------------------------------------------------------ export
@@ -358,6 +401,54 @@ def blest_bfs_static_scratch(n: int, num_vss: int, d_real_ptrs, d_row_ids, d_mas
                                           _dev_ptr(d_masks), None if d_new_id is None else _dev_ptr(d_new_id),
                                           int(src_bvss), _dev_ptr(d_levels), int(update), _stream_ptr(stream)),
            "blest_bfs_static_scratch")
+
+
+def blest_server_create(handles, memory_cap_bytes=0, max_batch_sources=0, max_inflight=0, blocks_per_sm=0,
+                        max_queries_per_launch=0) -> int:
+    arr = (_vp * len(handles))(*handles)
+    p = ServerParams(int(memory_cap_bytes), int(max_batch_sources), int(max_inflight), int(blocks_per_sm),
+                     int(max_queries_per_launch))
+    s = _vp()
+    _check(lib().blest_server_create(arr, len(handles), ctypes.byref(p), ctypes.byref(s)), "blest_server_create")
+    return s.value
+
+
+def blest_server_submit(server: int, graph: int, srcs, levels=None) -> int:
+    """levels: None, a numpy int32 array (host) or a CUDA tensor / device pointer of k*n int32."""
+    s = _i32(srcs)
+    if levels is None:
+        ptr = None
+    elif isinstance(levels, np.ndarray):
+        if levels.dtype != np.int32 or not levels.flags.c_contiguous:
+            raise ValueError("levels must be a contiguous int32 array")
+        ptr = levels.ctypes.data
+    else:
+        ptr = _dev_ptr(levels)
+    t = ctypes.c_uint64()
+    _check(lib().blest_server_submit(server, int(graph), _ptr(s), len(s), ptr, ctypes.byref(t)), "blest_server_submit")
+    return t.value
+
+
+def blest_server_wait(server: int, ticket: int, timeout_s: float = -1.0) -> float:
+    lat = ctypes.c_double()
+    _check(lib().blest_server_wait(server, ctypes.c_uint64(ticket), float(timeout_s), ctypes.byref(lat)),
+           "blest_server_wait")
+    return lat.value
+
+
+def blest_server_pause(server: int, paused: bool) -> None:
+    _check(lib().blest_server_pause(server, 1 if paused else 0), "blest_server_pause")
+
+
+def blest_server_get_stats(server: int) -> dict:
+    st = ServerStats()
+    _check(lib().blest_server_get_stats(server, ctypes.byref(st)), "blest_server_get_stats")
+    return {f: getattr(st, f) for f, _ in st._fields_}
+
+
+def blest_server_destroy(server: int | None) -> None:
+    if server:
+        lib().blest_server_destroy(server)
 
 
 class BlestGraph:

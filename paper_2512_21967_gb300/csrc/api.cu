@@ -72,6 +72,7 @@ struct blest_graph {
     unsigned int qcap = 0;
     unsigned int* d_ctrl = nullptr;      // 256-byte control block (device_common.cuh layout)
     int32_t* d_level_sizes = nullptr;
+    unsigned long long* d_level_times = nullptr;
     int32_t* d_roots = nullptr;
     int64_t roots_cap = 0;
     cudaStream_t stream = nullptr;
@@ -86,12 +87,20 @@ struct blest_graph {
     int unroll = 2;
     int minb = 2;
     int filter = 1;
+    int depth = 0;
     int phantom = 0;
     // results
     blest_stats stats{};
     blest_run_info info{};
     std::vector<int64_t> offsets;        // batch handles: graph g owns [offsets[g], offsets[g+1])
     blest::MsbfsState ms;
+    // captured batch traversal (blest_batch_graph_capture)
+    cudaGraph_t cgraph = nullptr;
+    cudaGraphExec_t cgraph_exec = nullptr;
+    int32_t* d_graph_roots = nullptr;
+    int32_t* h_graph_roots = nullptr;    // pinned
+    int32_t graph_nroots = 0;
+    cudaEvent_t graph_done = nullptr;
 
     int nwords() const { return (n + 31) / 32; }
     int resolved_update() const {
@@ -115,7 +124,13 @@ void free_handle(blest_graph* h) {
     cudaFree(h->d_Q);
     cudaFree(h->d_ctrl);
     cudaFree(h->d_level_sizes);
+    cudaFree(h->d_level_times);
     cudaFree(h->d_roots);
+    if (h->cgraph_exec) cudaGraphExecDestroy(h->cgraph_exec);
+    if (h->cgraph) cudaGraphDestroy(h->cgraph);
+    cudaFree(h->d_graph_roots);
+    if (h->h_graph_roots) cudaFreeHost(h->h_graph_roots);
+    if (h->graph_done) cudaEventDestroy(h->graph_done);
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -163,6 +178,7 @@ blest_status finish_create(blest_graph* h, const Csr& g, const std::vector<int32
     BLEST_ALLOC(h->d_Q, sizeof(unsigned long long) * 3 * (size_t)h->qcap, "cudaMalloc(queues)");
     BLEST_ALLOC(h->d_ctrl, kCtrlBytes, "cudaMalloc(ctrl)");
     BLEST_ALLOC(h->d_level_sizes, sizeof(int32_t) * kLevelRecordCap, "cudaMalloc(level record)");
+    BLEST_ALLOC(h->d_level_times, sizeof(unsigned long long) * (2 * (size_t)kLevelRecordCap + 2), "cudaMalloc(level times)");
 #undef BLEST_ALLOC
     cudaMemsetAsync(h->d_ctrl, 0, kCtrlBytes, h->stream);
     if (!new_id.empty()) {
@@ -220,8 +236,8 @@ blest_status prepare_graph(int32_t n, const int32_t* row_ptr, const int32_t* col
     return BLEST_OK;
 }
 
-int pick_grid(blest_graph* h, int update, int pull, int unroll, int minb) {
-    int maxb = blest::bfs_max_blocks_per_sm(update, pull, unroll, minb);
+int pick_grid(blest_graph* h, int update, int pull, int unroll, int minb, int depth) {
+    int maxb = blest::bfs_max_blocks_per_sm(update, pull, unroll, minb, depth);
     if (maxb <= 0) return 0;
     int b = h->blocks_per_sm > 0 ? std::min(h->blocks_per_sm, maxb) : maxb;
     return b * h->sms;
@@ -229,7 +245,8 @@ int pick_grid(blest_graph* h, int update, int pull, int unroll, int minb) {
 
 // Enqueue one single-frontier traversal from the (BVSS-order) roots, writing
 // levels in original ids into d_out (device, n int32).
-blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots, int32_t* d_out, cudaStream_t st) {
+blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots, int32_t* d_out, cudaStream_t st,
+                               const int32_t* d_roots_preloaded = nullptr, int32_t n_preloaded = 0) {
     if (h->n == 0) return BLEST_OK;
     cudaError_t e;
     blest::BfsLaunch L;
@@ -238,7 +255,11 @@ blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots
     L.unroll = h->unroll;
     L.minb = h->minb;
     L.filter = h->filter;
-    L.grid = pick_grid(h, L.update, L.pull, L.unroll, L.minb);
+    // the TMA ring exists for the lazy kernel compiled for 2 blocks per SM
+    L.depth = (L.update == 2 && L.minb == 2) ? h->depth : 0;
+    if (L.depth == 0 && L.unroll > 2) L.unroll = 2;       // unroll 4 exists only for the TMA ring
+    if (L.depth == 4 && L.unroll > 2) L.unroll = 2;       // a 4-stage ring holds two groups of 2
+    L.grid = pick_grid(h, L.update, L.pull, L.unroll, L.minb, L.depth);
     if (L.grid <= 0) return fail(BLEST_ERR_CUDA, "no co-resident grid for the traversal kernel");
     L.n = h->n;
     L.qcap = h->qcap;
@@ -256,9 +277,14 @@ blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots
     }
     L.ctrl = h->d_ctrl;
     L.level_sizes = h->record ? h->d_level_sizes : nullptr;
+    L.level_times = h->d_level_times;
     L.level_cap = kLevelRecordCap;
     L.nroots = (int32_t)roots.size();
-    if (roots.size() > (size_t)blest::kInlineRoots) {
+    if (d_roots_preloaded) {
+        // roots already on the device (a captured launch reads them from there)
+        L.nroots = n_preloaded;
+        L.roots_device = d_roots_preloaded;
+    } else if (roots.size() > (size_t)blest::kInlineRoots) {
         if ((int64_t)roots.size() > h->roots_cap) {
             cudaFree(h->d_roots);
             h->d_roots = nullptr;
@@ -271,6 +297,10 @@ blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots
         L.roots_device = h->d_roots;
     } else {
         for (size_t i = 0; i < roots.size(); ++i) L.roots_host[i] = roots[i];
+    }
+    if (d_roots_preloaded && n_preloaded <= blest::kInlineRoots) {
+        // the kernel takes inline roots below kInlineRoots; a captured launch must read the device list
+        return fail(BLEST_ERR_INTERNAL, "device roots need more than the inline count");
     }
     L.out = d_out;
     L.timeout_ns = (uint64_t)h->timeout_us * 1000ull;
@@ -319,6 +349,34 @@ blest_status sync_status(blest_graph* h) {
 }
 
 }  // namespace
+
+namespace blest {
+// Read-only view of a handle's device arrays for the query server (server.cu).
+struct HandleView {
+    int32_t n;
+    int32_t nss;
+    int64_t nvss;
+    const int32_t* real_ptrs;
+    const int32_t* row_ids;
+    const uint32_t* masks;
+    const int32_t* new_id_dev;
+    const int32_t* new_id_host;
+    int sms;
+};
+bool handle_view(blest_handle h, HandleView* v) {
+    if (!h || !v || h->n == 0) return false;
+    v->n = h->n;
+    v->nss = h->bvss.nss;
+    v->nvss = h->bvss.nvss;
+    v->real_ptrs = h->bvss.real_ptrs;
+    v->row_ids = h->bvss.row_ids;
+    v->masks = h->bvss.masks;
+    v->new_id_dev = h->d_new_id;
+    v->new_id_host = h->h_new_id.empty() ? nullptr : h->h_new_id.data();
+    v->sms = h->sms;
+    return true;
+}
+}  // namespace blest
 
 extern "C" {
 
@@ -461,7 +519,7 @@ blest_status blest_set_option(blest_handle h, int32_t key, int64_t value) {
             h->record = (int)value;
             return BLEST_OK;
         case BLEST_OPT_UNROLL:
-            if (value != 1 && value != 2) break;
+            if (value != 1 && value != 2 && value != 4) break;
             h->unroll = (int)value;
             return BLEST_OK;
         case BLEST_OPT_VISITED_FILTER:
@@ -471,6 +529,10 @@ blest_status blest_set_option(blest_handle h, int32_t key, int64_t value) {
         case BLEST_OPT_MIN_BLOCKS:
             if (value != 2 && value != 3) break;
             h->minb = (int)value;
+            return BLEST_OK;
+        case BLEST_OPT_STAGE_DEPTH:
+            if (value != 0 && value != 4 && value != 8) break;
+            h->depth = (int)value;
             return BLEST_OK;
         case BLEST_OPT_TEST_PHANTOM_BLOCK:
             if (value != 0 && value != 1) break;
@@ -555,6 +617,78 @@ blest_status blest_batch_bfs(blest_handle h, const int32_t* srcs_local, int32_t*
     return blest_bfs_multiroot(h, glob.data(), (int32_t)glob.size(), levels);
 }
 
+blest_status blest_batch_graph_capture(blest_handle h, int32_t* d_levels) {
+    if (!h) return fail(BLEST_ERR_INVALID_ARG, "NULL handle");
+    if (h->offsets.empty()) return fail(BLEST_ERR_INVALID_ARG, "not a batch handle");
+    if (h->n > 0 && !d_levels) return fail(BLEST_ERR_INVALID_ARG, "levels is NULL");
+    const int32_t G = (int32_t)h->offsets.size() - 1;
+    std::vector<int32_t> first;   // a default source per non-empty graph
+    for (int32_t g = 0; g < G; ++g)
+        if (h->offsets[g + 1] > h->offsets[g]) first.push_back((int32_t)h->offsets[g]);
+    const int32_t nr = (int32_t)first.size();
+    // the captured kernel reads its sources from a device list; keep at least
+    // kInlineRoots + 1 entries by repeating the first source (a repeated root is harmless)
+    const int32_t cap = std::max<int32_t>(nr, blest::kInlineRoots + 1);
+    if (nr == 0) return fail(BLEST_ERR_INVALID_ARG, "batch has no vertex");
+    cudaError_t e;
+    if (h->cgraph_exec) { cudaGraphExecDestroy(h->cgraph_exec); h->cgraph_exec = nullptr; }
+    if (h->cgraph) { cudaGraphDestroy(h->cgraph); h->cgraph = nullptr; }
+    cudaFree(h->d_graph_roots);
+    h->d_graph_roots = nullptr;
+    if (h->h_graph_roots) { cudaFreeHost(h->h_graph_roots); h->h_graph_roots = nullptr; }
+    if ((e = cudaMalloc(&h->d_graph_roots, sizeof(int32_t) * cap)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(graph roots)");
+    if ((e = cudaHostAlloc(&h->h_graph_roots, sizeof(int32_t) * cap, cudaHostAllocDefault)) != cudaSuccess)
+        return cuda_fail(e, "cudaHostAlloc(graph roots)");
+    if (!h->graph_done && (e = cudaEventCreateWithFlags(&h->graph_done, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "cudaEventCreate");
+    for (int32_t i = 0; i < cap; ++i) {
+        const int32_t v = first[i < nr ? i : 0];
+        h->h_graph_roots[i] = h->h_new_id.empty() ? v : h->h_new_id[v];
+    }
+    h->graph_nroots = cap;
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    if ((e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(e, "cudaStreamBeginCapture");
+    blest_status s = BLEST_OK;
+    e = cudaMemcpyAsync(h->d_graph_roots, h->h_graph_roots, sizeof(int32_t) * cap, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) s = cuda_fail(e, "capture: copy roots");
+    if (!s) s = enqueue_traversal(h, {}, d_levels, h->stream, h->d_graph_roots, cap);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(h->stream, &graph);
+    if (!s && e != cudaSuccess) s = cuda_fail(e, "cudaStreamEndCapture");
+    if (s) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    h->cgraph = graph;
+    if ((e = cudaGraphInstantiate(&h->cgraph_exec, graph, 0)) != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    return BLEST_OK;
+}
+
+blest_status blest_batch_graph_launch(blest_handle h, const int32_t* srcs_local, void* stream) {
+    if (!h) return fail(BLEST_ERR_INVALID_ARG, "NULL handle");
+    if (!h->cgraph_exec) return fail(BLEST_ERR_INVALID_ARG, "no captured batch traversal on this handle");
+    const int32_t G = (int32_t)h->offsets.size() - 1;
+    if (G > 0 && !srcs_local) return fail(BLEST_ERR_INVALID_ARG, "srcs is NULL");
+    cudaError_t e;
+    // the pinned source list is read by the previous replay's copy: wait for it
+    if ((e = cudaEventSynchronize(h->graph_done)) != cudaSuccess) return cuda_fail(e, "wait for previous replay");
+    int32_t i = 0;
+    for (int32_t g = 0; g < G; ++g) {
+        const int64_t ng = h->offsets[g + 1] - h->offsets[g];
+        if (ng == 0) continue;
+        if (srcs_local[g] < 0 || srcs_local[g] >= ng) return fail(BLEST_ERR_INVALID_ARG, "source outside its graph");
+        const int32_t v = (int32_t)(h->offsets[g] + srcs_local[g]);
+        h->h_graph_roots[i++] = h->h_new_id.empty() ? v : h->h_new_id[v];
+    }
+    for (int32_t j = i; j < h->graph_nroots; ++j) h->h_graph_roots[j] = h->h_graph_roots[0];
+    cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
+    if ((e = cudaGraphLaunch(h->cgraph_exec, st)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    if ((e = cudaEventRecord(h->graph_done, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    h->last_stream = st;
+    return BLEST_OK;
+}
+
 blest_status blest_msbfs_device(blest_handle h, const int32_t* srcs, int32_t k, int32_t* d_levels, void* stream) {
     if (!h) return fail(BLEST_ERR_INVALID_ARG, "NULL handle");
     if (k < 0 || (k > 0 && !srcs)) return fail(BLEST_ERR_INVALID_ARG, "bad source list");
@@ -631,16 +765,26 @@ blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, bles
     std::vector<int32_t> roots;
     blest_status s = map_sources(h, srcs, k, roots);
     if (s) return s;
-    struct Cand { int update, pull, unroll, minb, filter, bps; };
+    struct Cand { int update, pull, unroll, minb, filter, bps, depth; };
     std::vector<Cand> cands;
     for (int u : {BLEST_UPDATE_EAGER, BLEST_UPDATE_LAZY})
         for (int p : {BLEST_PULL_POPC, BLEST_PULL_MMA})
             for (int r : {1, 2})
                 for (int m : {2, 3})
                     for (int f : {0, 1})
-                        for (int b : {0, 1}) cands.push_back({u, p, r, m, f, b});
-    struct Opts { int update_opt, pull, unroll, minb, filter, blocks_per_sm; };
-    const Opts saved{h->update_opt, h->pull, h->unroll, h->minb, h->filter, h->blocks_per_sm};
+                        for (int b : {0, 1}) cands.push_back({u, p, r, m, f, b, 0});
+    for (int f : {0, 1})
+        for (int b : {0, 1}) {
+            cands.push_back({BLEST_UPDATE_LAZY, BLEST_PULL_POPC, 1, 2, f, b, 4});
+            cands.push_back({BLEST_UPDATE_LAZY, BLEST_PULL_POPC, 2, 2, f, b, 4});
+            cands.push_back({BLEST_UPDATE_LAZY, BLEST_PULL_POPC, 1, 2, f, b, 8});
+            cands.push_back({BLEST_UPDATE_LAZY, BLEST_PULL_POPC, 2, 2, f, b, 8});
+            cands.push_back({BLEST_UPDATE_LAZY, BLEST_PULL_POPC, 4, 2, f, b, 8});
+            cands.push_back({BLEST_UPDATE_LAZY, BLEST_PULL_MMA, 1, 2, f, b, 4});
+            cands.push_back({BLEST_UPDATE_LAZY, BLEST_PULL_MMA, 2, 2, f, b, 8});
+        }
+    struct Opts { int update_opt, pull, unroll, minb, filter, blocks_per_sm, depth; };
+    const Opts saved{h->update_opt, h->pull, h->unroll, h->minb, h->filter, h->blocks_per_sm, h->depth};
     cudaEvent_t e0, e1;
     cudaError_t e;
     if ((e = cudaEventCreate(&e0)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
@@ -650,7 +794,7 @@ blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, bles
     const int rule_update = h->stats.update;
     for (const Cand& c : cands) {
         h->update_opt = c.update; h->pull = c.pull; h->unroll = c.unroll; h->minb = c.minb;
-        h->filter = c.filter; h->blocks_per_sm = c.bps;
+        h->filter = c.filter; h->blocks_per_sm = c.bps; h->depth = c.depth;
         std::vector<int32_t> one(1);
         for (int pass = 0; pass < 2 && !s; ++pass) {
             if (pass == 1) cudaEventRecord(e0, h->stream);
@@ -666,21 +810,39 @@ blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, bles
         cudaEventElapsedTime(&ms, e0, e1);
         const double per = (double)ms / k;
         if (per < best) { best = per; bestc = c; }
-        if (c.update == rule_update && c.pull == BLEST_PULL_POPC && c.unroll == saved.unroll && c.minb == saved.minb &&
-            c.filter == 0 && c.bps == 0)
+        if (c.update == rule_update && c.pull == BLEST_PULL_POPC && c.unroll == 2 && c.minb == 2 &&
+            c.filter == 0 && c.bps == 0 && c.depth == 0)
             rule = per;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->update_opt = saved.update_opt; h->pull = saved.pull; h->unroll = saved.unroll; h->minb = saved.minb;
-    h->filter = saved.filter; h->blocks_per_sm = saved.blocks_per_sm;
+    h->filter = saved.filter; h->blocks_per_sm = saved.blocks_per_sm; h->depth = saved.depth;
     if (s) return s;
     h->update_opt = bestc.update; h->pull = bestc.pull; h->unroll = bestc.unroll; h->minb = bestc.minb;
-    h->filter = bestc.filter; h->blocks_per_sm = bestc.bps;
+    h->filter = bestc.filter; h->blocks_per_sm = bestc.bps; h->depth = bestc.depth;
     if (out) {
         out->update = bestc.update; out->pull = bestc.pull; out->unroll = bestc.unroll; out->min_blocks = bestc.minb;
-        out->visited_filter = bestc.filter; out->blocks_per_sm = bestc.bps; out->candidates = (int32_t)cands.size();
+        out->visited_filter = bestc.filter; out->blocks_per_sm = bestc.bps; out->stage_depth = bestc.depth;
+        out->candidates = (int32_t)cands.size();
         out->best_ms = best; out->rule_ms = rule;
+    }
+    return BLEST_OK;
+}
+
+blest_status blest_get_level_times(blest_handle h, uint64_t* times_ns, int32_t cap) {
+    if (!h || (cap > 0 && !times_ns)) return fail(BLEST_ERR_INVALID_ARG, "NULL argument");
+    blest_status s = sync_status(h);
+    if (s) return s;
+    unsigned int ctrl[16];
+    cudaError_t e = cudaMemcpy(ctrl, h->d_ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read run info");
+    const int32_t levels = (int32_t)ctrl[6];
+    if (!h->record) return fail(BLEST_ERR_INVALID_ARG, "level recording is off (BLEST_OPT_RECORD_LEVELS)");
+    const int32_t m = std::min<int32_t>(cap, 2 * std::min<int32_t>(levels, kLevelRecordCap - 2) + 4);
+    if (m > 0) {
+        e = cudaMemcpy(times_ns, h->d_level_times, sizeof(uint64_t) * (size_t)m, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "read level times");
     }
     return BLEST_OK;
 }

@@ -50,6 +50,7 @@ struct BfsArgs {
     unsigned long long* Q[3];
     Ctrl* ctrl;
     int32_t* level_sizes;
+    unsigned long long* level_times;      // with level_sizes: 2 globaltimer stamps per level
     int32_t level_cap;
     const int32_t* roots;                 // device list (used when nroots > kInlineRoots)
     int32_t nroots;
@@ -112,11 +113,14 @@ __device__ __forceinline__ void sweep(const BfsArgs& a, int lvl, unsigned long l
                 if (UPDATE == 1) Fout[t] = diff;
             }
         }
-        uint32_t d = diff;
-        while (d) {
-            const int b = __ffs(d) - 1;
-            a.L[t * kWarp + b] = lvl;
-            d &= d - 1;
+        // level writes, transposed: for each of the warp's 32 words with new
+        // rows, the 32 lanes store that word's 32 levels as one coalesced line
+        unsigned int pend = __ballot_sync(0xffffffffu, diff != 0u);
+        while (pend) {
+            const int src = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const uint32_t dw = __shfl_sync(0xffffffffu, diff, src);
+            if ((dw >> lane) & 1u) a.L[(t0 + src) * kWarp + lane] = lvl;
         }
         int st[4], ln[4];
         uint32_t pay[4];
@@ -135,9 +139,205 @@ __device__ __forceinline__ void sweep(const BfsArgs& a, int lvl, unsigned long l
     }
 }
 
+// ---------------------------------------------------------- hit handling
+// Each phase below issues its memory operations for all of a lane's hits
+// (up to 4 per virtual slice set) before it uses any result, so a lane waits
+// for one round trip per phase rather than one per hit.
+
+// Lazy marking (Algorithm 3, stage 1): set the V_next bit of every hit row,
+// skipping rows already in V_curr (visited filter).  V_curr only gains bits
+// during a traversal, so a stale (older) word can only let through a redundant
+// mark, never suppress a needed one.
+template <int NV>
+__device__ __forceinline__ void mark_rows(const BfsArgs& a, const int4 (&rows)[NV], unsigned int hm) {
+    int u[4 * NV];
+    uint32_t w[4 * NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        u[4 * i + 0] = rows[i].x; u[4 * i + 1] = rows[i].y; u[4 * i + 2] = rows[i].z; u[4 * i + 3] = rows[i].w;
+    }
+    if (a.filter) {
+#pragma unroll
+        for (int k = 0; k < 4 * NV; ++k) w[k] = (hm >> k) & 1u ? a.vcur[u[k] >> 5] : 0u;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4 * NV; ++k) w[k] = 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < 4 * NV; ++k) {
+        const uint32_t bit = 1u << (u[k] & 31);
+        if (((hm >> k) & 1u) && !(w[k] & bit)) atomicOr(&a.vnext[u[k] >> 5], bit);
+    }
+}
+
+// Eager update (Algorithm 2): for every hit row not yet visited, set its level
+// and its frontier bit with a returning atomicOr; the lane that sets the first
+// bit of a slice set's frontier byte enqueues that slice set's VSS range.
+template <int NV>
+__device__ __forceinline__ void eager_update(const BfsArgs& a, const int4 (&rows)[NV], unsigned int hm, int lvl,
+                                             uint32_t* Fnext, unsigned long long* Qout, unsigned int* qcount_next,
+                                             int lane) {
+    constexpr int K = 4 * NV;
+    int u[K];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        u[4 * i + 0] = rows[i].x; u[4 * i + 1] = rows[i].y; u[4 * i + 2] = rows[i].z; u[4 * i + 3] = rows[i].w;
+    }
+    // phase 1: visited filter on the V bitmap (a subset of the visited set)
+    if (a.filter) {
+        uint32_t w[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) w[k] = (hm >> k) & 1u ? a.vcur[u[k] >> 5] : 0u;
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (w[k] & (1u << (u[k] & 31))) hm &= ~(1u << k);
+    }
+    // phase 2: level check
+    int lv[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) lv[k] = (hm >> k) & 1u ? ld_cg(&a.L[u[k]]) : 0;
+    unsigned int newm = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        if (((hm >> k) & 1u) && lv[k] < 0) newm |= 1u << k;
+    // phase 3: claim
+    uint32_t old[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        old[k] = 0xFFFFFFFFu;
+        if ((newm >> k) & 1u) {
+            const uint32_t bit = 1u << (u[k] & 31);
+            a.L[u[k]] = lvl;
+            if (a.filter) atomicOr(&a.vcur[u[k] >> 5], bit);
+            old[k] = atomicOr(&Fnext[u[k] >> 5], bit);
+        }
+    }
+    // phase 4: the first setter of a slice set's byte enqueues its VSS range
+    int st[K], ln[K];
+    uint32_t pay[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        st[k] = 0; ln[k] = 0; pay[k] = 0;
+        if (((newm >> k) & 1u) && ((old[k] >> (u[k] & 24)) & 0xFFu) == 0) {
+            const int s2 = u[k] >> 3;
+            st[k] = __ldg(&a.real_ptrs[s2]);
+            ln[k] = __ldg(&a.real_ptrs[s2 + 1]) - st[k];
+            pay[k] = (uint32_t)s2;
+        }
+    }
+    warp_enqueue<K>(a.qcap, a.ctrl, Qout, qcount_next, st, ln, pay, lane);
+}
+
+// ---------------------------------------------------------- staged stage 1
+// Lazy stage 1 with a per-warp TMA ring: lane 0 streams the 512-byte row-id and
+// 128-byte mask tiles of the warp's upcoming virtual slice sets into a ring of
+// DEPTH shared-memory stages with cp.async.bulk (L2 evict-first: the BVSS
+// stream is read once per level and must not push the bitmaps and levels out
+// of L2), each stage completing on its own mbarrier.  The warp processes tile
+// k from shared memory while tiles k+1 .. k+DEPTH-1 are in flight, so memory
+// parallelism does not depend on registers or occupancy.  Queue entries are
+// fetched 32 at a time (one per lane) one window ahead.  Every mbarrier wait
+// is bounded by the barrier timeout.
+constexpr int kStageBytes = 512 + 128;
+
+template <int DEPTH>
+__host__ __device__ constexpr int ring_bytes_per_warp() { return DEPTH * (kStageBytes + 8); }
+
+// All 32 lanes wait for the phase of parity `parity` of the mbarrier, bounded
+// by timeout_ns; true when it completed.  Every lane takes part in each vote.
+__device__ __forceinline__ bool warp_wait_stage(uint32_t bar, uint32_t parity, uint64_t timeout_ns) {
+    bool done = mbar_try_wait(bar, parity);
+    if (__all_sync(0xffffffffu, done)) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (;;) {
+        if (!done) done = mbar_try_wait(bar, parity);
+        if (__all_sync(0xffffffffu, done)) return true;
+        if (__any_sync(0xffffffffu, global_timer_ns() - t0 > timeout_ns)) return false;
+    }
+}
+
+template <int PULL, int DEPTH, int U>
+__device__ __forceinline__ bool stage1_staged(const BfsArgs& a, const unsigned long long* __restrict__ Qin,
+                                              unsigned int qn, unsigned char* ring, uint32_t& uses, uint64_t pol,
+                                              int lane, int gwarp, int nwarps) {
+    static_assert(DEPTH >= 2 * U, "the ring must hold at least two groups of tiles");
+    int4* rows = reinterpret_cast<int4*>(ring);
+    uint32_t* msk = reinterpret_cast<uint32_t*>(ring + DEPTH * 512);
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(ring + DEPTH * kStageBytes);
+    const unsigned int nk = qn > (unsigned int)gwarp ? (qn - (unsigned int)gwarp + (unsigned int)nwarps - 1) / nwarps : 0u;
+    if (nk == 0) return true;
+    // queue entries k = 32 j + lane of window j, one window ahead (DEPTH + U <= 32)
+    auto load_window = [&](unsigned int j) -> unsigned long long {
+        const unsigned int k = j * 32u + (unsigned int)lane;
+        return k < nk ? ld_cg(&Qin[(size_t)gwarp + (size_t)k * (size_t)nwarps]) : 0ull;
+    };
+    unsigned int wcur = 0;
+    unsigned long long e0 = load_window(0);
+    unsigned long long e1 = nk > 32u ? load_window(1) : 0ull;
+    auto entry = [&](unsigned int k) -> unsigned long long {
+        const unsigned long long x0 = __shfl_sync(0xffffffffu, e0, (int)(k & 31u));
+        const unsigned long long x1 = __shfl_sync(0xffffffffu, e1, (int)(k & 31u));
+        return (k >> 5) == wcur ? x0 : x1;
+    };
+    auto issue = [&](unsigned int k) {
+        const unsigned long long ent = entry(k);
+        if (lane == 0) {
+            const uint32_t s = (uses + k) % DEPTH;
+            const uint32_t nu = (uint32_t)ent;
+            const uint32_t bar = smem_addr(&bars[s]);
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, kStageBytes);
+            bulk_g2s(smem_addr(&rows[s * 32]), a.row_ids4 + (size_t)nu * kWarp, 512, bar, pol);
+            bulk_g2s(smem_addr(&msk[s * 32]), a.masks + (size_t)nu * kWarp, 128, bar, pol);
+        }
+    };
+    const unsigned int pro = nk < (unsigned int)DEPTH ? nk : (unsigned int)DEPTH;
+    for (unsigned int k = 0; k < pro; ++k) issue(k);
+    for (unsigned int k = 0; k < nk; k += U) {
+        if ((k >> 5) != wcur) {   // U divides 32, so a group never straddles two windows
+            e0 = e1;
+            ++wcur;
+            e1 = (wcur + 1u) * 32u < nk ? load_window(wcur + 1u) : 0ull;
+        }
+        int4 r[U];
+        uint32_t m[U], alpha[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            r[j] = make_int4(0, 0, 0, 0);
+            m[j] = 0u;
+            alpha[j] = 0u;
+            if (k + j >= nk) continue;
+            const uint32_t g = uses + k + j;
+            const uint32_t s = g % DEPTH;
+            if (!warp_wait_stage(smem_addr(&bars[s]), (g / DEPTH) & 1u, a.timeout_ns)) {
+                // give up: record the timeout, then wait (bounded again) for this warp's
+                // other copies in flight so that none lands after the block has left
+                if (lane == 0) raise_error(a.ctrl, 6u);
+                for (unsigned int t = k + j + 1; t < nk && t < k + j + DEPTH; ++t)
+                    warp_wait_stage(smem_addr(&bars[(uses + t) % DEPTH]), ((uses + t) / DEPTH) & 1u, a.timeout_ns);
+                uses += nk;
+                return false;
+            }
+            r[j] = rows[s * 32 + lane];
+            m[j] = msk[s * 32 + lane];
+            alpha[j] = (uint32_t)(entry(k + j) >> 32);
+        }
+        __syncwarp();   // the stages may be refilled once every lane holds its tiles in registers
+#pragma unroll
+        for (int j = 0; j < U; ++j)
+            if (k + j + DEPTH < nk) issue(k + j + DEPTH);
+        unsigned int hm = 0;
+#pragma unroll
+        for (int j = 0; j < U; ++j) hm |= pull_hits<PULL>(m[j], alpha[j], lane) << (4 * j);
+        mark_rows<U>(a, r, hm);
+    }
+    uses += nk;
+    return true;
+}
+
 // -------------------------------------------------------------------- kernel
 
-template <int UPDATE, int PULL, int UNROLL>
+template <int UPDATE, int PULL, int UNROLL, int DEPTH>
 __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
     const int lane = threadIdx.x & 31;
     const int gtid = (int)(blockIdx.x * blockDim.x + threadIdx.x);
@@ -147,13 +347,28 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
     const unsigned int nblocks = gridDim.x;
     unsigned int gen = 0;
     Ctrl* ctrl = a.ctrl;
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    unsigned char* ring = dyn_smem + (threadIdx.x >> 5) * (DEPTH > 0 ? ring_bytes_per_warp<DEPTH>() : 0);
+    uint32_t ring_uses = 0;
+    uint64_t pol = 0;
+    if (DEPTH > 0) {
+        if (lane == 0) {
+            unsigned long long* bars = reinterpret_cast<unsigned long long*>(ring + DEPTH * kStageBytes);
+            for (int i = 0; i < DEPTH; ++i) mbar_init(smem_addr(&bars[i]), 1);
+            mbar_init_fence();
+        }
+        __syncwarp();
+        pol = l2_evict_first_policy();
+    }
 
+    if (gtid == 0 && a.level_sizes) a.level_times[1] = global_timer_ns();   // kernel entry (block 0)
     // level 0: mark the sources (V_curr, V_next, L were cleared before launch)
     for (int i = gtid; i < a.nroots; i += nthreads) {
         const int r = a.nroots <= kInlineRoots ? a.inline_roots[i] : a.roots[i];
         atomicOr(&a.vnext[r >> 5], 1u << (r & 31));
     }
     if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns)) return;
+    if (gtid == 0 && a.level_sizes) a.level_times[0] = global_timer_ns();
     sweep<UPDATE>(a, 0, a.Q[1], &ctrl->qcount[1], a.F[1]);
     unsigned int qn = 0, qprev = 0;
     if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns, &ctrl->qcount[1], &qn)) return;
@@ -163,7 +378,10 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
         if (qn > a.qcap) qn = a.qcap;   // only after an overflow, which already raised an error
         if (gtid == 0) {
             ctrl->qcount[(lvl + 2) & 3] = 0;
-            if (a.level_sizes && lvl - 1 < a.level_cap) a.level_sizes[lvl - 1] = (int32_t)qn;
+            if (a.level_sizes && lvl - 1 < a.level_cap) {
+                a.level_sizes[lvl - 1] = (int32_t)qn;
+                a.level_times[2 * lvl] = global_timer_ns();    // stage 1 of level lvl starts
+            }
         }
         const unsigned long long* Qin = a.Q[lvl % 3];
         if (UPDATE == 1) {
@@ -179,6 +397,10 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
         unsigned int* qcount_next = &ctrl->qcount[(lvl + 1) & 3];
 
         // stage 1: pull the queued virtual slice sets, round-robin over warps
+        if (DEPTH > 0) {
+            stage1_staged<PULL, (DEPTH > 0 ? DEPTH : 2 * UNROLL), UNROLL>(a, Qin, qn, ring, ring_uses, pol, lane,
+                                                                            gwarp, nwarps);
+        } else
         for (unsigned int base = (unsigned int)gwarp; base < qn; base += (unsigned int)nwarps * UNROLL) {
             unsigned long long ent[UNROLL];
             int4 rows[UNROLL];
@@ -197,63 +419,31 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
                 }
             }
             if (UPDATE == 2) {
+                unsigned int hm = 0;   // bit 4i+q: sub-slot q of VSS i hit
 #pragma unroll
-                for (int i = 0; i < UNROLL; ++i) {
-                    if (ent[i] == ~0ull) continue;
-                    const uint32_t alpha = (uint32_t)(ent[i] >> 32);
-                    const unsigned int h = pull_hits<PULL>(msk[i], alpha, lane);
-                    const int r4[4] = {rows[i].x, rows[i].y, rows[i].z, rows[i].w};
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        if (!(h & (1u << q))) continue;
-                        const int u = r4[q];
-                        const uint32_t bit = 1u << (u & 31);
-                        // visited filter: V_curr only gains bits during a traversal, so a
-                        // stale (older) word can only let through a redundant mark
-                        if (a.filter && (a.vcur[u >> 5] & bit)) continue;
-                        atomicOr(&a.vnext[u >> 5], bit);
-                    }
-                }
+                for (int i = 0; i < UNROLL; ++i)
+                    if (ent[i] != ~0ull) hm |= pull_hits<PULL>(msk[i], (uint32_t)(ent[i] >> 32), lane) << (4 * i);
+                mark_rows<UNROLL>(a, rows, hm);
             } else {
-                int st[4 * UNROLL], ln[4 * UNROLL];
-                uint32_t pay[4 * UNROLL];
+                uint32_t alpha[UNROLL];
 #pragma unroll
                 for (int i = 0; i < UNROLL; ++i) {
-                    uint32_t alpha = 0;
+                    alpha[i] = 0;
                     if (ent[i] != ~0ull) {
                         const uint32_t s = (uint32_t)(ent[i] >> 32);
-                        alpha = (ld_cg(&Fcur[s >> 2]) >> (8 * (s & 3))) & 0xFFu;
-                    }
-                    // every lane of the warp runs the pull (the MMA needs the full warp)
-                    const unsigned int h = ent[i] != ~0ull ? pull_hits<PULL>(msk[i], alpha, lane) : 0u;
-                    const int r4[4] = {rows[i].x, rows[i].y, rows[i].z, rows[i].w};
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int k = 4 * i + q;
-                        st[k] = 0; ln[k] = 0; pay[k] = 0;
-                        if (!(h & (1u << q))) continue;
-                        const int u = r4[q];
-                        const uint32_t bit = 1u << (u & 31);
-                        // visited filter on the V bitmap (a subset of the visited set, see lazy)
-                        if (a.filter && (a.vcur[u >> 5] & bit)) continue;
-                        if (ld_cg(&a.L[u]) < 0) {
-                            a.L[u] = lvl;
-                            if (a.filter) atomicOr(&a.vcur[u >> 5], bit);
-                            const uint32_t old = atomicOr(&Fnext[u >> 5], bit);
-                            if (((old >> (u & 24)) & 0xFFu) == 0) {
-                                const int s2 = u >> 3;
-                                st[k] = __ldg(&a.real_ptrs[s2]);
-                                ln[k] = __ldg(&a.real_ptrs[s2 + 1]) - st[k];
-                                pay[k] = (uint32_t)s2;
-                            }
-                        }
+                        alpha[i] = (ld_cg(&Fcur[s >> 2]) >> (8 * (s & 3))) & 0xFFu;
                     }
                 }
-                warp_enqueue<4 * UNROLL>(a.qcap, ctrl, Qout, qcount_next, st, ln, pay, lane);
+                unsigned int hm = 0;
+#pragma unroll
+                for (int i = 0; i < UNROLL; ++i)   // every lane runs the pull (the MMA needs the full warp)
+                    hm |= (ent[i] != ~0ull ? pull_hits<PULL>(msk[i], alpha[i], lane) : 0u) << (4 * i);
+                eager_update<UNROLL>(a, rows, hm, lvl, Fnext, Qout, qcount_next, lane);
             }
         }
         if (UPDATE == 2) {
             if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns)) return;
+            if (gtid == 0 && a.level_sizes && lvl - 1 < a.level_cap) a.level_times[2 * lvl + 1] = global_timer_ns();
             sweep<UPDATE>(a, lvl, Qout, qcount_next, nullptr);
         }
         unsigned int qnext = 0;
@@ -262,16 +452,23 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
         qprev = qn;
         qn = qnext;
     }
-    if (gtid == 0) ctrl->levels = (unsigned int)lvl;
+    if (gtid == 0) {
+        ctrl->levels = (unsigned int)lvl;
+        if (a.level_sizes && lvl < a.level_cap) a.level_times[2 * lvl + 2] = global_timer_ns();   // traversal end
+    }
     // undo the reordering: out[v] = L[new_id[v]]
     if (a.new_id) {
         for (int v = gtid; v < a.n; v += nthreads) a.out[v] = ld_cg(&a.L[__ldg(&a.new_id[v])]);
     }
+    if (a.level_sizes && lvl < a.level_cap) {
+        __syncthreads();
+        if (gtid == 0) a.level_times[2 * lvl + 3] = global_timer_ns();   // block 0 done with its share
+    }
 }
 
-template <int UPDATE, int PULL, int UNROLL, int MINB>
+template <int UPDATE, int PULL, int UNROLL, int MINB, int DEPTH>
 __global__ void __launch_bounds__(kBfsBlock, MINB) bfs_kernel(BfsArgs a) {
-    bfs_body<UPDATE, PULL, UNROLL>(a);
+    bfs_body<UPDATE, PULL, UNROLL, DEPTH>(a);
     fold_status(a.ctrl);
 }
 
@@ -290,27 +487,42 @@ __global__ void debug_pull_kernel(const uint32_t* __restrict__ masks, const uint
 
 // ---------------------------------------------------------------- launching
 
-template <int UPDATE, int PULL, int UNROLL, int MINB>
+template <int UPDATE, int PULL, int UNROLL, int MINB, int DEPTH>
 static void* kernel_ptr() {
-    return reinterpret_cast<void*>(&bfs_kernel<UPDATE, PULL, UNROLL, MINB>);
+    return reinterpret_cast<void*>(&bfs_kernel<UPDATE, PULL, UNROLL, MINB, DEPTH>);
 }
 
-static void* pick_kernel(int update, int pull, int unroll, int minb) {
-#define BLEST_PICK(U, P, R, M) \
-    if (update == U && pull == P && unroll == R && minb == M) return kernel_ptr<U, P, R, M>();
-#define BLEST_PICK_M(U, P, R) BLEST_PICK(U, P, R, 2) BLEST_PICK(U, P, R, 3)
+static void* pick_kernel(int update, int pull, int unroll, int minb, int depth) {
+#define BLEST_PICK(U, P, R, M, D) \
+    if (update == U && pull == P && unroll == R && minb == M && depth == D) return kernel_ptr<U, P, R, M, D>();
+#define BLEST_PICK_M(U, P, R) BLEST_PICK(U, P, R, 2, 0) BLEST_PICK(U, P, R, 3, 0)
     BLEST_PICK_M(1, 0, 1) BLEST_PICK_M(1, 0, 2) BLEST_PICK_M(1, 1, 1) BLEST_PICK_M(1, 1, 2)
     BLEST_PICK_M(2, 0, 1) BLEST_PICK_M(2, 0, 2) BLEST_PICK_M(2, 1, 1) BLEST_PICK_M(2, 1, 2)
+    // staged (TMA ring) lazy variants: ring depth 4 or 8, unroll = tiles consumed per step
+#define BLEST_PICK_S(P) BLEST_PICK(2, P, 1, 2, 4) BLEST_PICK(2, P, 2, 2, 4) BLEST_PICK(2, P, 1, 2, 8) \
+    BLEST_PICK(2, P, 2, 2, 8) BLEST_PICK(2, P, 4, 2, 8)
+    BLEST_PICK_S(0) BLEST_PICK_S(1)
+#undef BLEST_PICK_S
 #undef BLEST_PICK_M
 #undef BLEST_PICK
     return nullptr;
 }
 
-int bfs_max_blocks_per_sm(int update, int pull, int unroll, int minb) {
-    void* k = pick_kernel(update, pull, unroll, minb);
+static size_t ring_smem_bytes(int depth) {
+    if (depth == 4) return (size_t)(kBfsBlock / kWarp) * ring_bytes_per_warp<4>();
+    if (depth == 8) return (size_t)(kBfsBlock / kWarp) * ring_bytes_per_warp<8>();
+    return 0;
+}
+
+int bfs_max_blocks_per_sm(int update, int pull, int unroll, int minb, int depth) {
+    void* k = pick_kernel(update, pull, unroll, minb, depth);
     if (!k) return 0;
+    const size_t smem = ring_smem_bytes(depth);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBfsBlock, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBfsBlock, smem) != cudaSuccess) return 0;
     return nb;
 }
 
@@ -325,8 +537,9 @@ cudaError_t launch_debug_pull(const uint32_t* d_masks, const uint8_t* d_alpha, i
 }
 
 cudaError_t launch_bfs_kernel(const BfsLaunch& L, cudaStream_t stream) {
-    void* k = pick_kernel(L.update, L.pull, L.unroll, L.minb);
+    void* k = pick_kernel(L.update, L.pull, L.unroll, L.minb, L.depth);
     if (!k) return cudaErrorInvalidValue;
+    const size_t smem = ring_smem_bytes(L.depth);
     BfsArgs a;
     a.n = L.n;
     a.nwords = (L.n + 31) / 32;
@@ -341,6 +554,7 @@ cudaError_t launch_bfs_kernel(const BfsLaunch& L, cudaStream_t stream) {
     for (int i = 0; i < 3; ++i) { a.F[i] = L.F[i]; a.Q[i] = L.Q[i]; }
     a.ctrl = reinterpret_cast<Ctrl*>(L.ctrl);
     a.level_sizes = L.level_sizes;
+    a.level_times = L.level_times;
     a.level_cap = L.level_cap;
     a.roots = L.roots_device;
     a.nroots = L.nroots;
@@ -350,7 +564,7 @@ cudaError_t launch_bfs_kernel(const BfsLaunch& L, cudaStream_t stream) {
     a.phantom = L.phantom;
     a.filter = L.filter;
     void* args[] = {&a};
-    return cudaLaunchCooperativeKernel(k, dim3((unsigned)L.grid), dim3(kBfsBlock), args, 0, stream);
+    return cudaLaunchCooperativeKernel(k, dim3((unsigned)L.grid), dim3(kBfsBlock), args, smem, stream);
 }
 
 }  // namespace blest

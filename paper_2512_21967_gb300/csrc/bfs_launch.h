@@ -15,6 +15,7 @@ struct BfsLaunch {
     int unroll = 2;            // 1, 2
     int minb = 2;              // __launch_bounds__ minimum blocks per SM: 2 or 3
     int filter = 1;            // skip marks of rows already in the V bitmap
+    int depth = 0;             // lazy stage 1 through a per-warp TMA ring of this many stages (0, 4, 8)
     int grid = 0;              // blocks (co-resident)
     int32_t n = 0;
     unsigned int qcap = 0;     // entries per queue buffer
@@ -29,6 +30,7 @@ struct BfsLaunch {
     unsigned long long* Q[3] = {nullptr, nullptr, nullptr};
     void* ctrl = nullptr;      // 64-byte control block
     int32_t* level_sizes = nullptr;
+    unsigned long long* level_times = nullptr;   // 2 * level_cap + 2 entries
     int32_t level_cap = 0;
     const int32_t* roots_device = nullptr;
     int32_t roots_host[kInlineRoots] = {0};
@@ -38,7 +40,7 @@ struct BfsLaunch {
     unsigned int phantom = 0;
 };
 
-int bfs_max_blocks_per_sm(int update, int pull, int unroll, int minb);
+int bfs_max_blocks_per_sm(int update, int pull, int unroll, int minb, int depth);
 int bfs_threads_per_block();
 cudaError_t launch_bfs_kernel(const BfsLaunch& L, cudaStream_t stream);
 

@@ -113,6 +113,54 @@ __device__ __forceinline__ bool grid_barrier(Ctrl* ctrl, unsigned int nblocks, u
     return s_ok != 0;
 }
 
+// ------------------------------------------------ TMA bulk copies + mbarriers
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, unsigned int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Generic-proxy accesses to shared memory before a later async-proxy (TMA) write.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// 1-D bulk copy global -> shared (TMA), completing `bytes` on the mbarrier.
+// src, dst and bytes must be multiples of 16.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+        ::"r"(dst), "l"(src), "r"(bytes), "r"(bar), "l"(pol)
+        : "memory");
+}
+
 __device__ __forceinline__ void raise_error(Ctrl* ctrl, unsigned int code) {
     atomicCAS(&ctrl->error, 0u, code);
 }
@@ -158,6 +206,111 @@ __device__ __forceinline__ void warp_enqueue(unsigned int qcap, Ctrl* ctrl, unsi
         return;
     }
     unsigned int pos = base + incl - cnt;
+    const bool big = cnt > 64;
+    if (!big) {
+#pragma unroll
+        for (int q = 0; q < NS; ++q)
+            for (int i = 0; i < ln[q]; ++i)
+                Qout[pos++] = (unsigned long long)(unsigned int)(st[q] + i) | ((unsigned long long)pay[q] << 32);
+    }
+    unsigned int bigmask = __ballot_sync(0xffffffffu, big);
+    while (bigmask) {
+        const int src = __ffs(bigmask) - 1;
+        bigmask &= bigmask - 1;
+        unsigned int p = __shfl_sync(0xffffffffu, pos, src);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            const int s0 = __shfl_sync(0xffffffffu, st[q], src);
+            const int l0 = __shfl_sync(0xffffffffu, ln[q], src);
+            const uint32_t p0 = __shfl_sync(0xffffffffu, pay[q], src);
+            for (int i = lane; i < l0; i += kWarp)
+                Qout[p + i] = (unsigned long long)(unsigned int)(s0 + i) | ((unsigned long long)p0 << 32);
+            p += (unsigned int)l0;
+        }
+    }
+}
+
+// Warp-coalesced queue append for one range per lane: lane i appends the VSS
+// range [st, st + ln) with payload pay.  One atomicAdd per warp reserves the
+// warp's total; then entry j of the warp's output (j = lane, lane + 32, ...) is
+// written by lane j mod 32, which finds the lane owning j by a binary search
+// over the warp's exclusive prefix of ln (5 shuffle steps), so every store
+// instruction writes 32 consecutive entries (256 contiguous bytes).
+__device__ __forceinline__ void warp_enqueue_coalesced(unsigned int qcap, Ctrl* ctrl, unsigned long long* Qout,
+                                                       unsigned int* qcount, int st, int ln, uint32_t pay,
+                                                       int lane) {
+    const unsigned int incl = warp_inclusive_scan((unsigned int)ln, lane);
+    const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) return;
+    unsigned int base = 0;
+    if (lane == 31) base = atomicAdd(qcount, total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    if (base + total > qcap || base + total < base) {
+        if (lane == 0) raise_error(ctrl, 7u);
+        return;
+    }
+    const unsigned int excl = incl - (unsigned int)ln;
+    for (unsigned int j0 = 0; j0 < total; j0 += kWarp) {
+        const unsigned int j = j0 + (unsigned int)lane;
+        // owner = largest lane L with excl(L) <= j (lanes with ln = 0 share their
+        // successor's excl and are skipped because the search takes the largest)
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const unsigned int e = __shfl_sync(0xffffffffu, excl, lo + step);
+            if (e <= j) lo += step;
+        }
+        const unsigned int e_own = __shfl_sync(0xffffffffu, excl, lo);
+        const int s_own = __shfl_sync(0xffffffffu, st, lo);
+        const uint32_t p_own = __shfl_sync(0xffffffffu, pay, lo);
+        if (j < total)
+            Qout[base + j] = (unsigned long long)(unsigned int)(s_own + (int)(j - e_own)) |
+                             ((unsigned long long)p_own << 32);
+    }
+}
+
+// Block-aggregated queue append: the same contract as warp_enqueue, but the
+// block's warps first sum their counts in shared memory and one thread per
+// block reserves the block's range with a single atomicAdd, so a sweep issues
+// one contending atomic per block iteration instead of one per warp.  Every
+// thread of the block must call it (block-uniform control flow).
+template <int NS>
+__device__ __forceinline__ void block_enqueue(unsigned int qcap, Ctrl* ctrl, unsigned long long* Qout,
+                                              unsigned int* qcount, const int (&st)[NS], const int (&ln)[NS],
+                                              const uint32_t (&pay)[NS], int lane) {
+    __shared__ unsigned int s_warp[32];
+    __shared__ unsigned int s_base;
+    const int wid = (int)(threadIdx.x >> 5);
+    const int nw = (int)(blockDim.x >> 5);
+    unsigned int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < NS; ++q) cnt += (unsigned int)ln[q];
+    const unsigned int incl = warp_inclusive_scan(cnt, lane);
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int run = 0;
+        for (int w = 0; w < nw; ++w) {
+            const unsigned int t = s_warp[w];
+            s_warp[w] = run;
+            run += t;
+        }
+        unsigned int base = 0;
+        if (run) {
+            base = atomicAdd(qcount, run);
+            if (base + run > qcap || base + run < base) {
+                raise_error(ctrl, 7u);
+                base = 0xFFFFFFFFu;
+            }
+        }
+        s_base = base;
+    }
+    __syncthreads();
+    const unsigned int base = s_base;
+    const unsigned int woff = s_warp[wid];
+    __syncthreads();   // s_warp / s_base may be rewritten by the next call
+    if (base == 0xFFFFFFFFu) return;
+    unsigned int pos = base + woff + incl - cnt;
     const bool big = cnt > 64;
     if (!big) {
 #pragma unroll

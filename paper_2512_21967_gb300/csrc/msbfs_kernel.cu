@@ -42,6 +42,7 @@ struct MsArgs {
     unsigned long long* Q[3];
     int32_t* lint;       // k x n, BVSS ids
     int32_t* out;        // k x n, original ids (== lint when new_id is NULL)
+    uint32_t* dirty;     // one bit per slice set touched by a mark in a sparse level (cleared by the sweep)
     const int32_t* roots;
     Ctrl* ctrl;
     int32_t* level_sizes;
@@ -53,11 +54,10 @@ struct MsArgs {
 template <int W>
 __device__ __forceinline__ void ms_sweep(const MsArgs& a, int lvl, unsigned long long* Qout, unsigned int* qcount) {
     const int lane = threadIdx.x & 31;
-    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
     const size_t n = (size_t)a.n;
-    for (int u0 = gwarp * kWarp; u0 < a.n; u0 += nwarps * kWarp) {
-        const int u = u0 + lane;
+    // block-strided so that every warp of a block runs the same iterations (block_enqueue)
+    for (int b0 = (int)blockIdx.x * (int)blockDim.x; b0 < a.n; b0 += (int)(gridDim.x * blockDim.x)) {
+        const int u = b0 + (int)threadIdx.x;
         bool any = false;
         if (u < a.n) {
 #pragma unroll
@@ -79,15 +79,71 @@ __device__ __forceinline__ void ms_sweep(const MsArgs& a, int lvl, unsigned long
             }
         }
         const unsigned int ball = __ballot_sync(0xffffffffu, any);
-        int st[1] = {0}, ln[1] = {0};
-        uint32_t pay[1] = {0};
+        int st = 0, ln = 0;
+        uint32_t pay = 0;
         if ((lane & 7) == 0 && ((ball >> lane) & 0xFFu)) {
             const int s = u >> 3;
-            st[0] = __ldg(&a.real_ptrs[s]);
-            ln[0] = __ldg(&a.real_ptrs[s + 1]) - st[0];
-            pay[0] = (uint32_t)s;
+            st = __ldg(&a.real_ptrs[s]);
+            ln = __ldg(&a.real_ptrs[s + 1]) - st;
+            pay = (uint32_t)s;
         }
-        warp_enqueue<1>(a.qcap, a.ctrl, Qout, qcount, st, ln, pay, lane);
+        warp_enqueue_coalesced(a.qcap, a.ctrl, Qout, qcount, st, ln, pay, lane);
+    }
+}
+
+// Sparse finalisation: only the slice sets marked dirty in stage 1 are swept.
+// Warp w takes dirty words t = w, w + nwarps, ...; lane b handles slice set
+// 32 t + b when its bit is set: the 8 vertices' words get diff = V_next ^ V_curr
+// (written to the frontier, zero included, so every vertex of a queued slice set
+// has a current frontier word), levels, and the enqueue.  Slice sets outside
+// the dirty set keep stale frontier words, but they are not queued, so stage 1
+// never reads them.
+template <int W>
+__device__ __forceinline__ void ms_sweep_sparse(const MsArgs& a, int lvl, unsigned long long* Qout,
+                                                unsigned int* qcount) {
+    const int lane = threadIdx.x & 31;
+    const int wpb = (int)(blockDim.x >> 5);
+    const size_t n = (size_t)a.n;
+    const int nss = (a.n + 7) >> 3;
+    const int dwords = (nss + 31) >> 5;
+    // block-strided over dirty words so that every warp of a block runs the same iterations
+    for (int t0 = (int)blockIdx.x * wpb; t0 < dwords; t0 += (int)gridDim.x * wpb) {
+        const int t = t0 + (int)(threadIdx.x >> 5);
+        const uint32_t dw = t < dwords ? ld_cg(&a.dirty[t]) : 0u;
+        if (lane == 0 && dw) a.dirty[t] = 0u;
+        const int s = 32 * t + lane;
+        bool any = false;
+        if ((dw >> lane) & 1u) {
+            for (int j = 0; j < 8; ++j) {
+                const int u = 8 * s + j;
+                if (u >= a.n) break;
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    const size_t idx = (size_t)u * W + w;
+                    const unsigned long long nx = ld_cg(&a.vnext[idx]);
+                    const unsigned long long cu = ld_cg(&a.vcur[idx]);
+                    unsigned long long d = nx ^ cu;
+                    a.front[idx] = d;
+                    if (d) {
+                        a.vcur[idx] = nx;
+                        any = true;
+                        while (d) {
+                            const int b = __ffsll((long long)d) - 1;
+                            a.lint[(size_t)(w * 64 + b) * n + (size_t)u] = lvl;
+                            d &= d - 1;
+                        }
+                    }
+                }
+            }
+        }
+        int st = 0, ln = 0;
+        uint32_t pay = 0;
+        if (any) {
+            st = __ldg(&a.real_ptrs[s]);
+            ln = __ldg(&a.real_ptrs[s + 1]) - st;
+            pay = (uint32_t)s;
+        }
+        warp_enqueue_coalesced(a.qcap, a.ctrl, Qout, qcount, st, ln, pay, lane);
     }
 }
 
@@ -113,6 +169,8 @@ __device__ __forceinline__ void ms_body(const MsArgs& a) {
     int lvl = 1;
     for (;; ++lvl) {
         if (qn > a.qcap) qn = a.qcap;   // only after an overflow, which already raised an error
+        // few queued VSSs: track the touched slice sets and sweep only those
+        const bool sparse = (unsigned long long)qn * 128ull <= (unsigned long long)a.n;
         if (gtid == 0) {
             ctrl->qcount[(lvl + 2) & 3] = 0;
             if (a.level_sizes && lvl - 1 < a.level_cap) a.level_sizes[lvl - 1] = (int32_t)qn;
@@ -163,11 +221,15 @@ __device__ __forceinline__ void ms_body(const MsArgs& a) {
                     // sources that already reached the row need no mark; V_curr only gains
                     // bits during a traversal, so a stale word can only let a mark through
                     const unsigned long long fresh = y[q][w] & ~a.vcur[(size_t)r4[q] * W + w];
-                    if (fresh) atomicOr(&a.vnext[(size_t)r4[q] * W + w], fresh);
+                    if (fresh) {
+                        atomicOr(&a.vnext[(size_t)r4[q] * W + w], fresh);
+                        if (sparse) atomicOr(&a.dirty[r4[q] >> 8], 1u << ((r4[q] >> 3) & 31));
+                    }
                 }
         }
         if (!grid_barrier(ctrl, gridDim.x, a.phantom, gen, a.timeout_ns)) return;
-        ms_sweep<W>(a, lvl, Qout, qcount_next);
+        if (sparse) ms_sweep_sparse<W>(a, lvl, Qout, qcount_next);
+        else ms_sweep<W>(a, lvl, Qout, qcount_next);
         unsigned int qnext = 0;
         if (!grid_barrier(ctrl, gridDim.x, a.phantom, gen, a.timeout_ns, qcount_next, &qnext)) return;
         if (qnext == 0) break;
@@ -211,6 +273,7 @@ void free_msbfs_state(MsbfsState& s) {
     cudaFree(s.Q);
     cudaFree(s.lint);
     cudaFree(s.roots);
+    cudaFree(s.dirty);
     s = MsbfsState();
 }
 
@@ -231,10 +294,13 @@ int run_msbfs(MsbfsState& s, const MsbfsLaunchCommon& c, const std::vector<int32
         if ((e = grow(s.Q, s.qcap, std::max<int64_t>(c.nvss, 1), 3)) != cudaSuccess) break;
         if (c.new_id && (e = grow(s.lint, s.lint_cap, (int64_t)k * c.n)) != cudaSuccess) break;
         if ((e = grow(s.roots, s.roots_cap, k)) != cudaSuccess) break;
+        const int64_t dwords = ((int64_t)c.nss + 31) / 32;
+        if ((e = grow(s.dirty, s.dirty_cap, dwords)) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(s.roots, roots.data() + i0, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
         cudaMemsetAsync(c.ctrl, 0, kCtrlClearBytes, st);
         cudaMemsetAsync(s.vcur, 0, sizeof(unsigned long long) * (size_t)words, st);
         cudaMemsetAsync(s.vnext, 0, sizeof(unsigned long long) * (size_t)words, st);
+        cudaMemsetAsync(s.dirty, 0, sizeof(uint32_t) * (size_t)dwords, st);
         MsArgs a;
         a.n = c.n;
         a.k = k;
@@ -251,6 +317,7 @@ int run_msbfs(MsbfsState& s, const MsbfsLaunchCommon& c, const std::vector<int32
         a.lint = c.new_id ? s.lint : out;
         a.out = out;
         a.roots = s.roots;
+        a.dirty = s.dirty;
         a.ctrl = reinterpret_cast<Ctrl*>(c.ctrl);
         a.level_sizes = c.level_sizes;
         a.level_cap = c.level_cap;

@@ -20,6 +20,8 @@ struct MsbfsState {
     int32_t* lint = nullptr;
     int64_t roots_cap = 0;
     int32_t* roots = nullptr;
+    int64_t dirty_cap = 0;             // words of the dirty-slice-set bitmap
+    uint32_t* dirty = nullptr;
 };
 
 struct MsbfsLaunchCommon {

@@ -239,3 +239,66 @@ def grid_workload(side: int, nsrc: int = 64, p: float = 0.9, seed_graph: int = 3
     pool = largest_component_pool(g)
     srcs = np.concatenate([[corner], pick_sources(g, nsrc, seed_src, pool)]).astype(np.int32)
     return g, srcs
+
+
+def batch_workload(num: int = 128, seed: int = 4, rmat_scales=(10, 18), grid_sides=(64, 1024)):
+    """Many graphs of uneven size: even indices are R-MAT graphs with scale drawn
+    uniformly from rmat_scales (inclusive, edgefactor 16), odd indices are grids
+    with side drawn uniformly from grid_sides (inclusive, keep probability 0.9).
+    Graph i uses stream seed*1000 + i; its size is draw i of stream `seed`; its one
+    source is draw 0 of stream seed*1000 + 500 + i over its largest component
+    (grids) or its degree > 0 vertices (R-MAT).  Returns [(graph, source, kind)]."""
+    sz = draws(seed, 0, num)
+    out = []
+    for i in range(num):
+        gs = seed * 1000 + i
+        if i % 2 == 0:
+            lo, hi = rmat_scales
+            scale = lo + int(bounded(sz[i:i + 1], hi - lo + 1)[0])
+            g = rmat_graph(scale, 16, gs)
+            src = int(pick_sources(g, 1, seed * 1000 + 500 + i)[0])
+            out.append((g, src, "rmat"))
+        else:
+            lo, hi = grid_sides
+            side = lo + int(bounded(sz[i:i + 1], hi - lo + 1)[0])
+            g, _ = grid_graph(side, 0.9, gs)
+            src = int(pick_sources(g, 1, seed * 1000 + 500 + i, largest_component_pool(g))[0])
+            out.append((g, src, "grid"))
+    return out
+
+
+def serving_workload(seed: int = 5, rmat_scales=(16, 22), grid_sides=(256, 2048), num_rmat: int = 8,
+                     num_grid: int = 8):
+    """Resident graph set of the serving workload: num_rmat R-MAT graphs with
+    scales spread evenly over rmat_scales and num_grid grids with sides spread
+    evenly over grid_sides (keep probability 0.9); graph i uses stream
+    seed*1000 + i.  Returns [(graph, source pool, kind)]."""
+    out = []
+    for i in range(num_rmat):
+        scale = rmat_scales[0] + round(i * (rmat_scales[1] - rmat_scales[0]) / max(1, num_rmat - 1))
+        g = rmat_graph(scale, 16, seed * 1000 + i)
+        out.append((g, np.nonzero(g.degrees() > 0)[0].astype(np.int32), "rmat"))
+    for i in range(num_grid):
+        side = grid_sides[0] + round(i * (grid_sides[1] - grid_sides[0]) / max(1, num_grid - 1))
+        g, _ = grid_graph(side, 0.9, seed * 1000 + num_rmat + i)
+        out.append((g, largest_component_pool(g), "grid"))
+    return out
+
+
+def query_stream(num: int, num_graphs: int, rate: float, seed: int, pools, max_sources: int = 32):
+    """Poisson stream: query i arrives at the sum of i+1 exponential gaps of mean
+    1/rate (inverse CDF of draw 3i of stream `seed`), targets graph
+    bounded(draw 3i+1, num_graphs) and has 1 + bounded(draw 3i+2, max_sources)
+    sources drawn from that graph's pool (stream seed + 1 + i)."""
+    d = draws(seed, 0, 3 * num)
+    u = (d[0::3] >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+    gaps = -np.log1p(-u) / rate
+    t = np.cumsum(gaps)
+    gi = bounded(d[1::3], num_graphs).astype(np.int64)
+    ks = 1 + bounded(d[2::3], max_sources).astype(np.int64)
+    out = []
+    for i in range(num):
+        pool = pools[gi[i]]
+        idx = bounded(draws(seed + 1 + i, 0, int(ks[i])), len(pool)).astype(np.int64)
+        out.append((float(t[i]), int(gi[i]), pool[idx].astype(np.int32)))
+    return out

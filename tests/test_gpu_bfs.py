@@ -104,13 +104,17 @@ def test_rmat16_all_sources_all_modes(cfg1, order):
         for upd, pull in MODES:
             blest.blest_set_option(h, blest.BLEST_OPT_UPDATE, upd)
             blest.blest_set_option(h, blest.BLEST_OPT_PULL, pull)
-            for unroll, minb, filt in ((2, 2, 1), (1, 3, 0), (2, 3, 1), (1, 2, 0)):
+            variants = [(2, 2, 1, 0), (1, 3, 0, 0), (2, 3, 1, 0), (1, 2, 0, 0)]
+            if upd == blest.BLEST_UPDATE_LAZY:
+                variants += [(1, 2, 1, 4), (1, 2, 0, 8), (1, 2, 1, 8)]
+            for unroll, minb, filt, depth in variants:
                 blest.blest_set_option(h, blest.BLEST_OPT_UNROLL, unroll)
                 blest.blest_set_option(h, blest.BLEST_OPT_MIN_BLOCKS, minb)
                 blest.blest_set_option(h, blest.BLEST_OPT_VISITED_FILTER, filt)
+                blest.blest_set_option(h, blest.BLEST_OPT_STAGE_DEPTH, depth)
                 for i, s in enumerate(srcs):
                     got = blest.blest_bfs(h, int(s))
-                    assert np.array_equal(got, exp[i]), f"mode {(upd, pull, unroll, minb, filt)} source {s}"
+                    assert np.array_equal(got, exp[i]), f"mode {(upd, pull, unroll, minb, filt, depth)} source {s}"
     finally:
         blest.blest_destroy(h)
 
@@ -123,8 +127,9 @@ def test_queue_sizes_match_replay(cfg1):
     try:
         b = ob.build(g.n, g.row_ptr, g.col_idx)
         blest.blest_set_option(h, blest.BLEST_OPT_RECORD_LEVELS, 1)
-        for upd in (blest.BLEST_UPDATE_EAGER, blest.BLEST_UPDATE_LAZY):
+        for upd, depth in ((blest.BLEST_UPDATE_EAGER, 0), (blest.BLEST_UPDATE_LAZY, 0), (blest.BLEST_UPDATE_LAZY, 8)):
             blest.blest_set_option(h, blest.BLEST_OPT_UPDATE, upd)
+            blest.blest_set_option(h, blest.BLEST_OPT_STAGE_DEPTH, depth)
             for i in range(4):
                 blest.blest_bfs(h, int(srcs[i]))
                 info, sizes = blest.blest_get_run_info(h, 4096)
@@ -298,5 +303,48 @@ def test_device_api_with_torch_stream(torch_cuda):
         blest.blest_msbfs_device(h, srcs, out2, stream=s)
         blest.blest_sync(h)
         assert np.array_equal(out2.cpu().numpy(), exp)
+    finally:
+        blest.blest_destroy(h)
+
+
+def test_autotune_keeps_levels_exact(gpu):
+    g, srcs = synth.rmat_workload(13, 8, seed_graph=7, seed_src=7)
+    exp = oracle.msbfs_levels(g.n, g.row_ptr, g.col_idx, srcs, threads=8)
+    h = blest.blest_graph_create(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_COMPRESS)
+    try:
+        r = blest.blest_autotune(h, srcs[:3])
+        assert r["candidates"] >= 64 and 0 < r["best_ms"] <= r["rule_ms"]
+        for i, s in enumerate(srcs):
+            assert np.array_equal(blest.blest_bfs(h, int(s)), exp[i])
+    finally:
+        blest.blest_destroy(h)
+
+
+def test_batch_graph_capture_replay(torch_cuda):
+    """One captured CUDA graph replayed with new sources gives every graph's own
+    single-source levels."""
+    torch = torch_cuda
+    graphs, orders = [], []
+    for i in range(20):
+        if i % 2 == 0:
+            graphs.append(synth.rmat_graph(6 + i % 7, 16, seed=400 + i))
+            orders.append(blest.BLEST_ORDER_COMPRESS)
+        else:
+            graphs.append(synth.grid_graph(10 + 3 * i, 0.9, seed=500 + i)[0])
+            orders.append(blest.BLEST_ORDER_BANDWIDTH)
+    h = blest.blest_batch_create([(g.n, g.row_ptr, g.col_idx) for g in graphs], orders)
+    try:
+        total = sum(g.n for g in graphs)
+        out = torch.empty(total, dtype=torch.int32, device="cuda")
+        blest.blest_batch_graph_capture(h, out)
+        for rep in range(3):
+            srcs = [int(synth.pick_sources(g, 1, seed=600 + 31 * rep + i)[0]) for i, g in enumerate(graphs)]
+            blest.blest_batch_graph_launch(h, srcs)
+            blest.blest_sync(h)
+            got = out.cpu().numpy()
+            off = 0
+            for g, s in zip(graphs, srcs):
+                assert np.array_equal(got[off:off + g.n], oracle.bfs_levels(g.n, g.row_ptr, g.col_idx, s))
+                off += g.n
     finally:
         blest.blest_destroy(h)
