@@ -82,10 +82,13 @@ typedef enum {
                                         (4 only with the 8-stage TMA ring) */
     BLEST_OPT_TEST_PHANTOM_BLOCK = 6,/* testing: 1 = every barrier waits for one block that does not
                                         exist, so the next traversal must end in BLEST_ERR_TIMEOUT */
-    BLEST_OPT_VISITED_FILTER = 7,    /* 1 (default) = test a visited bitmap before marking a row */
+    BLEST_OPT_VISITED_FILTER = 7,    /* 1 (default) = test a visited bitmap before marking a row; 2 = lazy
+                                        update also skips rows already marked at this level; 0 = off */
     BLEST_OPT_MIN_BLOCKS = 8,        /* kernel variant compiled for 2 (default) or 3 blocks per SM */
-    BLEST_OPT_STAGE_DEPTH = 9        /* lazy stage 1 through a per-warp TMA ring of 4 or 8 stages; 0 = plain
-                                        128-bit loads (default); used with BLEST_OPT_MIN_BLOCKS = 2 */
+    BLEST_OPT_STAGE_DEPTH = 9        /* lazy stage 1 prefetch: 0 = none (default); 2 = the next group's tiles
+                                        in registers while the current group's hits are handled; 4 or 8 = a
+                                        per-warp TMA ring of that many stages in shared memory; used with
+                                        BLEST_OPT_MIN_BLOCKS = 2 */
 } blest_option;
 
 /* Creation parameters; pass NULL to blest_graph_create_ex for the defaults. */
@@ -167,6 +170,13 @@ blest_status blest_get_stats(blest_handle h, blest_stats* out);
  * written in original ids.  Blocks until done.
  * Errors: INVALID_ARG (NULL handle/levels, src outside [0, n)), TIMEOUT, INTERNAL, CUDA. */
 blest_status blest_bfs(blest_handle h, int32_t src, int32_t* levels);
+
+/* BFS tree (the parent-array form of Section 2) of the traversal from src:
+ * levels as blest_bfs, and parents (host, n int32): parents[v] = the smallest
+ * original id among the neighbours of v one level closer to src (a unique
+ * choice), parents[src] = src, -1 for unreached vertices.  Computed by one
+ * extra pass over the BVSS after the traversal.  Errors: as blest_bfs. */
+blest_status blest_bfs_parents(blest_handle h, int32_t src, int32_t* levels, int32_t* parents);
 
 /* k independent BFS runs from srcs[0..k) (host array), as one Boolean SpMM per
  * level over an n x k frontier bit-matrix (Section 2, multi-source form).

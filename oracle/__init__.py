@@ -104,6 +104,22 @@ def msbfs_levels(n: int, row_ptr, col_idx, srcs, threads: int = 1) -> np.ndarray
     return out[:, :n]
 
 
+def bfs_parents(n: int, row_ptr, col_idx, src: int) -> tuple[np.ndarray, np.ndarray]:
+    """BFS tree in the parent-array form of Section 2 with a unique choice:
+    parent[v] = smallest id among the neighbours of v at level[v] - 1;
+    parent[src] = src; -1 for unreached vertices.  From the oracle levels."""
+    lv = bfs_levels(n, row_ptr, col_idx, src)
+    rp = np.asarray(row_ptr, dtype=np.int64)
+    ci = np.asarray(col_idx, dtype=np.int64)
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(rp))
+    ok = (lv[rows] >= 1) & (lv[ci] == lv[rows] - 1)
+    par = np.full(n, np.iinfo(np.int64).max, dtype=np.int64)
+    np.minimum.at(par, rows[ok], ci[ok])
+    par = np.where(lv < 0, -1, par)
+    par[src] = src
+    return lv, par.astype(np.int32)
+
+
 def reached_edges(row_ptr, levels: np.ndarray) -> int:
     """Undirected edges in the reached component: sum of degrees of reached
     vertices / 2 (Graph500-style TEPS numerator on a loop-free, deduplicated

@@ -22,7 +22,7 @@ __all__ = [
     "BLEST_ORDER_NONE", "BLEST_ORDER_COMPRESS", "BLEST_ORDER_BANDWIDTH", "BLEST_ORDER_AUTO",
     "BLEST_UPDATE_AUTO", "BLEST_UPDATE_EAGER", "BLEST_UPDATE_LAZY", "BLEST_PULL_POPC", "BLEST_PULL_MMA",
     "blest_graph_create", "blest_graph_create_ex", "blest_batch_create", "blest_destroy", "blest_set_option",
-    "blest_get_stats", "blest_bfs", "blest_msbfs", "blest_bfs_multiroot", "blest_batch_bfs",
+    "blest_get_stats", "blest_bfs", "blest_bfs_parents", "blest_msbfs", "blest_bfs_multiroot", "blest_batch_bfs",
     "blest_batch_graph_capture", "blest_batch_graph_launch", "blest_bfs_device",
     "blest_msbfs_device", "blest_bfs_multiroot_device", "blest_sync", "blest_get_run_info", "blest_get_level_times",
     "blest_export",
@@ -45,7 +45,8 @@ BLEST_ARRAY_MASKS, BLEST_ARRAY_NEW_ID, BLEST_ARRAY_VSS_COUNT = 3, 4, 5
 
 EXPORTED_SYMBOLS = [
     "blest_graph_create", "blest_graph_create_ex", "blest_batch_create", "blest_destroy", "blest_set_option",
-    "blest_get_stats", "blest_bfs", "blest_msbfs", "blest_bfs_multiroot", "blest_batch_bfs", "blest_batch_graph_capture",
+    "blest_get_stats", "blest_bfs", "blest_bfs_parents", "blest_msbfs", "blest_bfs_multiroot", "blest_batch_bfs",
+    "blest_batch_graph_capture",
     "blest_batch_graph_launch", "blest_bfs_device", "blest_msbfs_device", "blest_bfs_multiroot_device", "blest_sync",
     "blest_get_run_info", "blest_get_level_times", "blest_autotune",
     "blest_export_size", "blest_export", "blest_compute_order", "blest_is_social", "blest_debug_pull",
@@ -124,6 +125,7 @@ def lib():
             "blest_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(Stats)]),
             "blest_bfs": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p]),
             "blest_msbfs": (ctypes.c_int, [_vp, _i32p, ctypes.c_int32, _i32p]),
+            "blest_bfs_parents": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p, _i32p]),
             "blest_bfs_multiroot": (ctypes.c_int, [_vp, _i32p, ctypes.c_int32, _i32p]),
             "blest_batch_bfs": (ctypes.c_int, [_vp, _i32p, _i32p]),
             "blest_batch_graph_capture": (ctypes.c_int, [_vp, _vp]),
@@ -272,6 +274,14 @@ def blest_bfs(h: int, src: int, levels: np.ndarray | None = None) -> np.ndarray:
         raise ValueError("levels must be a contiguous int32 array of n entries")
     _check(lib().blest_bfs(h, int(src), _ptr(out)), "blest_bfs")
     return out
+
+
+def blest_bfs_parents(h: int, src: int) -> tuple[np.ndarray, np.ndarray]:
+    n = _n_of(h)
+    lv = np.empty(n, np.int32)
+    par = np.empty(n, np.int32)
+    _check(lib().blest_bfs_parents(h, int(src), _ptr(lv), _ptr(par)), "blest_bfs_parents")
+    return lv, par
 
 
 def blest_msbfs(h: int, srcs, levels: np.ndarray | None = None) -> np.ndarray:

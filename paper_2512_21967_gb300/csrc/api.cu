@@ -73,6 +73,10 @@ struct blest_graph {
     unsigned int* d_ctrl = nullptr;      // 256-byte control block (device_common.cuh layout)
     int32_t* d_level_sizes = nullptr;
     unsigned long long* d_level_times = nullptr;
+    int32_t* d_old_of = nullptr;         // BVSS id -> original id (parent output), made on first use
+    int32_t* d_cand = nullptr;           // parent candidates (BVSS ids), made on first use
+    int32_t* d_parents = nullptr;
+    bool need_internal_levels = false;   // the next traversal must leave L cleared for unreached rows
     int32_t* d_roots = nullptr;
     int64_t roots_cap = 0;
     cudaStream_t stream = nullptr;
@@ -125,6 +129,9 @@ void free_handle(blest_graph* h) {
     cudaFree(h->d_ctrl);
     cudaFree(h->d_level_sizes);
     cudaFree(h->d_level_times);
+    cudaFree(h->d_old_of);
+    cudaFree(h->d_cand);
+    cudaFree(h->d_parents);
     cudaFree(h->d_roots);
     if (h->cgraph_exec) cudaGraphExecDestroy(h->cgraph_exec);
     if (h->cgraph) cudaGraphDestroy(h->cgraph);
@@ -255,10 +262,12 @@ blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots
     L.unroll = h->unroll;
     L.minb = h->minb;
     L.filter = h->filter;
+    if (L.update == 1 && L.filter == 2) L.filter = 1;     // V_next is not used by the eager update
     // the TMA ring exists for the lazy kernel compiled for 2 blocks per SM
     L.depth = (L.update == 2 && L.minb == 2) ? h->depth : 0;
     if (L.depth == 0 && L.unroll > 2) L.unroll = 2;       // unroll 4 exists only for the TMA ring
     if (L.depth == 4 && L.unroll > 2) L.unroll = 2;       // a 4-stage ring holds two groups of 2
+    if (L.depth == 2 && L.unroll > 2) L.unroll = 2;       // the register double buffer exists for 1 and 2
     L.grid = pick_grid(h, L.update, L.pull, L.unroll, L.minb, L.depth);
     if (L.grid <= 0) return fail(BLEST_ERR_CUDA, "no co-resident grid for the traversal kernel");
     L.n = h->n;
@@ -268,6 +277,9 @@ blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots
     L.masks = h->bvss.masks;
     L.new_id = h->d_new_id;
     L.levels_internal = h->d_new_id ? h->d_L : d_out;
+    // a lazy traversal with a reordering leaves L uncleared: its epilogue takes
+    // the reached rows from V_curr (the parent pass needs cleared levels)
+    L.levels_from_bitmap = (L.update == 2 && h->d_new_id && !h->need_internal_levels) ? 1 : 0;
     L.vcur = h->d_vcur;
     L.vnext = h->d_vnext;
     const size_t nw = (size_t)h->nwords();
@@ -306,7 +318,7 @@ blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots
     L.timeout_ns = (uint64_t)h->timeout_us * 1000ull;
     L.phantom = h->phantom ? 1u : 0u;
     cudaMemsetAsync(h->d_ctrl, 0, kCtrlClearBytes, st);
-    cudaMemsetAsync(L.levels_internal, 0xFF, sizeof(int32_t) * (size_t)h->n, st);
+    if (!L.levels_from_bitmap) cudaMemsetAsync(L.levels_internal, 0xFF, sizeof(int32_t) * (size_t)h->n, st);
     cudaMemsetAsync(h->d_vcur, 0, sizeof(uint32_t) * nw, st);
     cudaMemsetAsync(h->d_vnext, 0, sizeof(uint32_t) * nw, st);
     if (L.update == 1) cudaMemsetAsync(h->d_F, 0, sizeof(uint32_t) * 3 * nw, st);
@@ -351,6 +363,9 @@ blest_status sync_status(blest_graph* h) {
 }  // namespace
 
 namespace blest {
+cudaError_t launch_parents(const int32_t* v2r, const int32_t* row_ids, const uint32_t* masks, int64_t nvss,
+                           const int32_t* L, const int32_t* old_of, const int32_t* new_id, int32_t n, int32_t* cand,
+                           int32_t* out, cudaStream_t st);   // parents.cu
 // Read-only view of a handle's device arrays for the query server (server.cu).
 struct HandleView {
     int32_t n;
@@ -523,7 +538,7 @@ blest_status blest_set_option(blest_handle h, int32_t key, int64_t value) {
             h->unroll = (int)value;
             return BLEST_OK;
         case BLEST_OPT_VISITED_FILTER:
-            if (value != 0 && value != 1) break;
+            if (value < 0 || value > 2) break;
             h->filter = (int)value;
             return BLEST_OK;
         case BLEST_OPT_MIN_BLOCKS:
@@ -531,7 +546,7 @@ blest_status blest_set_option(blest_handle h, int32_t key, int64_t value) {
             h->minb = (int)value;
             return BLEST_OK;
         case BLEST_OPT_STAGE_DEPTH:
-            if (value != 0 && value != 4 && value != 8) break;
+            if (value != 0 && value != 2 && value != 4 && value != 8) break;
             h->depth = (int)value;
             return BLEST_OK;
         case BLEST_OPT_TEST_PHANTOM_BLOCK:
@@ -587,6 +602,34 @@ blest_status blest_bfs(blest_handle h, int32_t src, int32_t* levels) {
     if (s) return s;
     cudaError_t e = cudaMemcpyAsync(levels, h->d_out, sizeof(int32_t) * (size_t)h->n, cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "copy levels");
+    return sync_status(h);
+}
+
+blest_status blest_bfs_parents(blest_handle h, int32_t src, int32_t* levels, int32_t* parents) {
+    if (!h) return fail(BLEST_ERR_INVALID_ARG, "NULL handle");
+    if (!levels || !parents) return fail(BLEST_ERR_INVALID_ARG, "levels or parents is NULL");
+    cudaError_t e;
+    const size_t bytes = sizeof(int32_t) * (size_t)std::max(h->n, 1);
+    if (!h->d_cand && (e = cudaMalloc(&h->d_cand, bytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(parents)");
+    if (!h->d_parents && (e = cudaMalloc(&h->d_parents, bytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(parents)");
+    if (!h->h_new_id.empty() && !h->d_old_of) {
+        std::vector<int32_t> old_of((size_t)h->n);
+        for (int32_t v = 0; v < h->n; ++v) old_of[h->h_new_id[v]] = v;
+        if ((e = cudaMalloc(&h->d_old_of, bytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(old_of)");
+        if ((e = cudaMemcpy(h->d_old_of, old_of.data(), bytes, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cuda_fail(e, "copy old_of");
+    }
+    h->need_internal_levels = true;
+    blest_status s = blest_bfs_device(h, src, h->d_out, h->stream);
+    h->need_internal_levels = false;
+    if (s) return s;
+    const int32_t* L = h->d_new_id ? h->d_L : h->d_out;   // levels in BVSS ids
+    if ((e = blest::launch_parents(h->bvss.v2r, h->bvss.row_ids, h->bvss.masks, h->bvss.nvss, L, h->d_old_of,
+                                   h->d_new_id, h->n, h->d_cand, h->d_parents, h->stream)) != cudaSuccess)
+        return cuda_fail(e, "parents launch");
+    if ((e = cudaMemcpyAsync(levels, h->d_out, sizeof(int32_t) * (size_t)h->n, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(parents, h->d_parents, sizeof(int32_t) * (size_t)h->n, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+        return cuda_fail(e, "copy results");
     return sync_status(h);
 }
 
@@ -771,10 +814,12 @@ blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, bles
         for (int p : {BLEST_PULL_POPC, BLEST_PULL_MMA})
             for (int r : {1, 2})
                 for (int m : {2, 3})
-                    for (int f : {0, 1})
+                    for (int f = 0; f <= (u == BLEST_UPDATE_LAZY ? 2 : 1); ++f)
                         for (int b : {0, 1}) cands.push_back({u, p, r, m, f, b, 0});
-    for (int f : {0, 1})
+    for (int f : {0, 1, 2})
         for (int b : {0, 1}) {
+            for (int p : {BLEST_PULL_POPC, BLEST_PULL_MMA})
+                for (int r : {1, 2}) cands.push_back({BLEST_UPDATE_LAZY, p, r, 2, f, b, 2});
             cands.push_back({BLEST_UPDATE_LAZY, BLEST_PULL_POPC, 1, 2, f, b, 4});
             cands.push_back({BLEST_UPDATE_LAZY, BLEST_PULL_POPC, 2, 2, f, b, 4});
             cands.push_back({BLEST_UPDATE_LAZY, BLEST_PULL_POPC, 1, 2, f, b, 8});

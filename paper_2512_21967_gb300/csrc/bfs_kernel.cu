@@ -58,7 +58,8 @@ struct BfsArgs {
     int32_t* out;                         // output in original ids (unused when new_id is NULL)
     uint64_t timeout_ns;
     unsigned int phantom;
-    int filter;                           // 1 = skip rows already set in the V bitmap
+    int filter;                           // 1 = skip rows already in V_curr; 2 = also V_next while few are visited
+    int levels_from_bitmap;               // 1: L was not cleared; V_curr marks the rows whose level is set
 };
 
 // ------------------------------------------------------------------- pull
@@ -101,6 +102,7 @@ __device__ __forceinline__ void sweep(const BfsArgs& a, int lvl, unsigned long l
     const int lane = threadIdx.x & 31;
     const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    unsigned int fresh = 0;   // rows this lane gave a level
     for (int t0 = gwarp * kWarp; t0 < a.nwords; t0 += nwarps * kWarp) {
         const int t = t0 + lane;
         uint32_t diff = 0;
@@ -111,6 +113,7 @@ __device__ __forceinline__ void sweep(const BfsArgs& a, int lvl, unsigned long l
             if (diff) {
                 a.vcur[t] = nx;
                 if (UPDATE == 1) Fout[t] = diff;
+                fresh += (unsigned int)__popc(diff);
             }
         }
         // level writes, transposed: for each of the warp's 32 words with new
@@ -137,6 +140,10 @@ __device__ __forceinline__ void sweep(const BfsArgs& a, int lvl, unsigned long l
         }
         warp_enqueue<4>(a.qcap, a.ctrl, Qout, qcount, st, ln, pay, lane);
     }
+    if (UPDATE == 2 && a.filter == 2) {
+        fresh = __reduce_add_sync(0xffffffffu, fresh);
+        if (lane == 0 && fresh) atomicAdd(&a.ctrl->reached, fresh);
+    }
 }
 
 // ---------------------------------------------------------- hit handling
@@ -145,18 +152,25 @@ __device__ __forceinline__ void sweep(const BfsArgs& a, int lvl, unsigned long l
 // for one round trip per phase rather than one per hit.
 
 // Lazy marking (Algorithm 3, stage 1): set the V_next bit of every hit row,
-// skipping rows already in V_curr (visited filter).  V_curr only gains bits
-// during a traversal, so a stale (older) word can only let through a redundant
-// mark, never suppress a needed one.
+// skipping rows already in V_curr (visited filter, filt 1) and, with filt 2,
+// rows another warp has already marked in V_next at this level.  Both bitmaps
+// only gain bits during a traversal, so a stale (older) word can only let
+// through a redundant mark, never suppress a needed one.  The V_next test pays
+// off while most hit rows are unvisited (marks then repeat on the same rows)
+// and costs an extra L2 load per hit once most are visited; the kernel applies
+// it only while fewer than n/4 rows have a level.
 template <int NV>
-__device__ __forceinline__ void mark_rows(const BfsArgs& a, const int4 (&rows)[NV], unsigned int hm) {
+__device__ __forceinline__ void mark_rows(const BfsArgs& a, const int4 (&rows)[NV], unsigned int hm, int filt) {
     int u[4 * NV];
     uint32_t w[4 * NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
         u[4 * i + 0] = rows[i].x; u[4 * i + 1] = rows[i].y; u[4 * i + 2] = rows[i].z; u[4 * i + 3] = rows[i].w;
     }
-    if (a.filter) {
+    if (filt == 2) {
+#pragma unroll
+        for (int k = 0; k < 4 * NV; ++k) w[k] = (hm >> k) & 1u ? a.vcur[u[k] >> 5] | ld_cg(&a.vnext[u[k] >> 5]) : 0u;
+    } else if (filt) {
 #pragma unroll
         for (int k = 0; k < 4 * NV; ++k) w[k] = (hm >> k) & 1u ? a.vcur[u[k] >> 5] : 0u;
     } else {
@@ -259,7 +273,7 @@ __device__ __forceinline__ bool warp_wait_stage(uint32_t bar, uint32_t parity, u
 template <int PULL, int DEPTH, int U>
 __device__ __forceinline__ bool stage1_staged(const BfsArgs& a, const unsigned long long* __restrict__ Qin,
                                               unsigned int qn, unsigned char* ring, uint32_t& uses, uint64_t pol,
-                                              int lane, int gwarp, int nwarps) {
+                                              int lane, int gwarp, int nwarps, int filt) {
     static_assert(DEPTH >= 2 * U, "the ring must hold at least two groups of tiles");
     int4* rows = reinterpret_cast<int4*>(ring);
     uint32_t* msk = reinterpret_cast<uint32_t*>(ring + DEPTH * 512);
@@ -329,10 +343,102 @@ __device__ __forceinline__ bool stage1_staged(const BfsArgs& a, const unsigned l
         unsigned int hm = 0;
 #pragma unroll
         for (int j = 0; j < U; ++j) hm |= pull_hits<PULL>(m[j], alpha[j], lane) << (4 * j);
-        mark_rows<U>(a, r, hm);
+        mark_rows<U>(a, r, hm, filt);
     }
     uses += nk;
     return true;
+}
+
+// ------------------------------------------------------------- unpermute
+// out[v] = L[new_id[v]] in original ids, eight vertices per thread in flight.
+// With levels_from_bitmap (lazy traversals, whose L is not cleared before the
+// launch) a vertex whose V_curr bit is clear was not reached and gets -1: at the
+// end of a lazy traversal V_curr holds exactly the rows a sweep gave a level.
+__device__ __forceinline__ void unpermute(const BfsArgs& a, int gtid, int nthreads) {
+    constexpr int K = 8;
+    for (int64_t b = gtid; b < a.n; b += (int64_t)K * nthreads) {
+        int u[K];
+        uint32_t w[K];
+        int lv[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int64_t v = b + (int64_t)k * nthreads;
+            u[k] = v < a.n ? __ldg(&a.new_id[v]) : -1;
+        }
+        // the V_curr word and the (possibly stale) level are loaded together
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            w[k] = (a.levels_from_bitmap && u[k] >= 0) ? ld_cg(&a.vcur[u[k] >> 5]) : ~0u;
+            lv[k] = u[k] >= 0 ? ld_cg(&a.L[u[k]]) : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (!((w[k] >> (u[k] & 31)) & 1u)) lv[k] = -1;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int64_t v = b + (int64_t)k * nthreads;
+            if (v < a.n) a.out[v] = lv[k];
+        }
+    }
+}
+
+// ------------------------------------------------ double-buffered stage 1
+// Lazy stage 1 with a two-deep software pipeline in registers: while the hits
+// of group g are filtered and marked, the row-id and mask tiles of group g+1
+// are already in flight and the queue entries of group g+2 are being read, so
+// a warp no longer waits for the queue, the tiles and the filter one after
+// another.  A group is U virtual slice sets, strided by the warp count.
+template <int PULL, int U>
+__device__ __forceinline__ void stage1_pipelined(const BfsArgs& a, const unsigned long long* __restrict__ Qin,
+                                                 unsigned int qn, uint64_t pol, int lane, int gwarp, int nwarps,
+                                                 int filt) {
+    const unsigned int stride = (unsigned int)nwarps * U;
+    unsigned int base = (unsigned int)gwarp;
+    if (base >= qn) return;
+    unsigned long long e_cur[U], e_nxt[U];
+    int4 r_cur[U];
+    uint32_t m_cur[U];
+    auto fetch_entries = [&](unsigned int b, unsigned long long (&e)[U]) {
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            const unsigned int p = b + (unsigned int)i * (unsigned int)nwarps;
+            e[i] = p < qn ? ld_cg(&Qin[p]) : ~0ull;
+        }
+    };
+    auto fetch_tiles = [&](const unsigned long long (&e)[U], int4 (&r)[U], uint32_t (&m)[U]) {
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            r[i] = make_int4(0, 0, 0, 0);
+            m[i] = 0u;
+            if (e[i] != ~0ull) {
+                const size_t tile = (size_t)(uint32_t)e[i] * kWarp + lane;
+                r[i] = ld_stream_v4(&a.row_ids4[tile], pol);
+                m[i] = ld_stream_u32(&a.masks[tile], pol);
+            }
+        }
+    };
+    fetch_entries(base, e_cur);
+    fetch_tiles(e_cur, r_cur, m_cur);
+    fetch_entries(base + stride, e_nxt);
+    for (; base < qn; base += stride) {
+        int4 r_nxt[U];
+        uint32_t m_nxt[U];
+        unsigned long long e_far[U];
+        fetch_tiles(e_nxt, r_nxt, m_nxt);
+        fetch_entries(base + 2u * stride, e_far);
+        unsigned int hm = 0;
+#pragma unroll
+        for (int i = 0; i < U; ++i)   // e_cur[i] is the same in every lane, so the MMA runs warp-wide
+            if (e_cur[i] != ~0ull) hm |= pull_hits<PULL>(m_cur[i], (uint32_t)(e_cur[i] >> 32), lane) << (4 * i);
+        mark_rows<U>(a, r_cur, hm, filt);
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            e_cur[i] = e_nxt[i];
+            e_nxt[i] = e_far[i];
+            r_cur[i] = r_nxt[i];
+            m_cur[i] = m_nxt[i];
+        }
+    }
 }
 
 // -------------------------------------------------------------------- kernel
@@ -348,17 +454,17 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
     unsigned int gen = 0;
     Ctrl* ctrl = a.ctrl;
     extern __shared__ __align__(128) unsigned char dyn_smem[];
-    unsigned char* ring = dyn_smem + (threadIdx.x >> 5) * (DEPTH > 0 ? ring_bytes_per_warp<DEPTH>() : 0);
+    // DEPTH 4 or 8: a shared-memory ring per warp; DEPTH 2 keeps its two stages in registers
+    unsigned char* ring = dyn_smem + (threadIdx.x >> 5) * (DEPTH > 2 ? ring_bytes_per_warp<DEPTH>() : 0);
     uint32_t ring_uses = 0;
-    uint64_t pol = 0;
-    if (DEPTH > 0) {
+    const uint64_t pol = l2_evict_first_policy();
+    if (DEPTH > 2) {
         if (lane == 0) {
             unsigned long long* bars = reinterpret_cast<unsigned long long*>(ring + DEPTH * kStageBytes);
             for (int i = 0; i < DEPTH; ++i) mbar_init(smem_addr(&bars[i]), 1);
             mbar_init_fence();
         }
         __syncwarp();
-        pol = l2_evict_first_policy();
     }
 
     if (gtid == 0 && a.level_sizes) a.level_times[1] = global_timer_ns();   // kernel entry (block 0)
@@ -397,9 +503,13 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
         unsigned int* qcount_next = &ctrl->qcount[(lvl + 1) & 3];
 
         // stage 1: pull the queued virtual slice sets, round-robin over warps
-        if (DEPTH > 0) {
-            stage1_staged<PULL, (DEPTH > 0 ? DEPTH : 2 * UNROLL), UNROLL>(a, Qin, qn, ring, ring_uses, pol, lane,
-                                                                            gwarp, nwarps);
+        // the lazy filter of this level: the V_next test only while few rows are visited
+        const int filt = (a.filter == 2 && ld_cg(&ctrl->reached) >= (unsigned int)a.n / 4u) ? 1 : a.filter;
+        if (DEPTH == 2) {
+            stage1_pipelined<PULL, UNROLL>(a, Qin, qn, pol, lane, gwarp, nwarps, filt);
+        } else if (DEPTH > 0) {
+            stage1_staged<PULL, (DEPTH > 2 ? DEPTH : 2 * UNROLL), UNROLL>(a, Qin, qn, ring, ring_uses, pol, lane,
+                                                                            gwarp, nwarps, filt);
         } else
         for (unsigned int base = (unsigned int)gwarp; base < qn; base += (unsigned int)nwarps * UNROLL) {
             unsigned long long ent[UNROLL];
@@ -414,8 +524,8 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
             for (int i = 0; i < UNROLL; ++i) {
                 if (ent[i] != ~0ull) {
                     const size_t tile = (size_t)(uint32_t)ent[i] * kWarp + lane;
-                    rows[i] = __ldg(&a.row_ids4[tile]);
-                    msk[i] = __ldg(&a.masks[tile]);
+                    rows[i] = ld_stream_v4(&a.row_ids4[tile], pol);
+                    msk[i] = ld_stream_u32(&a.masks[tile], pol);
                 }
             }
             if (UPDATE == 2) {
@@ -423,7 +533,7 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
 #pragma unroll
                 for (int i = 0; i < UNROLL; ++i)
                     if (ent[i] != ~0ull) hm |= pull_hits<PULL>(msk[i], (uint32_t)(ent[i] >> 32), lane) << (4 * i);
-                mark_rows<UNROLL>(a, rows, hm);
+                mark_rows<UNROLL>(a, rows, hm, filt);
             } else {
                 uint32_t alpha[UNROLL];
 #pragma unroll
@@ -457,9 +567,7 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
         if (a.level_sizes && lvl < a.level_cap) a.level_times[2 * lvl + 2] = global_timer_ns();   // traversal end
     }
     // undo the reordering: out[v] = L[new_id[v]]
-    if (a.new_id) {
-        for (int v = gtid; v < a.n; v += nthreads) a.out[v] = ld_cg(&a.L[__ldg(&a.new_id[v])]);
-    }
+    if (a.new_id) unpermute(a, gtid, nthreads);
     if (a.level_sizes && lvl < a.level_cap) {
         __syncthreads();
         if (gtid == 0) a.level_times[2 * lvl + 3] = global_timer_ns();   // block 0 done with its share
@@ -502,6 +610,8 @@ static void* pick_kernel(int update, int pull, int unroll, int minb, int depth) 
 #define BLEST_PICK_S(P) BLEST_PICK(2, P, 1, 2, 4) BLEST_PICK(2, P, 2, 2, 4) BLEST_PICK(2, P, 1, 2, 8) \
     BLEST_PICK(2, P, 2, 2, 8) BLEST_PICK(2, P, 4, 2, 8)
     BLEST_PICK_S(0) BLEST_PICK_S(1)
+    // register double-buffered lazy variants (depth 2)
+    BLEST_PICK(2, 0, 1, 2, 2) BLEST_PICK(2, 0, 2, 2, 2) BLEST_PICK(2, 1, 1, 2, 2) BLEST_PICK(2, 1, 2, 2, 2)
 #undef BLEST_PICK_S
 #undef BLEST_PICK_M
 #undef BLEST_PICK
@@ -563,6 +673,7 @@ cudaError_t launch_bfs_kernel(const BfsLaunch& L, cudaStream_t stream) {
     a.timeout_ns = L.timeout_ns;
     a.phantom = L.phantom;
     a.filter = L.filter;
+    a.levels_from_bitmap = L.levels_from_bitmap;
     void* args[] = {&a};
     return cudaLaunchCooperativeKernel(k, dim3((unsigned)L.grid), dim3(kBfsBlock), args, smem, stream);
 }

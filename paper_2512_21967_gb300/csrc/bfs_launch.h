@@ -14,8 +14,9 @@ struct BfsLaunch {
     int pull = 0;              // 0 CUDA cores, 1 b1 MMA
     int unroll = 2;            // 1, 2
     int minb = 2;              // __launch_bounds__ minimum blocks per SM: 2 or 3
-    int filter = 1;            // skip marks of rows already in the V bitmap
-    int depth = 0;             // lazy stage 1 through a per-warp TMA ring of this many stages (0, 4, 8)
+    int filter = 1;            // 1: skip marks of rows already in V_curr; 2: also V_next (lazy)
+    int levels_from_bitmap = 0;// 1: L not cleared; the epilogue reads reached rows off V_curr (lazy)
+    int depth = 0;             // lazy stage 1 prefetch: 0 none, 2 register double buffer, 4/8 TMA ring stages
     int grid = 0;              // blocks (co-resident)
     int32_t n = 0;
     unsigned int qcap = 0;     // entries per queue buffer
@@ -28,7 +29,7 @@ struct BfsLaunch {
     uint32_t* vnext = nullptr;
     uint32_t* F[3] = {nullptr, nullptr, nullptr};
     unsigned long long* Q[3] = {nullptr, nullptr, nullptr};
-    void* ctrl = nullptr;      // 64-byte control block
+    void* ctrl = nullptr;      // 256-byte control block (device_common.cuh)
     int32_t* level_sizes = nullptr;
     unsigned long long* level_times = nullptr;   // 2 * level_cap + 2 entries
     int32_t level_cap = 0;

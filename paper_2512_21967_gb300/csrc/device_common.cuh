@@ -15,7 +15,8 @@ struct Ctrl {
     unsigned int error;        // first blest_status raised on the device (0 = none)
     unsigned int qcount[4];    // queue sizes, index = level & 3
     unsigned int levels;       // levels processed
-    unsigned int pad[9];
+    unsigned int reached;      // rows given a level so far (counted only when a filter needs it)
+    unsigned int pad[8];
 };
 static_assert(sizeof(Ctrl) == 64, "Ctrl is one 64-byte block");
 
@@ -150,6 +151,23 @@ __device__ __forceinline__ uint64_t l2_evict_first_policy() {
     uint64_t pol;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
     return pol;
+}
+
+// Streaming loads of read-once data (the BVSS tiles): no L1 allocation, L2
+// eviction policy from createpolicy (evict-first), so that the reused working
+// set (visited bitmap in L1; levels, bitmaps and queues in L2) stays resident.
+__device__ __forceinline__ int4 ld_stream_v4(const int4* p, uint64_t pol) {
+    int4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_stream_u32(const uint32_t* p, uint64_t pol) {
+    uint32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
 }
 
 // 1-D bulk copy global -> shared (TMA), completing `bytes` on the mbarrier.

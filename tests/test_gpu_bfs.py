@@ -106,7 +106,8 @@ def test_rmat16_all_sources_all_modes(cfg1, order):
             blest.blest_set_option(h, blest.BLEST_OPT_PULL, pull)
             variants = [(2, 2, 1, 0), (1, 3, 0, 0), (2, 3, 1, 0), (1, 2, 0, 0)]
             if upd == blest.BLEST_UPDATE_LAZY:
-                variants += [(1, 2, 1, 4), (1, 2, 0, 8), (1, 2, 1, 8)]
+                variants += [(1, 2, 1, 4), (1, 2, 0, 8), (1, 2, 1, 8), (2, 2, 2, 0), (1, 3, 2, 0),
+                             (1, 2, 1, 2), (2, 2, 2, 2), (2, 2, 0, 2), (2, 2, 2, 8)]
             for unroll, minb, filt, depth in variants:
                 blest.blest_set_option(h, blest.BLEST_OPT_UNROLL, unroll)
                 blest.blest_set_option(h, blest.BLEST_OPT_MIN_BLOCKS, minb)
@@ -127,7 +128,8 @@ def test_queue_sizes_match_replay(cfg1):
     try:
         b = ob.build(g.n, g.row_ptr, g.col_idx)
         blest.blest_set_option(h, blest.BLEST_OPT_RECORD_LEVELS, 1)
-        for upd, depth in ((blest.BLEST_UPDATE_EAGER, 0), (blest.BLEST_UPDATE_LAZY, 0), (blest.BLEST_UPDATE_LAZY, 8)):
+        for upd, depth in ((blest.BLEST_UPDATE_EAGER, 0), (blest.BLEST_UPDATE_LAZY, 0), (blest.BLEST_UPDATE_LAZY, 8),
+                           (blest.BLEST_UPDATE_LAZY, 2)):
             blest.blest_set_option(h, blest.BLEST_OPT_UPDATE, upd)
             blest.blest_set_option(h, blest.BLEST_OPT_STAGE_DEPTH, depth)
             for i in range(4):
@@ -348,3 +350,57 @@ def test_batch_graph_capture_replay(torch_cuda):
                 off += g.n
     finally:
         blest.blest_destroy(h)
+
+
+@pytest.mark.parametrize("order", ["none", "compress", "bandwidth"])
+def test_parents_match_oracle(gpu, order):
+    g = synth.rmat_graph(12, 16, seed=31)
+    srcs = synth.pick_sources(g, 4, seed=2)
+    h = blest.blest_graph_create(g.n, g.row_ptr, g.col_idx, ORDERS[order])
+    try:
+        for s in srcs:
+            lv, par = blest.blest_bfs_parents(h, int(s))
+            elv, epar = oracle.bfs_parents(g.n, g.row_ptr, g.col_idx, int(s))
+            assert np.array_equal(lv, elv) and np.array_equal(par, epar)
+    finally:
+        blest.blest_destroy(h)
+    gg, srcs2 = synth.grid_workload(64, 3, seed_graph=8, seed_src=8)
+    h = blest.blest_graph_create(gg.n, gg.row_ptr, gg.col_idx, blest.BLEST_ORDER_BANDWIDTH)
+    try:
+        for s in srcs2:
+            lv, par = blest.blest_bfs_parents(h, int(s))
+            elv, epar = oracle.bfs_parents(gg.n, gg.row_ptr, gg.col_idx, int(s))
+            assert np.array_equal(lv, elv) and np.array_equal(par, epar)
+    finally:
+        blest.blest_destroy(h)
+
+
+@pytest.mark.parametrize("update", ["eager", "lazy"])
+def test_stale_levels_do_not_leak(gpu, update):
+    """Two components: a traversal of the second after one of the first must
+    report the first as unreached, although the handle's internal level array
+    still holds the earlier levels (a lazy traversal with a reordering does not
+    clear it and reads the reached rows off its visited bitmap)."""
+    a = synth.rmat_graph(10, 8, seed=41, relabel=False)
+    b = synth.rmat_graph(9, 8, seed=42, relabel=False)
+    n = a.n + b.n
+    src = np.concatenate([np.repeat(np.arange(a.n), np.diff(a.row_ptr)),
+                          a.n + np.repeat(np.arange(b.n), np.diff(b.row_ptr))]).astype(np.int32)
+    dst = np.concatenate([a.col_idx, a.n + b.col_idx]).astype(np.int32)
+    g = synth.csr_from_edges(n, src, dst, relabel=synth.permutation(n, 43))
+    comp = synth.components(g)
+    big = np.bincount(comp).argsort()[::-1]
+    s1 = int(np.nonzero(comp == big[0])[0][0])
+    s2 = int(np.nonzero(comp == big[1])[0][0])
+    upd = blest.BLEST_UPDATE_EAGER if update == "eager" else blest.BLEST_UPDATE_LAZY
+    for order in (blest.BLEST_ORDER_COMPRESS, blest.BLEST_ORDER_BANDWIDTH, blest.BLEST_ORDER_NONE):
+        h = blest.blest_graph_create_ex(g.n, g.row_ptr, g.col_idx, order, window=64)
+        try:
+            blest.blest_set_option(h, blest.BLEST_OPT_UPDATE, upd)
+            for s in (s1, s2, s1, s2):
+                got = blest.blest_bfs(h, s)
+                assert np.array_equal(got, oracle.bfs_levels(g.n, g.row_ptr, g.col_idx, s))
+            got = blest.blest_bfs_multiroot(h, [s2])
+            assert np.array_equal(got, oracle.bfs_levels(g.n, g.row_ptr, g.col_idx, s2))
+        finally:
+            blest.blest_destroy(h)

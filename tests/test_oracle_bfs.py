@@ -162,3 +162,49 @@ def test_planted_mistake_is_caught():
     assert not np.array_equal(lvl, brute_force_levels(n, g, 0))
     with pytest.raises(AssertionError):
         check_invariants(g, 0, lvl)
+
+
+def check_tree(g, src, lvl, par):
+    """par is a BFS tree of lvl: the source is its own parent, every reached
+    vertex's parent is a neighbour one level closer, unreached ones have -1,
+    and following parents from any vertex ends at the source."""
+    nbr = [set(g.col_idx[g.row_ptr[v]:g.row_ptr[v + 1]].tolist()) for v in range(g.n)]
+    assert par[src] == src
+    for v in range(g.n):
+        if lvl[v] < 0:
+            assert par[v] == -1
+        elif v != src:
+            assert int(par[v]) in nbr[v] and lvl[par[v]] == lvl[v] - 1
+            assert par[v] == min(c for c in nbr[v] if lvl[c] == lvl[v] - 1)   # the unique choice
+    for v in range(g.n):
+        x, steps = v, 0
+        while lvl[x] > 0 and steps <= g.n:
+            x, steps = int(par[x]), steps + 1
+        assert lvl[v] < 0 or x == src
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_parents_form_the_min_id_bfs_tree(seed):
+    g = synth.rmat_graph(7, 8, seed=seed)
+    src = int(synth.pick_sources(g, 1, seed)[0])
+    lvl, par = oracle.bfs_parents(g.n, g.row_ptr, g.col_idx, src)
+    assert np.array_equal(lvl, brute_force_levels(g.n, g, src))
+    check_tree(g, src, lvl, par)
+
+
+def test_parents_path_closed_form():
+    n = 12
+    g = csr_from_undirected(n, [(i, i + 1) for i in range(n - 1)])
+    _, par = oracle.bfs_parents(n, g.row_ptr, g.col_idx, 5)
+    assert par.tolist() == [1, 2, 3, 4, 5, 5, 5, 6, 7, 8, 9, 10]
+
+
+def test_planted_parent_mistake_is_caught():
+    g = synth.rmat_graph(6, 8, seed=3)
+    src = int(synth.pick_sources(g, 1, 1)[0])
+    lvl, par = oracle.bfs_parents(g.n, g.row_ptr, g.col_idx, src)
+    bad = par.copy()
+    v = int(np.nonzero(lvl >= 2)[0][0])
+    bad[v] = src if src not in g.col_idx[g.row_ptr[v]:g.row_ptr[v + 1]] else -1
+    with pytest.raises(AssertionError):
+        check_tree(g, src, lvl, bad)
