@@ -671,10 +671,11 @@ def main():
     ap.add_argument("--pull", choices=["popc", "mma"], default="popc")
     ap.add_argument("--unroll", type=int, default=2)
     ap.add_argument("--minb", type=int, default=2)
-    ap.add_argument("--filter", type=int, default=1)
+    ap.add_argument("--filter", type=int, default=2, help="visited filter: 0 off, 1 V_curr, 2 V_curr + V_next early")
     ap.add_argument("--sources", type=int, default=0, help="use only the first N sources of the workload")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner, use the flags as given")
-    ap.add_argument("--depth", type=int, default=0, help="TMA ring depth of the lazy kernel (0, 4, 8)")
+    ap.add_argument("--depth", type=int, default=2,
+                    help="lazy stage-1 prefetch: 0 none, 2 register double buffer, 4 or 8 TMA ring stages")
     ap.add_argument("--queries", type=int, default=2000, help="serving: queries per arrival rate")
     ap.add_argument("--rates", default="100,400,1600", help="serving: arrival rates in queries/s")
     ap.add_argument("--windows", default="0,8,64,512,4096,16384,65536",
