@@ -85,10 +85,20 @@ typedef enum {
     BLEST_OPT_VISITED_FILTER = 7,    /* 1 (default) = test a visited bitmap before marking a row; 2 = lazy
                                         update also skips rows already marked at this level; 0 = off */
     BLEST_OPT_MIN_BLOCKS = 8,        /* kernel variant compiled for 2 (default) or 3 blocks per SM */
-    BLEST_OPT_STAGE_DEPTH = 9        /* lazy stage 1 prefetch: 0 = none (default); 2 = the next group's tiles
+    BLEST_OPT_STAGE_DEPTH = 9,       /* lazy stage 1 prefetch: 0 = none (default); 2 = the next group's tiles
                                         in registers while the current group's hits are handled; 4 or 8 = a
                                         per-warp TMA ring of that many stages in shared memory; used with
                                         BLEST_OPT_MIN_BLOCKS = 2 */
+    BLEST_OPT_LAYOUT = 10,           /* BVSS layout read by the lazy register paths (stage depth 0 or 2,
+                                        2 blocks/SM): 0 = every VSS padded to tau = 128 slices (Section
+                                        3.1.2, default); 1 = compact groups of 4 slices, only the last
+                                        group of a slice set padded (built from the padded layout on
+                                        first use: about 5 B per slice more device memory) */
+    BLEST_OPT_SCHEDULE = 11          /* stage-1 work split of the double-buffered path (stage depth 2):
+                                        0 = static, warp w takes queue entries w, w + W, ... (default);
+                                        1 = static for the first 7/8 of the queue, then warps take
+                                        chunks of the rest from a per-level counter, sized (entries
+                                        left) / (2 x warps) within [2 x unroll, 64] (guided) */
 } blest_option;
 
 /* Creation parameters; pass NULL to blest_graph_create_ex for the defaults. */
@@ -236,6 +246,14 @@ blest_status blest_get_run_info(blest_handle h, blest_run_info* info, int32_t* q
  * unpermute epilogue.  Up to cap entries. */
 blest_status blest_get_level_times(blest_handle h, uint64_t* times_ns, int32_t cap);
 
+/* Load balance of the last single-frontier traversal (recorded with
+ * BLEST_OPT_RECORD_LEVELS = 1): for level l >= 1, first_ns[l-1] and
+ * last_ns[l-1] are the globaltimer stamps (ns) at which the first and the last
+ * block of the persistent grid finished the level's stage 1; their gap is the
+ * time blocks wait at the level's barrier for the slowest one.  Up to cap
+ * entries each; both arrays host, caller-owned.  Waits for the handle's work. */
+blest_status blest_get_level_arrivals(blest_handle h, uint64_t* first_ns, uint64_t* last_ns, int32_t cap);
+
 /* ---------------------------------------------------------------- autotune */
 
 /* Result of blest_autotune: the options it kept and what they measured. */
@@ -247,6 +265,8 @@ typedef struct {
     int32_t visited_filter;
     int32_t blocks_per_sm;       /* 0 = as many as fit */
     int32_t stage_depth;         /* BLEST_OPT_STAGE_DEPTH kept */
+    int32_t layout;              /* BLEST_OPT_LAYOUT kept */
+    int32_t schedule;            /* BLEST_OPT_SCHEDULE kept */
     int32_t candidates;          /* variants timed */
     double  best_ms;             /* mean device time per traversal of the kept variant */
     double  rule_ms;             /* same for the Section 5 rule (lazy iff U_div > 25,000), CUDA-core pull */
@@ -269,7 +289,13 @@ typedef enum {
     BLEST_ARRAY_ROW_IDS = 2,         /* int32[128 * num_vss] */
     BLEST_ARRAY_MASKS = 3,           /* uint32[32 * num_vss] */
     BLEST_ARRAY_NEW_ID = 4,          /* int32[n]: new_id[original id] */
-    BLEST_ARRAY_VSS_COUNT = 5        /* int32[num_vss]: unpadded slices per VSS */
+    BLEST_ARRAY_VSS_COUNT = 5,       /* int32[num_vss]: unpadded slices per VSS */
+    /* compact layout (BLEST_OPT_LAYOUT = 1; exporting builds it): slice k of
+       slice set s, in row order, is sub-slot k % 4 of group goff[s] + k / 4;
+       the last group of a slice set is padded with its last row id, mask 0 */
+    BLEST_ARRAY_COMPACT_OFFSETS = 6, /* int32[num_slice_sets + 1]: goff, goff[num_slice_sets] = groups */
+    BLEST_ARRAY_COMPACT_ROWS = 7,    /* int32[4 * groups] */
+    BLEST_ARRAY_COMPACT_MASKS = 8    /* uint32[groups]: byte q = mask of sub-slot q */
 } blest_array;
 
 int64_t blest_export_size(blest_handle h, int32_t which);

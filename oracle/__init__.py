@@ -16,8 +16,12 @@ Contents, each plain and slow on purpose:
   grid, complete, disconnected) and the level invariants, in
   ``tests/test_oracle_bfs.py``.
 * ``bvss`` -- the BVSS arrays of Section 3.1 (realPtrs, virtualToReal, rowIds,
-  masks) built slice set by slice set.  Pinned by a decode round trip back to
-  the adjacency, the Figure 1 caption example and the Table 3 column relations.
+  masks) built slice set by slice set, and the compact layout (groups of four
+  slices, only the last group of a slice set padded).  Pinned by decode round
+  trips back to the adjacency, the Figure 1 caption example and the Table 3
+  column relations.
+* ``bfs_parents`` -- the BFS tree with the smallest-id parent, from the oracle
+  levels; pinned by tree invariants and a closed form.
 * ``orderings`` -- Reverse Cuthill-McKee (Section 3.2.1) and JaccardWithWindows
   (Algorithm 1) with the pre-pass, in pure Python.  Pinned by closed forms
   (sigma = 1 gives the identity; planted twin groups; path and grid bandwidth).

@@ -140,3 +140,45 @@ def slice_set_stats(n: int, row_ptr, col_idx, sigma: int = 8):
     key = (col_of_entry // sigma) * np.int64(n) + ci        # (slice set, row) pairs
     uniq = np.unique(key)
     return np.bincount(uniq // np.int64(n), minlength=nss).astype(np.int64)
+
+
+@dataclass
+class Compact:
+    """The compact layout (one reading of Section 3.1.2 against Table 3, whose
+    social-graph rows store far fewer slices than 128 per VSS): slices of a
+    slice set are packed four to a group in row order, and only the last
+    group of each slice set is padded.  A VSS is up to 32 consecutive groups."""
+    goff: np.ndarray       # int32[nss + 1]: first group of each slice set
+    rows: np.ndarray       # int32[4 * groups]
+    masks: np.ndarray      # uint32[groups]: byte q = mask of sub-slot q
+
+    @property
+    def groups(self) -> int:
+        return int(self.goff[-1])
+
+
+def compact(n: int, row_ptr, col_idx, sigma: int = 8) -> Compact:
+    """Slice k of slice set s (sorted by row) goes to sub-slot k % 4 of group
+    goff[s] + k // 4, goff = exclusive prefix sum of ceil(c_s / 4); padded
+    sub-slots repeat the last real row with a zero mask.  Built straight from
+    the slice sets, not from the padded arrays."""
+    spt = 32 // sigma
+    rp = np.asarray(row_ptr, dtype=np.int64)
+    ci = np.asarray(col_idx, dtype=np.int64)
+    nss = (n + sigma - 1) // sigma
+    per_set = [slice_set(n, rp, ci, s, sigma) for s in range(nss)]
+    goff = np.zeros(nss + 1, dtype=np.int64)
+    goff[1:] = np.cumsum([(len(sl) + spt - 1) // spt for sl in per_set])
+    rows = np.zeros(spt * int(goff[-1]), dtype=np.int64)
+    masks = np.zeros(int(goff[-1]), dtype=np.uint64)
+    for s, sl in enumerate(per_set):
+        ng = int(goff[s + 1] - goff[s])
+        for k in range(ng * spt):
+            g, sub = int(goff[s]) + k // spt, k % spt
+            if k < len(sl):
+                u, m = sl[k]
+            else:
+                u, m = sl[-1][0], 0
+            rows[spt * g + sub] = u
+            masks[g] |= np.uint64(m) << np.uint64(sigma * sub)
+    return Compact(goff.astype(np.int32), rows.astype(np.int32), masks.astype(np.uint32))

@@ -25,6 +25,7 @@ __all__ = [
     "blest_get_stats", "blest_bfs", "blest_bfs_parents", "blest_msbfs", "blest_bfs_multiroot", "blest_batch_bfs",
     "blest_batch_graph_capture", "blest_batch_graph_launch", "blest_bfs_device",
     "blest_msbfs_device", "blest_bfs_multiroot_device", "blest_sync", "blest_get_run_info", "blest_get_level_times",
+    "blest_get_level_arrivals",
     "blest_export",
     "blest_autotune", "blest_export_size", "blest_compute_order", "blest_is_social", "blest_debug_pull",
     "blest_bfs_static_scratch", "blest_server_create", "blest_server_submit", "blest_server_wait",
@@ -39,16 +40,18 @@ BLEST_UPDATE_AUTO, BLEST_UPDATE_EAGER, BLEST_UPDATE_LAZY = 0, 1, 2
 BLEST_PULL_POPC, BLEST_PULL_MMA = 0, 1
 BLEST_OPT_UPDATE, BLEST_OPT_PULL, BLEST_OPT_BLOCKS_PER_SM, BLEST_OPT_BARRIER_TIMEOUT_US = 0, 1, 2, 3
 BLEST_OPT_RECORD_LEVELS, BLEST_OPT_UNROLL, BLEST_OPT_TEST_PHANTOM_BLOCK = 4, 5, 6
-BLEST_OPT_VISITED_FILTER, BLEST_OPT_MIN_BLOCKS, BLEST_OPT_STAGE_DEPTH = 7, 8, 9
+BLEST_OPT_VISITED_FILTER, BLEST_OPT_MIN_BLOCKS, BLEST_OPT_STAGE_DEPTH, BLEST_OPT_LAYOUT = 7, 8, 9, 10
+BLEST_OPT_SCHEDULE = 11
 BLEST_ARRAY_REAL_PTRS, BLEST_ARRAY_VIRTUAL_TO_REAL, BLEST_ARRAY_ROW_IDS = 0, 1, 2
 BLEST_ARRAY_MASKS, BLEST_ARRAY_NEW_ID, BLEST_ARRAY_VSS_COUNT = 3, 4, 5
+BLEST_ARRAY_COMPACT_OFFSETS, BLEST_ARRAY_COMPACT_ROWS, BLEST_ARRAY_COMPACT_MASKS = 6, 7, 8
 
 EXPORTED_SYMBOLS = [
     "blest_graph_create", "blest_graph_create_ex", "blest_batch_create", "blest_destroy", "blest_set_option",
     "blest_get_stats", "blest_bfs", "blest_bfs_parents", "blest_msbfs", "blest_bfs_multiroot", "blest_batch_bfs",
     "blest_batch_graph_capture",
     "blest_batch_graph_launch", "blest_bfs_device", "blest_msbfs_device", "blest_bfs_multiroot_device", "blest_sync",
-    "blest_get_run_info", "blest_get_level_times", "blest_autotune",
+    "blest_get_run_info", "blest_get_level_times", "blest_get_level_arrivals", "blest_autotune",
     "blest_export_size", "blest_export", "blest_compute_order", "blest_is_social", "blest_debug_pull",
     "blest_server_create", "blest_server_submit", "blest_server_wait", "blest_server_pause", "blest_server_get_stats",
     "blest_server_destroy", "blest_bfs_static_scratch", "blest_status_string", "blest_last_error",
@@ -81,7 +84,8 @@ class Stats(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     _fields_ = [("update", ctypes.c_int32), ("pull", ctypes.c_int32), ("unroll", ctypes.c_int32),
                 ("min_blocks", ctypes.c_int32), ("visited_filter", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("stage_depth", ctypes.c_int32), ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_double), ("rule_ms", ctypes.c_double)]
+                ("stage_depth", ctypes.c_int32), ("layout", ctypes.c_int32), ("schedule", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_double), ("rule_ms", ctypes.c_double)]
 
 
 class ServerParams(ctypes.Structure):
@@ -137,6 +141,8 @@ def lib():
             "blest_get_run_info": (ctypes.c_int, [_vp, ctypes.POINTER(RunInfo), _i32p, ctypes.c_int32]),
             "blest_autotune": (ctypes.c_int, [_vp, _i32p, ctypes.c_int32, ctypes.POINTER(TuneResult)]),
             "blest_get_level_times": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32]),
+            "blest_get_level_arrivals": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64),
+                                                        ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32]),
             "blest_export_size": (ctypes.c_int64, [_vp, ctypes.c_int32]),
             "blest_export": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.c_int64]),
             "blest_compute_order": (ctypes.c_int, [ctypes.c_int32, _i32p, _i32p, ctypes.c_int,
@@ -361,9 +367,19 @@ def blest_get_level_times(h: int, cap: int = 1 << 17) -> np.ndarray:
     return out
 
 
+def blest_get_level_arrivals(h: int, cap: int) -> tuple[np.ndarray, np.ndarray]:
+    """(first, last) globaltimer stamps at which blocks finished each level's stage 1."""
+    first = np.zeros(cap, np.uint64)
+    last = np.zeros(cap, np.uint64)
+    p = ctypes.POINTER(ctypes.c_uint64)
+    _check(lib().blest_get_level_arrivals(h, first.ctypes.data_as(p), last.ctypes.data_as(p), int(cap)),
+           "blest_get_level_arrivals")
+    return first, last
+
+
 # ------------------------------------------------------------------ export
 
-_EXPORT_DTYPES = {BLEST_ARRAY_MASKS: np.uint32}
+_EXPORT_DTYPES = {BLEST_ARRAY_MASKS: np.uint32, BLEST_ARRAY_COMPACT_MASKS: np.uint32}
 
 
 def blest_export_size(h: int, which: int) -> int:

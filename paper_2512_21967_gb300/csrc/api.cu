@@ -61,6 +61,7 @@ struct blest_graph {
     int32_t n = 0;
     int64_t nnz = 0;
     blest::DeviceBvss bvss;
+    blest::DeviceCompact compact;        // compact layout, built on first use
     std::vector<int32_t> h_new_id;       // empty = identity
     int32_t* d_new_id = nullptr;
     int32_t* d_L = nullptr;              // internal levels (BVSS ids)
@@ -73,6 +74,7 @@ struct blest_graph {
     unsigned int* d_ctrl = nullptr;      // 256-byte control block (device_common.cuh layout)
     int32_t* d_level_sizes = nullptr;
     unsigned long long* d_level_times = nullptr;
+    unsigned long long* d_arrive = nullptr;   // 2 * kLevelRecordCap: first, then last stage-1 block ends
     int32_t* d_old_of = nullptr;         // BVSS id -> original id (parent output), made on first use
     int32_t* d_cand = nullptr;           // parent candidates (BVSS ids), made on first use
     int32_t* d_parents = nullptr;
@@ -92,6 +94,8 @@ struct blest_graph {
     int minb = 2;
     int filter = 1;
     int depth = 0;
+    int layout = 0;
+    int sched = 0;
     int phantom = 0;
     // results
     blest_stats stats{};
@@ -116,6 +120,7 @@ struct blest_graph {
 namespace {
 
 void free_handle(blest_graph* h) {
+    blest::free_compact_device(h->compact);
     if (!h) return;
     blest::free_bvss_device(h->bvss);
     blest::free_msbfs_state(h->ms);
@@ -129,6 +134,7 @@ void free_handle(blest_graph* h) {
     cudaFree(h->d_ctrl);
     cudaFree(h->d_level_sizes);
     cudaFree(h->d_level_times);
+    cudaFree(h->d_arrive);
     cudaFree(h->d_old_of);
     cudaFree(h->d_cand);
     cudaFree(h->d_parents);
@@ -186,6 +192,7 @@ blest_status finish_create(blest_graph* h, const Csr& g, const std::vector<int32
     BLEST_ALLOC(h->d_ctrl, kCtrlBytes, "cudaMalloc(ctrl)");
     BLEST_ALLOC(h->d_level_sizes, sizeof(int32_t) * kLevelRecordCap, "cudaMalloc(level record)");
     BLEST_ALLOC(h->d_level_times, sizeof(unsigned long long) * (2 * (size_t)kLevelRecordCap + 2), "cudaMalloc(level times)");
+    BLEST_ALLOC(h->d_arrive, sizeof(unsigned long long) * 2 * (size_t)kLevelRecordCap, "cudaMalloc(level arrivals)");
 #undef BLEST_ALLOC
     cudaMemsetAsync(h->d_ctrl, 0, kCtrlBytes, h->stream);
     if (!new_id.empty()) {
@@ -243,8 +250,17 @@ blest_status prepare_graph(int32_t n, const int32_t* row_ptr, const int32_t* col
     return BLEST_OK;
 }
 
-int pick_grid(blest_graph* h, int update, int pull, int unroll, int minb, int depth) {
-    int maxb = blest::bfs_max_blocks_per_sm(update, pull, unroll, minb, depth);
+// The compact layout is derived from the padded BVSS the first time it is asked for.
+blest_status ensure_compact(blest_graph* h) {
+    if (h->compact.goff || h->bvss.nss == 0) return BLEST_OK;
+    const char* err = nullptr;
+    const int rc = blest::build_compact_device(h->bvss, h->stream, h->compact, &err);
+    if (rc) return fail((blest_status)rc, err ? err : "compact layout build failed");
+    return BLEST_OK;
+}
+
+int pick_grid(blest_graph* h, int update, int pull, int unroll, int minb, int depth, int layout) {
+    int maxb = blest::bfs_max_blocks_per_sm(update, pull, unroll, minb, depth, layout);
     if (maxb <= 0) return 0;
     int b = h->blocks_per_sm > 0 ? std::min(h->blocks_per_sm, maxb) : maxb;
     return b * h->sms;
@@ -263,18 +279,24 @@ blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots
     L.minb = h->minb;
     L.filter = h->filter;
     if (L.update == 1 && L.filter == 2) L.filter = 1;     // V_next is not used by the eager update
+    L.sched = h->sched;
     // the TMA ring exists for the lazy kernel compiled for 2 blocks per SM
     L.depth = (L.update == 2 && L.minb == 2) ? h->depth : 0;
     if (L.depth == 0 && L.unroll > 2) L.unroll = 2;       // unroll 4 exists only for the TMA ring
     if (L.depth == 4 && L.unroll > 2) L.unroll = 2;       // a 4-stage ring holds two groups of 2
     if (L.depth == 2 && L.unroll > 2) L.unroll = 2;       // the register double buffer exists for 1 and 2
-    L.grid = pick_grid(h, L.update, L.pull, L.unroll, L.minb, L.depth);
+    // the compact layout serves the lazy register paths (depth 0 or 2) at 2 blocks per SM
+    L.layout = (h->layout == 1 && L.update == 2 && L.minb == 2 && L.depth <= 2 && h->compact.goff) ? 1 : 0;
+    L.grid = pick_grid(h, L.update, L.pull, L.unroll, L.minb, L.depth, L.layout);
     if (L.grid <= 0) return fail(BLEST_ERR_CUDA, "no co-resident grid for the traversal kernel");
     L.n = h->n;
     L.qcap = h->qcap;
     L.real_ptrs = h->bvss.real_ptrs;
     L.row_ids = h->bvss.row_ids;
     L.masks = h->bvss.masks;
+    L.goff = h->compact.goff;
+    L.rows_c = h->compact.rows;
+    L.masks_c = h->compact.masks;
     L.new_id = h->d_new_id;
     L.levels_internal = h->d_new_id ? h->d_L : d_out;
     // a lazy traversal with a reordering leaves L uncleared: its epilogue takes
@@ -290,6 +312,8 @@ blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots
     L.ctrl = h->d_ctrl;
     L.level_sizes = h->record ? h->d_level_sizes : nullptr;
     L.level_times = h->d_level_times;
+    L.arrive_first = h->d_arrive;
+    L.arrive_last = h->d_arrive + kLevelRecordCap;
     L.level_cap = kLevelRecordCap;
     L.nroots = (int32_t)roots.size();
     if (d_roots_preloaded) {
@@ -319,6 +343,10 @@ blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots
     L.phantom = h->phantom ? 1u : 0u;
     cudaMemsetAsync(h->d_ctrl, 0, kCtrlClearBytes, st);
     if (!L.levels_from_bitmap) cudaMemsetAsync(L.levels_internal, 0xFF, sizeof(int32_t) * (size_t)h->n, st);
+    if (L.level_sizes) {
+        cudaMemsetAsync(L.arrive_first, 0xFF, sizeof(unsigned long long) * kLevelRecordCap, st);
+        cudaMemsetAsync(L.arrive_last, 0, sizeof(unsigned long long) * kLevelRecordCap, st);
+    }
     cudaMemsetAsync(h->d_vcur, 0, sizeof(uint32_t) * nw, st);
     cudaMemsetAsync(h->d_vnext, 0, sizeof(uint32_t) * nw, st);
     if (L.update == 1) cudaMemsetAsync(h->d_F, 0, sizeof(uint32_t) * 3 * nw, st);
@@ -548,6 +576,19 @@ blest_status blest_set_option(blest_handle h, int32_t key, int64_t value) {
         case BLEST_OPT_STAGE_DEPTH:
             if (value != 0 && value != 2 && value != 4 && value != 8) break;
             h->depth = (int)value;
+            return BLEST_OK;
+        case BLEST_OPT_LAYOUT: {
+            if (value != 0 && value != 1) break;
+            if (value == 1) {
+                blest_status st = ensure_compact(h);
+                if (st) return st;
+            }
+            h->layout = (int)value;
+            return BLEST_OK;
+        }
+        case BLEST_OPT_SCHEDULE:
+            if (value != 0 && value != 1) break;
+            h->sched = (int)value;
             return BLEST_OK;
         case BLEST_OPT_TEST_PHANTOM_BLOCK:
             if (value != 0 && value != 1) break;
@@ -808,7 +849,7 @@ blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, bles
     std::vector<int32_t> roots;
     blest_status s = map_sources(h, srcs, k, roots);
     if (s) return s;
-    struct Cand { int update, pull, unroll, minb, filter, bps, depth; };
+    struct Cand { int update, pull, unroll, minb, filter, bps, depth, layout = 0, sched = 0; };
     std::vector<Cand> cands;
     for (int u : {BLEST_UPDATE_EAGER, BLEST_UPDATE_LAZY})
         for (int p : {BLEST_PULL_POPC, BLEST_PULL_MMA})
@@ -819,7 +860,16 @@ blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, bles
     for (int f : {0, 1, 2})
         for (int b : {0, 1}) {
             for (int p : {BLEST_PULL_POPC, BLEST_PULL_MMA})
-                for (int r : {1, 2}) cands.push_back({BLEST_UPDATE_LAZY, p, r, 2, f, b, 2});
+                for (int r : {1, 2}) {
+                    cands.push_back({BLEST_UPDATE_LAZY, p, r, 2, f, b, 2});
+                    cands.push_back({BLEST_UPDATE_LAZY, p, r, 2, f, b, 2, 0, 1});   // block-dynamic schedule
+                    // compact layout (register paths)
+                    if (b == 0) {
+                        cands.push_back({BLEST_UPDATE_LAZY, p, r, 2, f, b, 0, 1});
+                        cands.push_back({BLEST_UPDATE_LAZY, p, r, 2, f, b, 2, 1});
+                        cands.push_back({BLEST_UPDATE_LAZY, p, r, 2, f, b, 2, 1, 1});
+                    }
+                }
             cands.push_back({BLEST_UPDATE_LAZY, BLEST_PULL_POPC, 1, 2, f, b, 4});
             cands.push_back({BLEST_UPDATE_LAZY, BLEST_PULL_POPC, 2, 2, f, b, 4});
             cands.push_back({BLEST_UPDATE_LAZY, BLEST_PULL_POPC, 1, 2, f, b, 8});
@@ -828,8 +878,10 @@ blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, bles
             cands.push_back({BLEST_UPDATE_LAZY, BLEST_PULL_MMA, 1, 2, f, b, 4});
             cands.push_back({BLEST_UPDATE_LAZY, BLEST_PULL_MMA, 2, 2, f, b, 8});
         }
-    struct Opts { int update_opt, pull, unroll, minb, filter, blocks_per_sm, depth; };
-    const Opts saved{h->update_opt, h->pull, h->unroll, h->minb, h->filter, h->blocks_per_sm, h->depth};
+    struct Opts { int update_opt, pull, unroll, minb, filter, blocks_per_sm, depth, layout, sched; };
+    const Opts saved{h->update_opt, h->pull, h->unroll, h->minb, h->filter, h->blocks_per_sm, h->depth, h->layout,
+                     h->sched};
+    if ((s = ensure_compact(h)) != BLEST_OK) return s;
     cudaEvent_t e0, e1;
     cudaError_t e;
     if ((e = cudaEventCreate(&e0)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
@@ -839,7 +891,8 @@ blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, bles
     const int rule_update = h->stats.update;
     for (const Cand& c : cands) {
         h->update_opt = c.update; h->pull = c.pull; h->unroll = c.unroll; h->minb = c.minb;
-        h->filter = c.filter; h->blocks_per_sm = c.bps; h->depth = c.depth;
+        h->filter = c.filter; h->blocks_per_sm = c.bps; h->depth = c.depth; h->layout = c.layout;
+        h->sched = c.sched;
         std::vector<int32_t> one(1);
         for (int pass = 0; pass < 2 && !s; ++pass) {
             if (pass == 1) cudaEventRecord(e0, h->stream);
@@ -856,21 +909,40 @@ blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, bles
         const double per = (double)ms / k;
         if (per < best) { best = per; bestc = c; }
         if (c.update == rule_update && c.pull == BLEST_PULL_POPC && c.unroll == 2 && c.minb == 2 &&
-            c.filter == 0 && c.bps == 0 && c.depth == 0)
+            c.filter == 0 && c.bps == 0 && c.depth == 0 && c.layout == 0 && c.sched == 0)
             rule = per;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->update_opt = saved.update_opt; h->pull = saved.pull; h->unroll = saved.unroll; h->minb = saved.minb;
     h->filter = saved.filter; h->blocks_per_sm = saved.blocks_per_sm; h->depth = saved.depth;
+    h->layout = saved.layout;
+    h->sched = saved.sched;
     if (s) return s;
     h->update_opt = bestc.update; h->pull = bestc.pull; h->unroll = bestc.unroll; h->minb = bestc.minb;
-    h->filter = bestc.filter; h->blocks_per_sm = bestc.bps; h->depth = bestc.depth;
+    h->filter = bestc.filter; h->blocks_per_sm = bestc.bps; h->depth = bestc.depth; h->layout = bestc.layout;
+    h->sched = bestc.sched;
     if (out) {
         out->update = bestc.update; out->pull = bestc.pull; out->unroll = bestc.unroll; out->min_blocks = bestc.minb;
         out->visited_filter = bestc.filter; out->blocks_per_sm = bestc.bps; out->stage_depth = bestc.depth;
+        out->layout = bestc.layout;
+        out->schedule = bestc.sched;
         out->candidates = (int32_t)cands.size();
         out->best_ms = best; out->rule_ms = rule;
+    }
+    return BLEST_OK;
+}
+
+blest_status blest_get_level_arrivals(blest_handle h, uint64_t* first_ns, uint64_t* last_ns, int32_t cap) {
+    if (!h || (cap > 0 && (!first_ns || !last_ns))) return fail(BLEST_ERR_INVALID_ARG, "NULL argument");
+    blest_status s = sync_status(h);
+    if (s) return s;
+    const int32_t m = std::min<int32_t>(cap, kLevelRecordCap);
+    if (m > 0) {
+        cudaError_t e = cudaMemcpy(first_ns, h->d_arrive, sizeof(uint64_t) * (size_t)m, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(last_ns, h->d_arrive + kLevelRecordCap, sizeof(uint64_t) * (size_t)m, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "read level arrivals");
     }
     return BLEST_OK;
 }
@@ -901,6 +973,12 @@ int64_t blest_export_size(blest_handle h, int32_t which) {
         case BLEST_ARRAY_MASKS: return 4 * 32 * h->bvss.nvss;
         case BLEST_ARRAY_NEW_ID: return 4 * (int64_t)h->n;
         case BLEST_ARRAY_VSS_COUNT: return 4 * h->bvss.nvss;
+        case BLEST_ARRAY_COMPACT_OFFSETS: return 4 * ((int64_t)h->bvss.nss + 1);
+        case BLEST_ARRAY_COMPACT_ROWS:
+        case BLEST_ARRAY_COMPACT_MASKS: {
+            if (ensure_compact(h)) return -1;
+            return (which == BLEST_ARRAY_COMPACT_ROWS ? 16 : 4) * h->compact.groups;
+        }
     }
     return -1;
 }
@@ -918,6 +996,15 @@ blest_status blest_export(blest_handle h, int32_t which, void* host_out, int64_t
         case BLEST_ARRAY_ROW_IDS: src = h->bvss.row_ids; break;
         case BLEST_ARRAY_MASKS: src = h->bvss.masks; break;
         case BLEST_ARRAY_VSS_COUNT: src = h->bvss.vss_count; break;
+        case BLEST_ARRAY_COMPACT_OFFSETS:
+        case BLEST_ARRAY_COMPACT_ROWS:
+        case BLEST_ARRAY_COMPACT_MASKS: {
+            blest_status cs = ensure_compact(h);
+            if (cs) return cs;
+            src = which == BLEST_ARRAY_COMPACT_OFFSETS ? (const void*)h->compact.goff
+                : which == BLEST_ARRAY_COMPACT_ROWS ? (const void*)h->compact.rows : (const void*)h->compact.masks;
+            break;
+        }
         case BLEST_ARRAY_NEW_ID:
             if (h->h_new_id.empty()) {
                 int32_t* o = (int32_t*)host_out;

@@ -42,6 +42,9 @@ struct BfsArgs {
     const int32_t* __restrict__ real_ptrs;
     const int4* __restrict__ row_ids4;
     const uint32_t* __restrict__ masks;
+    const int32_t* __restrict__ goff;     // compact layout: first group of each slice set (nss + 1)
+    const int4* __restrict__ rows_c;      // compact layout: 4 row ids per group
+    const uint32_t* __restrict__ masks_c; // compact layout: 4 packed masks per group
     const int32_t* __restrict__ new_id;  // NULL: identity, L is the output
     int32_t* L;
     uint32_t* vcur;
@@ -51,6 +54,8 @@ struct BfsArgs {
     Ctrl* ctrl;
     int32_t* level_sizes;
     unsigned long long* level_times;      // with level_sizes: 2 globaltimer stamps per level
+    unsigned long long* arrive_first;     // with level_sizes: earliest / latest block end of stage 1
+    unsigned long long* arrive_last;
     int32_t level_cap;
     const int32_t* roots;                 // device list (used when nroots > kInlineRoots)
     int32_t nroots;
@@ -60,6 +65,7 @@ struct BfsArgs {
     unsigned int phantom;
     int filter;                           // 1 = skip rows already in V_curr; 2 = also V_next while few are visited
     int levels_from_bitmap;               // 1: L was not cleared; V_curr marks the rows whose level is set
+    int sched;                            // stage-1 schedule of the double-buffered path: 0 static, 1 dynamic
 };
 
 // ------------------------------------------------------------------- pull
@@ -96,7 +102,9 @@ __device__ __forceinline__ unsigned int pull_hits(uint32_t mask, uint32_t alpha,
 // t with diff = V_next ^ V_curr != 0 gets V_curr = V_next, its new rows get
 // level lvl, and each slice set (byte) of diff is enqueued with payload alpha
 // (lazy) or its id (eager, which also stores diff into the frontier bitmap).
-template <int UPDATE>
+// LAYOUT 1 enqueues the slice set's VSSs of the compact layout (group offset,
+// group count, alpha) instead of VSS ids.
+template <int UPDATE, int LAYOUT>
 __device__ __forceinline__ void sweep(const BfsArgs& a, int lvl, unsigned long long* Qout, unsigned int* qcount,
                                       uint32_t* Fout) {
     const int lane = threadIdx.x & 31;
@@ -125,20 +133,26 @@ __device__ __forceinline__ void sweep(const BfsArgs& a, int lvl, unsigned long l
             const uint32_t dw = __shfl_sync(0xffffffffu, diff, src);
             if ((dw >> lane) & 1u) a.L[(t0 + src) * kWarp + lane] = lvl;
         }
-        int st[4], ln[4];
+        int st[4], ln[4], tot[4];
         uint32_t pay[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const uint32_t byte = (diff >> (8 * q)) & 0xFFu;
-            st[q] = 0; ln[q] = 0; pay[q] = 0;
+            st[q] = 0; ln[q] = 0; tot[q] = 0; pay[q] = 0;
             if (byte) {
                 const int s = 4 * t + q;
-                st[q] = __ldg(&a.real_ptrs[s]);
-                ln[q] = __ldg(&a.real_ptrs[s + 1]) - st[q];
+                if (LAYOUT == 1) {
+                    st[q] = __ldg(&a.goff[s]);
+                    tot[q] = __ldg(&a.goff[s + 1]) - st[q];
+                    ln[q] = (tot[q] + 31) >> 5;
+                } else {
+                    st[q] = __ldg(&a.real_ptrs[s]);
+                    ln[q] = __ldg(&a.real_ptrs[s + 1]) - st[q];
+                }
                 pay[q] = UPDATE == 2 ? byte : (uint32_t)s;
             }
         }
-        warp_enqueue<4>(a.qcap, a.ctrl, Qout, qcount, st, ln, pay, lane);
+        warp_enqueue<4, LAYOUT == 1>(a.qcap, a.ctrl, Qout, qcount, st, ln, pay, lane, tot);
     }
     if (UPDATE == 2 && a.filter == 2) {
         fresh = __reduce_add_sync(0xffffffffu, fresh);
@@ -239,7 +253,7 @@ __device__ __forceinline__ void eager_update(const BfsArgs& a, const int4 (&rows
             pay[k] = (uint32_t)s2;
         }
     }
-    warp_enqueue<K>(a.qcap, a.ctrl, Qout, qcount_next, st, ln, pay, lane);
+    warp_enqueue<K>(a.qcap, a.ctrl, Qout, qcount_next, st, ln, pay, lane, ln);
 }
 
 // ---------------------------------------------------------- staged stage 1
@@ -334,7 +348,7 @@ __device__ __forceinline__ bool stage1_staged(const BfsArgs& a, const unsigned l
             }
             r[j] = rows[s * 32 + lane];
             m[j] = msk[s * 32 + lane];
-            alpha[j] = (uint32_t)(entry(k + j) >> 32);
+            alpha[j] = (uint32_t)(entry(k + j) >> 32) & 0xFFu;
         }
         __syncwarp();   // the stages may be refilled once every lane holds its tiles in registers
 #pragma unroll
@@ -382,54 +396,111 @@ __device__ __forceinline__ void unpermute(const BfsArgs& a, int gtid, int nthrea
     }
 }
 
+// --------------------------------------------------------- tile loads
+// The lane's 4 row ids and 4 packed masks of a queued virtual slice set.
+// Layout 0 (Section 3.1.2): every VSS holds 32 lanes x 4 slices, padded.
+// Layout 1 (compact): the VSS is ng = bits 40..44 + 1 consecutive groups of 4
+// slices starting at group bits 0..31; lanes >= ng hold nothing (mask 0).
+// Both streams are read once per level, with an L2 evict-first hint.
+template <int LAYOUT>
+__device__ __forceinline__ void load_tile(const BfsArgs& a, unsigned long long e, int lane, uint64_t pol, int4& r,
+                                          uint32_t& m) {
+    if (LAYOUT == 1) {
+        const uint32_t ng = (uint32_t)(e >> 40) + 1u;
+        if ((uint32_t)lane < ng) {
+            const size_t g = (size_t)(uint32_t)e + (size_t)lane;
+            r = ld_stream_v4(&a.rows_c[g], pol);
+            m = ld_stream_u32(&a.masks_c[g], pol);
+        }
+    } else {
+        const size_t tile = (size_t)(uint32_t)e * kWarp + lane;
+        r = ld_stream_v4(&a.row_ids4[tile], pol);
+        m = ld_stream_u32(&a.masks[tile], pol);
+    }
+}
+
 // ------------------------------------------------ double-buffered stage 1
 // Lazy stage 1 with a two-deep software pipeline in registers: while the hits
 // of group g are filtered and marked, the row-id and mask tiles of group g+1
 // are already in flight and the queue entries of group g+2 are being read, so
 // a warp no longer waits for the queue, the tiles and the filter one after
-// another.  A group is U virtual slice sets, strided by the warp count.
-template <int PULL, int U>
+// another.  A group is U queue entries.
+//
+// Schedules.  Static (sched 0): warp w takes entries w, w + W, w + 2W, ... (W =
+// warps), U at a time.  Static + dynamic tail (sched 1): the first 7/8 of the
+// queue is split statically as above, and a warp that has finished its static
+// share takes chunks of the last 1/8 from the level's counter in the control
+// block (guided self-scheduling: (entries left) / 2W at its previous grab,
+// within [2U, 64]), so blocks on faster SMs absorb the end of the level.
+constexpr unsigned int kChunkMax = 64;
+
+template <int PULL, int U, int LAYOUT>
 __device__ __forceinline__ void stage1_pipelined(const BfsArgs& a, const unsigned long long* __restrict__ Qin,
                                                  unsigned int qn, uint64_t pol, int lane, int gwarp, int nwarps,
-                                                 int filt) {
+                                                 int filt, unsigned int* work) {
+    const bool dyn = work != nullptr;
     const unsigned int stride = (unsigned int)nwarps * U;
-    unsigned int base = (unsigned int)gwarp;
-    if (base >= qn) return;
+    const unsigned int slim = dyn ? qn - qn / 8u : qn;   // end of the static part
+    unsigned int sbase = (unsigned int)gwarp;
+    if (!dyn && sbase >= qn) return;
+    unsigned int c_lo = 0, c_hi = 0, seen = slim;   // dynamic tail: current chunk, last position seen
     unsigned long long e_cur[U], e_nxt[U];
     int4 r_cur[U];
     uint32_t m_cur[U];
-    auto fetch_entries = [&](unsigned int b, unsigned long long (&e)[U]) {
+    // the queue entries of the warp's next group (~0 past the end; positions only grow)
+    auto next_group = [&](unsigned long long (&e)[U]) {
+        unsigned int p[U];
+        if (sbase < slim) {
 #pragma unroll
-        for (int i = 0; i < U; ++i) {
-            const unsigned int p = b + (unsigned int)i * (unsigned int)nwarps;
-            e[i] = p < qn ? ld_cg(&Qin[p]) : ~0ull;
+            for (int i = 0; i < U; ++i) {
+                const unsigned int q = sbase + (unsigned int)i * (unsigned int)nwarps;
+                p[i] = q < slim ? q : 0xFFFFFFFFu;
+            }
+            sbase += stride;
+        } else if (dyn) {
+            if (c_lo >= c_hi && seen < qn) {
+                const unsigned int left = qn - seen;
+                unsigned int c = left / (2u * (unsigned int)nwarps);
+                c = c < 2u * U ? 2u * U : (c > kChunkMax ? kChunkMax : c);
+                unsigned int s0 = 0;
+                if (lane == 0) s0 = atomicAdd(work, c);
+                s0 = __shfl_sync(0xffffffffu, s0, 0);
+                const unsigned int left_now = qn - slim;             // positions slim + [0, left_now)
+                seen = s0 < left_now ? slim + s0 : qn;
+                c_lo = seen;
+                c_hi = s0 < left_now ? (left_now - s0 < c ? qn : seen + c) : qn;
+            }
+#pragma unroll
+            for (int i = 0; i < U; ++i) p[i] = c_lo + (unsigned int)i < c_hi ? c_lo + (unsigned int)i : 0xFFFFFFFFu;
+            c_lo = c_lo + U < c_hi ? c_lo + U : c_hi;
+        } else {
+#pragma unroll
+            for (int i = 0; i < U; ++i) p[i] = 0xFFFFFFFFu;
         }
+#pragma unroll
+        for (int i = 0; i < U; ++i) e[i] = p[i] != 0xFFFFFFFFu ? ld_cg(&Qin[p[i]]) : ~0ull;
     };
     auto fetch_tiles = [&](const unsigned long long (&e)[U], int4 (&r)[U], uint32_t (&m)[U]) {
 #pragma unroll
         for (int i = 0; i < U; ++i) {
             r[i] = make_int4(0, 0, 0, 0);
             m[i] = 0u;
-            if (e[i] != ~0ull) {
-                const size_t tile = (size_t)(uint32_t)e[i] * kWarp + lane;
-                r[i] = ld_stream_v4(&a.row_ids4[tile], pol);
-                m[i] = ld_stream_u32(&a.masks[tile], pol);
-            }
+            if (e[i] != ~0ull) load_tile<LAYOUT>(a, e[i], lane, pol, r[i], m[i]);
         }
     };
-    fetch_entries(base, e_cur);
+    next_group(e_cur);
     fetch_tiles(e_cur, r_cur, m_cur);
-    fetch_entries(base + stride, e_nxt);
-    for (; base < qn; base += stride) {
+    next_group(e_nxt);
+    while (e_cur[0] != ~0ull) {
         int4 r_nxt[U];
         uint32_t m_nxt[U];
         unsigned long long e_far[U];
         fetch_tiles(e_nxt, r_nxt, m_nxt);
-        fetch_entries(base + 2u * stride, e_far);
+        next_group(e_far);
         unsigned int hm = 0;
 #pragma unroll
         for (int i = 0; i < U; ++i)   // e_cur[i] is the same in every lane, so the MMA runs warp-wide
-            if (e_cur[i] != ~0ull) hm |= pull_hits<PULL>(m_cur[i], (uint32_t)(e_cur[i] >> 32), lane) << (4 * i);
+            if (e_cur[i] != ~0ull) hm |= pull_hits<PULL>(m_cur[i], (uint32_t)(e_cur[i] >> 32) & 0xFFu, lane) << (4 * i);
         mark_rows<U>(a, r_cur, hm, filt);
 #pragma unroll
         for (int i = 0; i < U; ++i) {
@@ -443,7 +514,7 @@ __device__ __forceinline__ void stage1_pipelined(const BfsArgs& a, const unsigne
 
 // -------------------------------------------------------------------- kernel
 
-template <int UPDATE, int PULL, int UNROLL, int DEPTH>
+template <int UPDATE, int PULL, int UNROLL, int DEPTH, int LAYOUT>
 __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
     const int lane = threadIdx.x & 31;
     const int gtid = (int)(blockIdx.x * blockDim.x + threadIdx.x);
@@ -475,7 +546,7 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
     }
     if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns)) return;
     if (gtid == 0 && a.level_sizes) a.level_times[0] = global_timer_ns();
-    sweep<UPDATE>(a, 0, a.Q[1], &ctrl->qcount[1], a.F[1]);
+    sweep<UPDATE, LAYOUT>(a, 0, a.Q[1], &ctrl->qcount[1], a.F[1]);
     unsigned int qn = 0, qprev = 0;
     if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns, &ctrl->qcount[1], &qn)) return;
 
@@ -484,6 +555,7 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
         if (qn > a.qcap) qn = a.qcap;   // only after an overflow, which already raised an error
         if (gtid == 0) {
             ctrl->qcount[(lvl + 2) & 3] = 0;
+            ctrl->work[(lvl + 1) & 1] = 0;   // counter of the next level (this level's is work[lvl & 1])
             if (a.level_sizes && lvl - 1 < a.level_cap) {
                 a.level_sizes[lvl - 1] = (int32_t)qn;
                 a.level_times[2 * lvl] = global_timer_ns();    // stage 1 of level lvl starts
@@ -506,7 +578,8 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
         // the lazy filter of this level: the V_next test only while few rows are visited
         const int filt = (a.filter == 2 && ld_cg(&ctrl->reached) >= (unsigned int)a.n / 4u) ? 1 : a.filter;
         if (DEPTH == 2) {
-            stage1_pipelined<PULL, UNROLL>(a, Qin, qn, pol, lane, gwarp, nwarps, filt);
+            stage1_pipelined<PULL, UNROLL, LAYOUT>(a, Qin, qn, pol, lane, gwarp, nwarps, filt,
+                                                   a.sched ? &ctrl->work[lvl & 1] : nullptr);
         } else if (DEPTH > 0) {
             stage1_staged<PULL, (DEPTH > 2 ? DEPTH : 2 * UNROLL), UNROLL>(a, Qin, qn, ring, ring_uses, pol, lane,
                                                                             gwarp, nwarps, filt);
@@ -522,17 +595,16 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
             }
 #pragma unroll
             for (int i = 0; i < UNROLL; ++i) {
-                if (ent[i] != ~0ull) {
-                    const size_t tile = (size_t)(uint32_t)ent[i] * kWarp + lane;
-                    rows[i] = ld_stream_v4(&a.row_ids4[tile], pol);
-                    msk[i] = ld_stream_u32(&a.masks[tile], pol);
-                }
+                rows[i] = make_int4(0, 0, 0, 0);
+                msk[i] = 0u;
+                if (ent[i] != ~0ull) load_tile<LAYOUT>(a, ent[i], lane, pol, rows[i], msk[i]);
             }
             if (UPDATE == 2) {
                 unsigned int hm = 0;   // bit 4i+q: sub-slot q of VSS i hit
 #pragma unroll
                 for (int i = 0; i < UNROLL; ++i)
-                    if (ent[i] != ~0ull) hm |= pull_hits<PULL>(msk[i], (uint32_t)(ent[i] >> 32), lane) << (4 * i);
+                    if (ent[i] != ~0ull)
+                        hm |= pull_hits<PULL>(msk[i], (uint32_t)(ent[i] >> 32) & 0xFFu, lane) << (4 * i);
                 mark_rows<UNROLL>(a, rows, hm, filt);
             } else {
                 uint32_t alpha[UNROLL];
@@ -551,10 +623,19 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
                 eager_update<UNROLL>(a, rows, hm, lvl, Fnext, Qout, qcount_next, lane);
             }
         }
+        if (a.level_sizes && lvl - 1 < a.level_cap) {
+            // record when this block finished stage 1 (first and last over blocks)
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const unsigned long long t = global_timer_ns();
+                atomicMin(&a.arrive_first[lvl - 1], t);
+                atomicMax(&a.arrive_last[lvl - 1], t);
+            }
+        }
         if (UPDATE == 2) {
             if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns)) return;
             if (gtid == 0 && a.level_sizes && lvl - 1 < a.level_cap) a.level_times[2 * lvl + 1] = global_timer_ns();
-            sweep<UPDATE>(a, lvl, Qout, qcount_next, nullptr);
+            sweep<UPDATE, LAYOUT>(a, lvl, Qout, qcount_next, nullptr);
         }
         unsigned int qnext = 0;
         if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns, qcount_next, &qnext)) return;
@@ -574,9 +655,9 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
     }
 }
 
-template <int UPDATE, int PULL, int UNROLL, int MINB, int DEPTH>
+template <int UPDATE, int PULL, int UNROLL, int MINB, int DEPTH, int LAYOUT>
 __global__ void __launch_bounds__(kBfsBlock, MINB) bfs_kernel(BfsArgs a) {
-    bfs_body<UPDATE, PULL, UNROLL, DEPTH>(a);
+    bfs_body<UPDATE, PULL, UNROLL, DEPTH, LAYOUT>(a);
     fold_status(a.ctrl);
 }
 
@@ -595,14 +676,23 @@ __global__ void debug_pull_kernel(const uint32_t* __restrict__ masks, const uint
 
 // ---------------------------------------------------------------- launching
 
-template <int UPDATE, int PULL, int UNROLL, int MINB, int DEPTH>
+template <int UPDATE, int PULL, int UNROLL, int MINB, int DEPTH, int LAYOUT>
 static void* kernel_ptr() {
-    return reinterpret_cast<void*>(&bfs_kernel<UPDATE, PULL, UNROLL, MINB, DEPTH>);
+    return reinterpret_cast<void*>(&bfs_kernel<UPDATE, PULL, UNROLL, MINB, DEPTH, LAYOUT>);
 }
 
-static void* pick_kernel(int update, int pull, int unroll, int minb, int depth) {
+static void* pick_kernel(int update, int pull, int unroll, int minb, int depth, int layout) {
+    if (layout == 1) {
+        // compact layout: lazy, register path (plain or double-buffered), 2 blocks per SM
+#define BLEST_PICK_C(P, R, D) \
+    if (update == 2 && pull == P && unroll == R && minb == 2 && depth == D) return kernel_ptr<2, P, R, 2, D, 1>();
+        BLEST_PICK_C(0, 1, 0) BLEST_PICK_C(0, 2, 0) BLEST_PICK_C(0, 1, 2) BLEST_PICK_C(0, 2, 2)
+        BLEST_PICK_C(1, 1, 0) BLEST_PICK_C(1, 2, 0) BLEST_PICK_C(1, 1, 2) BLEST_PICK_C(1, 2, 2)
+#undef BLEST_PICK_C
+        return nullptr;
+    }
 #define BLEST_PICK(U, P, R, M, D) \
-    if (update == U && pull == P && unroll == R && minb == M && depth == D) return kernel_ptr<U, P, R, M, D>();
+    if (update == U && pull == P && unroll == R && minb == M && depth == D) return kernel_ptr<U, P, R, M, D, 0>();
 #define BLEST_PICK_M(U, P, R) BLEST_PICK(U, P, R, 2, 0) BLEST_PICK(U, P, R, 3, 0)
     BLEST_PICK_M(1, 0, 1) BLEST_PICK_M(1, 0, 2) BLEST_PICK_M(1, 1, 1) BLEST_PICK_M(1, 1, 2)
     BLEST_PICK_M(2, 0, 1) BLEST_PICK_M(2, 0, 2) BLEST_PICK_M(2, 1, 1) BLEST_PICK_M(2, 1, 2)
@@ -624,8 +714,8 @@ static size_t ring_smem_bytes(int depth) {
     return 0;
 }
 
-int bfs_max_blocks_per_sm(int update, int pull, int unroll, int minb, int depth) {
-    void* k = pick_kernel(update, pull, unroll, minb, depth);
+int bfs_max_blocks_per_sm(int update, int pull, int unroll, int minb, int depth, int layout) {
+    void* k = pick_kernel(update, pull, unroll, minb, depth, layout);
     if (!k) return 0;
     const size_t smem = ring_smem_bytes(depth);
     if (smem > 48 * 1024 &&
@@ -647,7 +737,7 @@ cudaError_t launch_debug_pull(const uint32_t* d_masks, const uint8_t* d_alpha, i
 }
 
 cudaError_t launch_bfs_kernel(const BfsLaunch& L, cudaStream_t stream) {
-    void* k = pick_kernel(L.update, L.pull, L.unroll, L.minb, L.depth);
+    void* k = pick_kernel(L.update, L.pull, L.unroll, L.minb, L.depth, L.layout);
     if (!k) return cudaErrorInvalidValue;
     const size_t smem = ring_smem_bytes(L.depth);
     BfsArgs a;
@@ -657,6 +747,9 @@ cudaError_t launch_bfs_kernel(const BfsLaunch& L, cudaStream_t stream) {
     a.real_ptrs = L.real_ptrs;
     a.row_ids4 = reinterpret_cast<const int4*>(L.row_ids);
     a.masks = L.masks;
+    a.goff = L.goff;
+    a.rows_c = reinterpret_cast<const int4*>(L.rows_c);
+    a.masks_c = L.masks_c;
     a.new_id = L.new_id;
     a.L = L.levels_internal;
     a.vcur = L.vcur;
@@ -665,6 +758,8 @@ cudaError_t launch_bfs_kernel(const BfsLaunch& L, cudaStream_t stream) {
     a.ctrl = reinterpret_cast<Ctrl*>(L.ctrl);
     a.level_sizes = L.level_sizes;
     a.level_times = L.level_times;
+    a.arrive_first = L.arrive_first;
+    a.arrive_last = L.arrive_last;
     a.level_cap = L.level_cap;
     a.roots = L.roots_device;
     a.nroots = L.nroots;
@@ -674,6 +769,7 @@ cudaError_t launch_bfs_kernel(const BfsLaunch& L, cudaStream_t stream) {
     a.phantom = L.phantom;
     a.filter = L.filter;
     a.levels_from_bitmap = L.levels_from_bitmap;
+    a.sched = L.sched;
     void* args[] = {&a};
     return cudaLaunchCooperativeKernel(k, dim3((unsigned)L.grid), dim3(kBfsBlock), args, smem, stream);
 }

@@ -16,13 +16,18 @@ struct BfsLaunch {
     int minb = 2;              // __launch_bounds__ minimum blocks per SM: 2 or 3
     int filter = 1;            // 1: skip marks of rows already in V_curr; 2: also V_next (lazy)
     int levels_from_bitmap = 0;// 1: L not cleared; the epilogue reads reached rows off V_curr (lazy)
+    int sched = 0;             // double-buffered stage 1: 0 static round-robin, 1 dynamic (guided)
     int depth = 0;             // lazy stage 1 prefetch: 0 none, 2 register double buffer, 4/8 TMA ring stages
+    int layout = 0;            // 0: tau-padded VSSs (Section 3.1.2); 1: compact groups (lazy, depth 0 or 2)
     int grid = 0;              // blocks (co-resident)
     int32_t n = 0;
     unsigned int qcap = 0;     // entries per queue buffer
     const int32_t* real_ptrs = nullptr;
     const int32_t* row_ids = nullptr;
     const uint32_t* masks = nullptr;
+    const int32_t* goff = nullptr;      // compact layout arrays (layout 1)
+    const int32_t* rows_c = nullptr;
+    const uint32_t* masks_c = nullptr;
     const int32_t* new_id = nullptr;
     int32_t* levels_internal = nullptr;
     uint32_t* vcur = nullptr;
@@ -32,6 +37,8 @@ struct BfsLaunch {
     void* ctrl = nullptr;      // 256-byte control block (device_common.cuh)
     int32_t* level_sizes = nullptr;
     unsigned long long* level_times = nullptr;   // 2 * level_cap + 2 entries
+    unsigned long long* arrive_first = nullptr;  // level_cap entries each (with level_sizes)
+    unsigned long long* arrive_last = nullptr;
     int32_t level_cap = 0;
     const int32_t* roots_device = nullptr;
     int32_t roots_host[kInlineRoots] = {0};
@@ -41,7 +48,7 @@ struct BfsLaunch {
     unsigned int phantom = 0;
 };
 
-int bfs_max_blocks_per_sm(int update, int pull, int unroll, int minb, int depth);
+int bfs_max_blocks_per_sm(int update, int pull, int unroll, int minb, int depth, int layout);
 int bfs_threads_per_block();
 cudaError_t launch_bfs_kernel(const BfsLaunch& L, cudaStream_t stream);
 
@@ -57,6 +64,20 @@ struct DeviceBvss {
     uint32_t* masks = nullptr;      // 32 * nvss
     int32_t* vss_count = nullptr;   // nvss
 };
+
+// Compact BVSS layout, derived from the tau-padded one: slice k of slice set s
+// (in row order) is sub-slot k % 4 of group goff[s] + k / 4; only the last
+// group of a slice set is padded (row id of its last slice, mask 0).  A VSS is
+// up to 32 consecutive groups of one slice set, so every slice set has the same
+// number of VSSs as in the padded layout.
+struct DeviceCompact {
+    int64_t groups = 0;
+    int32_t* goff = nullptr;        // nss + 1 (goff[nss] = groups)
+    int32_t* rows = nullptr;        // 4 * groups
+    uint32_t* masks = nullptr;      // groups
+};
+int build_compact_device(const DeviceBvss& b, cudaStream_t st, DeviceCompact& out, const char** err);
+void free_compact_device(DeviceCompact& c);
 
 // Builds the BVSS of the (sorted, symmetric) device CSR.  Allocates the arrays
 // of `out` with cudaMalloc.  Returns a blest_status code; err gets a message.

@@ -249,6 +249,49 @@ __global__ void udiv_kernel(const int32_t* __restrict__ row_ids, const int32_t* 
     }
 }
 
+// ------------------------------------------------------------ compact layout
+
+// Groups of slice set s: ceil(c_s / 4), c_s = 128 (VSSs - 1) + slices of its last VSS.
+__global__ void compact_count_kernel(const int32_t* __restrict__ real_ptrs, const int32_t* __restrict__ vss_count,
+                                     int32_t nss, int32_t* __restrict__ groups) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nss; s += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v0 = real_ptrs[s], v1 = real_ptrs[s + 1];
+        const int64_t c = v1 > v0 ? 128ll * (v1 - v0 - 1) + vss_count[v1 - 1] : 0;
+        groups[s] = (int32_t)((c + 3) / 4);
+    }
+}
+
+// A warp per padded VSS nu (slice set s, i-th of s): its slice k (lane k % 32,
+// sub-slot k / 32) is slice 128 i + k of s, stored at group goff[s] + 32 i + k / 4,
+// sub-slot k % 4.  The lane holding the last slice of s pads the rest of its group.
+__global__ void compact_place_kernel(const int32_t* __restrict__ real_ptrs, const int32_t* __restrict__ v2r,
+                                     const int32_t* __restrict__ row_ids, const uint32_t* __restrict__ masks,
+                                     const int32_t* __restrict__ vss_count, int64_t nvss,
+                                     const int32_t* __restrict__ goff, int32_t* __restrict__ rows_c,
+                                     uint8_t* __restrict__ mask_bytes_c) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t nu = w; nu < nvss; nu += nw) {
+        const int32_t s = v2r[nu];
+        const int64_t i = nu - real_ptrs[s];
+        const int c = vss_count[nu];
+        const bool last_vss = nu + 1 == real_ptrs[s + 1];
+        const uint32_t m = masks[nu * 32 + lane];
+        for (int q = 0; q < 4; ++q) {
+            const int k = 32 * q + lane;
+            if (k >= c) break;
+            const int64_t kk = 128 * i + k;                       // slice index within s
+            const int64_t slot = 4 * (int64_t)goff[s] + kk;       // group * 4 + sub-slot
+            const int32_t row = row_ids[nu * 128 + lane * 4 + q];
+            rows_c[slot] = row;
+            mask_bytes_c[slot] = (uint8_t)((m >> (8 * q)) & 0xFFu);
+            if (last_vss && k == c - 1)
+                for (int64_t p = slot + 1; (p & 3) != 0; ++p) rows_c[p] = row;   // masks were zeroed
+        }
+    }
+}
+
 int grid_for(int64_t work, int threads) {
     int64_t g = (work + threads - 1) / threads;
     if (g < 1) g = 1;
@@ -330,6 +373,49 @@ done:
     cudaFree(tmp);
     if (rc != 0) free_bvss_device(out);
     return rc;
+}
+
+int build_compact_device(const DeviceBvss& b, cudaStream_t st, DeviceCompact& out, const char** err) {
+    int rc = 0;
+    int32_t* groups = nullptr;
+    int64_t* tmp = nullptr;
+    int32_t total = 0;
+    const int64_t nb = ((int64_t)b.nss + kScanChunk - 1) / kScanChunk + 1;
+    BLEST_CK(cudaMalloc(&out.goff, sizeof(int32_t) * ((size_t)b.nss + 1)));
+    BLEST_CK(cudaMalloc(&groups, sizeof(int32_t) * (size_t)std::max(b.nss, 1)));
+    BLEST_CK(cudaMalloc(&tmp, sizeof(int64_t) * (size_t)nb));
+    if (b.nss > 0) {
+        compact_count_kernel<<<grid_for(b.nss, 256), 256, 0, st>>>(b.real_ptrs, b.vss_count, b.nss, groups);
+        BLEST_CK(cudaGetLastError());
+    }
+    BLEST_CK(exclusive_scan(groups, (int64_t)b.nss, out.goff, tmp, st));
+    BLEST_CK(cudaMemcpyAsync(&total, out.goff + b.nss, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    BLEST_CK(cudaStreamSynchronize(st));
+    out.groups = total;
+    BLEST_CK(cudaMalloc(&out.rows, sizeof(int32_t) * 4 * (size_t)std::max<int64_t>(total, 1)));
+    BLEST_CK(cudaMalloc(&out.masks, sizeof(uint32_t) * (size_t)std::max<int64_t>(total, 1)));
+    BLEST_CK(cudaMemsetAsync(out.masks, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(total, 1), st));
+    if (b.nvss > 0) {
+        compact_place_kernel<<<grid_for(b.nvss * 32, 256), 256, 0, st>>>(
+            b.real_ptrs, b.v2r, b.row_ids, b.masks, b.vss_count, b.nvss, out.goff, out.rows,
+            reinterpret_cast<uint8_t*>(out.masks));
+        BLEST_CK(cudaGetLastError());
+    }
+    BLEST_CK(cudaStreamSynchronize(st));
+done:
+    cudaFree(groups);
+    cudaFree(tmp);
+    if (rc != 0) free_compact_device(out);
+    return rc;
+}
+
+void free_compact_device(DeviceCompact& c) {
+    cudaFree(c.goff);
+    cudaFree(c.rows);
+    cudaFree(c.masks);
+    c.goff = c.rows = nullptr;
+    c.masks = nullptr;
+    c.groups = 0;
 }
 
 void free_bvss_device(DeviceBvss& b) {

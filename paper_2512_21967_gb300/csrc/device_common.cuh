@@ -16,7 +16,8 @@ struct Ctrl {
     unsigned int qcount[4];    // queue sizes, index = level & 3
     unsigned int levels;       // levels processed
     unsigned int reached;      // rows given a level so far (counted only when a filter needs it)
-    unsigned int pad[8];
+    unsigned int work[2];      // dynamic stage-1 schedule: next queue position, index = level & 1
+    unsigned int pad[6];
 };
 static_assert(sizeof(Ctrl) == 64, "Ctrl is one 64-byte block");
 
@@ -201,15 +202,28 @@ __device__ __forceinline__ void fold_status(Ctrl* ctrl) {
     }
 }
 
-// Warp-aggregated queue append (Section 4.2): lane i appends the VSS ranges
-// [st[q], st[q] + ln[q]) of up to NS slice sets, payload pay[q] in the upper
-// 32 bits of each entry.  One atomicAdd on the queue size per warp; lanes with
-// long ranges (hub slice sets) are written by the whole warp together.
-// Raises BLEST_ERR_INTERNAL (7) instead of writing past qcap.
-template <int NS>
+// Queue entry i of a slot: the VSS id st + i with the payload in the upper 32
+// bits, or, for the compact layout (GROUPS), the VSS that starts at group
+// st + 32 i of a slice set covering tot groups, with its group count - 1 in
+// bits 40..44 (payload = the 8-bit alpha in bits 32..39).
+template <bool GROUPS>
+__device__ __forceinline__ unsigned long long queue_entry(int st, uint32_t pay, int tot, int i) {
+    if (!GROUPS) return (unsigned long long)(unsigned int)(st + i) | ((unsigned long long)pay << 32);
+    const int left = tot - 32 * i;
+    const unsigned int ng = (unsigned int)(left < 32 ? left : 32) - 1u;
+    return (unsigned long long)(unsigned int)(st + 32 * i) | ((unsigned long long)pay << 32) |
+           ((unsigned long long)ng << 40);
+}
+
+// Warp-aggregated queue append (Section 4.2): lane i appends ln[q] entries
+// for each of its up to NS slots (a slice set's VSS range, see queue_entry).
+// One atomicAdd on the queue size per warp; lanes with long ranges (hub slice
+// sets) are written by the whole warp together.  Raises BLEST_ERR_INTERNAL (7)
+// instead of writing past qcap.
+template <int NS, bool GROUPS = false>
 __device__ __forceinline__ void warp_enqueue(unsigned int qcap, Ctrl* ctrl, unsigned long long* Qout,
                                              unsigned int* qcount, const int (&st)[NS], const int (&ln)[NS],
-                                             const uint32_t (&pay)[NS], int lane) {
+                                             const uint32_t (&pay)[NS], int lane, const int (&tot)[NS]) {
     unsigned int cnt = 0;
 #pragma unroll
     for (int q = 0; q < NS; ++q) cnt += (unsigned int)ln[q];
@@ -228,8 +242,7 @@ __device__ __forceinline__ void warp_enqueue(unsigned int qcap, Ctrl* ctrl, unsi
     if (!big) {
 #pragma unroll
         for (int q = 0; q < NS; ++q)
-            for (int i = 0; i < ln[q]; ++i)
-                Qout[pos++] = (unsigned long long)(unsigned int)(st[q] + i) | ((unsigned long long)pay[q] << 32);
+            for (int i = 0; i < ln[q]; ++i) Qout[pos++] = queue_entry<GROUPS>(st[q], pay[q], tot[q], i);
     }
     unsigned int bigmask = __ballot_sync(0xffffffffu, big);
     while (bigmask) {
@@ -241,8 +254,8 @@ __device__ __forceinline__ void warp_enqueue(unsigned int qcap, Ctrl* ctrl, unsi
             const int s0 = __shfl_sync(0xffffffffu, st[q], src);
             const int l0 = __shfl_sync(0xffffffffu, ln[q], src);
             const uint32_t p0 = __shfl_sync(0xffffffffu, pay[q], src);
-            for (int i = lane; i < l0; i += kWarp)
-                Qout[p + i] = (unsigned long long)(unsigned int)(s0 + i) | ((unsigned long long)p0 << 32);
+            const int t0 = GROUPS ? __shfl_sync(0xffffffffu, tot[q], src) : 0;
+            for (int i = lane; i < l0; i += kWarp) Qout[p + i] = queue_entry<GROUPS>(s0, p0, t0, i);
             p += (unsigned int)l0;
         }
     }
@@ -284,72 +297,6 @@ __device__ __forceinline__ void warp_enqueue_coalesced(unsigned int qcap, Ctrl* 
         if (j < total)
             Qout[base + j] = (unsigned long long)(unsigned int)(s_own + (int)(j - e_own)) |
                              ((unsigned long long)p_own << 32);
-    }
-}
-
-// Block-aggregated queue append: the same contract as warp_enqueue, but the
-// block's warps first sum their counts in shared memory and one thread per
-// block reserves the block's range with a single atomicAdd, so a sweep issues
-// one contending atomic per block iteration instead of one per warp.  Every
-// thread of the block must call it (block-uniform control flow).
-template <int NS>
-__device__ __forceinline__ void block_enqueue(unsigned int qcap, Ctrl* ctrl, unsigned long long* Qout,
-                                              unsigned int* qcount, const int (&st)[NS], const int (&ln)[NS],
-                                              const uint32_t (&pay)[NS], int lane) {
-    __shared__ unsigned int s_warp[32];
-    __shared__ unsigned int s_base;
-    const int wid = (int)(threadIdx.x >> 5);
-    const int nw = (int)(blockDim.x >> 5);
-    unsigned int cnt = 0;
-#pragma unroll
-    for (int q = 0; q < NS; ++q) cnt += (unsigned int)ln[q];
-    const unsigned int incl = warp_inclusive_scan(cnt, lane);
-    if (lane == 31) s_warp[wid] = incl;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned int run = 0;
-        for (int w = 0; w < nw; ++w) {
-            const unsigned int t = s_warp[w];
-            s_warp[w] = run;
-            run += t;
-        }
-        unsigned int base = 0;
-        if (run) {
-            base = atomicAdd(qcount, run);
-            if (base + run > qcap || base + run < base) {
-                raise_error(ctrl, 7u);
-                base = 0xFFFFFFFFu;
-            }
-        }
-        s_base = base;
-    }
-    __syncthreads();
-    const unsigned int base = s_base;
-    const unsigned int woff = s_warp[wid];
-    __syncthreads();   // s_warp / s_base may be rewritten by the next call
-    if (base == 0xFFFFFFFFu) return;
-    unsigned int pos = base + woff + incl - cnt;
-    const bool big = cnt > 64;
-    if (!big) {
-#pragma unroll
-        for (int q = 0; q < NS; ++q)
-            for (int i = 0; i < ln[q]; ++i)
-                Qout[pos++] = (unsigned long long)(unsigned int)(st[q] + i) | ((unsigned long long)pay[q] << 32);
-    }
-    unsigned int bigmask = __ballot_sync(0xffffffffu, big);
-    while (bigmask) {
-        const int src = __ffs(bigmask) - 1;
-        bigmask &= bigmask - 1;
-        unsigned int p = __shfl_sync(0xffffffffu, pos, src);
-#pragma unroll
-        for (int q = 0; q < NS; ++q) {
-            const int s0 = __shfl_sync(0xffffffffu, st[q], src);
-            const int l0 = __shfl_sync(0xffffffffu, ln[q], src);
-            const uint32_t p0 = __shfl_sync(0xffffffffu, pay[q], src);
-            for (int i = lane; i < l0; i += kWarp)
-                Qout[p + i] = (unsigned long long)(unsigned int)(s0 + i) | ((unsigned long long)p0 << 32);
-            p += (unsigned int)l0;
-        }
     }
 }
 

@@ -55,7 +55,7 @@ template <int W>
 __device__ __forceinline__ void ms_sweep(const MsArgs& a, int lvl, unsigned long long* Qout, unsigned int* qcount) {
     const int lane = threadIdx.x & 31;
     const size_t n = (size_t)a.n;
-    // block-strided so that every warp of a block runs the same iterations (block_enqueue)
+    // one row per thread, block-strided: consecutive rows of a warp share their bitmap lines
     for (int b0 = (int)blockIdx.x * (int)blockDim.x; b0 < a.n; b0 += (int)(gridDim.x * blockDim.x)) {
         const int u = b0 + (int)threadIdx.x;
         bool any = false;

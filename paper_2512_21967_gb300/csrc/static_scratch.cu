@@ -98,7 +98,7 @@ extern "C" blest_status blest_bfs_static_scratch(int32_t n, int64_t num_vss, con
     L.unroll = 2;
     L.minb = 2;
     L.filter = 1;
-    const int per_sm = blest::bfs_max_blocks_per_sm(L.update, L.pull, L.unroll, L.minb, L.depth);
+    const int per_sm = blest::bfs_max_blocks_per_sm(L.update, L.pull, L.unroll, L.minb, L.depth, 0);
     if (per_sm <= 0) return fail(BLEST_ERR_CUDA, "traversal kernel cannot be resident");
     L.grid = per_sm * sms;
     L.n = n;

@@ -104,18 +104,22 @@ def test_rmat16_all_sources_all_modes(cfg1, order):
         for upd, pull in MODES:
             blest.blest_set_option(h, blest.BLEST_OPT_UPDATE, upd)
             blest.blest_set_option(h, blest.BLEST_OPT_PULL, pull)
-            variants = [(2, 2, 1, 0), (1, 3, 0, 0), (2, 3, 1, 0), (1, 2, 0, 0)]
+            variants = [(2, 2, 1, 0, 0, 0), (1, 3, 0, 0, 0, 0), (2, 3, 1, 0, 0, 0), (1, 2, 0, 0, 0, 0)]
             if upd == blest.BLEST_UPDATE_LAZY:
-                variants += [(1, 2, 1, 4), (1, 2, 0, 8), (1, 2, 1, 8), (2, 2, 2, 0), (1, 3, 2, 0),
-                             (1, 2, 1, 2), (2, 2, 2, 2), (2, 2, 0, 2), (2, 2, 2, 8)]
-            for unroll, minb, filt, depth in variants:
+                variants += [(1, 2, 1, 4, 0, 0), (1, 2, 0, 8, 0, 0), (1, 2, 1, 8, 0, 0), (2, 2, 2, 0, 0, 0),
+                             (1, 3, 2, 0, 0, 0), (1, 2, 1, 2, 0, 0), (2, 2, 2, 2, 0, 0), (2, 2, 0, 2, 0, 0),
+                             (2, 2, 2, 8, 0, 0), (1, 2, 1, 0, 1, 0), (2, 2, 2, 0, 1, 0), (1, 2, 0, 2, 1, 0),
+                             (2, 2, 2, 2, 1, 0), (2, 2, 2, 2, 0, 1), (1, 2, 1, 2, 0, 1), (2, 2, 2, 2, 1, 1)]
+            for unroll, minb, filt, depth, layout, sched in variants:
+                blest.blest_set_option(h, blest.BLEST_OPT_SCHEDULE, sched)
                 blest.blest_set_option(h, blest.BLEST_OPT_UNROLL, unroll)
                 blest.blest_set_option(h, blest.BLEST_OPT_MIN_BLOCKS, minb)
                 blest.blest_set_option(h, blest.BLEST_OPT_VISITED_FILTER, filt)
                 blest.blest_set_option(h, blest.BLEST_OPT_STAGE_DEPTH, depth)
+                blest.blest_set_option(h, blest.BLEST_OPT_LAYOUT, layout)
                 for i, s in enumerate(srcs):
                     got = blest.blest_bfs(h, int(s))
-                    assert np.array_equal(got, exp[i]), f"mode {(upd, pull, unroll, minb, filt, depth)} source {s}"
+                    assert np.array_equal(got, exp[i]), f"mode {(upd, pull, unroll, minb, filt, depth, layout, sched)} source {s}"
     finally:
         blest.blest_destroy(h)
 
@@ -128,10 +132,14 @@ def test_queue_sizes_match_replay(cfg1):
     try:
         b = ob.build(g.n, g.row_ptr, g.col_idx)
         blest.blest_set_option(h, blest.BLEST_OPT_RECORD_LEVELS, 1)
-        for upd, depth in ((blest.BLEST_UPDATE_EAGER, 0), (blest.BLEST_UPDATE_LAZY, 0), (blest.BLEST_UPDATE_LAZY, 8),
-                           (blest.BLEST_UPDATE_LAZY, 2)):
+        for upd, depth, layout, sched in ((blest.BLEST_UPDATE_EAGER, 0, 0, 0), (blest.BLEST_UPDATE_LAZY, 0, 0, 0),
+                                          (blest.BLEST_UPDATE_LAZY, 8, 0, 0), (blest.BLEST_UPDATE_LAZY, 2, 0, 0),
+                                          (blest.BLEST_UPDATE_LAZY, 2, 1, 0), (blest.BLEST_UPDATE_LAZY, 0, 1, 0),
+                                          (blest.BLEST_UPDATE_LAZY, 2, 0, 1), (blest.BLEST_UPDATE_LAZY, 2, 1, 1)):
             blest.blest_set_option(h, blest.BLEST_OPT_UPDATE, upd)
+            blest.blest_set_option(h, blest.BLEST_OPT_SCHEDULE, sched)
             blest.blest_set_option(h, blest.BLEST_OPT_STAGE_DEPTH, depth)
+            blest.blest_set_option(h, blest.BLEST_OPT_LAYOUT, layout)
             for i in range(4):
                 blest.blest_bfs(h, int(srcs[i]))
                 info, sizes = blest.blest_get_run_info(h, 4096)
@@ -397,6 +405,7 @@ def test_stale_levels_do_not_leak(gpu, update):
         h = blest.blest_graph_create_ex(g.n, g.row_ptr, g.col_idx, order, window=64)
         try:
             blest.blest_set_option(h, blest.BLEST_OPT_UPDATE, upd)
+            blest.blest_set_option(h, blest.BLEST_OPT_LAYOUT, 1 if update == "lazy" and order != blest.BLEST_ORDER_NONE else 0)
             for s in (s1, s2, s1, s2):
                 got = blest.blest_bfs(h, s)
                 assert np.array_equal(got, oracle.bfs_levels(g.n, g.row_ptr, g.col_idx, s))
@@ -404,3 +413,46 @@ def test_stale_levels_do_not_leak(gpu, update):
             assert np.array_equal(got, oracle.bfs_levels(g.n, g.row_ptr, g.col_idx, s2))
         finally:
             blest.blest_destroy(h)
+
+
+@pytest.mark.parametrize("scale,seed", [(8, 3), (10, 5)])
+def test_compact_layout_matches_oracle(gpu, scale, seed):
+    """The device-built compact layout equals the oracle's, array for array
+    (identity order, so BVSS ids are original ids)."""
+    g = synth.rmat_graph(scale, 16, seed=seed)
+    h = blest.blest_graph_create(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_NONE)
+    try:
+        c = ob.compact(g.n, g.row_ptr, g.col_idx)
+        assert np.array_equal(blest.blest_export(h, blest.BLEST_ARRAY_COMPACT_OFFSETS), c.goff)
+        assert np.array_equal(blest.blest_export(h, blest.BLEST_ARRAY_COMPACT_ROWS), c.rows)
+        assert np.array_equal(blest.blest_export(h, blest.BLEST_ARRAY_COMPACT_MASKS), c.masks)
+    finally:
+        blest.blest_destroy(h)
+
+
+@pytest.mark.parametrize("update", ["eager", "lazy"])
+def test_level_timeline_and_arrivals(cfg1, update):
+    """Record mode: the level stamps increase, and every block's end of stage 1
+    lies between that level's stage-1 start and the stamp taken after the
+    barrier that waits for all blocks (causality on the global timer)."""
+    g, srcs, exp = cfg1
+    h = blest.blest_graph_create(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_COMPRESS)
+    try:
+        blest.blest_set_option(h, blest.BLEST_OPT_UPDATE,
+                               blest.BLEST_UPDATE_EAGER if update == "eager" else blest.BLEST_UPDATE_LAZY)
+        blest.blest_set_option(h, blest.BLEST_OPT_RECORD_LEVELS, 1)
+        for s in srcs[:3]:
+            assert np.array_equal(blest.blest_bfs(h, int(s)), exp[list(srcs).index(s)])
+            info, _ = blest.blest_get_run_info(h, 64)
+            L = info["levels"]
+            t = blest.blest_get_level_times(h, 2 * L + 4).astype(np.int64)
+            first, last = blest.blest_get_level_arrivals(h, L)
+            first, last = first.astype(np.int64), last.astype(np.int64)
+            assert t[1] <= t[0] <= t[2]
+            for l in range(1, L + 1):
+                after = t[2 * l + 1] if update == "lazy" else t[2 * l + 2]
+                assert first[l - 1] <= last[l - 1] <= after
+                assert t[2 * l] <= after
+            assert t[2 * L + 2] <= t[2 * L + 3]
+    finally:
+        blest.blest_destroy(h)

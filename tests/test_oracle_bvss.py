@@ -148,3 +148,62 @@ def test_planted_mistake_transposed_placement_fails():
     bad = ob.BVSS(b.n, b.sigma, b.real_ptrs, b.virtual_to_real,
                   b.row_ids.reshape(-1, 32, 4).transpose(0, 2, 1).reshape(-1).copy(), b.masks, b.vss_count)
     assert decode(bad) != adjacency_pairs(g)
+
+
+def decode_compact(c: ob.Compact, sigma: int = 8):
+    """Adjacency back from the compact arrays alone."""
+    out = set()
+    nss = len(c.goff) - 1
+    for s in range(nss):
+        for g in range(int(c.goff[s]), int(c.goff[s + 1])):
+            for sub in range(4):
+                m = (int(c.masks[g]) >> (sigma * sub)) & 0xFF
+                u = int(c.rows[4 * g + sub])
+                for j in range(sigma):
+                    if (m >> j) & 1:
+                        out.add((u, sigma * s + j))
+    return out
+
+
+@pytest.mark.parametrize("scale,seed", [(7, 1), (9, 4)])
+def test_compact_round_trip_and_relations(scale, seed):
+    g = synth.rmat_graph(scale, 16, seed=seed)
+    c = ob.compact(g.n, g.row_ptr, g.col_idx)
+    b = ob.build(g.n, g.row_ptr, g.col_idx)
+    assert decode_compact(c) == adjacency_pairs(g)
+    per_set = ob.slice_set_stats(g.n, g.row_ptr, g.col_idx)
+    # groups per slice set = ceil(c_s / 4); VSSs per slice set (32 groups each) = the padded count
+    assert np.array_equal(np.diff(c.goff), (per_set + 3) // 4)
+    assert np.array_equal((np.diff(c.goff) + 31) // 32, np.diff(b.real_ptrs))
+    # at most 3 padded sub-slots per slice set, against up to 127 per VSS in the padded layout
+    assert 4 * c.groups - ob.unpadded_slices(b) <= 3 * int(np.count_nonzero(per_set))
+    assert 4 * c.groups <= len(b.row_ids)
+
+
+def test_compact_order_and_padding():
+    g = synth.rmat_graph(8, 16, seed=9)
+    c = ob.compact(g.n, g.row_ptr, g.col_idx)
+    for s in range(len(c.goff) - 1):
+        sl = ob.slice_set(g.n, g.row_ptr, g.col_idx, s)
+        got = []
+        for g_ in range(int(c.goff[s]), int(c.goff[s + 1])):
+            for sub in range(4):
+                got.append((int(c.rows[4 * g_ + sub]), (int(c.masks[g_]) >> (8 * sub)) & 0xFF))
+        assert got[:len(sl)] == sl                               # row order, one slot per slice
+        assert all(m == 0 and u == sl[-1][0] for u, m in got[len(sl):])
+
+
+def test_compact_planted_mistake_fails():
+    """Packing the groups lane-major (slice k at sub-slot k // 32, as in the
+    padded layout) instead of four consecutive slices per group must break
+    the decode."""
+    g = synth.rmat_graph(9, 16, seed=2)
+    c = ob.compact(g.n, g.row_ptr, g.col_idx)
+    bad_rows = c.rows.copy()
+    s = int(np.argmax(np.diff(c.goff)))            # a slice set with many groups
+    g0, g1 = int(c.goff[s]), int(c.goff[s + 1])
+    ng = g1 - g0
+    blk = bad_rows[4 * g0:4 * g1].reshape(ng, 4)
+    bad_rows[4 * g0:4 * g1] = blk.T.reshape(-1)[:4 * ng] if ng == 4 else np.roll(blk, 1, axis=0).reshape(-1)
+    bad = ob.Compact(c.goff, bad_rows, c.masks)
+    assert decode_compact(bad) != adjacency_pairs(g)
