@@ -238,7 +238,7 @@ __device__ __forceinline__ void warp_enqueue(unsigned int qcap, Ctrl* ctrl, unsi
         return;
     }
     unsigned int pos = base + incl - cnt;
-    const bool big = cnt > 64;
+    const bool big = cnt > 16;   // longer runs are written by the whole warp: a lane-serial loop diverges
     if (!big) {
 #pragma unroll
         for (int q = 0; q < NS; ++q)
