@@ -52,6 +52,40 @@ WORKLOADS = {
 }
 
 
+# DRAM traffic of the traversal kernel comes from an ncu capture (profiles/),
+# valid only for the kernel sources it was taken on: the capture records their
+# sha256 and the ratio of DRAM bytes to the algorithmic bytes of its launch.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "bfs_kernel_traffic.txt")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2512_21967_gb300", "csrc", f)
+                  for f in ("bfs_kernel.cu", "device_common.cuh", "bfs_launch.h")]
+
+
+def kernel_sources_sha256():
+    import hashlib
+    d = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            d.update(fh.read())
+    return d.hexdigest()
+
+
+def traffic_ratio():
+    """(DRAM bytes per algorithmic byte, note), or (None, why) when the kernel
+    changed since the capture or no capture is committed."""
+    try:
+        kv = {}
+        with open(TRAFFIC_FILE) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_sources_sha256") != kernel_sources_sha256():
+            return None, "kernel sources changed since the ncu capture"
+        return float(kv["dram_bytes_per_algorithmic_byte"]), kv.get("capture", "")
+    except (OSError, KeyError, ValueError):
+        return None, "no ncu capture committed"
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -213,6 +247,8 @@ def run_ours(args):
     blest.blest_set_option(h, blest.BLEST_OPT_MIN_BLOCKS, args.minb)
     blest.blest_set_option(h, blest.BLEST_OPT_VISITED_FILTER, args.filter)
     blest.blest_set_option(h, blest.BLEST_OPT_STAGE_DEPTH, args.depth)
+    blest.blest_set_option(h, blest.BLEST_OPT_SCHEDULE, args.sched)
+    blest.blest_set_option(h, blest.BLEST_OPT_LAYOUT, args.layout)
     if not args.no_tune and not msk:
         # the autotuner times every kernel variant on 4 of the sources (untimed setup)
         t0 = time.time()
@@ -299,6 +335,7 @@ def run_ours(args):
     avg_bytes = float(abytes.mean())
     hbm, peak_kind = peaks()
     achieved = avg_bytes / (avg_launch_ms / 1e3) / 1e9
+    tr_ratio, tr_note = traffic_ratio()
 
     # end to end through the host-buffer C call
     e2e = None
@@ -326,15 +363,17 @@ def run_ours(args):
                        "order": order_name, "window": args.window,
                        "update": "lazy" if lazy else "eager", "pull": ["popc", "mma"][run_info["pull"]],
                        "variant": {k: tune[k] for k in ("unroll", "min_blocks", "visited_filter", "blocks_per_sm",
-                                                        "stage_depth")}
+                                                        "stage_depth", "layout", "schedule")}
                        if tune else {"unroll": args.unroll, "min_blocks": args.minb, "visited_filter": args.filter,
-                                     "blocks_per_sm": args.blocks_per_sm, "stage_depth": args.depth},
+                                     "blocks_per_sm": args.blocks_per_sm, "stage_depth": args.depth,
+                                     "layout": args.layout, "schedule": args.sched},
                        "autotune": tune,
                        "grid_blocks": run_info["grid_blocks"],
                        "l2": "flushed by a 256 MiB write before every traversal, outside its event pair",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                         "frac": round(achieved / hbm, 4), "peak_kind": peak_kind, "traffic": None,
+                         "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
+                         "traffic": round(tr_ratio * avg_bytes) if tr_ratio else None, "traffic_note": tr_note,
                          "kernel": "bfs_kernel (fused persistent traversal)",
                          "bytes_per_launch": avg_bytes, "avg_launch_ms": round(avg_launch_ms, 5)},
             "cpu_baseline": cpu,
@@ -680,6 +719,8 @@ def main():
     ap.add_argument("--rates", default="100,400,1600", help="serving: arrival rates in queries/s")
     ap.add_argument("--windows", default="0,8,64,512,4096,16384,65536",
                     help="window sweep: JaccardWithWindows windows (0 = no reordering)")
+    ap.add_argument("--sched", type=int, default=0, help="stage-1 schedule of depth 2: 0 static, 1 static + dynamic tail")
+    ap.add_argument("--layout", type=int, default=0, help="BVSS layout of the lazy register paths: 0 padded, 1 compact")
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--cpu-sources", type=int, default=12)
     ap.add_argument("--ref-sources", type=int, default=2)

@@ -232,6 +232,35 @@ blest_status blest_bfs_multiroot_device(blest_handle h, const int32_t* srcs, int
  * status they reported (BLEST_OK if none failed). */
 blest_status blest_sync(blest_handle h);
 
+/* Checkpoint of a handle's preprocessed graph: the vertex order, the BVSS
+ * arrays of Section 3.1, the batch boundaries and the statistics, so that
+ * blest_graph_load skips the reordering and the build.  Binary file in this
+ * library's format version 1 (magic "BLESTG1", native little-endian layout of
+ * blest_stats); options, the compact layout and traversal state are not
+ * saved.  blest_graph_save returns INVALID_ARG if the file cannot be written. */
+blest_status blest_graph_save(blest_handle h, const char* path);
+
+/* Reads a file written by blest_graph_save.  Every index in it (vertex order,
+ * realPtrs, virtualToReal, VSS counts, row ids, mask bits against the columns
+ * that exist) is checked against the header's sizes on the host before any
+ * device memory is allocated; the first inconsistency returns INVALID_ARG with
+ * a message.  *out is NULL on failure. */
+blest_status blest_graph_load(const char* path, blest_handle* out);
+
+/* Distance statistics of k single-source traversals, run as batched
+ * multi-source traversals (the multi-source applications of Section 6:
+ * closeness centrality and diameter).  For source srcs[i] (original id):
+ * reached[i] = vertices at finite distance, the source included; sum_dist[i] =
+ * the sum of those distances; ecc[i] = the largest (the source's eccentricity
+ * within its component).  Closeness = (reached - 1) / sum_dist (0 for an
+ * isolated source) and the diameter lower bound max_i ecc[i] follow from them.
+ * All three outputs are host arrays of k entries, caller-owned.  Sources are
+ * processed in batches of up to 256 whose level rows fit in 4 GiB of device
+ * scratch allocated for the call; returns INVALID_ARG for a source out of
+ * range (before any work), OOM if the scratch cannot be allocated. */
+blest_status blest_distance_stats(blest_handle h, const int32_t* srcs, int32_t k, int64_t* reached,
+                                  int64_t* sum_dist, int32_t* ecc);
+
 /* Per-level queue sizes of the last traversal (recorded when
  * BLEST_OPT_RECORD_LEVELS = 1): queue_sizes[l-1] = virtual slice sets processed
  * at level l, up to cap entries.  Waits for the handle's work first. */

@@ -22,6 +22,8 @@ Contents, each plain and slow on purpose:
   column relations.
 * ``bfs_parents`` -- the BFS tree with the smallest-id parent, from the oracle
   levels; pinned by tree invariants and a closed form.
+* ``distance_stats`` -- reached count, distance sum and eccentricity per
+  source (closeness and diameter, Section 6); pinned by closed forms.
 * ``orderings`` -- Reverse Cuthill-McKee (Section 3.2.1) and JaccardWithWindows
   (Algorithm 1) with the pre-pass, in pure Python.  Pinned by closed forms
   (sigma = 1 gives the identity; planted twin groups; path and grid bandwidth).
@@ -122,6 +124,18 @@ def bfs_parents(n: int, row_ptr, col_idx, src: int) -> tuple[np.ndarray, np.ndar
     par = np.where(lv < 0, -1, par)
     par[src] = src
     return lv, par.astype(np.int32)
+
+
+def distance_stats(n: int, row_ptr, col_idx, srcs, threads: int = 1):
+    """Per source: (vertices reached, sum of their distances, eccentricity),
+    from the oracle levels -- the quantities behind closeness centrality and
+    the diameter bound, the multi-source applications named in Section 6."""
+    lv = msbfs_levels(n, row_ptr, col_idx, srcs, threads=threads).astype(np.int64)
+    ok = lv >= 0
+    reached = ok.sum(axis=1).astype(np.int64)
+    total = np.where(ok, lv, 0).sum(axis=1).astype(np.int64)
+    ecc = np.where(ok, lv, -1).max(axis=1).astype(np.int32) if n > 0 else np.full(len(srcs), -1, np.int32)
+    return reached, total, ecc
 
 
 def reached_edges(row_ptr, levels: np.ndarray) -> int:

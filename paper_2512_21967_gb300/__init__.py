@@ -11,6 +11,7 @@ there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes
+import os
 import threading
 
 import numpy as np
@@ -25,7 +26,7 @@ __all__ = [
     "blest_get_stats", "blest_bfs", "blest_bfs_parents", "blest_msbfs", "blest_bfs_multiroot", "blest_batch_bfs",
     "blest_batch_graph_capture", "blest_batch_graph_launch", "blest_bfs_device",
     "blest_msbfs_device", "blest_bfs_multiroot_device", "blest_sync", "blest_get_run_info", "blest_get_level_times",
-    "blest_get_level_arrivals",
+    "blest_get_level_arrivals", "blest_distance_stats", "blest_graph_save", "blest_graph_load",
     "blest_export",
     "blest_autotune", "blest_export_size", "blest_compute_order", "blest_is_social", "blest_debug_pull",
     "blest_bfs_static_scratch", "blest_server_create", "blest_server_submit", "blest_server_wait",
@@ -35,6 +36,8 @@ __all__ = [
 BLEST_OK = 0
 STATUS_NAMES = {0: "BLEST_OK", 1: "BLEST_ERR_INVALID_ARG", 2: "BLEST_ERR_NOT_SYMMETRIC", 3: "BLEST_ERR_TOO_LARGE",
                 4: "BLEST_ERR_OOM", 5: "BLEST_ERR_CUDA", 6: "BLEST_ERR_TIMEOUT", 7: "BLEST_ERR_INTERNAL"}
+(BLEST_ERR_INVALID_ARG, BLEST_ERR_NOT_SYMMETRIC, BLEST_ERR_TOO_LARGE, BLEST_ERR_OOM, BLEST_ERR_CUDA,
+ BLEST_ERR_TIMEOUT, BLEST_ERR_INTERNAL) = 1, 2, 3, 4, 5, 6, 7
 BLEST_ORDER_NONE, BLEST_ORDER_COMPRESS, BLEST_ORDER_BANDWIDTH, BLEST_ORDER_AUTO = 0, 1, 2, 3
 BLEST_UPDATE_AUTO, BLEST_UPDATE_EAGER, BLEST_UPDATE_LAZY = 0, 1, 2
 BLEST_PULL_POPC, BLEST_PULL_MMA = 0, 1
@@ -51,7 +54,8 @@ EXPORTED_SYMBOLS = [
     "blest_get_stats", "blest_bfs", "blest_bfs_parents", "blest_msbfs", "blest_bfs_multiroot", "blest_batch_bfs",
     "blest_batch_graph_capture",
     "blest_batch_graph_launch", "blest_bfs_device", "blest_msbfs_device", "blest_bfs_multiroot_device", "blest_sync",
-    "blest_get_run_info", "blest_get_level_times", "blest_get_level_arrivals", "blest_autotune",
+    "blest_get_run_info", "blest_get_level_times", "blest_get_level_arrivals", "blest_distance_stats", "blest_graph_save", "blest_graph_load",
+    "blest_autotune",
     "blest_export_size", "blest_export", "blest_compute_order", "blest_is_social", "blest_debug_pull",
     "blest_server_create", "blest_server_submit", "blest_server_wait", "blest_server_pause", "blest_server_get_stats",
     "blest_server_destroy", "blest_bfs_static_scratch", "blest_status_string", "blest_last_error",
@@ -143,6 +147,11 @@ def lib():
             "blest_get_level_times": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32]),
             "blest_get_level_arrivals": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64),
                                                         ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32]),
+            "blest_graph_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
+            "blest_graph_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_vp)]),
+            "blest_distance_stats": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                                    ctypes.POINTER(ctypes.c_int32)]),
             "blest_export_size": (ctypes.c_int64, [_vp, ctypes.c_int32]),
             "blest_export": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.c_int64]),
             "blest_compute_order": (ctypes.c_int, [ctypes.c_int32, _i32p, _i32p, ctypes.c_int,
@@ -375,6 +384,30 @@ def blest_get_level_arrivals(h: int, cap: int) -> tuple[np.ndarray, np.ndarray]:
     _check(lib().blest_get_level_arrivals(h, first.ctypes.data_as(p), last.ctypes.data_as(p), int(cap)),
            "blest_get_level_arrivals")
     return first, last
+
+
+def blest_graph_save(h: int, path: str) -> None:
+    _check(lib().blest_graph_save(h, os.fsencode(path)), "blest_graph_save")
+
+
+def blest_graph_load(path: str) -> int:
+    out = _vp()
+    _check(lib().blest_graph_load(os.fsencode(path), ctypes.byref(out)), "blest_graph_load")
+    return out.value
+
+
+def blest_distance_stats(h: int, srcs) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """(reached, sum of distances, eccentricity) per source, each of len(srcs)."""
+    s = _i32(srcs)
+    k = len(s)
+    reached = np.zeros(k, np.int64)
+    total = np.zeros(k, np.int64)
+    ecc = np.zeros(k, np.int32)
+    p64 = ctypes.POINTER(ctypes.c_int64)
+    _check(lib().blest_distance_stats(h, s.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), k,
+                                      reached.ctypes.data_as(p64), total.ctypes.data_as(p64),
+                                      ecc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "blest_distance_stats")
+    return reached, total, ecc
 
 
 # ------------------------------------------------------------------ export

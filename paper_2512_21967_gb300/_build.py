@@ -13,7 +13,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libblest.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-CU_SOURCES = ["api.cu", "bfs_kernel.cu", "bvss_build.cu", "msbfs_kernel.cu", "parents.cu", "server.cu", "static_scratch.cu"]
+CU_SOURCES = ["api.cu", "bfs_kernel.cu", "bvss_build.cu", "msbfs_kernel.cu", "parents.cu", "server.cu", "static_scratch.cu", "stats.cu"]
 CPP_SOURCES = ["host_graph.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

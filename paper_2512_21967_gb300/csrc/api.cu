@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -149,8 +150,7 @@ void free_handle(blest_graph* h) {
 }
 
 // Device part of create: upload the relabelled CSR, build BVSS, allocate state.
-blest_status finish_create(blest_graph* h, const Csr& g, const std::vector<int32_t>& new_id, double t_order) {
-    double t0 = now_s();
+blest_status init_device(blest_graph* h) {
     cudaError_t e;
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -158,6 +158,42 @@ blest_status finish_create(blest_graph* h, const Csr& g, const std::vector<int32
         return cuda_fail(e, "cudaDeviceGetAttribute");
     if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess)
         return cuda_fail(e, "cudaStreamCreate");
+    return BLEST_OK;
+}
+
+// Traversal state of a handle whose BVSS is on the device, and the vertex order.
+blest_status alloc_state(blest_graph* h, const std::vector<int32_t>& new_id) {
+    cudaError_t e;
+    const size_t nw = (size_t)h->nwords();
+    h->qcap = (unsigned int)std::max<int64_t>(h->bvss.nvss, 1);
+#define BLEST_ALLOC(ptr, bytes, what) \
+    if ((e = cudaMalloc(&(ptr), (bytes))) != cudaSuccess) return cuda_fail(e, what);
+    BLEST_ALLOC(h->d_L, sizeof(int32_t) * std::max<size_t>(h->n, 1), "cudaMalloc(levels)");
+    BLEST_ALLOC(h->d_out, sizeof(int32_t) * std::max<size_t>(h->n, 1), "cudaMalloc(out)");
+    BLEST_ALLOC(h->d_vcur, sizeof(uint32_t) * std::max<size_t>(nw, 1), "cudaMalloc(vcur)");
+    BLEST_ALLOC(h->d_vnext, sizeof(uint32_t) * std::max<size_t>(nw, 1), "cudaMalloc(vnext)");
+    BLEST_ALLOC(h->d_F, sizeof(uint32_t) * 3 * std::max<size_t>(nw, 1), "cudaMalloc(frontier)");
+    BLEST_ALLOC(h->d_Q, sizeof(unsigned long long) * 3 * (size_t)h->qcap, "cudaMalloc(queues)");
+    BLEST_ALLOC(h->d_ctrl, kCtrlBytes, "cudaMalloc(ctrl)");
+    BLEST_ALLOC(h->d_level_sizes, sizeof(int32_t) * kLevelRecordCap, "cudaMalloc(level record)");
+    BLEST_ALLOC(h->d_level_times, sizeof(unsigned long long) * (2 * (size_t)kLevelRecordCap + 2), "cudaMalloc(level times)");
+    BLEST_ALLOC(h->d_arrive, sizeof(unsigned long long) * 2 * (size_t)kLevelRecordCap, "cudaMalloc(level arrivals)");
+#undef BLEST_ALLOC
+    cudaMemsetAsync(h->d_ctrl, 0, kCtrlBytes, h->stream);
+    if (!new_id.empty()) {
+        h->h_new_id = new_id;
+        if ((e = cudaMalloc(&h->d_new_id, sizeof(int32_t) * (size_t)h->n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(new_id)");
+        cudaMemcpyAsync(h->d_new_id, new_id.data(), sizeof(int32_t) * (size_t)h->n, cudaMemcpyHostToDevice, h->stream);
+    }
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(e, "create");
+    return BLEST_OK;
+}
+
+blest_status finish_create(blest_graph* h, const Csr& g, const std::vector<int32_t>& new_id, double t_order) {
+    double t0 = now_s();
+    cudaError_t e;
+    blest_status bs = init_device(h);
+    if (bs) return bs;
     h->n = g.n;
     h->nnz = g.nnz();
     int32_t *d_rp = nullptr, *d_ci = nullptr;
@@ -177,31 +213,9 @@ blest_status finish_create(blest_graph* h, const Csr& g, const std::vector<int32
     double udiv = 0.0;
     rc = blest::update_divergence_device(h->bvss, h->stream, &udiv, &err);
     if (rc) return fail((blest_status)rc, std::string("update divergence: ") + (err ? err : "?"));
+    if ((bs = alloc_state(h, new_id)) != BLEST_OK) return bs;
 
-    // traversal state
     const size_t nw = (size_t)h->nwords();
-    h->qcap = (unsigned int)std::max<int64_t>(h->bvss.nvss, 1);
-#define BLEST_ALLOC(ptr, bytes, what) \
-    if ((e = cudaMalloc(&(ptr), (bytes))) != cudaSuccess) return cuda_fail(e, what);
-    BLEST_ALLOC(h->d_L, sizeof(int32_t) * std::max<size_t>(g.n, 1), "cudaMalloc(levels)");
-    BLEST_ALLOC(h->d_out, sizeof(int32_t) * std::max<size_t>(g.n, 1), "cudaMalloc(out)");
-    BLEST_ALLOC(h->d_vcur, sizeof(uint32_t) * std::max<size_t>(nw, 1), "cudaMalloc(vcur)");
-    BLEST_ALLOC(h->d_vnext, sizeof(uint32_t) * std::max<size_t>(nw, 1), "cudaMalloc(vnext)");
-    BLEST_ALLOC(h->d_F, sizeof(uint32_t) * 3 * std::max<size_t>(nw, 1), "cudaMalloc(frontier)");
-    BLEST_ALLOC(h->d_Q, sizeof(unsigned long long) * 3 * (size_t)h->qcap, "cudaMalloc(queues)");
-    BLEST_ALLOC(h->d_ctrl, kCtrlBytes, "cudaMalloc(ctrl)");
-    BLEST_ALLOC(h->d_level_sizes, sizeof(int32_t) * kLevelRecordCap, "cudaMalloc(level record)");
-    BLEST_ALLOC(h->d_level_times, sizeof(unsigned long long) * (2 * (size_t)kLevelRecordCap + 2), "cudaMalloc(level times)");
-    BLEST_ALLOC(h->d_arrive, sizeof(unsigned long long) * 2 * (size_t)kLevelRecordCap, "cudaMalloc(level arrivals)");
-#undef BLEST_ALLOC
-    cudaMemsetAsync(h->d_ctrl, 0, kCtrlBytes, h->stream);
-    if (!new_id.empty()) {
-        h->h_new_id = new_id;
-        if ((e = cudaMalloc(&h->d_new_id, sizeof(int32_t) * (size_t)g.n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(new_id)");
-        cudaMemcpyAsync(h->d_new_id, new_id.data(), sizeof(int32_t) * (size_t)g.n, cudaMemcpyHostToDevice, h->stream);
-    }
-    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(e, "create");
-
     blest_stats& s = h->stats;
     s.n = g.n;
     s.nnz = h->nnz;
@@ -391,6 +405,8 @@ blest_status sync_status(blest_graph* h) {
 }  // namespace
 
 namespace blest {
+cudaError_t launch_distance_stats(const int32_t* lv, int32_t k, int64_t n, unsigned long long* acc, int* ecc,
+                                  cudaStream_t st);   // stats.cu
 cudaError_t launch_parents(const int32_t* v2r, const int32_t* row_ids, const uint32_t* masks, int64_t nvss,
                            const int32_t* L, const int32_t* old_of, const int32_t* new_id, int32_t n, int32_t* cand,
                            int32_t* out, cudaStream_t st);   // parents.cu
@@ -420,6 +436,42 @@ bool handle_view(blest_handle h, HandleView* v) {
     return true;
 }
 }  // namespace blest
+
+// ---------------------------------------------------------------- checkpoint helpers
+
+namespace {
+
+struct CheckpointHeader {
+    char magic[8];          // "BLESTG1"
+    int32_t version;        // 1
+    int32_t n;
+    int64_t nnz;
+    int32_t nss;
+    int32_t has_new_id;
+    int64_t nvss;
+    int64_t unpadded;
+    int64_t num_offsets;    // batch handles: graph boundaries (0 for a single graph)
+};
+
+template <class T>
+bool write_all(FILE* f, const T* p, size_t count) {
+    return count == 0 || std::fwrite(p, sizeof(T), count, f) == count;
+}
+
+template <class T>
+bool read_all(FILE* f, T* p, size_t count) {
+    return count == 0 || std::fread(p, sizeof(T), count, f) == count;
+}
+
+template <class T>
+cudaError_t upload(T** dst, const std::vector<T>& src, size_t at_least, cudaStream_t st) {
+    cudaError_t e = cudaMalloc(dst, sizeof(T) * std::max(src.size(), at_least));
+    if (e == cudaSuccess && !src.empty())
+        e = cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, st);
+    return e;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -463,6 +515,127 @@ blest_status blest_graph_create_ex(int32_t n, const int32_t* row_ptr, const int3
     s = finish_create(h.get(), *g, new_id, t_order);
     if (s) return s;
     h->stats.order = used;
+    *out = h.release();
+    return BLEST_OK;
+}
+
+// ---------------------------------------------------------------- checkpoint
+
+blest_status blest_graph_save(blest_handle h, const char* path) {
+    if (!h || !path) return fail(BLEST_ERR_INVALID_ARG, "NULL argument");
+    blest_status s = sync_status(h);
+    if (s) return s;
+    const blest::DeviceBvss& b = h->bvss;
+    std::vector<int32_t> rp((size_t)b.nss + 1), v2r((size_t)b.nvss), rows(128 * (size_t)b.nvss), cnt((size_t)b.nvss);
+    std::vector<uint32_t> masks(32 * (size_t)b.nvss);
+    cudaError_t e = cudaSuccess;
+    if (b.real_ptrs) e = cudaMemcpy(rp.data(), b.real_ptrs, 4 * rp.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && b.nvss > 0) {
+        if ((e = cudaMemcpy(v2r.data(), b.v2r, 4 * v2r.size(), cudaMemcpyDeviceToHost)) == cudaSuccess &&
+            (e = cudaMemcpy(rows.data(), b.row_ids, 4 * rows.size(), cudaMemcpyDeviceToHost)) == cudaSuccess &&
+            (e = cudaMemcpy(masks.data(), b.masks, 4 * masks.size(), cudaMemcpyDeviceToHost)) == cudaSuccess)
+            e = cudaMemcpy(cnt.data(), b.vss_count, 4 * cnt.size(), cudaMemcpyDeviceToHost);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "read BVSS for saving");
+    CheckpointHeader hd{};
+    std::memcpy(hd.magic, "BLESTG1", 8);
+    hd.version = 1;
+    hd.n = h->n;
+    hd.nnz = h->nnz;
+    hd.nss = b.nss;
+    hd.has_new_id = h->h_new_id.empty() ? 0 : 1;
+    hd.nvss = b.nvss;
+    hd.unpadded = b.unpadded;
+    hd.num_offsets = (int64_t)h->offsets.size();
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(BLEST_ERR_INVALID_ARG, std::string("cannot open ") + path + " for writing");
+    bool ok = write_all(f, &hd, 1) && write_all(f, &h->stats, 1) &&
+              write_all(f, h->offsets.data(), h->offsets.size()) &&
+              write_all(f, h->h_new_id.data(), h->h_new_id.size()) && write_all(f, rp.data(), rp.size()) &&
+              write_all(f, v2r.data(), v2r.size()) && write_all(f, rows.data(), rows.size()) &&
+              write_all(f, masks.data(), masks.size()) && write_all(f, cnt.data(), cnt.size());
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(BLEST_ERR_INVALID_ARG, std::string("short write to ") + path);
+    return BLEST_OK;
+}
+
+blest_status blest_graph_load(const char* path, blest_handle* out) {
+    if (!out || !path) return fail(BLEST_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(BLEST_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    std::unique_ptr<FILE, int (*)(FILE*)> closer(f, std::fclose);
+    CheckpointHeader hd{};
+    blest_stats st{};
+    if (!read_all(f, &hd, 1) || std::memcmp(hd.magic, "BLESTG1", 8) != 0 || hd.version != 1)
+        return fail(BLEST_ERR_INVALID_ARG, "not a version-1 BLEST graph file");
+    if (hd.n < 0 || hd.n > kMaxVertices || hd.nss != (hd.n + 7) / 8 || hd.nnz < 0 || hd.nnz >= ((int64_t)1 << 31) ||
+        hd.nvss < 0 || hd.nvss >= ((int64_t)1 << 31) || hd.unpadded < 0 || hd.unpadded > 128 * hd.nvss ||
+        hd.num_offsets < 0 || hd.num_offsets > (int64_t)hd.n + 2 || (hd.has_new_id != 0 && hd.has_new_id != 1))
+        return fail(BLEST_ERR_INVALID_ARG, "inconsistent sizes in the file header");
+    const size_t n = (size_t)hd.n, nss = (size_t)hd.nss, nvss = (size_t)hd.nvss;
+    std::vector<int64_t> offsets((size_t)hd.num_offsets);
+    std::vector<int32_t> new_id(hd.has_new_id ? n : 0), rp(nss + 1), v2r(nvss), rows(128 * nvss), cnt(nvss);
+    std::vector<uint32_t> masks(32 * nvss);
+    if (!read_all(f, &st, 1) || !read_all(f, offsets.data(), offsets.size()) ||
+        !read_all(f, new_id.data(), new_id.size()) || !read_all(f, rp.data(), rp.size()) ||
+        !read_all(f, v2r.data(), v2r.size()) || !read_all(f, rows.data(), rows.size()) ||
+        !read_all(f, masks.data(), masks.size()) || !read_all(f, cnt.data(), cnt.size()))
+        return fail(BLEST_ERR_INVALID_ARG, "the file is shorter than its header says");
+    // every index the kernels follow is checked before anything reaches the device
+    if (!new_id.empty()) {
+        std::vector<char> seen(n, 0);
+        for (int32_t v : new_id) {
+            if (v < 0 || (size_t)v >= n || seen[(size_t)v]) return fail(BLEST_ERR_INVALID_ARG, "new_id is not a permutation");
+            seen[(size_t)v] = 1;
+        }
+    }
+    if (!offsets.empty()) {
+        if (offsets.front() != 0 || offsets.back() != hd.n) return fail(BLEST_ERR_INVALID_ARG, "bad graph offsets");
+        for (size_t i = 1; i < offsets.size(); ++i)
+            if (offsets[i] < offsets[i - 1]) return fail(BLEST_ERR_INVALID_ARG, "bad graph offsets");
+    }
+    if (rp[0] != 0 || (int64_t)rp[nss] != hd.nvss) return fail(BLEST_ERR_INVALID_ARG, "bad realPtrs");
+    int64_t unpadded = 0;
+    for (size_t sidx = 0; sidx < nss; ++sidx) {
+        if (rp[sidx + 1] < rp[sidx]) return fail(BLEST_ERR_INVALID_ARG, "realPtrs not monotone");
+        const uint32_t colmask = (8 * sidx + 8 <= n) ? 0xFFu : ((1u << (n - 8 * sidx)) - 1u);   // columns < n
+        for (int64_t nu = rp[sidx]; nu < rp[sidx + 1]; ++nu) {
+            const int c = cnt[(size_t)nu];
+            const bool last = nu + 1 == rp[sidx + 1];
+            if (v2r[(size_t)nu] != (int32_t)sidx || c < 1 || c > 128 || (!last && c != 128))
+                return fail(BLEST_ERR_INVALID_ARG, "bad virtualToReal or VSS count");
+            unpadded += c;
+            for (int k = 0; k < 128; ++k) {
+                const int lane = k & 31, sub = k >> 5;
+                const int32_t u = rows[(size_t)nu * 128 + 4 * lane + sub];
+                const uint32_t m = (masks[(size_t)nu * 32 + lane] >> (8 * sub)) & 0xFFu;
+                if (u < 0 || (size_t)u >= n) return fail(BLEST_ERR_INVALID_ARG, "row id out of range");
+                if ((k < c && m == 0) || (k >= c && m != 0) || (m & ~colmask))
+                    return fail(BLEST_ERR_INVALID_ARG, "mask inconsistent with the VSS count or the columns");
+            }
+        }
+    }
+    if (unpadded != hd.unpadded) return fail(BLEST_ERR_INVALID_ARG, "unpadded slice count mismatch");
+
+    std::unique_ptr<blest_graph, void (*)(blest_graph*)> h(new blest_graph(), free_handle);
+    blest_status bs = init_device(h.get());
+    if (bs) return bs;
+    h->n = hd.n;
+    h->nnz = hd.nnz;
+    h->offsets = offsets;
+    blest::DeviceBvss& b = h->bvss;
+    b.n = hd.n;
+    b.nss = hd.nss;
+    b.nvss = hd.nvss;
+    b.unpadded = hd.unpadded;
+    cudaError_t e;
+    if ((e = upload(&b.real_ptrs, rp, 1, h->stream)) != cudaSuccess || (e = upload(&b.v2r, v2r, 1, h->stream)) != cudaSuccess ||
+        (e = upload(&b.row_ids, rows, 1, h->stream)) != cudaSuccess || (e = upload(&b.masks, masks, 1, h->stream)) != cudaSuccess ||
+        (e = upload(&b.vss_count, cnt, 1, h->stream)) != cudaSuccess)
+        return cuda_fail(e, "upload BVSS");
+    if ((bs = alloc_state(h.get(), new_id)) != BLEST_OK) return bs;
+    h->stats = st;
     *out = h.release();
     return BLEST_OK;
 }
@@ -822,6 +995,54 @@ blest_status blest_msbfs(blest_handle h, const int32_t* srcs, int32_t k, int32_t
     blest_status s2 = sync_status(h);
     cudaFree(d);
     return s ? s : s2;
+}
+
+blest_status blest_distance_stats(blest_handle h, const int32_t* srcs, int32_t k, int64_t* reached,
+                                  int64_t* sum_dist, int32_t* ecc) {
+    if (!h) return fail(BLEST_ERR_INVALID_ARG, "NULL handle");
+    if (k < 0 || (k > 0 && (!srcs || !reached || !sum_dist || !ecc))) return fail(BLEST_ERR_INVALID_ARG, "bad arguments");
+    if (k == 0) return BLEST_OK;
+    std::vector<int32_t> roots;
+    blest_status s = map_sources(h, srcs, k, roots);   // validates the whole list before any work
+    if (s) return s;
+    // sources in batches whose level rows fit in 4 GiB (at most 256, one multi-source launch)
+    const int64_t n = std::max<int64_t>(h->n, 1);
+    const int32_t batch = (int32_t)std::max<int64_t>(1, std::min<int64_t>({256, k, ((int64_t)4 << 30) / (4 * n)}));
+    int32_t* d_lv = nullptr;
+    unsigned long long* d_acc = nullptr;
+    int* d_ecc = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&d_lv, sizeof(int32_t) * (size_t)batch * (size_t)n)) != cudaSuccess ||
+        (e = cudaMalloc(&d_acc, sizeof(unsigned long long) * 2 * (size_t)batch)) != cudaSuccess ||
+        (e = cudaMalloc(&d_ecc, sizeof(int) * (size_t)batch)) != cudaSuccess) {
+        cudaFree(d_lv);
+        cudaFree(d_acc);
+        return cuda_fail(e, "cudaMalloc(distance stats)");
+    }
+    std::vector<unsigned long long> acc(2 * (size_t)batch);
+    for (int32_t b0 = 0; b0 < k && !s; b0 += batch) {
+        const int32_t kb = std::min(batch, k - b0);
+        s = blest_msbfs_device(h, srcs + b0, kb, d_lv, h->stream);
+        if (s) break;
+        if ((e = blest::launch_distance_stats(d_lv, kb, h->n, d_acc, d_ecc, h->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(acc.data(), d_acc, sizeof(unsigned long long) * 2 * (size_t)kb,
+                                 cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(ecc + b0, d_ecc, sizeof(int) * (size_t)kb, cudaMemcpyDeviceToHost, h->stream)) !=
+                cudaSuccess) {
+            s = cuda_fail(e, "distance stats");
+            break;
+        }
+        if ((s = sync_status(h)) != BLEST_OK) break;
+        for (int32_t i = 0; i < kb; ++i) {
+            reached[b0 + i] = (int64_t)acc[i];
+            sum_dist[b0 + i] = (int64_t)acc[kb + i];
+        }
+    }
+    sync_status(h);
+    cudaFree(d_lv);
+    cudaFree(d_acc);
+    cudaFree(d_ecc);
+    return s;
 }
 
 blest_status blest_get_run_info(blest_handle h, blest_run_info* info, int32_t* queue_sizes, int32_t cap) {

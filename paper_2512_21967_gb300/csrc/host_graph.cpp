@@ -65,7 +65,7 @@ int clean_csr(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int thr
         for (int64_t u = lo; u < hi; ++u) {
             int32_t* a = tmp.data() + row_ptr[u];
             int64_t len = row_ptr[u + 1] - row_ptr[u];
-            std::memcpy(a, col_idx + row_ptr[u], (size_t)len * sizeof(int32_t));
+            if (len > 0) std::memcpy(a, col_idx + row_ptr[u], (size_t)len * sizeof(int32_t));
             std::sort(a, a + len);
             int64_t w = 0;
             for (int64_t i = 0; i < len; ++i)
@@ -77,7 +77,8 @@ int clean_csr(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int thr
     out.ci.resize((size_t)out.rp[n]);
     parallel_chunks(threads, n, 4096, [&](int64_t lo, int64_t hi) {
         for (int64_t u = lo; u < hi; ++u)
-            std::memcpy(out.ci.data() + out.rp[u], tmp.data() + row_ptr[u], (size_t)newdeg[u] * sizeof(int32_t));
+            if (newdeg[u] > 0)
+                std::memcpy(out.ci.data() + out.rp[u], tmp.data() + row_ptr[u], (size_t)newdeg[u] * sizeof(int32_t));
     });
     return BLEST_OK;
 }

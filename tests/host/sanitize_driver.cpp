@@ -1,0 +1,99 @@
+// Drives the host preprocessing (input cleaning, symmetry check, the three
+// orderings, the classifier, relabelling) on awkward inputs so that a build
+// with AddressSanitizer and UndefinedBehaviorSanitizer can check every path.
+// Exit code 0 when every ordering is a permutation and every relabelled graph
+// keeps its edge count; sanitizer reports abort the run by themselves.
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "host_graph.h"
+
+namespace {
+
+uint64_t mix(uint64_t z) {   // SplitMix64 finaliser (Vigna), for test inputs only
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Raw, deliberately messy symmetric CSR: duplicates, self-loops, isolated vertices.
+void make_graph(int32_t n, int64_t m, uint64_t seed, bool hubs, std::vector<int32_t>& rp, std::vector<int32_t>& ci) {
+    std::vector<std::vector<int32_t>> adj((size_t)n);
+    for (int64_t e = 0; e < m && n > 0; ++e) {
+        const uint64_t a = mix(seed + 2 * (uint64_t)e + 1), b = mix(seed + 2 * (uint64_t)e + 2);
+        int32_t u = (int32_t)(a % (uint64_t)n);
+        int32_t v = (int32_t)(b % (uint64_t)n);
+        if (hubs && (a & 3) == 0) u = (int32_t)(a % 3 % (uint64_t)n);   // a few heavy rows
+        adj[(size_t)u].push_back(v);
+        adj[(size_t)v].push_back(u);
+        if ((b & 15) == 0) adj[(size_t)u].push_back(v);   // duplicate
+    }
+    rp.assign((size_t)n + 1, 0);
+    ci.clear();
+    for (int32_t u = 0; u < n; ++u) {
+        for (int32_t v : adj[(size_t)u]) ci.push_back(v);
+        rp[(size_t)u + 1] = (int32_t)ci.size();
+    }
+}
+
+bool is_perm(const std::vector<int32_t>& p, int32_t n) {
+    if ((int32_t)p.size() != n) return false;
+    std::vector<char> seen((size_t)n, 0);
+    for (int32_t x : p) {
+        if (x < 0 || x >= n || seen[(size_t)x]) return false;
+        seen[(size_t)x] = 1;
+    }
+    return true;
+}
+
+}  // namespace
+
+int main() {
+    int failures = 0;
+    const int32_t sizes[] = {0, 1, 2, 7, 9, 64, 333, 2048};
+    for (int32_t n : sizes) {
+        for (int hubs = 0; hubs < 2; ++hubs) {
+            std::vector<int32_t> rp, ci;
+            make_graph(n, 3 * (int64_t)n, 17 + (uint64_t)n, hubs != 0, rp, ci);
+            blest::Csr g;
+            std::string err;
+            if (blest::clean_csr(n, rp.data(), ci.empty() ? nullptr : ci.data(), 2, g, err) != 0) {
+                std::printf("clean_csr failed n=%d: %s\n", n, err.c_str());
+                ++failures;
+                continue;
+            }
+            int64_t bu = -1, bv = -1;
+            if (!blest::is_symmetric(g, 2, &bu, &bv)) { std::printf("asymmetric n=%d\n", n); ++failures; }
+            (void)blest::is_social_like(g);
+            std::vector<int32_t> ids;
+            blest::order_rcm(g, ids);
+            failures += !is_perm(ids, n);
+            blest::order_hub_prepass(g, ids);
+            failures += !is_perm(ids, n);
+            for (int32_t w : {8, 64, 4096}) {
+                blest::order_jaccard_windows(g, 8, w, 3, ids);
+                failures += !is_perm(ids, n);
+                blest::order_compress(g, 8, w, 2, ids);
+                failures += !is_perm(ids, n);
+                blest::Csr r;
+                blest::relabel_csr(g, ids, 2, r);
+                failures += r.nnz() != g.nnz();
+            }
+        }
+    }
+    // invalid inputs are rejected, not read out of bounds
+    {
+        const int32_t rp[] = {0, 2, 1};
+        const int32_t ci[] = {1, 0};
+        blest::Csr g;
+        std::string err;
+        failures += blest::clean_csr(2, rp, ci, 1, g, err) == 0;
+        const int32_t rp2[] = {0, 1, 2};
+        const int32_t ci2[] = {5, 0};
+        failures += blest::clean_csr(2, rp2, ci2, 1, g, err) == 0;
+    }
+    std::printf("failures=%d\n", failures);
+    return failures == 0 ? 0 : 1;
+}

@@ -125,3 +125,22 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.blest_sync(None) == 1
     lib.blest_destroy(None)
     assert blest.blest_export_size(None, 0) == -1
+
+
+def test_graph_load_rejects_bad_files(tmp_path):
+    """A checkpoint is untrusted input: wrong magic, a truncated file and an
+    out-of-range row id are refused on the host, before any device work."""
+    p = tmp_path / "bad.blest"
+    p.write_bytes(b"NOTBLEST" + bytes(200))
+    with pytest.raises(blest.BlestError) as e:
+        blest.blest_graph_load(str(p))
+    assert e.value.status == blest.BLEST_ERR_INVALID_ARG
+    with pytest.raises(blest.BlestError):
+        blest.blest_graph_load(str(tmp_path / "missing.blest"))
+    # a valid-looking header for n = 16 with one VSS, then a truncated body
+    import struct
+    hdr = b"BLESTG1\x00" + struct.pack("<iiqiiqqq", 1, 16, 4, 2, 0, 1, 2, 0)
+    p.write_bytes(hdr + bytes(16))
+    with pytest.raises(blest.BlestError) as e:
+        blest.blest_graph_load(str(p))
+    assert "shorter" in str(e.value)

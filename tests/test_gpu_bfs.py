@@ -456,3 +456,87 @@ def test_level_timeline_and_arrivals(cfg1, update):
             assert t[2 * L + 2] <= t[2 * L + 3]
     finally:
         blest.blest_destroy(h)
+
+
+def test_distance_stats_match_oracle(gpu):
+    """Closeness / diameter statistics over 300 sources (two multi-source
+    batches) on an R-MAT graph with isolated vertices, and on a grid."""
+    g = synth.rmat_graph(11, 8, seed=77)
+    srcs = synth.pick_sources(g, 300, seed=5)
+    srcs[7] = int(np.nonzero(np.diff(g.row_ptr) == 0)[0][0])   # an isolated source
+    h = blest.blest_graph_create(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_COMPRESS)
+    try:
+        got = blest.blest_distance_stats(h, srcs)
+        exp = oracle.distance_stats(g.n, g.row_ptr, g.col_idx, srcs, threads=8)
+        for a, b in zip(got, exp):
+            assert np.array_equal(a, b)
+        assert got[0][7] == 1 and got[1][7] == 0 and got[2][7] == 0
+        with pytest.raises(blest.BlestError):
+            blest.blest_distance_stats(h, [0, g.n])
+    finally:
+        blest.blest_destroy(h)
+    gg, gs = synth.grid_workload(48, 5, seed_graph=9, seed_src=9)
+    h = blest.blest_graph_create(gg.n, gg.row_ptr, gg.col_idx, blest.BLEST_ORDER_BANDWIDTH)
+    try:
+        got = blest.blest_distance_stats(h, gs)
+        exp = oracle.distance_stats(gg.n, gg.row_ptr, gg.col_idx, gs)
+        for a, b in zip(got, exp):
+            assert np.array_equal(a, b)
+    finally:
+        blest.blest_destroy(h)
+
+
+def test_checkpoint_round_trip(gpu, tmp_path):
+    """A saved and reloaded handle has the same arrays, statistics and levels;
+    a file with one row id corrupted is refused."""
+    g = synth.rmat_graph(12, 16, seed=13)
+    srcs = synth.pick_sources(g, 6, seed=3)
+    h = blest.blest_graph_create_ex(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_COMPRESS, window=256)
+    path = str(tmp_path / "g.blest")
+    try:
+        blest.blest_graph_save(h, path)
+        h2 = blest.blest_graph_load(path)
+        try:
+            for which in (blest.BLEST_ARRAY_REAL_PTRS, blest.BLEST_ARRAY_VIRTUAL_TO_REAL, blest.BLEST_ARRAY_ROW_IDS,
+                          blest.BLEST_ARRAY_MASKS, blest.BLEST_ARRAY_NEW_ID, blest.BLEST_ARRAY_VSS_COUNT):
+                assert np.array_equal(blest.blest_export(h, which), blest.blest_export(h2, which))
+            assert blest.blest_get_stats(h) == blest.blest_get_stats(h2)
+            for s in srcs:
+                assert np.array_equal(blest.blest_bfs(h2, int(s)), oracle.bfs_levels(g.n, g.row_ptr, g.col_idx, int(s)))
+        finally:
+            blest.blest_destroy(h2)
+    finally:
+        blest.blest_destroy(h)
+    raw = bytearray(open(path, "rb").read())
+    # corrupt the last int32 of the row-id array: it sits just before masks and counts
+    nvss = int(np.frombuffer(bytes(raw[32:40]), np.int64)[0])
+    tail = 4 * 32 * nvss + 4 * nvss
+    pos = len(raw) - tail - 4
+    raw[pos:pos + 4] = np.array([g.n + 5], np.int32).tobytes()
+    bad = str(tmp_path / "bad.blest")
+    open(bad, "wb").write(bytes(raw))
+    with pytest.raises(blest.BlestError) as e:
+        blest.blest_graph_load(bad)
+    assert "row id" in str(e.value)
+
+
+def test_checkpoint_batch_handle(gpu, tmp_path):
+    graphs = [synth.rmat_graph(9, 8, seed=s) for s in (1, 2)] + [synth.grid_graph(20, 0.9, seed=3)[0]]
+    h = blest.blest_batch_create([(g.n, g.row_ptr, g.col_idx) for g in graphs],
+                                 [blest.BLEST_ORDER_COMPRESS, blest.BLEST_ORDER_COMPRESS, blest.BLEST_ORDER_BANDWIDTH])
+    path = str(tmp_path / "b.blest")
+    try:
+        blest.blest_graph_save(h, path)
+        want = blest.blest_batch_bfs(h, [3, 5, 7])
+    finally:
+        blest.blest_destroy(h)
+    h2 = blest.blest_graph_load(path)
+    try:
+        got = blest.blest_batch_bfs(h2, [3, 5, 7])
+        assert np.array_equal(got, want)
+        off = 0
+        for g, s in zip(graphs, (3, 5, 7)):
+            assert np.array_equal(got[off:off + g.n], oracle.bfs_levels(g.n, g.row_ptr, g.col_idx, s))
+            off += g.n
+    finally:
+        blest.blest_destroy(h2)

@@ -1,0 +1,33 @@
+"""The host preprocessing (cleaning, orderings, classifier, relabelling)
+built with AddressSanitizer and UndefinedBehaviorSanitizer and driven over
+awkward inputs: empty and one-vertex graphs, isolated vertices, duplicates,
+self-loops, hub rows, windows larger than the graph, invalid CSR."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+from conftest import ROOT
+
+CSRC = os.path.join(ROOT, "paper_2512_21967_gb300", "csrc")
+DRIVER = os.path.join(ROOT, "tests", "host", "sanitize_driver.cpp")
+
+
+def test_host_preprocessing_under_asan_ubsan(tmp_path):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no g++")
+    exe = str(tmp_path / "sanitize_driver")
+    cmd = [gxx, "-std=c++17", "-O1", "-g", "-fno-omit-frame-pointer", "-fsanitize=address,undefined",
+           "-fno-sanitize-recover=undefined", "-I", CSRC, os.path.join(CSRC, "host_graph.cpp"), DRIVER,
+           "-o", exe, "-pthread"]
+    build = subprocess.run(cmd, capture_output=True, text=True)
+    if build.returncode != 0 and "sanitize" in build.stderr and "cannot find" in build.stderr:
+        pytest.skip("sanitizer runtime not installed")
+    assert build.returncode == 0, build.stderr[-3000:]
+    env = dict(os.environ, ASAN_OPTIONS="detect_leaks=1:abort_on_error=1", UBSAN_OPTIONS="halt_on_error=1")
+    run = subprocess.run([exe], capture_output=True, text=True, env=env, timeout=300)
+    assert run.returncode == 0, (run.stdout[-2000:], run.stderr[-4000:])
+    assert "runtime error" not in run.stderr
+    assert "failures=0" in run.stdout

@@ -208,3 +208,37 @@ def test_planted_parent_mistake_is_caught():
     bad[v] = src if src not in g.col_idx[g.row_ptr[v]:g.row_ptr[v + 1]] else -1
     with pytest.raises(AssertionError):
         check_tree(g, src, lvl, bad)
+
+
+def test_distance_stats_closed_forms():
+    """Path from an end: sum n(n-1)/2, eccentricity n-1; star centre: n-1 and 1;
+    full w x h grid from a corner: sum of x + y, eccentricity w + h - 2; a
+    vertex of a K6 + C6 graph reaches only its own component."""
+    n = 23
+    g = csr_from_undirected(n, [(i, i + 1) for i in range(n - 1)])
+    r, t, e = oracle.distance_stats(n, g.row_ptr, g.col_idx, [0, 11])
+    assert r.tolist() == [n, n] and t[0] == n * (n - 1) // 2 and e.tolist() == [n - 1, 11]
+    assert t[1] == 2 * sum(range(1, 12)) and (n - 1) / t[0] == 2 / n          # closeness of an end
+    s = csr_from_undirected(9, [(0, i) for i in range(1, 9)])
+    r, t, e = oracle.distance_stats(9, s.row_ptr, s.col_idx, [0, 3])
+    assert r.tolist() == [9, 9] and t.tolist() == [8, 1 + 2 * 7] and e.tolist() == [1, 2]
+    w, h = 7, 5
+    edges = [(y * w + x, y * w + x + 1) for y in range(h) for x in range(w - 1)]
+    edges += [(y * w + x, (y + 1) * w + x) for y in range(h - 1) for x in range(w)]
+    gg = csr_from_undirected(w * h, edges)
+    r, t, e = oracle.distance_stats(w * h, gg.row_ptr, gg.col_idx, [0])
+    assert t[0] == h * w * (w - 1) // 2 + w * h * (h - 1) // 2 and e[0] == w + h - 2
+    edges = [(i, j) for i in range(6) for j in range(i + 1, 6)] + [(6 + i, 6 + (i + 1) % 6) for i in range(6)]
+    kc = csr_from_undirected(13, edges)
+    r, t, e = oracle.distance_stats(13, kc.row_ptr, kc.col_idx, [2, 7, 12])
+    assert r.tolist() == [6, 6, 1] and t.tolist() == [5, 1 + 1 + 2 + 2 + 3, 0] and e.tolist() == [1, 3, 0]
+
+
+def test_distance_stats_planted_mistake():
+    """Counting the source's own level once more per neighbour ring (an
+    off-by-one in the sum) must break the path closed form."""
+    n = 10
+    g = csr_from_undirected(n, [(i, i + 1) for i in range(n - 1)])
+    lv = oracle.bfs_levels(n, g.row_ptr, g.col_idx, 0)
+    bad = int((lv[lv >= 0] + 1).sum())
+    assert bad != oracle.distance_stats(n, g.row_ptr, g.col_idx, [0])[1][0]
