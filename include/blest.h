@@ -96,9 +96,10 @@ typedef enum {
                                         first use: about 5 B per slice more device memory) */
     BLEST_OPT_SCHEDULE = 11          /* stage-1 work split of the double-buffered path (stage depth 2):
                                         0 = static, warp w takes queue entries w, w + W, ... (default);
-                                        1 = static for the first 7/8 of the queue, then warps take
-                                        chunks of the rest from a per-level counter, sized (entries
-                                        left) / (2 x warps) within [2 x unroll, 64] (guided) */
+                                        1 = on levels with at least 16 queue entries per warp, static
+                                        for the first 7/8 of the queue, then warps take chunks of the
+                                        rest from a per-level counter, sized (entries left) /
+                                        (2 x warps) within [2 x unroll, 64] (guided); else as 0 */
 } blest_option;
 
 /* Creation parameters; pass NULL to blest_graph_create_ex for the defaults. */

@@ -67,9 +67,15 @@ struct blest_graph {
     int32_t* d_new_id = nullptr;
     int32_t* d_L = nullptr;              // internal levels (BVSS ids)
     int32_t* d_out = nullptr;            // staging for host-output calls (original ids)
+    // [F0 F1 F2 | V_curr | V_next | dirty | control block] in one allocation, so that
+    // one memset clears the bitmaps a traversal needs and the control block's counters
+    unsigned char* d_state = nullptr;
+    size_t bitmap_bytes = 0;             // each bitmap, rounded up to 256 B
+    size_t dirty_bytes = 0;              // 1 bit per bitmap word, rounded up to 256 B
     uint32_t* d_vcur = nullptr;
     uint32_t* d_vnext = nullptr;
-    uint32_t* d_F = nullptr;             // 3 * nwords
+    uint32_t* d_dirty = nullptr;
+    uint32_t* d_F = nullptr;             // 3 bitmaps, bitmap_bytes apart (eager frontier)
     unsigned long long* d_Q = nullptr;   // 3 * qcap
     unsigned int qcap = 0;
     unsigned int* d_ctrl = nullptr;      // 256-byte control block (device_common.cuh layout)
@@ -128,11 +134,8 @@ void free_handle(blest_graph* h) {
     cudaFree(h->d_new_id);
     cudaFree(h->d_L);
     cudaFree(h->d_out);
-    cudaFree(h->d_vcur);
-    cudaFree(h->d_vnext);
-    cudaFree(h->d_F);
+    cudaFree(h->d_state);
     cudaFree(h->d_Q);
-    cudaFree(h->d_ctrl);
     cudaFree(h->d_level_sizes);
     cudaFree(h->d_level_times);
     cudaFree(h->d_arrive);
@@ -170,11 +173,15 @@ blest_status alloc_state(blest_graph* h, const std::vector<int32_t>& new_id) {
     if ((e = cudaMalloc(&(ptr), (bytes))) != cudaSuccess) return cuda_fail(e, what);
     BLEST_ALLOC(h->d_L, sizeof(int32_t) * std::max<size_t>(h->n, 1), "cudaMalloc(levels)");
     BLEST_ALLOC(h->d_out, sizeof(int32_t) * std::max<size_t>(h->n, 1), "cudaMalloc(out)");
-    BLEST_ALLOC(h->d_vcur, sizeof(uint32_t) * std::max<size_t>(nw, 1), "cudaMalloc(vcur)");
-    BLEST_ALLOC(h->d_vnext, sizeof(uint32_t) * std::max<size_t>(nw, 1), "cudaMalloc(vnext)");
-    BLEST_ALLOC(h->d_F, sizeof(uint32_t) * 3 * std::max<size_t>(nw, 1), "cudaMalloc(frontier)");
+    h->bitmap_bytes = (sizeof(uint32_t) * std::max<size_t>(nw, 1) + 255) / 256 * 256;
+    h->dirty_bytes = (sizeof(uint32_t) * ((std::max<size_t>(nw, 1) + 31) / 32) + 255) / 256 * 256;
+    BLEST_ALLOC(h->d_state, 5 * h->bitmap_bytes + h->dirty_bytes + kCtrlBytes, "cudaMalloc(bitmaps)");
+    h->d_F = reinterpret_cast<uint32_t*>(h->d_state);
+    h->d_vcur = reinterpret_cast<uint32_t*>(h->d_state + 3 * h->bitmap_bytes);
+    h->d_vnext = reinterpret_cast<uint32_t*>(h->d_state + 4 * h->bitmap_bytes);
+    h->d_dirty = reinterpret_cast<uint32_t*>(h->d_state + 5 * h->bitmap_bytes);
+    h->d_ctrl = reinterpret_cast<unsigned int*>(h->d_state + 5 * h->bitmap_bytes + h->dirty_bytes);
     BLEST_ALLOC(h->d_Q, sizeof(unsigned long long) * 3 * (size_t)h->qcap, "cudaMalloc(queues)");
-    BLEST_ALLOC(h->d_ctrl, kCtrlBytes, "cudaMalloc(ctrl)");
     BLEST_ALLOC(h->d_level_sizes, sizeof(int32_t) * kLevelRecordCap, "cudaMalloc(level record)");
     BLEST_ALLOC(h->d_level_times, sizeof(unsigned long long) * (2 * (size_t)kLevelRecordCap + 2), "cudaMalloc(level times)");
     BLEST_ALLOC(h->d_arrive, sizeof(unsigned long long) * 2 * (size_t)kLevelRecordCap, "cudaMalloc(level arrivals)");
@@ -318,9 +325,9 @@ blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots
     L.levels_from_bitmap = (L.update == 2 && h->d_new_id && !h->need_internal_levels) ? 1 : 0;
     L.vcur = h->d_vcur;
     L.vnext = h->d_vnext;
-    const size_t nw = (size_t)h->nwords();
+    L.dirty = h->d_dirty;
     for (int i = 0; i < 3; ++i) {
-        L.F[i] = h->d_F + i * nw;
+        L.F[i] = reinterpret_cast<uint32_t*>(h->d_state + i * h->bitmap_bytes);
         L.Q[i] = h->d_Q + i * (size_t)h->qcap;
     }
     L.ctrl = h->d_ctrl;
@@ -355,15 +362,14 @@ blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots
     L.out = d_out;
     L.timeout_ns = (uint64_t)h->timeout_us * 1000ull;
     L.phantom = h->phantom ? 1u : 0u;
-    cudaMemsetAsync(h->d_ctrl, 0, kCtrlClearBytes, st);
+    // [F (eager only) | V_curr | V_next | dirty | control block up to the sticky status word]
+    const size_t skip = L.update == 1 ? 0 : 3 * h->bitmap_bytes;
+    cudaMemsetAsync(h->d_state + skip, 0, 5 * h->bitmap_bytes + h->dirty_bytes - skip + kCtrlClearBytes, st);
     if (!L.levels_from_bitmap) cudaMemsetAsync(L.levels_internal, 0xFF, sizeof(int32_t) * (size_t)h->n, st);
     if (L.level_sizes) {
         cudaMemsetAsync(L.arrive_first, 0xFF, sizeof(unsigned long long) * kLevelRecordCap, st);
         cudaMemsetAsync(L.arrive_last, 0, sizeof(unsigned long long) * kLevelRecordCap, st);
     }
-    cudaMemsetAsync(h->d_vcur, 0, sizeof(uint32_t) * nw, st);
-    cudaMemsetAsync(h->d_vnext, 0, sizeof(uint32_t) * nw, st);
-    if (L.update == 1) cudaMemsetAsync(h->d_F, 0, sizeof(uint32_t) * 3 * nw, st);
     if ((e = blest::launch_bfs_kernel(L, st)) != cudaSuccess) return cuda_fail(e, "traversal launch");
     h->last_stream = st;
     h->info.update = L.update == 1 ? BLEST_UPDATE_EAGER : BLEST_UPDATE_LAZY;

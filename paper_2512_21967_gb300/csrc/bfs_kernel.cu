@@ -49,6 +49,7 @@ struct BfsArgs {
     int32_t* L;
     uint32_t* vcur;
     uint32_t* vnext;
+    uint32_t* dirty;                      // 1 bit per V_next word touched on a sparse level (NULL = never sparse)
     uint32_t* F[3];
     unsigned long long* Q[3];
     Ctrl* ctrl;
@@ -104,17 +105,29 @@ __device__ __forceinline__ unsigned int pull_hits(uint32_t mask, uint32_t alpha,
 // (lazy) or its id (eager, which also stores diff into the frontier bitmap).
 // LAYOUT 1 enqueues the slice set's VSSs of the compact layout (group offset,
 // group count, alpha) instead of VSS ids.
+//
+// Sparse levels (stage 1 set a dirty bit per touched V_next word): the warp
+// visits only the 32-word blocks whose dirty word is nonzero, clears it, and
+// treats the other words of the block as unchanged.
 template <int UPDATE, int LAYOUT>
 __device__ __forceinline__ void sweep(const BfsArgs& a, int lvl, unsigned long long* Qout, unsigned int* qcount,
-                                      uint32_t* Fout) {
+                                      uint32_t* Fout, bool sparse) {
     const int lane = threadIdx.x & 31;
     const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    const int nblk = (a.nwords + kWarp - 1) / kWarp;
     unsigned int fresh = 0;   // rows this lane gave a level
-    for (int t0 = gwarp * kWarp; t0 < a.nwords; t0 += nwarps * kWarp) {
+    for (int b = gwarp; b < nblk; b += nwarps) {
+        const int t0 = b * kWarp;
         const int t = t0 + lane;
+        uint32_t live = 0xFFFFFFFFu;
+        if (sparse) {
+            live = ld_cg(&a.dirty[b]);
+            if (live == 0u) continue;   // warp-uniform
+            if (lane == 0) a.dirty[b] = 0u;
+        }
         uint32_t diff = 0;
-        if (t < a.nwords) {
+        if (t < a.nwords && ((live >> lane) & 1u)) {
             const uint32_t nx = ld_cg(&a.vnext[t]);
             const uint32_t cu = ld_cg(&a.vcur[t]);
             diff = nx ^ cu;
@@ -174,7 +187,8 @@ __device__ __forceinline__ void sweep(const BfsArgs& a, int lvl, unsigned long l
 // and costs an extra L2 load per hit once most are visited; the kernel applies
 // it only while fewer than n/4 rows have a level.
 template <int NV>
-__device__ __forceinline__ void mark_rows(const BfsArgs& a, const int4 (&rows)[NV], unsigned int hm, int filt) {
+__device__ __forceinline__ void mark_rows(const BfsArgs& a, const int4 (&rows)[NV], unsigned int hm, int filt,
+                                          uint32_t* dirty) {
     int u[4 * NV];
     uint32_t w[4 * NV];
 #pragma unroll
@@ -194,7 +208,10 @@ __device__ __forceinline__ void mark_rows(const BfsArgs& a, const int4 (&rows)[N
 #pragma unroll
     for (int k = 0; k < 4 * NV; ++k) {
         const uint32_t bit = 1u << (u[k] & 31);
-        if (((hm >> k) & 1u) && !(w[k] & bit)) atomicOr(&a.vnext[u[k] >> 5], bit);
+        if (((hm >> k) & 1u) && !(w[k] & bit)) {
+            atomicOr(&a.vnext[u[k] >> 5], bit);
+            if (dirty) atomicOr(&dirty[u[k] >> 10], 1u << ((u[k] >> 5) & 31));
+        }
     }
 }
 
@@ -287,7 +304,7 @@ __device__ __forceinline__ bool warp_wait_stage(uint32_t bar, uint32_t parity, u
 template <int PULL, int DEPTH, int U>
 __device__ __forceinline__ bool stage1_staged(const BfsArgs& a, const unsigned long long* __restrict__ Qin,
                                               unsigned int qn, unsigned char* ring, uint32_t& uses, uint64_t pol,
-                                              int lane, int gwarp, int nwarps, int filt) {
+                                              int lane, int gwarp, int nwarps, int filt, uint32_t* dirty) {
     static_assert(DEPTH >= 2 * U, "the ring must hold at least two groups of tiles");
     int4* rows = reinterpret_cast<int4*>(ring);
     uint32_t* msk = reinterpret_cast<uint32_t*>(ring + DEPTH * 512);
@@ -357,7 +374,7 @@ __device__ __forceinline__ bool stage1_staged(const BfsArgs& a, const unsigned l
         unsigned int hm = 0;
 #pragma unroll
         for (int j = 0; j < U; ++j) hm |= pull_hits<PULL>(m[j], alpha[j], lane) << (4 * j);
-        mark_rows<U>(a, r, hm, filt);
+        mark_rows<U>(a, r, hm, filt, dirty);
     }
     uses += nk;
     return true;
@@ -427,8 +444,9 @@ __device__ __forceinline__ void load_tile(const BfsArgs& a, unsigned long long e
 // another.  A group is U queue entries.
 //
 // Schedules.  Static (sched 0): warp w takes entries w, w + W, w + 2W, ... (W =
-// warps), U at a time.  Static + dynamic tail (sched 1): the first 7/8 of the
-// queue is split statically as above, and a warp that has finished its static
+// warps), U at a time.  Static + dynamic tail (sched 1, on queues of at least
+// 16 entries per warp): the first 7/8 of the queue is split statically as
+// above, and a warp that has finished its static
 // share takes chunks of the last 1/8 from the level's counter in the control
 // block (guided self-scheduling: (entries left) / 2W at its previous grab,
 // within [2U, 64]), so blocks on faster SMs absorb the end of the level.
@@ -437,8 +455,10 @@ constexpr unsigned int kChunkMax = 64;
 template <int PULL, int U, int LAYOUT>
 __device__ __forceinline__ void stage1_pipelined(const BfsArgs& a, const unsigned long long* __restrict__ Qin,
                                                  unsigned int qn, uint64_t pol, int lane, int gwarp, int nwarps,
-                                                 int filt, unsigned int* work) {
-    const bool dyn = work != nullptr;
+                                                 int filt, unsigned int* work, uint32_t* dirty) {
+    // the dynamic tail only pays on long queues: on a short one nearly every warp
+    // would go straight to the counter and the atomics would serialise
+    const bool dyn = work != nullptr && qn >= 16u * (unsigned int)nwarps;
     const unsigned int stride = (unsigned int)nwarps * U;
     const unsigned int slim = dyn ? qn - qn / 8u : qn;   // end of the static part
     unsigned int sbase = (unsigned int)gwarp;
@@ -501,7 +521,7 @@ __device__ __forceinline__ void stage1_pipelined(const BfsArgs& a, const unsigne
 #pragma unroll
         for (int i = 0; i < U; ++i)   // e_cur[i] is the same in every lane, so the MMA runs warp-wide
             if (e_cur[i] != ~0ull) hm |= pull_hits<PULL>(m_cur[i], (uint32_t)(e_cur[i] >> 32) & 0xFFu, lane) << (4 * i);
-        mark_rows<U>(a, r_cur, hm, filt);
+        mark_rows<U>(a, r_cur, hm, filt, dirty);
 #pragma unroll
         for (int i = 0; i < U; ++i) {
             e_cur[i] = e_nxt[i];
@@ -539,14 +559,19 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
     }
 
     if (gtid == 0 && a.level_sizes) a.level_times[1] = global_timer_ns();   // kernel entry (block 0)
-    // level 0: mark the sources (V_curr, V_next, L were cleared before launch)
+    // level 0: mark the sources (V_curr, V_next and the dirty bits were cleared before launch).
+    // A level is sparse when its queue (or source list) is short against the bitmap: then
+    // stage 1 records the V_next words it touches and the sweep visits only those.
+    const unsigned int sparse_cap = a.dirty ? (unsigned int)(a.nwords >> 6) : 0u;
+    const bool sparse0 = a.dirty != nullptr && (unsigned int)a.nroots <= sparse_cap;
     for (int i = gtid; i < a.nroots; i += nthreads) {
         const int r = a.nroots <= kInlineRoots ? a.inline_roots[i] : a.roots[i];
         atomicOr(&a.vnext[r >> 5], 1u << (r & 31));
+        if (sparse0) atomicOr(&a.dirty[r >> 10], 1u << ((r >> 5) & 31));
     }
     if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns)) return;
     if (gtid == 0 && a.level_sizes) a.level_times[0] = global_timer_ns();
-    sweep<UPDATE, LAYOUT>(a, 0, a.Q[1], &ctrl->qcount[1], a.F[1]);
+    sweep<UPDATE, LAYOUT>(a, 0, a.Q[1], &ctrl->qcount[1], a.F[1], sparse0);
     unsigned int qn = 0, qprev = 0;
     if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns, &ctrl->qcount[1], &qn)) return;
 
@@ -577,12 +602,14 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
         // stage 1: pull the queued virtual slice sets, round-robin over warps
         // the lazy filter of this level: the V_next test only while few rows are visited
         const int filt = (a.filter == 2 && ld_cg(&ctrl->reached) >= (unsigned int)a.n / 4u) ? 1 : a.filter;
+        const bool sparse = UPDATE == 2 && a.dirty != nullptr && qn <= sparse_cap;
+        uint32_t* dirty = sparse ? a.dirty : nullptr;
         if (DEPTH == 2) {
             stage1_pipelined<PULL, UNROLL, LAYOUT>(a, Qin, qn, pol, lane, gwarp, nwarps, filt,
-                                                   a.sched ? &ctrl->work[lvl & 1] : nullptr);
+                                                   a.sched ? &ctrl->work[lvl & 1] : nullptr, dirty);
         } else if (DEPTH > 0) {
             stage1_staged<PULL, (DEPTH > 2 ? DEPTH : 2 * UNROLL), UNROLL>(a, Qin, qn, ring, ring_uses, pol, lane,
-                                                                            gwarp, nwarps, filt);
+                                                                            gwarp, nwarps, filt, dirty);
         } else
         for (unsigned int base = (unsigned int)gwarp; base < qn; base += (unsigned int)nwarps * UNROLL) {
             unsigned long long ent[UNROLL];
@@ -605,7 +632,7 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
                 for (int i = 0; i < UNROLL; ++i)
                     if (ent[i] != ~0ull)
                         hm |= pull_hits<PULL>(msk[i], (uint32_t)(ent[i] >> 32) & 0xFFu, lane) << (4 * i);
-                mark_rows<UNROLL>(a, rows, hm, filt);
+                mark_rows<UNROLL>(a, rows, hm, filt, dirty);
             } else {
                 uint32_t alpha[UNROLL];
 #pragma unroll
@@ -635,7 +662,7 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
         if (UPDATE == 2) {
             if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns)) return;
             if (gtid == 0 && a.level_sizes && lvl - 1 < a.level_cap) a.level_times[2 * lvl + 1] = global_timer_ns();
-            sweep<UPDATE, LAYOUT>(a, lvl, Qout, qcount_next, nullptr);
+            sweep<UPDATE, LAYOUT>(a, lvl, Qout, qcount_next, nullptr, sparse);
         }
         unsigned int qnext = 0;
         if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns, qcount_next, &qnext)) return;
@@ -754,6 +781,7 @@ cudaError_t launch_bfs_kernel(const BfsLaunch& L, cudaStream_t stream) {
     a.L = L.levels_internal;
     a.vcur = L.vcur;
     a.vnext = L.vnext;
+    a.dirty = L.dirty;
     for (int i = 0; i < 3; ++i) { a.F[i] = L.F[i]; a.Q[i] = L.Q[i]; }
     a.ctrl = reinterpret_cast<Ctrl*>(L.ctrl);
     a.level_sizes = L.level_sizes;

@@ -32,6 +32,7 @@ struct BfsLaunch {
     int32_t* levels_internal = nullptr;
     uint32_t* vcur = nullptr;
     uint32_t* vnext = nullptr;
+    uint32_t* dirty = nullptr;          // ceil(nwords / 32) words, zero before launch (NULL: no sparse levels)
     uint32_t* F[3] = {nullptr, nullptr, nullptr};
     unsigned long long* Q[3] = {nullptr, nullptr, nullptr};
     void* ctrl = nullptr;      // 256-byte control block (device_common.cuh)
