@@ -279,10 +279,13 @@ blest_status blest_get_level_times(blest_handle h, uint64_t* times_ns, int32_t c
 /* Load balance of the last single-frontier traversal (recorded with
  * BLEST_OPT_RECORD_LEVELS = 1): for level l >= 1, first_ns[l-1] and
  * last_ns[l-1] are the globaltimer stamps (ns) at which the first and the last
- * block of the persistent grid finished the level's stage 1; their gap is the
- * time blocks wait at the level's barrier for the slowest one.  Up to cap
- * entries each; both arrays host, caller-owned.  Waits for the handle's work. */
-blest_status blest_get_level_arrivals(blest_handle h, uint64_t* first_ns, uint64_t* last_ns, int32_t cap);
+ * block of the persistent grid finished the level's stage 1 (phase 0) or its
+ * finalisation sweep (phase 1, lazy levels only; entries of eager levels are
+ * left at UINT64_MAX / 0); their gap is the time blocks wait at the level's
+ * barrier for the slowest one.  Up to cap entries each; both arrays host,
+ * caller-owned.  INVALID_ARG for another phase.  Waits for the handle's work. */
+blest_status blest_get_level_arrivals(blest_handle h, int32_t phase, uint64_t* first_ns, uint64_t* last_ns,
+                                      int32_t cap);
 
 /* ---------------------------------------------------------------- autotune */
 

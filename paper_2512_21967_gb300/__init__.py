@@ -145,7 +145,7 @@ def lib():
             "blest_get_run_info": (ctypes.c_int, [_vp, ctypes.POINTER(RunInfo), _i32p, ctypes.c_int32]),
             "blest_autotune": (ctypes.c_int, [_vp, _i32p, ctypes.c_int32, ctypes.POINTER(TuneResult)]),
             "blest_get_level_times": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32]),
-            "blest_get_level_arrivals": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64),
+            "blest_get_level_arrivals": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64),
                                                         ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32]),
             "blest_graph_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
             "blest_graph_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_vp)]),
@@ -376,12 +376,13 @@ def blest_get_level_times(h: int, cap: int = 1 << 17) -> np.ndarray:
     return out
 
 
-def blest_get_level_arrivals(h: int, cap: int) -> tuple[np.ndarray, np.ndarray]:
-    """(first, last) globaltimer stamps at which blocks finished each level's stage 1."""
+def blest_get_level_arrivals(h: int, cap: int, phase: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """(first, last) globaltimer stamps at which blocks finished each level's
+    stage 1 (phase 0) or finalisation sweep (phase 1)."""
     first = np.zeros(cap, np.uint64)
     last = np.zeros(cap, np.uint64)
     p = ctypes.POINTER(ctypes.c_uint64)
-    _check(lib().blest_get_level_arrivals(h, first.ctypes.data_as(p), last.ctypes.data_as(p), int(cap)),
+    _check(lib().blest_get_level_arrivals(h, int(phase), first.ctypes.data_as(p), last.ctypes.data_as(p), int(cap)),
            "blest_get_level_arrivals")
     return first, last
 

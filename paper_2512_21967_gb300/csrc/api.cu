@@ -81,8 +81,8 @@ struct blest_graph {
     unsigned int* d_ctrl = nullptr;      // 256-byte control block (device_common.cuh layout)
     int32_t* d_level_sizes = nullptr;
     unsigned long long* d_level_times = nullptr;
-    unsigned long long* d_arrive = nullptr;   // 2 * kLevelRecordCap: first, then last stage-1 block ends
-    int32_t* d_old_of = nullptr;         // BVSS id -> original id (parent output), made on first use
+    unsigned long long* d_arrive = nullptr;   // 4 * kLevelRecordCap: first (stage 1, sweep), then last
+    int32_t* d_old_of = nullptr;         // BVSS id -> original id (direct level writes, parent output)
     int32_t* d_cand = nullptr;           // parent candidates (BVSS ids), made on first use
     int32_t* d_parents = nullptr;
     bool need_internal_levels = false;   // the next traversal must leave L cleared for unreached rows
@@ -184,13 +184,19 @@ blest_status alloc_state(blest_graph* h, const std::vector<int32_t>& new_id) {
     BLEST_ALLOC(h->d_Q, sizeof(unsigned long long) * 3 * (size_t)h->qcap, "cudaMalloc(queues)");
     BLEST_ALLOC(h->d_level_sizes, sizeof(int32_t) * kLevelRecordCap, "cudaMalloc(level record)");
     BLEST_ALLOC(h->d_level_times, sizeof(unsigned long long) * (2 * (size_t)kLevelRecordCap + 2), "cudaMalloc(level times)");
-    BLEST_ALLOC(h->d_arrive, sizeof(unsigned long long) * 2 * (size_t)kLevelRecordCap, "cudaMalloc(level arrivals)");
+    BLEST_ALLOC(h->d_arrive, sizeof(unsigned long long) * 4 * (size_t)kLevelRecordCap, "cudaMalloc(level arrivals)");
 #undef BLEST_ALLOC
     cudaMemsetAsync(h->d_ctrl, 0, kCtrlBytes, h->stream);
     if (!new_id.empty()) {
         h->h_new_id = new_id;
+        std::vector<int32_t> old_of((size_t)h->n);
+        for (int32_t v = 0; v < h->n; ++v) old_of[(size_t)new_id[(size_t)v]] = v;
         if ((e = cudaMalloc(&h->d_new_id, sizeof(int32_t) * (size_t)h->n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(new_id)");
+        if ((e = cudaMalloc(&h->d_old_of, sizeof(int32_t) * (size_t)h->n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(old_of)");
         cudaMemcpyAsync(h->d_new_id, new_id.data(), sizeof(int32_t) * (size_t)h->n, cudaMemcpyHostToDevice, h->stream);
+        cudaMemcpyAsync(h->d_old_of, old_of.data(), sizeof(int32_t) * (size_t)h->n, cudaMemcpyHostToDevice, h->stream);
+        // the host copy must live until the upload is done
+        if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(e, "upload order");
     }
     if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(e, "create");
     return BLEST_OK;
@@ -320,9 +326,10 @@ blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots
     L.masks_c = h->compact.masks;
     L.new_id = h->d_new_id;
     L.levels_internal = h->d_new_id ? h->d_L : d_out;
-    // a lazy traversal with a reordering leaves L uncleared: its epilogue takes
-    // the reached rows from V_curr (the parent pass needs cleared levels)
-    L.levels_from_bitmap = (L.update == 2 && h->d_new_id && !h->need_internal_levels) ? 1 : 0;
+    // a lazy traversal with a reordering writes levels straight to out (cleared to
+    // -1 before the launch) and needs no unpermute; the parent pass needs L
+    L.direct = (L.update == 2 && h->d_new_id && h->d_old_of && !h->need_internal_levels) ? 1 : 0;
+    L.old_of = h->d_old_of;
     L.vcur = h->d_vcur;
     L.vnext = h->d_vnext;
     L.dirty = h->d_dirty;
@@ -334,7 +341,7 @@ blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots
     L.level_sizes = h->record ? h->d_level_sizes : nullptr;
     L.level_times = h->d_level_times;
     L.arrive_first = h->d_arrive;
-    L.arrive_last = h->d_arrive + kLevelRecordCap;
+    L.arrive_last = h->d_arrive + 2 * kLevelRecordCap;
     L.level_cap = kLevelRecordCap;
     L.nroots = (int32_t)roots.size();
     if (d_roots_preloaded) {
@@ -365,10 +372,10 @@ blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots
     // [F (eager only) | V_curr | V_next | dirty | control block up to the sticky status word]
     const size_t skip = L.update == 1 ? 0 : 3 * h->bitmap_bytes;
     cudaMemsetAsync(h->d_state + skip, 0, 5 * h->bitmap_bytes + h->dirty_bytes - skip + kCtrlClearBytes, st);
-    if (!L.levels_from_bitmap) cudaMemsetAsync(L.levels_internal, 0xFF, sizeof(int32_t) * (size_t)h->n, st);
+    cudaMemsetAsync(L.direct ? d_out : L.levels_internal, 0xFF, sizeof(int32_t) * (size_t)h->n, st);
     if (L.level_sizes) {
-        cudaMemsetAsync(L.arrive_first, 0xFF, sizeof(unsigned long long) * kLevelRecordCap, st);
-        cudaMemsetAsync(L.arrive_last, 0, sizeof(unsigned long long) * kLevelRecordCap, st);
+        cudaMemsetAsync(L.arrive_first, 0xFF, sizeof(unsigned long long) * 2 * kLevelRecordCap, st);
+        cudaMemsetAsync(L.arrive_last, 0, sizeof(unsigned long long) * 2 * kLevelRecordCap, st);
     }
     if ((e = blest::launch_bfs_kernel(L, st)) != cudaSuccess) return cuda_fail(e, "traversal launch");
     h->last_stream = st;
@@ -1160,15 +1167,19 @@ blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, bles
     return BLEST_OK;
 }
 
-blest_status blest_get_level_arrivals(blest_handle h, uint64_t* first_ns, uint64_t* last_ns, int32_t cap) {
+blest_status blest_get_level_arrivals(blest_handle h, int32_t phase, uint64_t* first_ns, uint64_t* last_ns,
+                                      int32_t cap) {
     if (!h || (cap > 0 && (!first_ns || !last_ns))) return fail(BLEST_ERR_INVALID_ARG, "NULL argument");
+    if (phase != 0 && phase != 1) return fail(BLEST_ERR_INVALID_ARG, "phase must be 0 (stage 1) or 1 (sweep)");
     blest_status s = sync_status(h);
     if (s) return s;
     const int32_t m = std::min<int32_t>(cap, kLevelRecordCap);
     if (m > 0) {
-        cudaError_t e = cudaMemcpy(first_ns, h->d_arrive, sizeof(uint64_t) * (size_t)m, cudaMemcpyDeviceToHost);
+        const size_t off = (size_t)phase * kLevelRecordCap;
+        cudaError_t e = cudaMemcpy(first_ns, h->d_arrive + off, sizeof(uint64_t) * (size_t)m, cudaMemcpyDeviceToHost);
         if (e == cudaSuccess)
-            e = cudaMemcpy(last_ns, h->d_arrive + kLevelRecordCap, sizeof(uint64_t) * (size_t)m, cudaMemcpyDeviceToHost);
+            e = cudaMemcpy(last_ns, h->d_arrive + 2 * kLevelRecordCap + off, sizeof(uint64_t) * (size_t)m,
+                           cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "read level arrivals");
     }
     return BLEST_OK;

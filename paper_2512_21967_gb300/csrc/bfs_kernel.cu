@@ -37,7 +37,7 @@ namespace blest {
 constexpr int kBfsBlock = 512;
 
 struct BfsArgs {
-    int32_t n, nwords;
+    int32_t n, nwords, nss;
     unsigned int qcap;
     const int32_t* __restrict__ real_ptrs;
     const int4* __restrict__ row_ids4;
@@ -56,7 +56,7 @@ struct BfsArgs {
     int32_t* level_sizes;
     unsigned long long* level_times;      // with level_sizes: 2 globaltimer stamps per level
     unsigned long long* arrive_first;     // with level_sizes: earliest / latest block end of stage 1
-    unsigned long long* arrive_last;
+    unsigned long long* arrive_last;      // (entries [0, cap)) and of the lazy sweep ([cap, 2 cap))
     int32_t level_cap;
     const int32_t* roots;                 // device list (used when nroots > kInlineRoots)
     int32_t nroots;
@@ -65,7 +65,8 @@ struct BfsArgs {
     uint64_t timeout_ns;
     unsigned int phantom;
     int filter;                           // 1 = skip rows already in V_curr; 2 = also V_next while few are visited
-    int levels_from_bitmap;               // 1: L was not cleared; V_curr marks the rows whose level is set
+    const int32_t* __restrict__ old_of;   // BVSS id -> original id (with direct)
+    int direct;                           // 1: the sweeps write levels straight to out (original ids)
     int sched;                            // stage-1 schedule of the double-buffered path: 0 static, 1 dynamic
 };
 
@@ -112,24 +113,41 @@ __device__ __forceinline__ unsigned int pull_hits(uint32_t mask, uint32_t alpha,
 template <int UPDATE, int LAYOUT>
 __device__ __forceinline__ void sweep(const BfsArgs& a, int lvl, unsigned long long* Qout, unsigned int* qcount,
                                       uint32_t* Fout, bool sparse) {
+    // Work split: in round k, warp w of block B takes the block of 32 words
+    // B + (w + 16 k) gridDim.x, so consecutive 32-word blocks go to consecutive
+    // thread blocks: the orderings put the hubs, whose slice sets carry most of
+    // the queue entries, at the lowest ids, and one SM must not write them all
+    // while the rest of the grid waits at the barrier.  Queue space is reserved
+    // once per block and round (thread 0, after the warps posted their totals in
+    // shared memory), not once per warp: the queue size is one address that
+    // every block hits during a sweep.
+    constexpr int kWarpsPerBlock = kBfsBlock / kWarp;
+    __shared__ unsigned int s_off[kWarpsPerBlock];
+    __shared__ unsigned int s_base;
     const int lane = threadIdx.x & 31;
-    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    const int warp = threadIdx.x >> 5;
     const int nblk = (a.nwords + kWarp - 1) / kWarp;
+    const int round = (int)gridDim.x * kWarpsPerBlock;
     unsigned int fresh = 0;   // rows this lane gave a level
-    for (int b = gwarp; b < nblk; b += nwarps) {
+    for (int r0 = (int)blockIdx.x; r0 < nblk; r0 += round) {   // block-uniform bound
+        const int b = r0 + warp * (int)gridDim.x;
         const int t0 = b * kWarp;
         const int t = t0 + lane;
-        uint32_t live = 0xFFFFFFFFu;
-        if (sparse) {
-            live = ld_cg(&a.dirty[b]);
-            if (live == 0u) continue;   // warp-uniform
-            if (lane == 0) a.dirty[b] = 0u;
+        uint32_t live = b < nblk ? 0xFFFFFFFFu : 0u;
+        if (sparse && b < nblk) {
+            live = ld_cg(&a.dirty[b]);   // the same word in every lane
+            if (live != 0u && lane == 0) a.dirty[b] = 0u;
         }
         uint32_t diff = 0;
+        int rp[5] = {0, 0, 0, 0, 0};   // VSS (or group) offsets of the word's 4 slice sets and the next
         if (t < a.nwords && ((live >> lane) & 1u)) {
             const uint32_t nx = ld_cg(&a.vnext[t]);
             const uint32_t cu = ld_cg(&a.vcur[t]);
+            // issued with the bitmap loads, not after them: their addresses do not depend on diff
+            const int32_t* ptrs = LAYOUT == 1 ? a.goff : a.real_ptrs;
+#pragma unroll
+            for (int q = 0; q < 5; ++q)
+                if (4 * t + q <= a.nss) rp[q] = __ldg(&ptrs[4 * t + q]);
             diff = nx ^ cu;
             if (diff) {
                 a.vcur[t] = nx;
@@ -139,33 +157,79 @@ __device__ __forceinline__ void sweep(const BfsArgs& a, int lvl, unsigned long l
         }
         // level writes, transposed: for each of the warp's 32 words with new
         // rows, the 32 lanes store that word's 32 levels as one coalesced line
+        // (direct: each lane reads its row's original id, 8 words at a time so
+        // that those reads overlap, and stores its level there)
         unsigned int pend = __ballot_sync(0xffffffffu, diff != 0u);
-        while (pend) {
-            const int src = __ffs(pend) - 1;
-            pend &= pend - 1;
-            const uint32_t dw = __shfl_sync(0xffffffffu, diff, src);
-            if ((dw >> lane) & 1u) a.L[(t0 + src) * kWarp + lane] = lvl;
+        if (a.direct) {
+            while (pend) {
+                int o[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    o[j] = -1;
+                    if (pend) {
+                        const int src = __ffs(pend) - 1;
+                        pend &= pend - 1;
+                        const uint32_t dw = __shfl_sync(0xffffffffu, diff, src);
+                        if ((dw >> lane) & 1u) o[j] = __ldg(&a.old_of[(t0 + src) * kWarp + lane]);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (o[j] >= 0) a.out[o[j]] = lvl;
+            }
+        } else {
+            while (pend) {
+                const int src = __ffs(pend) - 1;
+                pend &= pend - 1;
+                const uint32_t dw = __shfl_sync(0xffffffffu, diff, src);
+                if ((dw >> lane) & 1u) a.L[(t0 + src) * kWarp + lane] = lvl;
+            }
         }
         int st[4], ln[4], tot[4];
         uint32_t pay[4];
+        unsigned int cnt = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const uint32_t byte = (diff >> (8 * q)) & 0xFFu;
             st[q] = 0; ln[q] = 0; tot[q] = 0; pay[q] = 0;
-            if (byte) {
+            if (byte) {   // a row of slice set s exists, so s < nss and rp[q + 1] was loaded
                 const int s = 4 * t + q;
+                st[q] = rp[q];
                 if (LAYOUT == 1) {
-                    st[q] = __ldg(&a.goff[s]);
-                    tot[q] = __ldg(&a.goff[s + 1]) - st[q];
+                    tot[q] = rp[q + 1] - rp[q];
                     ln[q] = (tot[q] + 31) >> 5;
                 } else {
-                    st[q] = __ldg(&a.real_ptrs[s]);
-                    ln[q] = __ldg(&a.real_ptrs[s + 1]) - st[q];
+                    ln[q] = rp[q + 1] - rp[q];
                 }
                 pay[q] = UPDATE == 2 ? byte : (uint32_t)s;
             }
+            cnt += (unsigned int)ln[q];
         }
-        warp_enqueue<4, LAYOUT == 1>(a.qcap, a.ctrl, Qout, qcount, st, ln, pay, lane, tot);
+        const unsigned int incl = warp_inclusive_scan(cnt, lane);
+        if (lane == 31) s_off[warp] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned int run = 0;
+            for (int w = 0; w < kWarpsPerBlock; ++w) {
+                const unsigned int x = s_off[w];
+                s_off[w] = run;
+                run += x;
+            }
+            unsigned int base = 0;
+            if (run) {
+                base = atomicAdd(qcount, run);
+                if (base + run > a.qcap || base + run < base) {
+                    raise_error(a.ctrl, 7u);
+                    base = 0xFFFFFFFFu;
+                }
+            }
+            s_base = base;
+        }
+        __syncthreads();
+        // s_off and s_base are rewritten only after the next round's first barrier
+        const unsigned int base = s_base;
+        if (base != 0xFFFFFFFFu && __shfl_sync(0xffffffffu, incl, 31) != 0u)
+            warp_write_entries<4, LAYOUT == 1>(Qout, base + s_off[warp] + incl - cnt, cnt, st, ln, pay, tot, lane);
     }
     if (UPDATE == 2 && a.filter == 2) {
         fresh = __reduce_add_sync(0xffffffffu, fresh);
@@ -381,30 +445,20 @@ __device__ __forceinline__ bool stage1_staged(const BfsArgs& a, const unsigned l
 }
 
 // ------------------------------------------------------------- unpermute
-// out[v] = L[new_id[v]] in original ids, eight vertices per thread in flight.
-// With levels_from_bitmap (lazy traversals, whose L is not cleared before the
-// launch) a vertex whose V_curr bit is clear was not reached and gets -1: at the
-// end of a lazy traversal V_curr holds exactly the rows a sweep gave a level.
+// out[v] = L[new_id[v]] in original ids, eight vertices per thread in flight
+// (traversals whose sweeps wrote L, not out directly).
 __device__ __forceinline__ void unpermute(const BfsArgs& a, int gtid, int nthreads) {
     constexpr int K = 8;
     for (int64_t b = gtid; b < a.n; b += (int64_t)K * nthreads) {
         int u[K];
-        uint32_t w[K];
         int lv[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int64_t v = b + (int64_t)k * nthreads;
             u[k] = v < a.n ? __ldg(&a.new_id[v]) : -1;
         }
-        // the V_curr word and the (possibly stale) level are loaded together
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            w[k] = (a.levels_from_bitmap && u[k] >= 0) ? ld_cg(&a.vcur[u[k] >> 5]) : ~0u;
-            lv[k] = u[k] >= 0 ? ld_cg(&a.L[u[k]]) : -1;
-        }
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-            if (!((w[k] >> (u[k] & 31)) & 1u)) lv[k] = -1;
+        for (int k = 0; k < K; ++k) lv[k] = u[k] >= 0 ? ld_cg(&a.L[u[k]]) : -1;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int64_t v = b + (int64_t)k * nthreads;
@@ -663,6 +717,14 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
             if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns)) return;
             if (gtid == 0 && a.level_sizes && lvl - 1 < a.level_cap) a.level_times[2 * lvl + 1] = global_timer_ns();
             sweep<UPDATE, LAYOUT>(a, lvl, Qout, qcount_next, nullptr, sparse);
+            if (a.level_sizes && lvl - 1 < a.level_cap) {
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    const unsigned long long t = global_timer_ns();
+                    atomicMin(&a.arrive_first[a.level_cap + lvl - 1], t);
+                    atomicMax(&a.arrive_last[a.level_cap + lvl - 1], t);
+                }
+            }
         }
         unsigned int qnext = 0;
         if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns, qcount_next, &qnext)) return;
@@ -675,7 +737,7 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
         if (a.level_sizes && lvl < a.level_cap) a.level_times[2 * lvl + 2] = global_timer_ns();   // traversal end
     }
     // undo the reordering: out[v] = L[new_id[v]]
-    if (a.new_id) unpermute(a, gtid, nthreads);
+    if (a.new_id && !a.direct) unpermute(a, gtid, nthreads);
     if (a.level_sizes && lvl < a.level_cap) {
         __syncthreads();
         if (gtid == 0) a.level_times[2 * lvl + 3] = global_timer_ns();   // block 0 done with its share
@@ -770,6 +832,7 @@ cudaError_t launch_bfs_kernel(const BfsLaunch& L, cudaStream_t stream) {
     BfsArgs a;
     a.n = L.n;
     a.nwords = (L.n + 31) / 32;
+    a.nss = (L.n + 7) / 8;
     a.qcap = L.qcap;
     a.real_ptrs = L.real_ptrs;
     a.row_ids4 = reinterpret_cast<const int4*>(L.row_ids);
@@ -796,7 +859,8 @@ cudaError_t launch_bfs_kernel(const BfsLaunch& L, cudaStream_t stream) {
     a.timeout_ns = L.timeout_ns;
     a.phantom = L.phantom;
     a.filter = L.filter;
-    a.levels_from_bitmap = L.levels_from_bitmap;
+    a.old_of = L.old_of;
+    a.direct = L.direct;
     a.sched = L.sched;
     void* args[] = {&a};
     return cudaLaunchCooperativeKernel(k, dim3((unsigned)L.grid), dim3(kBfsBlock), args, smem, stream);

@@ -15,7 +15,8 @@ struct BfsLaunch {
     int unroll = 2;            // 1, 2
     int minb = 2;              // __launch_bounds__ minimum blocks per SM: 2 or 3
     int filter = 1;            // 1: skip marks of rows already in V_curr; 2: also V_next (lazy)
-    int levels_from_bitmap = 0;// 1: L not cleared; the epilogue reads reached rows off V_curr (lazy)
+    int direct = 0;            // 1: sweeps write levels to out through old_of, no unpermute (lazy)
+    const int32_t* old_of = nullptr;   // BVSS id -> original id (direct)
     int sched = 0;             // double-buffered stage 1: 0 static round-robin, 1 dynamic (guided)
     int depth = 0;             // lazy stage 1 prefetch: 0 none, 2 register double buffer, 4/8 TMA ring stages
     int layout = 0;            // 0: tau-padded VSSs (Section 3.1.2); 1: compact groups (lazy, depth 0 or 2)
@@ -38,7 +39,7 @@ struct BfsLaunch {
     void* ctrl = nullptr;      // 256-byte control block (device_common.cuh)
     int32_t* level_sizes = nullptr;
     unsigned long long* level_times = nullptr;   // 2 * level_cap + 2 entries
-    unsigned long long* arrive_first = nullptr;  // level_cap entries each (with level_sizes)
+    unsigned long long* arrive_first = nullptr;  // 2 level_cap entries each: stage 1, then sweep
     unsigned long long* arrive_last = nullptr;
     int32_t level_cap = 0;
     const int32_t* roots_device = nullptr;

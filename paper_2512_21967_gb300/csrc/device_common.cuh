@@ -215,30 +215,16 @@ __device__ __forceinline__ unsigned long long queue_entry(int st, uint32_t pay, 
            ((unsigned long long)ng << 40);
 }
 
-// Warp-aggregated queue append (Section 4.2): lane i appends ln[q] entries
-// for each of its up to NS slots (a slice set's VSS range, see queue_entry).
-// One atomicAdd on the queue size per warp; lanes with long ranges (hub slice
-// sets) are written by the whole warp together.  Raises BLEST_ERR_INTERNAL (7)
-// instead of writing past qcap.
-template <int NS, bool GROUPS = false>
-__device__ __forceinline__ void warp_enqueue(unsigned int qcap, Ctrl* ctrl, unsigned long long* Qout,
-                                             unsigned int* qcount, const int (&st)[NS], const int (&ln)[NS],
-                                             const uint32_t (&pay)[NS], int lane, const int (&tot)[NS]) {
-    unsigned int cnt = 0;
-#pragma unroll
-    for (int q = 0; q < NS; ++q) cnt += (unsigned int)ln[q];
-    const unsigned int incl = warp_inclusive_scan(cnt, lane);
-    const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
-    if (total == 0) return;
-    unsigned int base = 0;
-    if (lane == 31) base = atomicAdd(qcount, total);
-    base = __shfl_sync(0xffffffffu, base, 31);
-    if (base + total > qcap || base + total < base) {
-        if (lane == 0) raise_error(ctrl, 7u);
-        return;
-    }
-    unsigned int pos = base + incl - cnt;
-    const bool big = cnt > 16;   // longer runs are written by the whole warp: a lane-serial loop diverges
+// Writes lane i's entries of up to NS slots (a slice set's VSS range, see
+// queue_entry) at Qout[pos ...), pos = the lane's first position.  Short runs
+// are written by their lane; runs longer than 16 entries (hub slice sets) by
+// the whole warp together, since a lane-serial loop would make the warp wait
+// for its busiest lane.  Every lane of the warp must call it.
+template <int NS, bool GROUPS>
+__device__ __forceinline__ void warp_write_entries(unsigned long long* Qout, unsigned int pos, unsigned int cnt,
+                                                   const int (&st)[NS], const int (&ln)[NS],
+                                                   const uint32_t (&pay)[NS], const int (&tot)[NS], int lane) {
+    const bool big = cnt > 16;
     if (!big) {
 #pragma unroll
         for (int q = 0; q < NS; ++q)
@@ -259,6 +245,29 @@ __device__ __forceinline__ void warp_enqueue(unsigned int qcap, Ctrl* ctrl, unsi
             p += (unsigned int)l0;
         }
     }
+}
+
+// Warp-aggregated queue append (Section 4.2): one atomicAdd on the queue size
+// per warp, then warp_write_entries.  Raises BLEST_ERR_INTERNAL (7) instead of
+// writing past qcap.
+template <int NS, bool GROUPS = false>
+__device__ __forceinline__ void warp_enqueue(unsigned int qcap, Ctrl* ctrl, unsigned long long* Qout,
+                                             unsigned int* qcount, const int (&st)[NS], const int (&ln)[NS],
+                                             const uint32_t (&pay)[NS], int lane, const int (&tot)[NS]) {
+    unsigned int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < NS; ++q) cnt += (unsigned int)ln[q];
+    const unsigned int incl = warp_inclusive_scan(cnt, lane);
+    const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) return;
+    unsigned int base = 0;
+    if (lane == 31) base = atomicAdd(qcount, total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    if (base + total > qcap || base + total < base) {
+        if (lane == 0) raise_error(ctrl, 7u);
+        return;
+    }
+    warp_write_entries<NS, GROUPS>(Qout, base + incl - cnt, cnt, st, ln, pay, tot, lane);
 }
 
 // Warp-coalesced queue append for one range per lane: lane i appends the VSS

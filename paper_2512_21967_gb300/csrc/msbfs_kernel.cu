@@ -55,9 +55,14 @@ template <int W>
 __device__ __forceinline__ void ms_sweep(const MsArgs& a, int lvl, unsigned long long* Qout, unsigned int* qcount) {
     const int lane = threadIdx.x & 31;
     const size_t n = (size_t)a.n;
-    // one row per thread, block-strided: consecutive rows of a warp share their bitmap lines
-    for (int b0 = (int)blockIdx.x * (int)blockDim.x; b0 < a.n; b0 += (int)(gridDim.x * blockDim.x)) {
-        const int u = b0 + (int)threadIdx.x;
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    const int nchunks = (a.n + kWarp - 1) / kWarp;
+    // one row per lane, 32 consecutive rows per warp step (they share bitmap
+    // lines); consecutive chunks go to consecutive thread blocks so that the hub
+    // rows at the lowest ids, whose slice sets carry most queue entries, are
+    // spread over the SMs
+    for (int c = (int)blockIdx.x + (int)(threadIdx.x >> 5) * (int)gridDim.x; c < nchunks; c += nwarps) {
+        const int u = c * kWarp + lane;
         bool any = false;
         if (u < a.n) {
 #pragma unroll

@@ -448,11 +448,18 @@ def test_level_timeline_and_arrivals(cfg1, update):
             t = blest.blest_get_level_times(h, 2 * L + 4).astype(np.int64)
             first, last = blest.blest_get_level_arrivals(h, L)
             first, last = first.astype(np.int64), last.astype(np.int64)
+            sf, sl = blest.blest_get_level_arrivals(h, L, phase=1)
             assert t[1] <= t[0] <= t[2]
             for l in range(1, L + 1):
                 after = t[2 * l + 1] if update == "lazy" else t[2 * l + 2]
                 assert first[l - 1] <= last[l - 1] <= after
                 assert t[2 * l] <= after
+                if update == "lazy":
+                    # a block's sweep starts after the barrier that waits for every block's stage 1,
+                    # and the next level starts after the barrier that waits for every sweep
+                    assert last[l - 1] <= int(sf[l - 1]) <= int(sl[l - 1]) <= t[2 * l + 2]
+                else:
+                    assert int(sf[l - 1]) == 2**64 - 1 and int(sl[l - 1]) == 0
             assert t[2 * L + 2] <= t[2 * L + 3]
     finally:
         blest.blest_destroy(h)
