@@ -296,13 +296,18 @@ def test_batch_of_uneven_graphs(gpu):
         blest.blest_destroy(h)
 
 
-def test_device_api_with_torch_stream(torch_cuda):
+@pytest.mark.parametrize("update", ["eager", "lazy"])
+def test_device_api_with_torch_stream(torch_cuda, update):
+    """Device output into rows of a caller's tensor on the caller's stream
+    (the lazy path writes levels straight into that buffer)."""
     torch = torch_cuda
     g = synth.rmat_graph(13, 16, seed=9)
     srcs = synth.pick_sources(g, 5, seed=1)
     exp = oracle.msbfs_levels(g.n, g.row_ptr, g.col_idx, srcs)
     h = blest.blest_graph_create(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_COMPRESS)
     try:
+        blest.blest_set_option(h, blest.BLEST_OPT_UPDATE,
+                               blest.BLEST_UPDATE_EAGER if update == "eager" else blest.BLEST_UPDATE_LAZY)
         s = torch.cuda.Stream()
         out = torch.empty((len(srcs), g.n), dtype=torch.int32, device="cuda")
         for i, src in enumerate(srcs):
@@ -330,7 +335,8 @@ def test_autotune_keeps_levels_exact(gpu):
         blest.blest_destroy(h)
 
 
-def test_batch_graph_capture_replay(torch_cuda):
+@pytest.mark.parametrize("update", ["eager", "lazy"])
+def test_batch_graph_capture_replay(torch_cuda, update):
     """One captured CUDA graph replayed with new sources gives every graph's own
     single-source levels."""
     torch = torch_cuda
@@ -344,6 +350,8 @@ def test_batch_graph_capture_replay(torch_cuda):
             orders.append(blest.BLEST_ORDER_BANDWIDTH)
     h = blest.blest_batch_create([(g.n, g.row_ptr, g.col_idx) for g in graphs], orders)
     try:
+        blest.blest_set_option(h, blest.BLEST_OPT_UPDATE,
+                               blest.BLEST_UPDATE_EAGER if update == "eager" else blest.BLEST_UPDATE_LAZY)
         total = sum(g.n for g in graphs)
         out = torch.empty(total, dtype=torch.int32, device="cuda")
         blest.blest_batch_graph_capture(h, out)
