@@ -311,9 +311,9 @@ blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots
     L.depth = (L.update == 2 && L.minb == 2) ? h->depth : 0;
     if (L.depth == 0 && L.unroll > 2) L.unroll = 2;       // unroll 4 exists only for the TMA ring
     if (L.depth == 4 && L.unroll > 2) L.unroll = 2;       // a 4-stage ring holds two groups of 2
-    if (L.depth == 2 && L.unroll > 2) L.unroll = 2;       // the register double buffer exists for 1 and 2
+    if ((L.depth == 2 || L.depth == 3) && L.unroll > 2) L.unroll = 2;   // the register pipelines exist for 1 and 2
     // the compact layout serves the lazy register paths (depth 0 or 2) at 2 blocks per SM
-    L.layout = (h->layout == 1 && L.update == 2 && L.minb == 2 && L.depth <= 2 && h->compact.goff) ? 1 : 0;
+    L.layout = (h->layout == 1 && L.update == 2 && L.minb == 2 && (L.depth == 0 || L.depth == 2) && h->compact.goff) ? 1 : 0;
     L.grid = pick_grid(h, L.update, L.pull, L.unroll, L.minb, L.depth, L.layout);
     if (L.grid <= 0) return fail(BLEST_ERR_CUDA, "no co-resident grid for the traversal kernel");
     L.n = h->n;
@@ -760,7 +760,7 @@ blest_status blest_set_option(blest_handle h, int32_t key, int64_t value) {
             h->minb = (int)value;
             return BLEST_OK;
         case BLEST_OPT_STAGE_DEPTH:
-            if (value != 0 && value != 2 && value != 4 && value != 8) break;
+            if (value != 0 && value != 2 && value != 3 && value != 4 && value != 8) break;
             h->depth = (int)value;
             return BLEST_OK;
         case BLEST_OPT_LAYOUT: {
@@ -1096,7 +1096,11 @@ blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, bles
             for (int p : {BLEST_PULL_POPC, BLEST_PULL_MMA})
                 for (int r : {1, 2}) {
                     cands.push_back({BLEST_UPDATE_LAZY, p, r, 2, f, b, 2});
-                    cands.push_back({BLEST_UPDATE_LAZY, p, r, 2, f, b, 2, 0, 1});   // block-dynamic schedule
+                    cands.push_back({BLEST_UPDATE_LAZY, p, r, 2, f, b, 2, 0, 1});   // static + dynamic tail
+                    if (p == BLEST_PULL_POPC && f > 0) {                        // tiles two groups ahead
+                        cands.push_back({BLEST_UPDATE_LAZY, p, r, 2, f, b, 3, 0, 0});
+                        cands.push_back({BLEST_UPDATE_LAZY, p, r, 2, f, b, 3, 0, 1});
+                    }
                     // compact layout (register paths)
                     if (b == 0) {
                         cands.push_back({BLEST_UPDATE_LAZY, p, r, 2, f, b, 0, 1});

@@ -506,7 +506,7 @@ __device__ __forceinline__ void load_tile(const BfsArgs& a, unsigned long long e
 // within [2U, 64]), so blocks on faster SMs absorb the end of the level.
 constexpr unsigned int kChunkMax = 64;
 
-template <int PULL, int U, int LAYOUT>
+template <int PULL, int U, int LAYOUT, int PD>
 __device__ __forceinline__ void stage1_pipelined(const BfsArgs& a, const unsigned long long* __restrict__ Qin,
                                                  unsigned int qn, uint64_t pol, int lane, int gwarp, int nwarps,
                                                  int filt, unsigned int* work, uint32_t* dirty) {
@@ -518,9 +518,6 @@ __device__ __forceinline__ void stage1_pipelined(const BfsArgs& a, const unsigne
     unsigned int sbase = (unsigned int)gwarp;
     if (!dyn && sbase >= qn) return;
     unsigned int c_lo = 0, c_hi = 0, seen = slim;   // dynamic tail: current chunk, last position seen
-    unsigned long long e_cur[U], e_nxt[U];
-    int4 r_cur[U];
-    uint32_t m_cur[U];
     // the queue entries of the warp's next group (~0 past the end; positions only grow)
     auto next_group = [&](unsigned long long (&e)[U]) {
         unsigned int p[U];
@@ -562,27 +559,36 @@ __device__ __forceinline__ void stage1_pipelined(const BfsArgs& a, const unsigne
             if (e[i] != ~0ull) load_tile<LAYOUT>(a, e[i], lane, pol, r[i], m[i]);
         }
     };
-    next_group(e_cur);
-    fetch_tiles(e_cur, r_cur, m_cur);
-    next_group(e_nxt);
-    while (e_cur[0] != ~0ull) {
-        int4 r_nxt[U];
-        uint32_t m_nxt[U];
-        unsigned long long e_far[U];
-        fetch_tiles(e_nxt, r_nxt, m_nxt);
-        next_group(e_far);
+    // PD = prefetch distance: the tiles of the next PD groups are in flight and the
+    // queue entries of the group after them are being read while group 0 is handled
+    unsigned long long e[PD + 2][U];
+    int4 r[PD + 1][U];
+    uint32_t m[PD + 1][U];
+#pragma unroll
+    for (int k = 0; k < PD; ++k) {
+        next_group(e[k]);
+        fetch_tiles(e[k], r[k], m[k]);
+    }
+    next_group(e[PD]);
+    while (e[0][0] != ~0ull) {
+        fetch_tiles(e[PD], r[PD], m[PD]);
+        next_group(e[PD + 1]);
         unsigned int hm = 0;
 #pragma unroll
-        for (int i = 0; i < U; ++i)   // e_cur[i] is the same in every lane, so the MMA runs warp-wide
-            if (e_cur[i] != ~0ull) hm |= pull_hits<PULL>(m_cur[i], (uint32_t)(e_cur[i] >> 32) & 0xFFu, lane) << (4 * i);
-        mark_rows<U>(a, r_cur, hm, filt, dirty);
+        for (int i = 0; i < U; ++i)   // e[0][i] is the same in every lane, so the MMA runs warp-wide
+            if (e[0][i] != ~0ull) hm |= pull_hits<PULL>(m[0][i], (uint32_t)(e[0][i] >> 32) & 0xFFu, lane) << (4 * i);
+        mark_rows<U>(a, r[0], hm, filt, dirty);
 #pragma unroll
-        for (int i = 0; i < U; ++i) {
-            e_cur[i] = e_nxt[i];
-            e_nxt[i] = e_far[i];
-            r_cur[i] = r_nxt[i];
-            m_cur[i] = m_nxt[i];
-        }
+        for (int k = 0; k < PD; ++k)
+#pragma unroll
+            for (int i = 0; i < U; ++i) {
+                r[k][i] = r[k + 1][i];
+                m[k][i] = m[k + 1][i];
+            }
+#pragma unroll
+        for (int k = 0; k <= PD; ++k)
+#pragma unroll
+            for (int i = 0; i < U; ++i) e[k][i] = e[k + 1][i];
     }
 }
 
@@ -599,11 +605,11 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
     unsigned int gen = 0;
     Ctrl* ctrl = a.ctrl;
     extern __shared__ __align__(128) unsigned char dyn_smem[];
-    // DEPTH 4 or 8: a shared-memory ring per warp; DEPTH 2 keeps its two stages in registers
-    unsigned char* ring = dyn_smem + (threadIdx.x >> 5) * (DEPTH > 2 ? ring_bytes_per_warp<DEPTH>() : 0);
+    // DEPTH 4 or 8: a shared-memory ring per warp; DEPTH 2 and 3 keep their stages in registers
+    unsigned char* ring = dyn_smem + (threadIdx.x >> 5) * (DEPTH > 3 ? ring_bytes_per_warp<DEPTH>() : 0);
     uint32_t ring_uses = 0;
     const uint64_t pol = l2_evict_first_policy();
-    if (DEPTH > 2) {
+    if (DEPTH > 3) {
         if (lane == 0) {
             unsigned long long* bars = reinterpret_cast<unsigned long long*>(ring + DEPTH * kStageBytes);
             for (int i = 0; i < DEPTH; ++i) mbar_init(smem_addr(&bars[i]), 1);
@@ -658,11 +664,11 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
         const int filt = (a.filter == 2 && ld_cg(&ctrl->reached) >= (unsigned int)a.n / 4u) ? 1 : a.filter;
         const bool sparse = UPDATE == 2 && a.dirty != nullptr && qn <= sparse_cap;
         uint32_t* dirty = sparse ? a.dirty : nullptr;
-        if (DEPTH == 2) {
-            stage1_pipelined<PULL, UNROLL, LAYOUT>(a, Qin, qn, pol, lane, gwarp, nwarps, filt,
+        if (DEPTH == 2 || DEPTH == 3) {
+            stage1_pipelined<PULL, UNROLL, LAYOUT, (DEPTH == 3 ? 2 : 1)>(a, Qin, qn, pol, lane, gwarp, nwarps, filt,
                                                    a.sched ? &ctrl->work[lvl & 1] : nullptr, dirty);
-        } else if (DEPTH > 0) {
-            stage1_staged<PULL, (DEPTH > 2 ? DEPTH : 2 * UNROLL), UNROLL>(a, Qin, qn, ring, ring_uses, pol, lane,
+        } else if (DEPTH > 3) {
+            stage1_staged<PULL, (DEPTH > 3 ? DEPTH : 2 * UNROLL), UNROLL>(a, Qin, qn, ring, ring_uses, pol, lane,
                                                                             gwarp, nwarps, filt, dirty);
         } else
         for (unsigned int base = (unsigned int)gwarp; base < qn; base += (unsigned int)nwarps * UNROLL) {
@@ -789,8 +795,9 @@ static void* pick_kernel(int update, int pull, int unroll, int minb, int depth, 
 #define BLEST_PICK_S(P) BLEST_PICK(2, P, 1, 2, 4) BLEST_PICK(2, P, 2, 2, 4) BLEST_PICK(2, P, 1, 2, 8) \
     BLEST_PICK(2, P, 2, 2, 8) BLEST_PICK(2, P, 4, 2, 8)
     BLEST_PICK_S(0) BLEST_PICK_S(1)
-    // register double-buffered lazy variants (depth 2)
+    // register-pipelined lazy variants (depth 2: tiles one group ahead, 3: two groups ahead)
     BLEST_PICK(2, 0, 1, 2, 2) BLEST_PICK(2, 0, 2, 2, 2) BLEST_PICK(2, 1, 1, 2, 2) BLEST_PICK(2, 1, 2, 2, 2)
+    BLEST_PICK(2, 0, 1, 2, 3) BLEST_PICK(2, 0, 2, 2, 3) BLEST_PICK(2, 1, 1, 2, 3) BLEST_PICK(2, 1, 2, 2, 3)
 #undef BLEST_PICK_S
 #undef BLEST_PICK_M
 #undef BLEST_PICK

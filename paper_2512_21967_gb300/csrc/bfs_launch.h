@@ -18,7 +18,7 @@ struct BfsLaunch {
     int direct = 0;            // 1: sweeps write levels to out through old_of, no unpermute (lazy)
     const int32_t* old_of = nullptr;   // BVSS id -> original id (direct)
     int sched = 0;             // double-buffered stage 1: 0 static round-robin, 1 dynamic (guided)
-    int depth = 0;             // lazy stage 1 prefetch: 0 none, 2 register double buffer, 4/8 TMA ring stages
+    int depth = 0;             // lazy stage 1 prefetch: 0 none, 2/3 register pipeline, 4/8 TMA ring stages
     int layout = 0;            // 0: tau-padded VSSs (Section 3.1.2); 1: compact groups (lazy, depth 0 or 2)
     int grid = 0;              // blocks (co-resident)
     int32_t n = 0;

@@ -109,7 +109,8 @@ def test_rmat16_all_sources_all_modes(cfg1, order):
                 variants += [(1, 2, 1, 4, 0, 0), (1, 2, 0, 8, 0, 0), (1, 2, 1, 8, 0, 0), (2, 2, 2, 0, 0, 0),
                              (1, 3, 2, 0, 0, 0), (1, 2, 1, 2, 0, 0), (2, 2, 2, 2, 0, 0), (2, 2, 0, 2, 0, 0),
                              (2, 2, 2, 8, 0, 0), (1, 2, 1, 0, 1, 0), (2, 2, 2, 0, 1, 0), (1, 2, 0, 2, 1, 0),
-                             (2, 2, 2, 2, 1, 0), (2, 2, 2, 2, 0, 1), (1, 2, 1, 2, 0, 1), (2, 2, 2, 2, 1, 1)]
+                             (2, 2, 2, 2, 1, 0), (2, 2, 2, 2, 0, 1), (1, 2, 1, 2, 0, 1), (2, 2, 2, 2, 1, 1),
+                             (2, 2, 2, 3, 0, 0), (1, 2, 1, 3, 0, 1), (2, 2, 2, 3, 0, 1)]
             for unroll, minb, filt, depth, layout, sched in variants:
                 blest.blest_set_option(h, blest.BLEST_OPT_SCHEDULE, sched)
                 blest.blest_set_option(h, blest.BLEST_OPT_UNROLL, unroll)
@@ -135,7 +136,8 @@ def test_queue_sizes_match_replay(cfg1):
         for upd, depth, layout, sched in ((blest.BLEST_UPDATE_EAGER, 0, 0, 0), (blest.BLEST_UPDATE_LAZY, 0, 0, 0),
                                           (blest.BLEST_UPDATE_LAZY, 8, 0, 0), (blest.BLEST_UPDATE_LAZY, 2, 0, 0),
                                           (blest.BLEST_UPDATE_LAZY, 2, 1, 0), (blest.BLEST_UPDATE_LAZY, 0, 1, 0),
-                                          (blest.BLEST_UPDATE_LAZY, 2, 0, 1), (blest.BLEST_UPDATE_LAZY, 2, 1, 1)):
+                                          (blest.BLEST_UPDATE_LAZY, 2, 0, 1), (blest.BLEST_UPDATE_LAZY, 2, 1, 1),
+                                          (blest.BLEST_UPDATE_LAZY, 3, 0, 1)):
             blest.blest_set_option(h, blest.BLEST_OPT_UPDATE, upd)
             blest.blest_set_option(h, blest.BLEST_OPT_SCHEDULE, sched)
             blest.blest_set_option(h, blest.BLEST_OPT_STAGE_DEPTH, depth)
