@@ -301,10 +301,18 @@ __device__ __forceinline__ void eager_update(const BfsArgs& a, const int4 (&rows
         for (int k = 0; k < K; ++k)
             if (w[k] & (1u << (u[k] & 31))) hm &= ~(1u << k);
     }
-    // phase 2: level check
-    int lv[K];
+    // phase 2: level check, with the VSS range of each hit row's slice set loaded
+    // alongside (needed only if this lane claims the row, but it saves a round trip)
+    int lv[K], rp0[K], rp1[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) lv[k] = (hm >> k) & 1u ? ld_cg(&a.L[u[k]]) : 0;
+    for (int k = 0; k < K; ++k) {
+        lv[k] = 0; rp0[k] = 0; rp1[k] = 0;
+        if ((hm >> k) & 1u) {
+            lv[k] = ld_cg(&a.L[u[k]]);
+            rp0[k] = __ldg(&a.real_ptrs[u[k] >> 3]);
+            rp1[k] = __ldg(&a.real_ptrs[(u[k] >> 3) + 1]);
+        }
+    }
     unsigned int newm = 0;
 #pragma unroll
     for (int k = 0; k < K; ++k)
@@ -328,10 +336,9 @@ __device__ __forceinline__ void eager_update(const BfsArgs& a, const int4 (&rows
     for (int k = 0; k < K; ++k) {
         st[k] = 0; ln[k] = 0; pay[k] = 0;
         if (((newm >> k) & 1u) && ((old[k] >> (u[k] & 24)) & 0xFFu) == 0) {
-            const int s2 = u[k] >> 3;
-            st[k] = __ldg(&a.real_ptrs[s2]);
-            ln[k] = __ldg(&a.real_ptrs[s2 + 1]) - st[k];
-            pay[k] = (uint32_t)s2;
+            st[k] = rp0[k];
+            ln[k] = rp1[k] - rp0[k];
+            pay[k] = (uint32_t)(u[k] >> 3);
         }
     }
     warp_enqueue<K>(a.qcap, a.ctrl, Qout, qcount_next, st, ln, pay, lane, ln);

@@ -66,11 +66,14 @@ __device__ __forceinline__ void st_release_gpu_u64(unsigned long long* p, unsign
 // (generation << 32 | *pub) into a flag on its own cache line; the waiting
 // blocks spin on that flag with acquire loads.  Every block returns the
 // published word through *published (the next queue size, so the level loop
-// needs no separate read of it).
+// needs no separate read of it).  The last block also reads ctrl->error and
+// publishes it as bit 63 of the flag, so that no waiting block needs a second
+// round trip to L2 after the release: the generation takes bits 32..62.
 // The wait is bounded: after timeout_ns it records BLEST_ERR_TIMEOUT (6) in
 // ctrl->error and returns false, as it does when another block has already
-// recorded an error.  `extra` adds phantom participants (test hook: a barrier
-// that can never complete).  `gen` is this block's barrier count.
+// recorded an error (checked every 32 polls, with the clock).  `extra` adds
+// phantom participants (test hook: a barrier that can never complete).  `gen`
+// is this block's barrier count.
 __device__ __forceinline__ bool grid_barrier(Ctrl* ctrl, unsigned int nblocks, unsigned int extra,
                                              unsigned int& gen, uint64_t timeout_ns,
                                              const unsigned int* pub = nullptr,
@@ -88,25 +91,32 @@ __device__ __forceinline__ bool grid_barrier(Ctrl* ctrl, unsigned int nblocks, u
         unsigned int value = 0;
         if (old + 1u == target) {
             __threadfence();
-            value = pub ? atomicOr(const_cast<unsigned int*>(pub), 0u) : 0u;   // coherent read at L2
-            st_release_gpu_u64(flag, ((unsigned long long)gen << 32) | value);
+            value = pub ? atomicOr(const_cast<unsigned int*>(pub), 0u) : 0u;   // coherent reads at L2
+            const unsigned long long err = atomicOr(&ctrl->error, 0u) != 0u ? 1ull : 0ull;
+            st_release_gpu_u64(flag, (err << 63) | ((unsigned long long)gen << 32) | value);
+            if (err) ok = 0;
         } else {
             const uint64_t t0 = global_timer_ns();
             unsigned int spins = 0;
             for (;;) {
                 const unsigned long long f = ld_acquire_gpu_u64(flag);
-                if ((unsigned int)(f >> 32) >= gen) { value = (unsigned int)f; break; }
-                if (ld_volatile_u32(&ctrl->error) != 0) { ok = 0; break; }
-                if ((++spins & 31u) == 0 && global_timer_ns() - t0 > timeout_ns) {
-                    atomicCAS(&ctrl->error, 0u, 6u);
-                    ok = 0;
+                if (((unsigned int)(f >> 32) & 0x7FFFFFFFu) >= gen) {
+                    value = (unsigned int)f;
+                    if (f >> 63) ok = 0;
                     break;
+                }
+                if ((++spins & 31u) == 0) {
+                    if (ld_volatile_u32(&ctrl->error) != 0) { ok = 0; break; }
+                    if (global_timer_ns() - t0 > timeout_ns) {
+                        atomicCAS(&ctrl->error, 0u, 6u);
+                        ok = 0;
+                        break;
+                    }
                 }
                 if (spins > 64) __nanosleep(32);
             }
         }
         __threadfence();
-        if (ld_volatile_u32(&ctrl->error) != 0) ok = 0;
         s_ok = ok;
         s_pub = value;
     }
