@@ -59,10 +59,19 @@ __device__ __forceinline__ void st_release_gpu_u64(unsigned long long* p, unsign
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// atomicAdd with acquire-release semantics at GPU scope: it releases the
+// calling thread's earlier writes (and, through a preceding __syncthreads, its
+// block's) and acquires those released by earlier RMWs on the same address.
+__device__ __forceinline__ unsigned int atom_add_acq_rel_gpu(unsigned int* p, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 // Grid barrier for a cooperative launch (all blocks co-resident).  Thread 0 of
-// each block arrives with a release (fence + atomic add on the arrival
-// counter).  The block that arrives last reads *pub (after an acquire fence, so
-// it sees every block's writes) and releases the others by storing
+// each block arrives with an acquire-release atomic add on the arrival counter,
+// which releases its block's writes.  The block that arrives last has thereby
+// acquired every block's writes; it reads *pub and releases the others by storing
 // (generation << 32 | *pub) into a flag on its own cache line; the waiting
 // blocks spin on that flag with acquire loads.  Every block returns the
 // published word through *published (the next queue size, so the level loop
@@ -85,12 +94,10 @@ __device__ __forceinline__ bool grid_barrier(Ctrl* ctrl, unsigned int nblocks, u
         gen += 1;
         unsigned long long* flag = reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned int*>(ctrl) + kFlagWord);
         const unsigned int target = gen * (nblocks + extra);
-        __threadfence();
-        const unsigned int old = atomicAdd(&ctrl->barrier, 1u);
+        const unsigned int old = atom_add_acq_rel_gpu(&ctrl->barrier, 1u);
         int ok = 1;
         unsigned int value = 0;
         if (old + 1u == target) {
-            __threadfence();
             value = pub ? atomicOr(const_cast<unsigned int*>(pub), 0u) : 0u;   // coherent reads at L2
             const unsigned long long err = atomicOr(&ctrl->error, 0u) != 0u ? 1ull : 0ull;
             st_release_gpu_u64(flag, (err << 63) | ((unsigned long long)gen << 32) | value);
@@ -116,8 +123,7 @@ __device__ __forceinline__ bool grid_barrier(Ctrl* ctrl, unsigned int nblocks, u
                 if (spins > 64) __nanosleep(32);
             }
         }
-        __threadfence();
-        s_ok = ok;
+        s_ok = ok;   // the flag's acquire load (or the acq_rel add) orders what follows
         s_pub = value;
     }
     __syncthreads();
