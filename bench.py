@@ -710,7 +710,8 @@ def main():
     ap.add_argument("--pull", choices=["popc", "mma"], default="popc")
     ap.add_argument("--unroll", type=int, default=2)
     ap.add_argument("--minb", type=int, default=2)
-    ap.add_argument("--filter", type=int, default=2, help="visited filter: 0 off, 1 V_curr, 2 V_curr + V_next early")
+    ap.add_argument("--filter", type=int, default=3,
+                    help="visited filter: 0 off, 1 V_curr, 2/3 V_curr + V_next (L2/L1) while few rows are visited")
     ap.add_argument("--sources", type=int, default=0, help="use only the first N sources of the workload")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner, use the flags as given")
     ap.add_argument("--depth", type=int, default=2,

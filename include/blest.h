@@ -83,7 +83,9 @@ typedef enum {
     BLEST_OPT_TEST_PHANTOM_BLOCK = 6,/* testing: 1 = every barrier waits for one block that does not
                                         exist, so the next traversal must end in BLEST_ERR_TIMEOUT */
     BLEST_OPT_VISITED_FILTER = 7,    /* 1 (default) = test a visited bitmap before marking a row; 2 = lazy
-                                        update also skips rows already marked at this level; 0 = off */
+                                        update also skips rows already marked at this level (V_next read
+                                        at L2), on levels where fewer than n/4 rows have a level; 3 = as 2
+                                        with V_next read through L1 (staler, cheaper); 0 = off */
     BLEST_OPT_MIN_BLOCKS = 8,        /* kernel variant compiled for 2 (default) or 3 blocks per SM */
     BLEST_OPT_STAGE_DEPTH = 9,       /* lazy stage 1 prefetch: 0 = none (default); 2 = the next group's tiles
                                         in registers while the current group's hits are handled; 3 = the

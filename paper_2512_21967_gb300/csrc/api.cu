@@ -305,7 +305,7 @@ blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots
     L.unroll = h->unroll;
     L.minb = h->minb;
     L.filter = h->filter;
-    if (L.update == 1 && L.filter == 2) L.filter = 1;     // V_next is not used by the eager update
+    if (L.update == 1 && L.filter >= 2) L.filter = 1;     // V_next is not used by the eager update
     L.sched = h->sched;
     // the TMA ring exists for the lazy kernel compiled for 2 blocks per SM
     L.depth = (L.update == 2 && L.minb == 2) ? h->depth : 0;
@@ -752,7 +752,7 @@ blest_status blest_set_option(blest_handle h, int32_t key, int64_t value) {
             h->unroll = (int)value;
             return BLEST_OK;
         case BLEST_OPT_VISITED_FILTER:
-            if (value < 0 || value > 2) break;
+            if (value < 0 || value > 3) break;
             h->filter = (int)value;
             return BLEST_OK;
         case BLEST_OPT_MIN_BLOCKS:
@@ -1089,9 +1089,9 @@ blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, bles
         for (int p : {BLEST_PULL_POPC, BLEST_PULL_MMA})
             for (int r : {1, 2})
                 for (int m : {2, 3})
-                    for (int f = 0; f <= (u == BLEST_UPDATE_LAZY ? 2 : 1); ++f)
+                    for (int f = 0; f <= (u == BLEST_UPDATE_LAZY ? 3 : 1); ++f)
                         for (int b : {0, 1}) cands.push_back({u, p, r, m, f, b, 0});
-    for (int f : {0, 1, 2})
+    for (int f : {0, 1, 2, 3})
         for (int b : {0, 1}) {
             for (int p : {BLEST_PULL_POPC, BLEST_PULL_MMA})
                 for (int r : {1, 2}) {

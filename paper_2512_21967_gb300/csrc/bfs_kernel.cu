@@ -64,7 +64,7 @@ struct BfsArgs {
     int32_t* out;                         // output in original ids (unused when new_id is NULL)
     uint64_t timeout_ns;
     unsigned int phantom;
-    int filter;                           // 1 = skip rows already in V_curr; 2 = also V_next while few are visited
+    int filter;                           // 1 = skip rows already in V_curr; 2/3 = also V_next (L2 / L1) while few are visited
     const int32_t* __restrict__ old_of;   // BVSS id -> original id (with direct)
     int direct;                           // 1: the sweeps write levels straight to out (original ids)
     int sched;                            // stage-1 schedule of the double-buffered path: 0 static, 1 dynamic
@@ -231,7 +231,7 @@ __device__ __forceinline__ void sweep(const BfsArgs& a, int lvl, unsigned long l
         if (base != 0xFFFFFFFFu && __shfl_sync(0xffffffffu, incl, 31) != 0u)
             warp_write_entries<4, LAYOUT == 1>(Qout, base + s_off[warp] + incl - cnt, cnt, st, ln, pay, tot, lane);
     }
-    if (UPDATE == 2 && a.filter == 2) {
+    if (UPDATE == 2 && a.filter >= 2) {
         fresh = __reduce_add_sync(0xffffffffu, fresh);
         if (lane == 0 && fresh) atomicAdd(&a.ctrl->reached, fresh);
     }
@@ -243,8 +243,9 @@ __device__ __forceinline__ void sweep(const BfsArgs& a, int lvl, unsigned long l
 // for one round trip per phase rather than one per hit.
 
 // Lazy marking (Algorithm 3, stage 1): set the V_next bit of every hit row,
-// skipping rows already in V_curr (visited filter, filt 1) and, with filt 2,
-// rows another warp has already marked in V_next at this level.  Both bitmaps
+// skipping rows already in V_curr (visited filter, filt 1) and, with filt 2 or
+// 3, rows another warp has already marked in V_next at this level (read at L2,
+// or through L1 where a line can be older but the load is cheap).  Both bitmaps
 // only gain bits during a traversal, so a stale (older) word can only let
 // through a redundant mark, never suppress a needed one.  The V_next test pays
 // off while most hit rows are unvisited (marks then repeat on the same rows)
@@ -262,6 +263,9 @@ __device__ __forceinline__ void mark_rows(const BfsArgs& a, const int4 (&rows)[N
     if (filt == 2) {
 #pragma unroll
         for (int k = 0; k < 4 * NV; ++k) w[k] = (hm >> k) & 1u ? a.vcur[u[k] >> 5] | ld_cg(&a.vnext[u[k] >> 5]) : 0u;
+    } else if (filt == 3) {   // V_next through L1: staler, so more redundant marks, but cheaper loads
+#pragma unroll
+        for (int k = 0; k < 4 * NV; ++k) w[k] = (hm >> k) & 1u ? a.vcur[u[k] >> 5] | a.vnext[u[k] >> 5] : 0u;
     } else if (filt) {
 #pragma unroll
         for (int k = 0; k < 4 * NV; ++k) w[k] = (hm >> k) & 1u ? a.vcur[u[k] >> 5] : 0u;
@@ -668,7 +672,7 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
 
         // stage 1: pull the queued virtual slice sets, round-robin over warps
         // the lazy filter of this level: the V_next test only while few rows are visited
-        const int filt = (a.filter == 2 && ld_cg(&ctrl->reached) >= (unsigned int)a.n / 4u) ? 1 : a.filter;
+        const int filt = (a.filter >= 2 && ld_cg(&ctrl->reached) >= (unsigned int)a.n / 4u) ? 1 : a.filter;
         const bool sparse = UPDATE == 2 && a.dirty != nullptr && qn <= sparse_cap;
         uint32_t* dirty = sparse ? a.dirty : nullptr;
         if (DEPTH == 2 || DEPTH == 3) {
@@ -824,6 +828,9 @@ int bfs_max_blocks_per_sm(int update, int pull, int unroll, int minb, int depth,
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
+    // the register paths keep almost nothing in shared memory: give L1 the whole
+    // carveout, where the visited-filter words of stage 1 are cached
+    if (smem == 0) cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBfsBlock, smem) != cudaSuccess) return 0;
     return nb;
