@@ -307,10 +307,13 @@ typedef struct {
     double  rule_ms;             /* same for the Section 5 rule (lazy iff U_div > 25,000), CUDA-core pull */
 } blest_tune_result;
 
-/* Time every single-source traversal variant (update scheme, pull back-end,
- * unroll, occupancy variant, visited filter, blocks per SM) on the k host
- * sources srcs[0..k) with CUDA events, each variant after one untimed pass,
- * and keep the fastest as the handle's options.  out may be NULL.
+/* Time single-source traversal variants on the k host sources srcs[0..k)
+ * with CUDA events, each variant after one untimed pass, and keep the fastest
+ * as the handle's options.  Two stages: a few representative variants of the
+ * eager and the lazy update (plus the Section 5 rule's plain kernel, reported
+ * as rule_ms) pick the update scheme; then every variant of that scheme is
+ * timed (pull back-end, unroll, occupancy variant, visited filter, blocks per
+ * SM, prefetch depth, layout, schedule).  out may be NULL.
  * Errors: INVALID_ARG (k < 1, bad source), TIMEOUT, INTERNAL, CUDA. */
 blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, blest_tune_result* out);
 

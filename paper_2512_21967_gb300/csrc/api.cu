@@ -1127,7 +1127,9 @@ blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, bles
     double best = 1e300, rule = -1.0;
     Cand bestc = cands[0];
     const int rule_update = h->stats.update;
-    for (const Cand& c : cands) {
+    int timed = 0;
+    // mean device time per traversal of one candidate (one untimed pass first); < 0 on error
+    auto time_one = [&](const Cand& c) -> double {
         h->update_opt = c.update; h->pull = c.pull; h->unroll = c.unroll; h->minb = c.minb;
         h->filter = c.filter; h->blocks_per_sm = c.bps; h->depth = c.depth; h->layout = c.layout;
         h->sched = c.sched;
@@ -1139,16 +1141,32 @@ blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, bles
                 s = enqueue_traversal(h, one, h->d_out, h->stream);
             }
         }
-        if (s) break;
+        if (s) return -1.0;
         cudaEventRecord(e1, h->stream);
-        if ((s = sync_status(h)) != BLEST_OK) break;
+        if ((s = sync_status(h)) != BLEST_OK) return -1.0;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
+        ++timed;
         const double per = (double)ms / k;
         if (per < best) { best = per; bestc = c; }
-        if (c.update == rule_update && c.pull == BLEST_PULL_POPC && c.unroll == 2 && c.minb == 2 &&
-            c.filter == 0 && c.bps == 0 && c.depth == 0 && c.layout == 0 && c.sched == 0)
-            rule = per;
+        return per;
+    };
+    // stage 1: the update scheme, from a few representative variants of each and
+    // the Section 5 rule's plain kernel; stage 2: every variant of the scheme that won
+    const Cand probes[] = {{BLEST_UPDATE_EAGER, BLEST_PULL_POPC, 1, 2, 0, 0, 0},
+                           {BLEST_UPDATE_EAGER, BLEST_PULL_POPC, 2, 2, 1, 0, 0},
+                           {BLEST_UPDATE_LAZY, BLEST_PULL_POPC, 2, 2, 3, 0, 2, 0, 1},
+                           {BLEST_UPDATE_LAZY, BLEST_PULL_POPC, 2, 2, 1, 0, 0},
+                           {rule_update, BLEST_PULL_POPC, 2, 2, 0, 0, 0}};
+    for (int i = 0; i < 5 && !s; ++i) {
+        const double per = time_one(probes[i]);
+        if (i == 4) rule = per;
+    }
+    const int scheme = bestc.update;
+    for (const Cand& c : cands) {
+        if (s) break;
+        if (c.update != scheme) continue;
+        time_one(c);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1165,7 +1183,7 @@ blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, bles
         out->visited_filter = bestc.filter; out->blocks_per_sm = bestc.bps; out->stage_depth = bestc.depth;
         out->layout = bestc.layout;
         out->schedule = bestc.sched;
-        out->candidates = (int32_t)cands.size();
+        out->candidates = (int32_t)timed;
         out->best_ms = best; out->rule_ms = rule;
     }
     return BLEST_OK;

@@ -331,7 +331,8 @@ def test_autotune_keeps_levels_exact(gpu):
     h = blest.blest_graph_create(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_COMPRESS)
     try:
         r = blest.blest_autotune(h, srcs[:3])
-        assert r["candidates"] >= 64 and 0 < r["best_ms"] <= r["rule_ms"]
+        # 5 probe variants pick the update scheme, then every variant of that scheme (>= 32) is timed
+        assert r["candidates"] >= 37 and 0 < r["best_ms"] <= r["rule_ms"]
         for i, s in enumerate(srcs):
             assert np.array_equal(blest.blest_bfs(h, int(s)), exp[i])
     finally:
