@@ -82,26 +82,27 @@ typedef enum {
                                         (4 only with the 8-stage TMA ring) */
     BLEST_OPT_TEST_PHANTOM_BLOCK = 6,/* testing: 1 = every barrier waits for one block that does not
                                         exist, so the next traversal must end in BLEST_ERR_TIMEOUT */
-    BLEST_OPT_VISITED_FILTER = 7,    /* 1 (default) = test a visited bitmap before marking a row; 2 = lazy
-                                        update also skips rows already marked at this level (V_next read
-                                        at L2), on levels where fewer than n/4 rows have a level; 3 = as 2
-                                        with V_next read through L1 (staler, cheaper); 0 = off */
+    BLEST_OPT_VISITED_FILTER = 7,    /* 1 = test a visited bitmap before marking a row; 2 = lazy update
+                                        also skips rows already marked at this level (V_next read at L2),
+                                        on levels where fewer than n/4 rows have a level; 3 (default) = as
+                                        2 with V_next read through L1 (staler, cheaper); 0 = off; the eager
+                                        update uses 1 for 2 and 3 */
     BLEST_OPT_MIN_BLOCKS = 8,        /* kernel variant compiled for 2 (default) or 3 blocks per SM */
-    BLEST_OPT_STAGE_DEPTH = 9,       /* lazy stage 1 prefetch: 0 = none (default); 2 = the next group's tiles
-                                        in registers while the current group's hits are handled; 3 = the
-                                        next two groups' tiles; 4 or 8 = a per-warp TMA ring of that many
-                                        stages in shared memory; used with BLEST_OPT_MIN_BLOCKS = 2 */
+    BLEST_OPT_STAGE_DEPTH = 9,       /* lazy stage 1 prefetch: 0 = none; 2 (default) = the next group's
+                                        tiles in registers while the current group's hits are handled; 3 =
+                                        the next two groups' tiles; 4 or 8 = a per-warp TMA ring of that
+                                        many stages in shared memory; used with BLEST_OPT_MIN_BLOCKS = 2 */
     BLEST_OPT_LAYOUT = 10,           /* BVSS layout read by the lazy register paths (stage depth 0 or 2,
                                         2 blocks/SM): 0 = every VSS padded to tau = 128 slices (Section
                                         3.1.2, default); 1 = compact groups of 4 slices, only the last
                                         group of a slice set padded (built from the padded layout on
                                         first use: about 5 B per slice more device memory) */
     BLEST_OPT_SCHEDULE = 11          /* stage-1 work split of the register pipelines (stage depth 2, 3):
-                                        0 = static, warp w takes queue entries w, w + W, ... (default);
+                                        0 = static, warp w takes queue entries w, w + W, ...;
                                         1 = on levels with at least 16 queue entries per warp, static
                                         for the first 7/8 of the queue, then warps take chunks of the
                                         rest from a per-level counter, sized (entries left) /
-                                        (2 x warps) within [2 x unroll, 64] (guided); else as 0 */
+                                        (2 x warps) within [2 x unroll, 64] (guided); else as 0 (default) */
 } blest_option;
 
 /* Creation parameters; pass NULL to blest_graph_create_ex for the defaults. */

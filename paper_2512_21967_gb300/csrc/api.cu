@@ -99,10 +99,12 @@ struct blest_graph {
     int record = 0;
     int unroll = 2;
     int minb = 2;
-    int filter = 1;
-    int depth = 0;
+    // defaults: the variant the autotuner picks on social-like graphs (lazy levels);
+    // eager levels ignore the lazy-only ones
+    int filter = 3;
+    int depth = 2;
     int layout = 0;
-    int sched = 0;
+    int sched = 1;
     int phantom = 0;
     // results
     blest_stats stats{};
