@@ -690,10 +690,12 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_t / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
-            "config": {"workload": f"single-source BFS, {g.name}, {len(srcs)} seeded sources", "n": g.n,
+            "config": {"workload": f"single-source BFS, {g.name}, {len(srcs)} seeded sources, {order_name} order",
+                       "n": g.n,
                        "directed_edges": g.nnz, "sources_per_step": per_step},
             "cpu_baseline": {"value": round(value, 5), "unit": "GTEPS", "cores": 1, "kind": "oracle",
-                             "sample": f"{per_step} source(s) per step, one thread, nproc={os.cpu_count()}"},
+                             "sample": f"{per_step} source(s) per step, one thread, nproc={os.cpu_count()}; "
+                                       "the oracle runs on the original vertex order"},
             "e2e": {"value": round(value, 5), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

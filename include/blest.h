@@ -173,8 +173,13 @@ blest_status blest_batch_create(int32_t num_graphs, const int32_t* n_each,
 /* Release the handle and all its device memory.  NULL is ignored. */
 void blest_destroy(blest_handle h);
 
+/* Set one option (blest_option key) for the handle's later traversals.
+ * INVALID_ARG for an unknown key or a value outside the key's range; setting
+ * BLEST_OPT_LAYOUT = 1 builds the compact layout first (OOM/CUDA on failure). */
 blest_status blest_set_option(blest_handle h, int32_t key, int64_t value);
 
+/* Copy the handle's statistics (Table 3 columns, timings) to *out (host,
+ * caller-owned).  INVALID_ARG for NULL arguments. */
 blest_status blest_get_stats(blest_handle h, blest_stats* out);
 
 /* --------------------------------------------------------------- traversal */
@@ -455,7 +460,11 @@ blest_status blest_bfs_static_scratch(int32_t n, int64_t num_vss, const int32_t*
                                       const int32_t* d_new_id, int32_t src_bvss, int32_t* d_levels,
                                       int32_t update, void* stream);
 
+/* Static name of a status code ("BLEST_OK", ...); never NULL. */
 const char* blest_status_string(blest_status s);
+
+/* Message of the last failure on the calling thread (thread-local, valid until
+ * the thread's next failing call); "" if none. */
 const char* blest_last_error(void);
 
 #ifdef __cplusplus
