@@ -607,9 +607,12 @@ def run_ours_window_sweep(args, torch, blest, dev, rank, world):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     out = torch.empty(g.n, dtype=torch.int32, device=dev)
     rows = []
-    for w in [int(x) for x in args.windows.split(",")]:
+    # each window with the BFS-from-hubs pre-pass; the last entries (g<w>) use the Gorder pre-pass
+    for spec in args.windows.split(","):
+        prepass = "gorder" if spec.startswith("g") else "hub"
+        w = int(spec[1:] if prepass == "gorder" else spec)
         order = blest.BLEST_ORDER_NONE if w == 0 else blest.BLEST_ORDER_COMPRESS
-        h = blest.blest_graph_create_ex(g.n, g.row_ptr, g.col_idx, order, window=max(w, 8))
+        h = blest.blest_graph_create_ex(g.n, g.row_ptr, g.col_idx, order, window=max(w, 8), prepass=prepass)
         st = blest.blest_get_stats(h)
         blest.blest_autotune(h, srcs[:4])
         edges, ms = 0, 0.0
@@ -626,7 +629,8 @@ def run_ours_window_sweep(args, torch, blest, dev, rank, world):
             ms += e0.elapsed_time(e1)
             edges += int(deg_t[out >= 0].sum().item()) // 2
         blest.blest_sync(h)
-        rows.append({"window": w if w else "none", "order_s": round(st["order_seconds"], 3),
+        rows.append({"window": w if w else "none", "prepass": prepass if w else None,
+                     "order_s": round(st["order_seconds"], 3),
                      "compression_ratio": round(st["compression_ratio"], 4), "num_vss": st["num_vss"],
                      "bfs_ms_mean": round(ms / len(srcs), 4), "gteps": round(edges / (ms / 1e3) / 1e9, 2)})
         blest.blest_destroy(h)
@@ -720,8 +724,8 @@ def main():
                     help="lazy stage-1 prefetch: 0 none, 2 register double buffer, 4 or 8 TMA ring stages")
     ap.add_argument("--queries", type=int, default=2000, help="serving: queries per arrival rate")
     ap.add_argument("--rates", default="100,400,1600", help="serving: arrival rates in queries/s")
-    ap.add_argument("--windows", default="0,8,64,512,4096,16384,65536",
-                    help="window sweep: JaccardWithWindows windows (0 = no reordering)")
+    ap.add_argument("--windows", default="0,8,64,512,4096,16384,65536,g4096",
+                    help="window sweep: JaccardWithWindows windows (0 = no reordering; g<w> = Gorder pre-pass)")
     ap.add_argument("--sched", type=int, default=0, help="stage-1 schedule of depth 2: 0 static, 1 static + dynamic tail")
     ap.add_argument("--layout", type=int, default=0, help="BVSS layout of the lazy register paths: 0 padded, 1 compact")
     ap.add_argument("--blocks-per-sm", type=int, default=0)

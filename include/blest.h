@@ -110,6 +110,9 @@ typedef struct {
     int32_t window;          /* JaccardWithWindows window w, a multiple of 8 (default 65536, Section 5) */
     int32_t threads;         /* host threads for reordering and cleaning; 0 = all cores */
     int32_t skip_symmetry_check; /* 1 = trust the caller that the input is symmetric */
+    int32_t prepass;         /* BLEST_ORDER_COMPRESS pre-pass before Algorithm 1: 0 = BFS from the
+                                highest-degree vertices (default), 1 = Gorder (window 5, common
+                                neighbours of degree <= 64 counted), slower, host only */
 } blest_create_params;
 
 /* Table 3 columns plus timings of the preprocessing, filled by blest_get_stats. */

@@ -154,10 +154,68 @@ def compose(first: np.ndarray, second: np.ndarray) -> np.ndarray:
     return np.asarray(second)[np.asarray(first)]
 
 
-def compress_order(n: int, row_ptr, col_idx, sigma: int = 8, w: int = 1 << 16) -> np.ndarray:
-    """The compression-oriented ordering: pre-pass, then Algorithm 1 on the
-    relabelled graph."""
-    p = hub_bfs_prepass(n, row_ptr, col_idx)
+def gorder(n: int, row_ptr, col_idx, w: int = 5, hub_cap: int = 64) -> np.ndarray:
+    """Gorder (Wei, Yu, Lu, Lin, SIGMOD 2016), the pre-pass Section 3.2 names,
+    restated from its published definition: a greedy permutation that places
+    next the unplaced vertex u with the largest score sum over the last w
+    placed vertices v of S(u, v) = S_s(u, v) + S_n(u, v), where S_n counts the
+    edges between u and v in both directions (2 for an edge of a symmetric
+    graph) and S_s the common neighbours of u and v.  Readings: the first
+    vertex has the largest degree; ties go to the smallest id; common
+    neighbours of degree above hub_cap are not counted (they say little about
+    locality and make the score updates quadratic in their degree).  Written
+    out directly -- every step scores every unplaced vertex -- for small n.
+    new_id[old]."""
+    adj = [set(a) for a in _adj(n, row_ptr, col_idx)]
+    deg = [len(a) for a in adj]
+
+    def score(u, v):
+        s_n = 2 if v in adj[u] else 0
+        s_s = sum(1 for x in adj[u] & adj[v] if deg[x] <= hub_cap)
+        return s_n + s_s
+
+    order = []
+    placed = [False] * n
+    for _ in range(n):
+        window = order[-w:]
+        best, best_key = -1, -1
+        for u in range(n):
+            if placed[u]:
+                continue
+            if not order:
+                key = deg[u]          # the first vertex: largest degree
+            else:
+                key = sum(score(u, v) for v in window)
+            if key > best_key:        # strict: ties keep the smallest id
+                best, best_key = u, key
+        placed[best] = True
+        order.append(best)
+    new_id = np.empty(n, dtype=np.int64)
+    for pos, v in enumerate(order):
+        new_id[v] = pos
+    return new_id
+
+
+def gorder_objective(n: int, row_ptr, col_idx, new_id, w: int = 5, hub_cap: int = 64) -> int:
+    """Gorder's objective F = sum of S(u, v) over vertex pairs at most w apart
+    in the order (S as in gorder)."""
+    adj = [set(a) for a in _adj(n, row_ptr, col_idx)]
+    deg = [len(a) for a in adj]
+    order = [0] * n
+    for v in range(n):
+        order[int(new_id[v])] = v
+    total = 0
+    for i in range(n):
+        for j in range(i + 1, min(n, i + w + 1)):
+            u, v = order[i], order[j]
+            total += (2 if v in adj[u] else 0) + sum(1 for x in adj[u] & adj[v] if deg[x] <= hub_cap)
+    return total
+
+
+def compress_order(n: int, row_ptr, col_idx, sigma: int = 8, w: int = 1 << 16, prepass: str = "hub") -> np.ndarray:
+    """The compression-oriented ordering: pre-pass (the BFS-from-hubs stand-in,
+    or Gorder), then Algorithm 1 on the relabelled graph."""
+    p = gorder(n, row_ptr, col_idx) if prepass == "gorder" else hub_bfs_prepass(n, row_ptr, col_idx)
     rp2, ci2 = relabel(n, row_ptr, col_idx, p)
     return compose(p, jaccard_windows(n, rp2, ci2, sigma, w))
 

@@ -70,7 +70,8 @@ class BlestError(RuntimeError):
 
 
 class CreateParams(ctypes.Structure):
-    _fields_ = [("window", ctypes.c_int32), ("threads", ctypes.c_int32), ("skip_symmetry_check", ctypes.c_int32)]
+    _fields_ = [("window", ctypes.c_int32), ("threads", ctypes.c_int32), ("skip_symmetry_check", ctypes.c_int32),
+                ("prepass", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -193,10 +194,13 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(_i32p)
 
 
-def _params(window=None, threads=None, skip_symmetry_check=False):
-    if window is None and threads is None and not skip_symmetry_check:
+PREPASS = {"hub": 0, "gorder": 1}
+
+
+def _params(window=None, threads=None, skip_symmetry_check=False, prepass="hub"):
+    if window is None and threads is None and not skip_symmetry_check and prepass == "hub":
         return None
-    return CreateParams(int(window or 0), int(threads or 0), 1 if skip_symmetry_check else 0)
+    return CreateParams(int(window or 0), int(threads or 0), 1 if skip_symmetry_check else 0, PREPASS[prepass])
 
 
 def _dev_ptr(x) -> int:
@@ -237,10 +241,10 @@ def blest_graph_create(n: int, row_ptr, col_idx, order: int = BLEST_ORDER_NONE) 
 
 
 def blest_graph_create_ex(n: int, row_ptr, col_idx, order: int = BLEST_ORDER_NONE, window=None, threads=None,
-                          skip_symmetry_check=False) -> int:
+                          skip_symmetry_check=False, prepass: str = "hub") -> int:
     rp, ci = _i32(row_ptr), _i32(col_idx)
     h = _vp()
-    p = _params(window, threads, skip_symmetry_check)
+    p = _params(window, threads, skip_symmetry_check, prepass)
     _check(lib().blest_graph_create_ex(int(n), _ptr(rp), _ptr(ci), int(order), ctypes.byref(p) if p else None,
                                        ctypes.byref(h)), "blest_graph_create_ex")
     return h.value
@@ -431,10 +435,11 @@ def blest_export(h: int, which: int) -> np.ndarray:
 
 # --------------------------------------------------------------- host only
 
-def blest_compute_order(n: int, row_ptr, col_idx, order: int, window=None, threads=None) -> np.ndarray:
+def blest_compute_order(n: int, row_ptr, col_idx, order: int, window=None, threads=None,
+                        prepass: str = "hub") -> np.ndarray:
     rp, ci = _i32(row_ptr), _i32(col_idx)
     out = np.empty(max(n, 1), np.int32)
-    p = _params(window, threads)
+    p = _params(window, threads, prepass=prepass)
     _check(lib().blest_compute_order(int(n), _ptr(rp), _ptr(ci), int(order), ctypes.byref(p) if p else None,
                                      _ptr(out)), "blest_compute_order")
     return out[:n]

@@ -272,7 +272,8 @@ blest_status prepare_graph(int32_t n, const int32_t* row_ptr, const int32_t* col
     int32_t ord = order;
     if (ord == BLEST_ORDER_AUTO) ord = blest::is_social_like(clean) ? BLEST_ORDER_COMPRESS : BLEST_ORDER_BANDWIDTH;
     new_id.clear();
-    if (ord == BLEST_ORDER_COMPRESS) blest::order_compress(clean, 8, window, threads, new_id);
+    if (ord == BLEST_ORDER_COMPRESS)
+        blest::order_compress(clean, 8, window, threads, new_id, params && params->prepass == 1 ? 1 : 0);
     else if (ord == BLEST_ORDER_BANDWIDTH) blest::order_rcm(clean, new_id);
     *order_used = ord;
     *t_order = now_s() - t0;

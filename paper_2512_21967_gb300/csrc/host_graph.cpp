@@ -245,6 +245,83 @@ void order_hub_prepass(const Csr& g, std::vector<int32_t>& new_id) {
     for (int32_t pos = 0; pos < n; ++pos) new_id[order[pos]] = pos;
 }
 
+// --------------------------------------------------------------- Gorder
+// The pre-pass Section 3.2 names (Wei, Yu, Lu, Lin, SIGMOD 2016), restated from
+// its published definition: place next the unplaced vertex with the largest
+// score summed over the last w placed vertices, S(u, v) = 2 [u ~ v] (edges in
+// both directions of a symmetric graph) + the common neighbours of u and v of
+// degree <= hub_cap.  The first vertex has the largest degree; ties go to the
+// smallest id.  Scores change by +-1 steps when a vertex enters or leaves the
+// window, so they are updated incrementally (through the vertex's neighbours
+// and, for neighbours of degree <= hub_cap, their neighbours), and a max
+// segment tree over vertex ids (key, then smaller id) finds the next vertex.
+void order_gorder(const Csr& g, int w, int32_t hub_cap, std::vector<int32_t>& new_id) {
+    const int32_t n = g.n;
+    new_id.assign((size_t)n, 0);
+    if (n == 0) return;
+    int32_t size = 1;
+    while (size < n) size <<= 1;
+    std::vector<int64_t> key((size_t)n, 0);
+    std::vector<uint8_t> placed((size_t)n, 0);
+    std::vector<int32_t> tree(2 * (size_t)size, -1);   // leaf = vertex id or -1 (none)
+    auto better = [&](int32_t a, int32_t b) {          // a beats b
+        if (a < 0) return false;
+        if (b < 0) return true;
+        return key[a] != key[b] ? key[a] > key[b] : a < b;
+    };
+    auto fix = [&](int32_t v) {
+        size_t i = (size_t)size + (size_t)v;
+        tree[i] = placed[v] ? -1 : v;
+        for (i >>= 1; i >= 1; i >>= 1) {
+            const int32_t l = tree[2 * i], r = tree[2 * i + 1];
+            tree[i] = better(l, r) ? l : (r >= 0 ? r : l);
+        }
+    };
+    for (int32_t v = 0; v < n; ++v) { key[v] = g.rp[v + 1] - g.rp[v]; tree[(size_t)size + v] = v; }
+    for (size_t i = (size_t)size - 1; i >= 1; --i) {
+        const int32_t l = tree[2 * i], r = tree[2 * i + 1];
+        tree[i] = better(l, r) ? l : (r >= 0 ? r : l);
+    }
+    // the first vertex is chosen on degree; after it every key starts at 0
+    const int32_t first = tree[1];
+    std::fill(key.begin(), key.end(), 0);
+    for (int32_t v = 0; v < n; ++v) tree[(size_t)size + v] = v;
+    for (size_t i = (size_t)size - 1; i >= 1; --i) {
+        const int32_t l = tree[2 * i], r = tree[2 * i + 1];
+        tree[i] = better(l, r) ? l : (r >= 0 ? r : l);
+    }
+    std::vector<int32_t> order;
+    order.reserve((size_t)n);
+    std::vector<int32_t> touched;
+    auto contribute = [&](int32_t v, int64_t sign) {
+        for (int32_t e = g.rp[v]; e < g.rp[v + 1]; ++e) {
+            const int32_t x = g.ci[e];
+            if (!placed[x]) { key[x] += 2 * sign; touched.push_back(x); }
+            if (g.rp[x + 1] - g.rp[x] > hub_cap) continue;
+            for (int32_t f = g.rp[x]; f < g.rp[x + 1]; ++f) {
+                const int32_t u = g.ci[f];
+                if (u != v && !placed[u]) { key[u] += sign; touched.push_back(u); }
+            }
+        }
+    };
+    auto place = [&](int32_t v) {
+        placed[v] = 1;
+        fix(v);
+        order.push_back(v);
+    };
+    place(first);
+    while ((int32_t)order.size() < n) {
+        touched.clear();
+        contribute(order.back(), +1);
+        if ((int)order.size() > w) contribute(order[order.size() - 1 - (size_t)w], -1);
+        std::sort(touched.begin(), touched.end());
+        touched.erase(std::unique(touched.begin(), touched.end()), touched.end());
+        for (int32_t u : touched) fix(u);
+        place(tree[1]);
+    }
+    for (int32_t pos = 0; pos < n; ++pos) new_id[order[pos]] = pos;
+}
+
 // ------------------------------------------------------- JaccardWithWindows
 // Algorithm 1.  Windows [s_k, e_k) of at most w ids are independent and run in
 // parallel.  Inside a window: M_k = ceil(L_k / sigma) clusters; each starts at
@@ -376,9 +453,11 @@ void order_jaccard_windows(const Csr& g, int sigma, int32_t window, int threads,
     for (auto& th : pool) th.join();
 }
 
-void order_compress(const Csr& g, int sigma, int32_t window, int threads, std::vector<int32_t>& new_id) {
+void order_compress(const Csr& g, int sigma, int32_t window, int threads, std::vector<int32_t>& new_id,
+                    int prepass) {
     std::vector<int32_t> pre;
-    order_hub_prepass(g, pre);
+    if (prepass == 1) order_gorder(g, 5, 64, pre);
+    else order_hub_prepass(g, pre);
     Csr g2;
     relabel_csr(g, pre, threads, g2);
     std::vector<int32_t> jw;

@@ -31,7 +31,12 @@ void order_rcm(const Csr& g, std::vector<int32_t>& new_id);
 void order_hub_prepass(const Csr& g, std::vector<int32_t>& new_id);
 void order_jaccard_windows(const Csr& g, int sigma, int32_t window, int threads,
                            std::vector<int32_t>& new_id);
-void order_compress(const Csr& g, int sigma, int32_t window, int threads, std::vector<int32_t>& new_id);
+// Gorder (the pre-pass Section 3.2 names): window w, common neighbours of degree <= hub_cap.
+void order_gorder(const Csr& g, int w, int32_t hub_cap, std::vector<int32_t>& new_id);
+// The compression-oriented ordering: a pre-pass (0: BFS from the hubs, 1: Gorder with
+// w = 5, hub_cap = 64), then JaccardWithWindows (Algorithm 1).
+void order_compress(const Csr& g, int sigma, int32_t window, int threads, std::vector<int32_t>& new_id,
+                    int prepass = 0);
 
 // Section 3.2.1: heavy-tail sharing (top 1% of vertices by degree hold > 5% of
 // the edges and top 10% hold > 40%) or a power-law-like log-log degree histogram.

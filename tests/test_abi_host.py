@@ -144,3 +144,15 @@ def test_graph_load_rejects_bad_files(tmp_path):
     with pytest.raises(blest.BlestError) as e:
         blest.blest_graph_load(str(p))
     assert "shorter" in str(e.value)
+
+
+@pytest.mark.parametrize("scale,seed", [(7, 1), (8, 3), (9, 5)])
+def test_gorder_prepass_matches_oracle(scale, seed):
+    """The compression ordering with the Gorder pre-pass (C++) equals the
+    oracle's, vertex for vertex (the R-MAT scale-9 graph has hubs above the
+    degree cap of 64)."""
+    g = synth.rmat_graph(scale, 8, seed=seed)
+    got = blest.blest_compute_order(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_COMPRESS, window=64,
+                                    prepass="gorder")
+    exp = oo.compress_order(g.n, g.row_ptr, g.col_idx, 8, 64, prepass="gorder")
+    assert np.array_equal(got, exp)

@@ -1,4 +1,7 @@
 """Pins for the oracle orderings (Section 3.2): closed forms and monotone checks."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -124,3 +127,56 @@ def test_relabel_preserves_levels():
     a = oracle.bfs_levels(g.n, g.row_ptr, g.col_idx, 3)
     b = oracle.bfs_levels(g.n, rp, ci, int(p[3]))
     assert np.array_equal(a, b[p])
+
+
+GORDER_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "gorder_hand.json")
+
+
+def test_gorder_hand_worked_example():
+    """Gorder's greedy on a 6-vertex graph, worked by hand from its definition
+    (tests/golden/gorder_hand.json), with and without a hub cap."""
+    gold = json.load(open(GORDER_GOLDEN))
+    e = np.array(gold["edges"], np.int32)
+    g = synth.csr_from_edges(gold["n"], e[:, 0], e[:, 1])
+    for case in gold["cases"]:
+        got = oo.gorder(g.n, g.row_ptr, g.col_idx, w=5, hub_cap=case["hub_cap"])
+        assert got.tolist() == case["new_id"]
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_gorder_invariants_and_objective(seed):
+    g = synth.rmat_graph(7, 8, seed=seed)
+    p = oo.gorder(g.n, g.row_ptr, g.col_idx)
+    assert sorted(p.tolist()) == list(range(g.n))
+    deg = np.diff(g.row_ptr)
+    first = int(np.nonzero(p == 0)[0][0])
+    assert deg[first] == deg.max() and first == int(np.argmax(deg))
+    # the greedy order scores far above a random order on Gorder's own objective
+    rnd = synth.permutation(g.n, 99 + seed)
+    assert oo.gorder_objective(g.n, g.row_ptr, g.col_idx, p) > 1.5 * oo.gorder_objective(g.n, g.row_ptr, g.col_idx, rnd)
+
+
+def test_gorder_planted_mistake_fails():
+    """Forgetting to drop the vertex that leaves the window (an unbounded
+    window) must change the order of the hand-worked graph's larger cousin."""
+    g = synth.rmat_graph(6, 8, seed=4)
+    adj = [set(g.col_idx[g.row_ptr[v]:g.row_ptr[v + 1]].tolist()) for v in range(g.n)]
+    deg = [len(a) for a in adj]
+
+    def unbounded(n):
+        order, placed = [], [False] * n
+        for _ in range(n):
+            best, bk = -1, -1
+            for u in range(n):
+                if placed[u]:
+                    continue
+                k = deg[u] if not order else sum((2 if v in adj[u] else 0) +
+                                                  sum(1 for x in adj[u] & adj[v] if deg[x] <= 64) for v in order)
+                if k > bk:
+                    best, bk = u, k
+            placed[best] = True
+            order.append(best)
+        out = np.empty(n, np.int64)
+        out[order] = np.arange(n)
+        return out
+    assert not np.array_equal(unbounded(g.n), oo.gorder(g.n, g.row_ptr, g.col_idx))
