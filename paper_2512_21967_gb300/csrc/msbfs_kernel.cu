@@ -2,15 +2,21 @@
 // column-wise form an n x k frontier matrix).  One persistent cooperative
 // launch runs up to 256 sources; each vertex carries W = ceil(k / 64) 64-bit
 // words of frontier and of visited bits.  Per level:
-//   stage 1: warps take queued virtual slice sets round-robin.  The 8 x k
-//     frontier tile of the slice set (8 W words) is loaded once per VSS by 8 W
-//     lanes and broadcast by shuffles; each lane ORs, for each of its 4 slices,
-//     the k-bit words of the columns its mask selects -- y_u |= OR_{j in mask}
-//     X[8s + j] -- and marks the result in V_next[u] with returnless 64-bit
-//     atomicOrs (the lazy marking of Algorithm 3, k bits at a time).
+//   stage 1: warps take queued virtual slice sets round-robin, with the next
+//     item's tile and frontier words (and the entry after it) loaded while the
+//     current one is pulled; tiles stream past L1 with an evict-first L2 policy.
+//     The 8 x k frontier tile of the slice set (8 W words) is loaded once per VSS
+//     by 8 W lanes and broadcast by shuffles; each lane ORs, for each of its 4
+//     slices, the k-bit words of the columns its mask selects --
+//     y_u |= OR_{j in mask} X[8s + j] -- and marks the result in V_next[u] with
+//     returnless 64-bit atomicOrs (the lazy marking of Algorithm 3, k bits at a time).
 //   stage 2: a coalesced sweep over vertices: diff = V_next ^ V_curr becomes
 //     the next frontier, newly set bits give levels, and the slice sets of
 //     vertices with any new bit are enqueued with one atomicAdd per warp.
+// Levels are kept vertex-major (a vertex's k levels are contiguous).  The sweep
+// writes them one vertex at a time across the warp, and a final warp-level
+// transpose turns them into the source-major output in original ids, so that
+// neither side gathers one 4-byte entry per memory sector.
 // The tensor-core form of this product would need the 8-bit masks unpacked to
 // an f16/b1 operand per VSS; with K = 8 columns per slice set the work is
 // memory-bound, so it stays on the CUDA cores.
@@ -40,8 +46,9 @@ struct MsArgs {
     unsigned long long* vnext;
     unsigned long long* front;
     unsigned long long* Q[3];
-    int32_t* lint;       // k x n, BVSS ids
-    int32_t* out;        // k x n, original ids (== lint when new_id is NULL)
+    int32_t* lint;       // n x kst, vertex-major: lint[u * kst + i] = level of BVSS vertex u from source i
+    int32_t kst;         // row stride of lint: k rounded up to a multiple of 8 (rows start on 32-byte sectors)
+    int32_t* out;        // k x n, source-major, original ids
     uint32_t* dirty;     // one bit per slice set touched by a mark in a sparse level (cleared by the sweep)
     const int32_t* roots;
     Ctrl* ctrl;
@@ -51,10 +58,26 @@ struct MsArgs {
     unsigned int phantom;
 };
 
+// Levels of the new bits, vertex-major.  Lane j holds the new-bit word d (sources
+// 64 w .. 64 w + 63) of vertex u0 + stride * j; for each such vertex with a new
+// bit the warp writes that vertex's entries with two stores of 32 consecutive
+// sources, so a store touches one row instead of 32.
+__device__ __forceinline__ void ms_write_levels(const MsArgs& a, unsigned long long d, int u0, int stride, int w,
+                                                int lvl, int lane) {
+    unsigned int todo = __ballot_sync(0xffffffffu, d != 0ull);
+    while (todo) {
+        const int j = __ffs(todo) - 1;
+        todo &= todo - 1u;
+        const unsigned long long dj = __shfl_sync(0xffffffffu, d, j);
+        int32_t* row = a.lint + (size_t)(u0 + stride * j) * (size_t)a.kst + (size_t)(64 * w);
+        if ((dj >> lane) & 1ull) row[lane] = lvl;
+        if ((dj >> (32 + lane)) & 1ull) row[32 + lane] = lvl;
+    }
+}
+
 template <int W>
 __device__ __forceinline__ void ms_sweep(const MsArgs& a, int lvl, unsigned long long* Qout, unsigned int* qcount) {
     const int lane = threadIdx.x & 31;
-    const size_t n = (size_t)a.n;
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
     const int nchunks = (a.n + kWarp - 1) / kWarp;
     // one row per lane, 32 consecutive rows per warp step (they share bitmap
@@ -64,24 +87,21 @@ __device__ __forceinline__ void ms_sweep(const MsArgs& a, int lvl, unsigned long
     for (int c = (int)blockIdx.x + (int)(threadIdx.x >> 5) * (int)gridDim.x; c < nchunks; c += nwarps) {
         const int u = c * kWarp + lane;
         bool any = false;
-        if (u < a.n) {
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
+        for (int w = 0; w < W; ++w) {
+            unsigned long long d = 0ull;
+            if (u < a.n) {
                 const size_t idx = (size_t)u * W + w;
                 const unsigned long long nx = ld_cg(&a.vnext[idx]);
                 const unsigned long long cu = ld_cg(&a.vcur[idx]);
-                unsigned long long d = nx ^ cu;
+                d = nx ^ cu;
                 a.front[idx] = d;
                 if (d) {
                     a.vcur[idx] = nx;
                     any = true;
-                    while (d) {
-                        const int b = __ffsll((long long)d) - 1;
-                        a.lint[(size_t)(w * 64 + b) * n + (size_t)u] = lvl;
-                        d &= d - 1;
-                    }
                 }
             }
+            ms_write_levels(a, d, c * kWarp, 1, w, lvl, lane);
         }
         const unsigned int ball = __ballot_sync(0xffffffffu, any);
         int st = 0, ln = 0;
@@ -108,7 +128,6 @@ __device__ __forceinline__ void ms_sweep_sparse(const MsArgs& a, int lvl, unsign
                                                 unsigned int* qcount) {
     const int lane = threadIdx.x & 31;
     const int wpb = (int)(blockDim.x >> 5);
-    const size_t n = (size_t)a.n;
     const int nss = (a.n + 7) >> 3;
     const int dwords = (nss + 31) >> 5;
     // block-strided over dirty words so that every warp of a block runs the same iterations
@@ -117,27 +136,26 @@ __device__ __forceinline__ void ms_sweep_sparse(const MsArgs& a, int lvl, unsign
         const uint32_t dw = t < dwords ? ld_cg(&a.dirty[t]) : 0u;
         if (lane == 0 && dw) a.dirty[t] = 0u;
         const int s = 32 * t + lane;
+        const bool mine = (dw >> lane) & 1u;
         bool any = false;
-        if ((dw >> lane) & 1u) {
+        if (dw) {   // warp-uniform; every lane runs the loop for the level writes
             for (int j = 0; j < 8; ++j) {
                 const int u = 8 * s + j;
-                if (u >= a.n) break;
 #pragma unroll
                 for (int w = 0; w < W; ++w) {
-                    const size_t idx = (size_t)u * W + w;
-                    const unsigned long long nx = ld_cg(&a.vnext[idx]);
-                    const unsigned long long cu = ld_cg(&a.vcur[idx]);
-                    unsigned long long d = nx ^ cu;
-                    a.front[idx] = d;
-                    if (d) {
-                        a.vcur[idx] = nx;
-                        any = true;
-                        while (d) {
-                            const int b = __ffsll((long long)d) - 1;
-                            a.lint[(size_t)(w * 64 + b) * n + (size_t)u] = lvl;
-                            d &= d - 1;
+                    unsigned long long d = 0ull;
+                    if (mine && u < a.n) {
+                        const size_t idx = (size_t)u * W + w;
+                        const unsigned long long nx = ld_cg(&a.vnext[idx]);
+                        const unsigned long long cu = ld_cg(&a.vcur[idx]);
+                        d = nx ^ cu;
+                        a.front[idx] = d;
+                        if (d) {
+                            a.vcur[idx] = nx;
+                            any = true;
                         }
                     }
+                    ms_write_levels(a, d, 8 * 32 * t + j, 8, w, lvl, lane);
                 }
             }
         }
@@ -152,6 +170,82 @@ __device__ __forceinline__ void ms_sweep_sparse(const MsArgs& a, int lvl, unsign
     }
 }
 
+// One queued VSS as stage 1 needs it: its tile (four row ids and the mask word
+// of this lane) and the 8 x k frontier tile of its slice set (lane j*W + w holds
+// word w of column 8s + j).
+template <int W>
+struct MsTile {
+    int4 r;
+    uint32_t m;
+    unsigned long long fw;
+};
+
+constexpr unsigned long long kNoEntry = ~0ull;
+
+template <int W>
+__device__ __forceinline__ MsTile<W> ms_load_tile(const MsArgs& a, unsigned long long ent, int lane, uint64_t pol) {
+    MsTile<W> t;
+    t.r = make_int4(0, 0, 0, 0);
+    t.m = 0u;
+    t.fw = 0ull;
+    if (ent == kNoEntry) return t;   // warp-uniform
+    const uint32_t nu = (uint32_t)ent;
+    const int s = (int)(ent >> 32);
+    if (lane < 8 * W) {
+        const int col = 8 * s + lane / W;
+        if (col < a.n) t.fw = ld_cg(&a.front[(size_t)col * W + (lane % W)]);
+    }
+    // read once per level: streamed past L1 with an evict-first L2 policy so that
+    // the bitmaps and the frontier stay resident in L2
+    const size_t tile = (size_t)nu * kWarp + lane;
+    t.r = ld_stream_v4(&a.row_ids4[tile], pol);
+    t.m = ld_stream_u32(&a.masks[tile], pol);
+    return t;
+}
+
+// y_u |= OR over the columns j of u's mask of the frontier word X[8s + j], then
+// the returnless marks of the fresh bits in V_next (Algorithm 3, k bits at a time).
+template <int W>
+__device__ __forceinline__ void ms_pull_tile(const MsArgs& a, const MsTile<W>& t, int lane, bool sparse) {
+    const unsigned int nzb = __ballot_sync(0xffffffffu, t.fw != 0ull);
+    uint32_t alpha = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        if ((nzb >> (j * W)) & ((1u << W) - 1u)) alpha |= 1u << j;
+    if (!alpha) return;   // warp-uniform: no column of this slice set is in the frontier
+    const uint32_t m = t.m & (alpha * 0x01010101u);
+    unsigned long long y[4][W];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int w = 0; w < W; ++w) y[q][w] = 0ull;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        if (!((alpha >> j) & 1u)) continue;   // warp-uniform
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const unsigned long long v = __shfl_sync(0xffffffffu, t.fw, j * W + w);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if ((m >> (8 * q + j)) & 1u) y[q][w] |= v;
+        }
+    }
+    const int r4[4] = {t.r.x, t.r.y, t.r.z, t.r.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            if (!y[q][w]) continue;
+            // sources that already reached the row need no mark; V_curr only gains
+            // bits during a traversal, so a stale word can only let a mark through
+            const unsigned long long fresh = y[q][w] & ~a.vcur[(size_t)r4[q] * W + w];
+            if (fresh) {
+                atomicOr(&a.vnext[(size_t)r4[q] * W + w], fresh);
+                if (sparse) atomicOr(&a.dirty[r4[q] >> 8], 1u << ((r4[q] >> 3) & 31));
+            }
+        }
+}
+
 template <int W>
 __device__ __forceinline__ void ms_body(const MsArgs& a) {
     const int lane = threadIdx.x & 31;
@@ -161,6 +255,7 @@ __device__ __forceinline__ void ms_body(const MsArgs& a) {
     const int nwarps = nthreads >> 5;
     unsigned int gen = 0;
     Ctrl* ctrl = a.ctrl;
+    const uint64_t pol = l2_evict_first_policy();
 
     for (int i = gtid; i < a.k; i += nthreads) {
         const int r = a.roots[i];
@@ -183,54 +278,19 @@ __device__ __forceinline__ void ms_body(const MsArgs& a) {
         const unsigned long long* Qin = a.Q[lvl % 3];
         unsigned long long* Qout = a.Q[(lvl + 1) % 3];
         unsigned int* qcount_next = &ctrl->qcount[(lvl + 1) & 3];
-        for (unsigned int p = (unsigned int)gwarp; p < qn; p += (unsigned int)nwarps) {
-            const unsigned long long ent = ld_cg(&Qin[p]);
-            const uint32_t nu = (uint32_t)ent;
-            const int s = (int)(ent >> 32);
-            // 8 x k frontier tile of slice set s: lane j*W + w holds word w of column 8s + j
-            unsigned long long fw = 0;
-            if (lane < 8 * W) {
-                const int col = 8 * s + lane / W;
-                if (col < a.n) fw = ld_cg(&a.front[(size_t)col * W + (lane % W)]);
-            }
-            const unsigned int nzb = __ballot_sync(0xffffffffu, fw != 0ull);
-            uint32_t alpha = 0;
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                if ((nzb >> (j * W)) & ((1u << W) - 1u)) alpha |= 1u << j;
-            const size_t tile = (size_t)nu * kWarp + lane;
-            const int4 r = __ldg(&a.row_ids4[tile]);
-            const uint32_t m = __ldg(&a.masks[tile]) & (alpha * 0x01010101u);
-            unsigned long long y[4][W];
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-                for (int w = 0; w < W; ++w) y[q][w] = 0ull;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                if (!((alpha >> j) & 1u)) continue;   // warp-uniform
-#pragma unroll
-                for (int w = 0; w < W; ++w) {
-                    const unsigned long long v = __shfl_sync(0xffffffffu, fw, j * W + w);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if ((m >> (8 * q + j)) & 1u) y[q][w] |= v;
-                }
-            }
-            const int r4[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-                for (int w = 0; w < W; ++w) {
-                    if (!y[q][w]) continue;
-                    // sources that already reached the row need no mark; V_curr only gains
-                    // bits during a traversal, so a stale word can only let a mark through
-                    const unsigned long long fresh = y[q][w] & ~a.vcur[(size_t)r4[q] * W + w];
-                    if (fresh) {
-                        atomicOr(&a.vnext[(size_t)r4[q] * W + w], fresh);
-                        if (sparse) atomicOr(&a.dirty[r4[q] >> 8], 1u << ((r4[q] >> 3) & 31));
-                    }
-                }
+        // software pipeline over this warp's items p, p + nwarps, ...: the entry two
+        // items ahead and the tile and frontier words one item ahead are in flight
+        // while the current item is pulled
+        const unsigned int nw = (unsigned int)nwarps;
+        unsigned int p = (unsigned int)gwarp;
+        unsigned long long e_next = p + nw < qn ? ld_cg(&Qin[p + nw]) : kNoEntry;
+        MsTile<W> t = ms_load_tile<W>(a, p < qn ? ld_cg(&Qin[p]) : kNoEntry, lane, pol);
+        for (; p < qn; p += nw) {
+            const unsigned long long e_after = p + 2u * nw < qn ? ld_cg(&Qin[p + 2u * nw]) : kNoEntry;
+            const MsTile<W> t_next = ms_load_tile<W>(a, e_next, lane, pol);
+            ms_pull_tile<W>(a, t, lane, sparse);
+            t = t_next;
+            e_next = e_after;
         }
         if (!grid_barrier(ctrl, gridDim.x, a.phantom, gen, a.timeout_ns)) return;
         if (sparse) ms_sweep_sparse<W>(a, lvl, Qout, qcount_next);
@@ -241,14 +301,33 @@ __device__ __forceinline__ void ms_body(const MsArgs& a) {
         qn = qnext;
     }
     if (gtid == 0) ctrl->levels = (unsigned int)lvl;
-    // out[i*n + v] = level of v from source i (original ids), -1 if unreached
-    const int64_t total = (int64_t)a.k * a.n;
-    for (int64_t x = gtid; x < total; x += nthreads) {
-        const int i = (int)(x / a.n);
-        const int v = (int)(x - (int64_t)i * a.n);
-        const int u = a.new_id ? __ldg(&a.new_id[v]) : v;
-        const bool reached = (ld_cg(&a.vcur[(size_t)u * W + (i >> 6)]) >> (i & 63)) & 1ull;
-        a.out[x] = reached ? ld_cg(&a.lint[(size_t)i * a.n + u]) : -1;
+    // out[i*n + v] = level of v from source i (original ids), -1 if unreached: a
+    // warp-level transpose of the vertex-major buffer.  Lane j takes vertex
+    // v = 32 b + j and reads its levels 4 sources (16 bytes) at a time; the warp
+    // then stores them source by source, 32 consecutive vertices per store.
+    const int nvb = (a.n + kWarp - 1) / kWarp;
+    for (int b = gwarp; b < nvb; b += nwarps) {
+        const int v = b * kWarp + lane;
+        const bool ok = v < a.n;
+        const int u = ok ? (a.new_id ? __ldg(&a.new_id[v]) : v) : 0;
+        const int4* row = reinterpret_cast<const int4*>(a.lint + (size_t)u * (size_t)a.kst);
+        int32_t* o = a.out + v;
+#pragma unroll 1
+        for (int w = 0; w < W; ++w) {
+            const unsigned long long vis = ok ? ld_cg(&a.vcur[(size_t)u * W + w]) : 0ull;
+            const int i_end = min(64 * w + 64, a.k);
+#pragma unroll 1
+            for (int i0 = 64 * w; i0 < i_end; i0 += 4) {
+                const uint32_t bits = (uint32_t)(vis >> (i0 - 64 * w)) & 0xFu;
+                // positions of sources that never reached u are never written, so never used
+                const int4 lv = bits ? ld_cg(&row[i0 >> 2]) : make_int4(-1, -1, -1, -1);
+                if (!ok) continue;
+                o[(size_t)i0 * (size_t)a.n] = bits & 1u ? lv.x : -1;
+                if (i0 + 1 < i_end) o[(size_t)(i0 + 1) * (size_t)a.n] = bits & 2u ? lv.y : -1;
+                if (i0 + 2 < i_end) o[(size_t)(i0 + 2) * (size_t)a.n] = bits & 4u ? lv.z : -1;
+                if (i0 + 3 < i_end) o[(size_t)(i0 + 3) * (size_t)a.n] = bits & 8u ? lv.w : -1;
+            }
+        }
     }
 }
 
@@ -259,8 +338,9 @@ __global__ void __launch_bounds__(kMsBlock) msbfs_kernel(MsArgs a) {
 }
 
 template <class T>
-cudaError_t grow(T*& p, int64_t& cap, int64_t need, int copies = 1) {
+cudaError_t grow(T*& p, int64_t& cap, int64_t need, bool caller_owned, int copies = 1) {
     if (need <= cap) return cudaSuccess;
+    if (caller_owned) return cudaErrorInvalidValue;   // never free or replace the caller's memory
     cudaFree(p);
     p = nullptr;
     cap = 0;
@@ -287,20 +367,22 @@ int run_msbfs(MsbfsState& s, const MsbfsLaunchCommon& c, const std::vector<int32
     const int64_t k_all = (int64_t)roots.size();
     if (k_all == 0 || c.n == 0) return 0;
     cudaError_t e = cudaSuccess;
-    for (int64_t i0 = 0; i0 < k_all; i0 += 256) {
-        const int k = (int)std::min<int64_t>(256, k_all - i0);
-        const int W = k <= 64 ? 1 : (k <= 128 ? 2 : 4);
+    const bool own = s.caller_owned;
+    for (int64_t i0 = 0; i0 < k_all; i0 += kMsbfsChunk) {
+        const int k = (int)std::min<int64_t>(kMsbfsChunk, k_all - i0);
+        const int W = msbfs_words(k);
         const int64_t words = (int64_t)c.n * W;
         int64_t cap_v = s.words_cap, cap_n = s.words_cap, cap_f = s.words_cap;
-        if ((e = grow(s.vcur, cap_v, words)) != cudaSuccess) break;
-        if ((e = grow(s.vnext, cap_n, words)) != cudaSuccess) break;
-        if ((e = grow(s.front, cap_f, words)) != cudaSuccess) break;
+        if ((e = grow(s.vcur, cap_v, words, own)) != cudaSuccess) break;
+        if ((e = grow(s.vnext, cap_n, words, own)) != cudaSuccess) break;
+        if ((e = grow(s.front, cap_f, words, own)) != cudaSuccess) break;
         s.words_cap = std::min(cap_v, std::min(cap_n, cap_f));
-        if ((e = grow(s.Q, s.qcap, std::max<int64_t>(c.nvss, 1), 3)) != cudaSuccess) break;
-        if (c.new_id && (e = grow(s.lint, s.lint_cap, (int64_t)k * c.n)) != cudaSuccess) break;
-        if ((e = grow(s.roots, s.roots_cap, k)) != cudaSuccess) break;
+        if ((e = grow(s.Q, s.qcap, std::max<int64_t>(c.nvss, 1), own, 3)) != cudaSuccess) break;
+        const int32_t kst = (k + 7) & ~7;
+        if ((e = grow(s.lint, s.lint_cap, msbfs_level_entries(c.n, k), own)) != cudaSuccess) break;
+        if ((e = grow(s.roots, s.roots_cap, k, own)) != cudaSuccess) break;
         const int64_t dwords = ((int64_t)c.nss + 31) / 32;
-        if ((e = grow(s.dirty, s.dirty_cap, dwords)) != cudaSuccess) break;
+        if ((e = grow(s.dirty, s.dirty_cap, dwords, own)) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(s.roots, roots.data() + i0, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
         cudaMemsetAsync(c.ctrl, 0, kCtrlClearBytes, st);
         cudaMemsetAsync(s.vcur, 0, sizeof(unsigned long long) * (size_t)words, st);
@@ -319,7 +401,8 @@ int run_msbfs(MsbfsState& s, const MsbfsLaunchCommon& c, const std::vector<int32
         a.front = s.front;
         for (int i = 0; i < 3; ++i) a.Q[i] = s.Q + (size_t)i * (size_t)s.qcap;
         int32_t* out = d_out + (size_t)i0 * (size_t)c.n;
-        a.lint = c.new_id ? s.lint : out;
+        a.lint = s.lint;
+        a.kst = kst;
         a.out = out;
         a.roots = s.roots;
         a.dirty = s.dirty;
@@ -337,7 +420,8 @@ int run_msbfs(MsbfsState& s, const MsbfsLaunchCommon& c, const std::vector<int32
         if ((e = cudaLaunchCooperativeKernel(kfn, dim3((unsigned)(nb * c.sms)), dim3(kMsBlock), args, 0, st)) != cudaSuccess) break;
     }
     if (e != cudaSuccess) {
-        *err = cudaGetErrorString(e);
+        *err = own && e == cudaErrorInvalidValue ? "caller-owned multi-source state is smaller than the launch"
+                                                 : cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? 4 : 5;
     }
     return 0;

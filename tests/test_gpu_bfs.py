@@ -255,6 +255,22 @@ def test_msbfs_grid_and_isolated(gpu):
         blest.blest_destroy(h)
 
 
+@pytest.mark.parametrize("k", [5, 70, 200])
+def test_msbfs_ragged_vertex_count(gpu, k):
+    """n = 37^2 = 1369 is not a multiple of the 32 vertices a warp transposes at a
+    time, and the three k give row strides 8, 72 and 200 (1, 2 and 4 words)."""
+    g, _ = synth.grid_graph(37, 0.9, seed=6)
+    assert g.n % 32 != 0
+    srcs = synth.pick_sources(g, k, seed=21)
+    exp = oracle.msbfs_levels(g.n, g.row_ptr, g.col_idx, srcs, threads=8)
+    for order in (blest.BLEST_ORDER_NONE, blest.BLEST_ORDER_BANDWIDTH):
+        h = blest.blest_graph_create(g.n, g.row_ptr, g.col_idx, order)
+        try:
+            assert np.array_equal(blest.blest_msbfs(h, srcs), exp)
+        finally:
+            blest.blest_destroy(h)
+
+
 def min_over_sources(g, srcs):
     per = oracle.msbfs_levels(g.n, g.row_ptr, g.col_idx, srcs, threads=8).astype(np.int64)
     per = np.where(per < 0, np.iinfo(np.int64).max, per).min(axis=0)
