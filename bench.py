@@ -520,25 +520,41 @@ def serve_stream(blest, srv, stream):
     submit_at = [0.0] * len(stream)
     lock = threading.Lock()
     done = threading.Event()
+    failed = []
 
     def waiter():
-        for i in range(len(stream)):
-            while tickets[i] is None:
-                time.sleep(0.0001)
-            srv_lat = blest.blest_server_wait(srv, tickets[i], 600.0)
-            with lock:
-                lat[i] = (submit_at[i] - stream[i][0]) + srv_lat
-        done.set()
+        try:
+            for i in range(len(stream)):
+                while tickets[i] is None:
+                    if failed:
+                        return
+                    time.sleep(0.0001)
+                srv_lat = blest.blest_server_wait(srv, tickets[i], 120.0)
+                with lock:
+                    lat[i] = (submit_at[i] - stream[i][0]) + srv_lat
+        except BaseException as ex:   # a failed query ends the run instead of leaving it waiting
+            failed.append(ex)
+        finally:
+            done.set()
 
     th = threading.Thread(target=waiter, daemon=True)
     th.start()
-    for i, (t_arr, g, srcs) in enumerate(stream):
-        now = time.perf_counter() - t0
-        if t_arr > now:
-            time.sleep(t_arr - now)
-        submit_at[i] = time.perf_counter() - t0
-        tickets[i] = blest.blest_server_submit(srv, g, srcs, None)
-    done.wait()
+    try:
+        for i, (t_arr, g, srcs) in enumerate(stream):
+            if failed:
+                break
+            now = time.perf_counter() - t0
+            if t_arr > now:
+                time.sleep(t_arr - now)
+            submit_at[i] = time.perf_counter() - t0
+            tickets[i] = blest.blest_server_submit(srv, g, srcs, None)
+    except BaseException as ex:
+        failed.append(ex)
+    # every query has a deadline of its arrival + 120 s in the waiter; this bounds the whole run
+    if not done.wait(timeout=(stream[-1][0] if stream else 0.0) + 300.0):
+        failed.append(TimeoutError("serving run did not finish"))
+    if failed:
+        raise failed[0]
     wall = time.perf_counter() - t0
     return np.array(lat), wall
 

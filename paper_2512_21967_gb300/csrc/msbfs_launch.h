@@ -2,14 +2,32 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <vector>
 
 namespace blest {
 
+constexpr int kMsbfsChunk = 256;   // sources per launch
+
+// 64-bit words per vertex of each bit matrix for a launch of k sources.
+inline int msbfs_words(int64_t k) {
+    const int64_t kc = std::min<int64_t>(k, kMsbfsChunk);
+    return kc <= 64 ? 1 : (kc <= 128 ? 2 : 4);
+}
+
+// int32 entries of the vertex-major internal level buffer for k sources: n rows
+// of the largest chunk's source count rounded up to a multiple of 8.
+inline int64_t msbfs_level_entries(int32_t n, int64_t k) {
+    const int64_t kc = std::min<int64_t>(k, kMsbfsChunk);
+    return ((kc + 7) & ~int64_t(7)) * (int64_t)n;
+}
+
 // Device buffers of a multi-source traversal, grown on demand and kept with
-// the handle between calls.
+// the handle between calls.  A state whose buffers the caller allocated
+// (caller_owned) is never reallocated: a launch it is too small for fails.
 struct MsbfsState {
+    bool caller_owned = false;
     int64_t words_cap = 0;             // u64 words per bitmap (n * W)
     unsigned long long* vcur = nullptr;
     unsigned long long* vnext = nullptr;

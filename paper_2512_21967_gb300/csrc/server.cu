@@ -110,11 +110,11 @@ struct blest_server {
 namespace {
 
 int64_t launch_bytes(const blest::HandleView& v, int k) {
-    const int W = k <= 64 ? 1 : (k <= 128 ? 2 : 4);
+    const int W = blest::msbfs_words(k);
     int64_t b = (int64_t)k * v.n * 4;                          // levels
     b += 3 * (int64_t)v.n * W * 8;                            // V_curr, V_next, frontier
     b += 3 * std::max<int64_t>(v.nvss, 1) * 8;                // queues
-    if (v.new_id_host) b += (int64_t)k * v.n * 4;              // levels in BVSS order
+    b += blest::msbfs_level_entries(v.n, k) * 4;              // vertex-major levels in BVSS ids
     b += (int64_t)k * 4 + 4 * 256;                             // roots, alignment slack
     b += ((int64_t)v.nss + 31) / 32 * 4;                       // dirty slice sets
     return b;
@@ -126,11 +126,11 @@ cudaError_t alloc_async(T*& p, int64_t count, cudaStream_t st) {
 }
 
 cudaError_t alloc_launch(Slot& s, const blest::HandleView& v, int k) {
-    const int W = k <= 64 ? 1 : (k <= 128 ? 2 : 4);
-    const int64_t words = (int64_t)v.n * W;
+    const int64_t words = (int64_t)v.n * blest::msbfs_words(k);
     cudaError_t e;
     blest::MsbfsState& m = s.ms;
     m = blest::MsbfsState();
+    m.caller_owned = true;   // stream-ordered pool memory: the launcher must not reallocate it
     if ((e = alloc_async(s.d_levels, (int64_t)k * v.n, s.stream)) != cudaSuccess) return e;
     if ((e = alloc_async(m.vcur, words, s.stream)) != cudaSuccess) return e;
     if ((e = alloc_async(m.vnext, words, s.stream)) != cudaSuccess) return e;
@@ -138,10 +138,9 @@ cudaError_t alloc_launch(Slot& s, const blest::HandleView& v, int k) {
     m.words_cap = words;
     if ((e = alloc_async(m.Q, 3 * std::max<int64_t>(v.nvss, 1), s.stream)) != cudaSuccess) return e;
     m.qcap = std::max<int64_t>(v.nvss, 1);
-    if (v.new_id_host) {
-        if ((e = alloc_async(m.lint, (int64_t)k * v.n, s.stream)) != cudaSuccess) return e;
-        m.lint_cap = (int64_t)k * v.n;
-    }
+    const int64_t lev = blest::msbfs_level_entries(v.n, k);
+    if ((e = alloc_async(m.lint, lev, s.stream)) != cudaSuccess) return e;
+    m.lint_cap = lev;
     if ((e = alloc_async(m.roots, k, s.stream)) != cudaSuccess) return e;
     m.roots_cap = k;
     const int64_t dwords = ((int64_t)v.nss + 31) / 32;

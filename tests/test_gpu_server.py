@@ -14,8 +14,10 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def served(gpu):
     graphs = [synth.rmat_graph(10, 16, seed=71), synth.rmat_graph(12, 16, seed=72), synth.rmat_graph(11, 8, seed=73),
-              synth.grid_graph(40, 0.9, seed=74)[0], synth.grid_graph(64, 0.9, seed=75)[0]]
-    orders = [blest.BLEST_ORDER_COMPRESS] * 3 + [blest.BLEST_ORDER_BANDWIDTH] * 2
+              synth.grid_graph(40, 0.9, seed=74)[0], synth.grid_graph(64, 0.9, seed=75)[0],
+              synth.rmat_graph(9, 16, seed=76)]
+    # the last graph keeps its own vertex ids (no reordering)
+    orders = [blest.BLEST_ORDER_COMPRESS] * 3 + [blest.BLEST_ORDER_BANDWIDTH] * 2 + [blest.BLEST_ORDER_NONE]
     handles = [blest.blest_graph_create(g.n, g.row_ptr, g.col_idx, o) for g, o in zip(graphs, orders)]
     rng = np.random.default_rng(7)
     queries = []
