@@ -31,3 +31,27 @@ def test_host_preprocessing_under_asan_ubsan(tmp_path):
     assert run.returncode == 0, (run.stdout[-2000:], run.stderr[-4000:])
     assert "runtime error" not in run.stderr
     assert "failures=0" in run.stdout
+
+
+def test_multi_source_chunk_sizing(tmp_path):
+    """Every chunk the multi-source launcher makes fits the state a caller sizes
+    for the whole launch with the same functions (the server's pre-allocation)."""
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no g++")
+    cuda_inc = None
+    for d in (os.environ.get("CUDA_HOME"), "/usr/local/cuda"):
+        if d and os.path.exists(os.path.join(d, "include", "cuda_runtime.h")):
+            cuda_inc = os.path.join(d, "include")
+            break
+    if cuda_inc is None:
+        pytest.skip("no CUDA headers")
+    exe = str(tmp_path / "msbfs_sizing")
+    cmd = [gxx, "-std=c++17", "-O1", "-fsanitize=undefined", "-fno-sanitize-recover=undefined", "-I", CSRC,
+           "-I", cuda_inc, os.path.join(ROOT, "tests", "host", "msbfs_sizing.cpp"), "-o", exe]
+    build = subprocess.run(cmd, capture_output=True, text=True)
+    if build.returncode != 0 and "sanitize" in build.stderr and "cannot find" in build.stderr:
+        pytest.skip("sanitizer runtime not installed")
+    assert build.returncode == 0, build.stderr[-3000:]
+    run = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert run.returncode == 0 and "failures=0" in run.stdout, run.stdout[-2000:]
