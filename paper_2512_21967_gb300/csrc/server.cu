@@ -105,9 +105,39 @@ struct blest_server {
     bool paused = false;
     std::string worker_error;
     std::thread worker;
+    int dev = 0;
 };
 
 namespace {
+
+// While any server lives, the device's default stream-ordered pool keeps up to
+// the largest memory cap cached between launches (its release threshold).  The
+// first server saves the threshold it found; the last one to go restores it and
+// returns the cached memory.
+std::mutex g_pool_mu;
+int g_pool_users = 0;
+uint64_t g_pool_saved = 0;
+
+void pool_acquire(int dev, int64_t cap) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+    uint64_t cur = 0;
+    cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &cur);
+    if (g_pool_users++ == 0) g_pool_saved = cur;
+    uint64_t thr = std::max<uint64_t>(cur, (uint64_t)cap);
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+}
+
+void pool_release(int dev) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (g_pool_users == 0 || --g_pool_users > 0) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+    uint64_t thr = g_pool_saved;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    cudaMemPoolTrimTo(pool, 0);
+}
 
 int64_t launch_bytes(const blest::HandleView& v, int k) {
     const int W = blest::msbfs_words(k);
@@ -334,12 +364,8 @@ blest_status blest_server_create(const blest_handle* graphs, int32_t num_graphs,
     blest_server* raw = sv.get();
     int dev = 0;
     cudaGetDevice(&dev);
-    // keep up to the memory cap cached in the stream-ordered pool between launches
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-        uint64_t thr = (uint64_t)raw->p.memory_cap_bytes;
-        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-    }
+    raw->dev = dev;
+    pool_acquire(dev, raw->p.memory_cap_bytes);
     raw->worker = std::thread([raw, dev]() {
         cudaSetDevice(dev);
         worker_main(raw);
@@ -435,6 +461,7 @@ void blest_server_destroy(blest_server_handle sv) {
         cudaFree(s.d_ctrl);
         cudaFreeHost(s.h_status);
     }
+    pool_release(sv->dev);
     delete sv;
 }
 
