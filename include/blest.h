@@ -204,7 +204,11 @@ blest_status blest_bfs_parents(blest_handle h, int32_t src, int32_t* levels, int
  * level over an n x k frontier bit-matrix (Section 2, multi-source form).
  * levels: host memory of k*n int32, row-major by source: levels[i*n + v] is the
  * level of v from srcs[i].  Duplicate sources are allowed.  k = 0 does nothing.
- * Errors: as blest_bfs. */
+ * Sources run in launches of at most 256.  The handle keeps the device state of
+ * the largest launch so far until blest_destroy: three bit matrices of n x W
+ * 64-bit words (W = 1, 2 or 4 for up to 64, 128 or 256 sources), an n x k8 int32
+ * level buffer (k8 = the launch's source count rounded up to 8), and 3 queues of
+ * numVSS entries.  Errors: as blest_bfs. */
 blest_status blest_msbfs(blest_handle h, const int32_t* srcs, int32_t k, int32_t* levels);
 
 /* One BFS whose level-0 frontier is the whole set srcs[0..k) (host array):
