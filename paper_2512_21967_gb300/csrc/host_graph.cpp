@@ -220,12 +220,14 @@ void order_rcm(const Csr& g, std::vector<int32_t>& new_id) {
 void order_hub_prepass(const Csr& g, std::vector<int32_t>& new_id) {
     int32_t n = g.n;
     new_id.assign((size_t)n, 0);
+    // roots by descending degree, ascending id within a degree (a counting sort)
+    int32_t dmax = 0;
+    for (int32_t v = 0; v < n; ++v) dmax = std::max(dmax, g.rp[v + 1] - g.rp[v]);
+    std::vector<int64_t> start((size_t)dmax + 2, 0);
+    for (int32_t v = 0; v < n; ++v) ++start[(size_t)(dmax - (g.rp[v + 1] - g.rp[v])) + 1];
+    for (size_t d = 1; d < start.size(); ++d) start[d] += start[d - 1];
     std::vector<int32_t> cand((size_t)n);
-    for (int32_t v = 0; v < n; ++v) cand[v] = v;
-    std::sort(cand.begin(), cand.end(), [&](int32_t a, int32_t b) {
-        int32_t da = g.rp[a + 1] - g.rp[a], db = g.rp[b + 1] - g.rp[b];
-        return da != db ? da > db : a < b;
-    });
+    for (int32_t v = 0; v < n; ++v) cand[(size_t)start[(size_t)(dmax - (g.rp[v + 1] - g.rp[v]))]++] = v;
     std::vector<uint8_t> seen((size_t)n, 0);
     std::vector<int32_t> order;
     order.reserve((size_t)n);
@@ -343,32 +345,62 @@ struct JaccardWorker {
     std::vector<int32_t> c, cstamp;
     std::vector<uint8_t> inq;
     std::vector<int32_t> touched;
-    std::vector<uint64_t> pairs;
-    std::vector<int32_t> revx, revptr, revj;
+    // Reverse index of the window: neighbour x -> the window rows that hold x.
+    // An open-addressing table keyed by x gives each x its list in revj
+    // (hoff, hlen); rows already placed are dropped from a list as it is walked.
+    std::vector<int32_t> hkey, hoff, hlen, revj;
+    int hshift = 60;
     int32_t stamp = 0;
 
     JaccardWorker(const Csr& gr, int s) : g(gr), sigma(s), ustamp((size_t)gr.n, 0) {}
 
+    // Fibonacci hashing: the high bits of x times 2^64 / golden ratio
+    size_t slot0(int32_t x) const { return (size_t)(((uint64_t)(uint32_t)x * 0x9E3779B97F4A7C15ull) >> hshift); }
+
+    // slot of x, or -1 if no row of the window holds x
+    int64_t find(int32_t x) const {
+        const size_t mask = hkey.size() - 1;
+        for (size_t h = slot0(x);; h = (h + 1) & mask) {
+            if (hkey[h] == x) return (int64_t)h;
+            if (hkey[h] < 0) return -1;
+        }
+    }
+
+    void build_index(int32_t s_k, int32_t L) {
+        const int32_t e0 = g.rp[s_k], e1 = g.rp[s_k + L];
+        const int64_t distinct_max = std::min<int64_t>((int64_t)e1 - e0, g.n);
+        size_t cap = 16;
+        hshift = 60;
+        while ((int64_t)cap < 2 * distinct_max) { cap <<= 1; --hshift; }   // load factor <= 1/2
+        const size_t mask = cap - 1;
+        hkey.assign(cap, -1);
+        hlen.assign(cap, 0);
+        hoff.resize(cap);
+        for (int32_t e = e0; e < e1; ++e) {
+            const int32_t x = g.ci[e];
+            size_t h = slot0(x);
+            while (hkey[h] >= 0 && hkey[h] != x) h = (h + 1) & mask;
+            hkey[h] = x;
+            ++hlen[h];
+        }
+        int32_t run = 0;
+        for (size_t h = 0; h < cap; ++h) { hoff[h] = run; run += hlen[h]; }
+        revj.resize((size_t)(e1 - e0));
+        std::vector<int32_t>& fill = c;   // scratch: per-slot fill position (c is reset by window())
+        fill.assign(cap, 0);
+        for (int32_t jl = 0; jl < L; ++jl)
+            for (int32_t e = g.rp[s_k + jl]; e < g.rp[s_k + jl + 1]; ++e) {
+                const size_t h = (size_t)find(g.ci[e]);
+                revj[(size_t)(hoff[h] + fill[h]++)] = jl;   // rows in ascending order per x
+            }
+    }
+
     void window(int32_t s_k, int32_t e_k, int32_t* new_id) {
         int32_t L = e_k - s_k;
+        build_index(s_k, L);
         c.assign((size_t)L, 0);
         cstamp.assign((size_t)L, 0);
         inq.assign((size_t)L, 1);
-        // reverse index
-        pairs.clear();
-        for (int32_t jl = 0; jl < L; ++jl) {
-            int32_t j = s_k + jl;
-            for (int32_t e = g.rp[j]; e < g.rp[j + 1]; ++e)
-                pairs.push_back(((uint64_t)(uint32_t)g.ci[e] << 32) | (uint32_t)jl);
-        }
-        std::sort(pairs.begin(), pairs.end());
-        revx.clear(); revptr.clear(); revj.resize(pairs.size());
-        for (size_t i = 0; i < pairs.size(); ++i) {
-            int32_t x = (int32_t)(pairs[i] >> 32);
-            if (revx.empty() || revx.back() != x) { revx.push_back(x); revptr.push_back((int32_t)i); }
-            revj[i] = (int32_t)(pairs[i] & 0xffffffffu);
-        }
-        revptr.push_back((int32_t)pairs.size());
 
         int32_t qptr = 0, remaining = L;
         int32_t M = (L + sigma - 1) / sigma;
@@ -409,21 +441,26 @@ struct JaccardWorker {
         }
     }
 
+    // U gains j's neighbours; every unplaced row sharing a new one gets c += 1.
+    // The pick above is the best ratio with ties to the smallest row, so it does
+    // not depend on the order in which rows are touched or listed.
     void add_to_u(int32_t j, int64_t& usize) {
         for (int32_t e = g.rp[j]; e < g.rp[j + 1]; ++e) {
             int32_t x = g.ci[e];
             if (ustamp[x] == stamp) continue;
             ustamp[x] = stamp;
             ++usize;
-            auto it = std::lower_bound(revx.begin(), revx.end(), x);
-            if (it == revx.end() || *it != x) continue;
-            size_t k = (size_t)(it - revx.begin());
-            for (int32_t i = revptr[k]; i < revptr[k + 1]; ++i) {
+            const int64_t h = find(x);
+            if (h < 0) continue;
+            int32_t w = hoff[h];
+            for (int32_t i = hoff[h], end = hoff[h] + hlen[h]; i < end; ++i) {
                 int32_t jl = revj[i];
-                if (!inq[jl]) continue;
+                if (!inq[jl]) continue;   // placed rows leave the list
+                revj[w++] = jl;
                 if (cstamp[jl] != stamp) { cstamp[jl] = stamp; c[jl] = 0; touched.push_back(jl); }
                 ++c[jl];
             }
+            hlen[h] = w - hoff[h];
         }
     }
 };
