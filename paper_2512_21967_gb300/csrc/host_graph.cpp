@@ -341,18 +341,19 @@ namespace {
 struct JaccardWorker {
     const Csr& g;
     int sigma;
-    std::vector<int32_t> ustamp;   // per vertex: stamp of the cluster whose U contains it
     std::vector<int32_t> c, cstamp;
     std::vector<uint8_t> inq;
     std::vector<int32_t> touched;
     // Reverse index of the window: neighbour x -> the window rows that hold x.
     // An open-addressing table keyed by x gives each x its list in revj
     // (hoff, hlen); rows already placed are dropped from a list as it is walked.
-    std::vector<int32_t> hkey, hoff, hlen, revj;
+    // Every neighbour of a window row has a slot, so the slot also records
+    // (ustamp) the cluster whose U holds x: no per-vertex array per thread.
+    std::vector<int32_t> hkey, hoff, hlen, ustamp, revj;
     int hshift = 60;
     int32_t stamp = 0;
 
-    JaccardWorker(const Csr& gr, int s) : g(gr), sigma(s), ustamp((size_t)gr.n, 0) {}
+    JaccardWorker(const Csr& gr, int s) : g(gr), sigma(s) {}
 
     // Fibonacci hashing: the high bits of x times 2^64 / golden ratio
     size_t slot0(int32_t x) const { return (size_t)(((uint64_t)(uint32_t)x * 0x9E3779B97F4A7C15ull) >> hshift); }
@@ -375,6 +376,7 @@ struct JaccardWorker {
         const size_t mask = cap - 1;
         hkey.assign(cap, -1);
         hlen.assign(cap, 0);
+        ustamp.assign(cap, 0);
         hoff.resize(cap);
         for (int32_t e = e0; e < e1; ++e) {
             const int32_t x = g.ci[e];
@@ -446,12 +448,10 @@ struct JaccardWorker {
     // not depend on the order in which rows are touched or listed.
     void add_to_u(int32_t j, int64_t& usize) {
         for (int32_t e = g.rp[j]; e < g.rp[j + 1]; ++e) {
-            int32_t x = g.ci[e];
-            if (ustamp[x] == stamp) continue;
-            ustamp[x] = stamp;
+            const size_t h = (size_t)find(g.ci[e]);   // j is a window row, so x has a slot
+            if (ustamp[h] == stamp) continue;
+            ustamp[h] = stamp;
             ++usize;
-            const int64_t h = find(x);
-            if (h < 0) continue;
             int32_t w = hoff[h];
             for (int32_t i = hoff[h], end = hoff[h] + hlen[h]; i < end; ++i) {
                 int32_t jl = revj[i];
