@@ -166,7 +166,8 @@ class ClockSampler:
 def byte_model(h, g, n):
     """Per-slice-set algorithmic bytes of one stage-1 visit: every VSS of the
     set costs 5 B per unpadded slice (4 B row id + 1 B mask) + 8 B to read its
-    queue entry + 8 B to write it one level earlier."""
+    queue entry + 8 B to write it one level earlier.  Also returns the vertex
+    order (original -> BVSS id) and the number of VSSs of each slice set."""
     import paper_2512_21967_gb300 as blest
     rp = blest.blest_export(h, blest.BLEST_ARRAY_REAL_PTRS).astype(np.int64)
     cnt = blest.blest_export(h, blest.BLEST_ARRAY_VSS_COUNT).astype(np.int64)
@@ -175,7 +176,7 @@ def byte_model(h, g, n):
     pref[1:] = np.cumsum(per_vss)
     w_s = pref[rp[1:]] - pref[rp[:-1]]
     new_id = blest.blest_export(h, blest.BLEST_ARRAY_NEW_ID).astype(np.int64)
-    return w_s, new_id
+    return w_s, new_id, rp[1:] - rp[:-1]
 
 
 def traversal_bytes(levels_t, new_id_t, w_s_t, nss, n, lazy, torch):
@@ -191,6 +192,56 @@ def traversal_bytes(levels_t, new_id_t, w_s_t, nss, n, lazy, torch):
     sweeps = (nlevels + 1) if lazy else 1       # level 0 plus one per lazy level
     sweep = sweeps * nwords * 8
     return stage1 + sweep + 4 * nreached + 12 * n, nreached
+
+
+def ms_traversal_bytes(levels_t, new_id_t, w_s_t, nvss_t, nss, n, torch):
+    """Algorithmic bytes of one multi-source traversal (levels_t: k x n, original
+    ids) under the model of the batched kernel, per launch of at most 256
+    sources with W = ceil(k/64) words per vertex:
+      stage 1, per level l and slice set s holding a vertex first reached at l-1
+        by any source: the visit bytes of s (5 B per unpadded slice + 16 B per
+        VSS) + its 8 x W frontier words (64 W B);
+      sweeps: level 0 and every processed level read V_next, V_curr and write the
+        frontier (24 W B per vertex); a level whose queue has at most n/128 VSSs
+        sweeps only the slice sets holding a newly reached vertex (8 vertices each);
+      levels: 4 B written and 4 B read back per (source, reached vertex), 4 B
+        written per (source, vertex) of the output, 8 W + 4 B per vertex read by
+        the final transpose (visited words, vertex order).
+    Returns (bytes, reached pairs)."""
+    k_all = int(levels_t.shape[0])
+    total, pairs_all = 0, 0
+    s_of_v = (new_id_t >> 3).long()
+    for c0 in range(0, k_all, 256):
+        lv_c = levels_t[c0:c0 + 256]
+        k = int(lv_c.shape[0])
+        W = 1 if k <= 64 else (2 if k <= 128 else 4)
+        keys = None
+        pairs, lmax = 0, 0
+        for i in range(0, k, 8):
+            lv = lv_c[i:i + 8]
+            reached = lv >= 0
+            pairs += int(reached.sum().item())
+            if not bool(reached.any()):
+                continue
+            lmax = max(lmax, int(lv.max().item()))
+            kk = torch.unique(lv.long()[reached] * nss + s_of_v.expand_as(lv)[reached])
+            keys = kk if keys is None else torch.unique(torch.cat([keys, kk]))
+        stage1 = 0
+        sweep = 24 * W * n                                   # level 0
+        if keys is not None:
+            lvl_of = keys // nss
+            ss = keys % nss
+            stage1 = int(w_s_t[ss].sum().item()) + 64 * W * int(keys.numel())
+            qn = torch.bincount(lvl_of, weights=nvss_t[ss].double(), minlength=lmax + 1).cpu().numpy()
+            sets = torch.bincount(lvl_of, minlength=lmax + 2).cpu().numpy()
+            for l in range(1, lmax + 2):                     # processed levels 1 .. lmax + 1
+                if float(qn[l - 1]) * 128 <= n:
+                    sweep += 24 * W * 8 * int(sets[l])
+                else:
+                    sweep += 24 * W * n
+        total += stage1 + sweep + 8 * pairs + 4 * k * n + (8 * W + 4) * n
+        pairs_all += pairs
+    return total, pairs_all
 
 
 # ------------------------------------------------------------------ ours
@@ -259,14 +310,15 @@ def run_ours(args):
     torch.cuda.set_stream(stream)      # flushes, events and traversals all on this stream
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     deg_t = torch.from_numpy(g.degrees()).to(dev)
-    w_s, new_id = byte_model(h, g, n)
+    w_s, new_id, nvss = byte_model(h, g, n)
     w_s_t = torch.from_numpy(w_s).to(dev)
     new_id_t = torch.from_numpy(new_id).to(dev)
     nss = (n + 7) // 8
 
     if msk:
+        model = (w_s_t, new_id_t, torch.from_numpy(nvss).to(dev), nss)
         return run_ours_msbfs(args, torch, blest, h, g, srcs, msk, dev, stream, flush, st, t_gen, t_create,
-                              rank, world)
+                              rank, world, model)
 
     out = torch.empty(n, dtype=torch.int32, device=dev)
     edges = np.zeros(len(srcs), np.int64)
@@ -396,7 +448,8 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_ours_msbfs(args, torch, blest, h, g, srcs, k, dev, stream, flush, st, t_gen, t_create, rank, world):
+def run_ours_msbfs(args, torch, blest, h, g, srcs, k, dev, stream, flush, st, t_gen, t_create, rank, world,
+                   model):
     n = g.n
     out = torch.empty((k, n), dtype=torch.int32, device=dev)
     deg_t = torch.from_numpy(g.degrees()).to(dev)
@@ -404,6 +457,8 @@ def run_ours_msbfs(args, torch, blest, h, g, srcs, k, dev, stream, flush, st, t_
         blest.blest_msbfs_device(h, srcs[:k], out, stream=stream)
     blest.blest_sync(h)
     edges = int(((out >= 0).to(torch.int64) * deg_t[None, :]).sum().item()) // 2
+    w_s_t, new_id_t, nvss_t, nss = model
+    ms_bytes, _ = ms_traversal_bytes(out, new_id_t, w_s_t, nvss_t, nss, n, torch)
     torch.cuda.synchronize(dev)
     sampler = ClockSampler() if rank == 0 else None
     evs = [[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(args.steps)]
@@ -437,6 +492,8 @@ def run_ours_msbfs(args, torch, blest, h, g, srcs, k, dev, stream, flush, st, t_
     loop_ms = float(sum(a_.elapsed_time(b_) for a_, b_ in le))
     loop_rate = len(loop_srcs) / (loop_ms / 1e3)
     batched_rate = k * args.steps / (ms / 1e3)
+    hbm, peak_kind = peaks()
+    achieved = ms_bytes / (ms / args.steps / 1e3) / 1e9
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
@@ -447,6 +504,12 @@ def run_ours_msbfs(args, torch, blest, h, g, srcs, k, dev, stream, flush, st, t_
                            "batched_over_loop": round(batched_rate / loop_rate, 2),
                            "single_source_variant": {kk: tune[kk] for kk in ("update", "unroll", "stage_depth",
                                                                               "visited_filter", "blocks_per_sm")}},
+                "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                             "frac": round(achieved / hbm, 4), "peak_kind": peak_kind, "traffic": None,
+                             "traffic_note": "no capture of this kernel revision",
+                             "kernel": "msbfs_kernel (one launch per call; the event pair also covers the "
+                                       "call's clears and source upload)",
+                             "bytes_per_launch": ms_bytes, "avg_launch_ms": round(ms / args.steps, 5)},
                 "gpu_launches": args.steps, "clocks": clocks,
                 "bvss": {kk: st[kk] for kk in ("num_vss", "unpadded_slices", "compression_ratio")},
                 "preprocess_s": {"generate": round(t_gen, 2), "create_total": round(t_create, 2)}}
