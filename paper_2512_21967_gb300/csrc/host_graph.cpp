@@ -84,17 +84,44 @@ int clean_csr(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int thr
 }
 
 bool is_symmetric(const Csr& g, int threads, int64_t* bad_u, int64_t* bad_v) {
+    // Rows are sorted and hold neither self-loops nor duplicates.  Reversal maps
+    // the edges (u, v) with v > u one-to-one onto edges with v < u, so the graph
+    // is symmetric iff every such upper edge has its reverse and there are as
+    // many upper as lower edges.  The reverse of (u, v) lies in row v below v.
     std::atomic<int64_t> found(-1);
     std::atomic<int64_t> found_v(-1);
+    std::atomic<int64_t> upper(0), lower(0);
     parallel_chunks(threads, g.n, 4096, [&](int64_t lo, int64_t hi) {
-        for (int64_t u = lo; u < hi && found.load(std::memory_order_relaxed) < 0; ++u)
-            for (int64_t e = g.rp[u]; e < g.rp[u + 1]; ++e) {
-                int32_t v = g.ci[e];
+        int64_t up = 0, low = 0;
+        for (int64_t u = lo; u < hi && found.load(std::memory_order_relaxed) < 0; ++u) {
+            const int32_t* rb = g.ci.data() + g.rp[u];
+            const int32_t* re = g.ci.data() + g.rp[u + 1];
+            const int32_t* mid = std::upper_bound(rb, re, (int32_t)u);   // first neighbour above u
+            low += mid - rb;
+            up += re - mid;
+            for (const int32_t* p = mid; p < re; ++p) {
+                const int32_t v = *p;
                 const int32_t* b = g.ci.data() + g.rp[v];
                 const int32_t* en = g.ci.data() + g.rp[v + 1];
                 if (!std::binary_search(b, en, (int32_t)u)) { found.store(u); found_v.store(v); break; }
             }
+        }
+        upper += up;
+        lower += low;
     });
+    if (found.load() < 0 && upper.load() != lower.load()) {
+        // some lower edge (u, v) has no reverse: find one for the message
+        parallel_chunks(threads, g.n, 4096, [&](int64_t lo, int64_t hi) {
+            for (int64_t u = lo; u < hi && found.load(std::memory_order_relaxed) < 0; ++u)
+                for (int64_t e = g.rp[u]; e < g.rp[u + 1]; ++e) {
+                    const int32_t v = g.ci[e];
+                    if (v >= u) break;
+                    const int32_t* b = g.ci.data() + g.rp[v];
+                    const int32_t* en = g.ci.data() + g.rp[v + 1];
+                    if (!std::binary_search(b, en, (int32_t)u)) { found.store(u); found_v.store(v); break; }
+                }
+        });
+    }
     if (found.load() >= 0) {
         if (bad_u) *bad_u = found.load();
         if (bad_v) *bad_v = found_v.load();

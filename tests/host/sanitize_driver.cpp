@@ -38,6 +38,39 @@ void make_graph(int32_t n, int64_t m, uint64_t seed, bool hubs, std::vector<int3
     }
 }
 
+bool has_edge(const blest::Csr& g, int64_t u, int64_t v) {
+    for (int64_t e = g.rp[(size_t)u]; e < g.rp[(size_t)u + 1]; ++e)
+        if (g.ci[(size_t)e] == v) return true;
+    return false;
+}
+
+// is_symmetric must reject g and name an edge (u, v) of g whose reverse is missing.
+int expect_asymmetric(const blest::Csr& g, const char* what) {
+    int64_t bu = -1, bv = -1;
+    if (blest::is_symmetric(g, 2, &bu, &bv)) {
+        std::printf("accepted asymmetric graph: %s\n", what);
+        return 1;
+    }
+    if (bu < 0 || bv < 0 || bu >= g.n || bv >= g.n || !has_edge(g, bu, bv) || has_edge(g, bv, bu)) {
+        std::printf("bad witness (%lld, %lld): %s\n", (long long)bu, (long long)bv, what);
+        return 1;
+    }
+    return 0;
+}
+
+// g with one direction of one edge removed
+blest::Csr drop_direction(const blest::Csr& g, int64_t u, int32_t v) {
+    blest::Csr r;
+    r.n = g.n;
+    r.rp.assign((size_t)g.n + 1, 0);
+    for (int32_t x = 0; x < g.n; ++x) {
+        for (int64_t e = g.rp[(size_t)x]; e < g.rp[(size_t)x + 1]; ++e)
+            if (!(x == u && g.ci[(size_t)e] == v)) r.ci.push_back(g.ci[(size_t)e]);
+        r.rp[(size_t)x + 1] = (int32_t)r.ci.size();
+    }
+    return r;
+}
+
 bool is_perm(const std::vector<int32_t>& p, int32_t n) {
     if ((int32_t)p.size() != n) return false;
     std::vector<char> seen((size_t)n, 0);
@@ -66,6 +99,13 @@ int main() {
             }
             int64_t bu = -1, bv = -1;
             if (!blest::is_symmetric(g, 2, &bu, &bv)) { std::printf("asymmetric n=%d\n", n); ++failures; }
+            // one direction of a few edges removed, edges below and above the diagonal alike
+            for (int64_t t = 0; t < 6 && g.nnz() > 0; ++t) {
+                const int64_t e = (int64_t)(mix(99 + (uint64_t)n + 7 * (uint64_t)t) % (uint64_t)g.nnz());
+                int64_t u = 0;
+                while (g.rp[(size_t)u + 1] <= e) ++u;
+                failures += expect_asymmetric(drop_direction(g, u, g.ci[(size_t)e]), "one direction dropped");
+            }
             (void)blest::is_social_like(g);
             std::vector<int32_t> ids;
             blest::order_rcm(g, ids);
@@ -82,6 +122,19 @@ int main() {
                 failures += r.nnz() != g.nnz();
             }
         }
+    }
+    // a lower edge without its reverse, next to a symmetric pair: only the edge count shows it
+    {
+        blest::Csr g;
+        g.n = 4;
+        g.rp = {0, 1, 2, 2, 3};   // 0-1 both ways, then 3 -> 1 alone
+        g.ci = {1, 0, 1};
+        failures += expect_asymmetric(g, "lower edge without reverse");
+        blest::Csr h;
+        h.n = 4;
+        h.rp = {0, 1, 1, 1, 2};   // 0 -> 1 alone (upper) and 3 -> 2 alone (lower): equal counts
+        h.ci = {1, 2};
+        failures += expect_asymmetric(h, "upper and lower edges without reverse");
     }
     // invalid inputs are rejected, not read out of bounds
     {
