@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <thread>
 
 #include "../../include/blest.h"
@@ -59,14 +60,14 @@ int clean_csr(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int thr
 
     out.n = n;
     out.rp.assign((size_t)n + 1, 0);
-    std::vector<int32_t> tmp((size_t)std::max<int64_t>(m, 1));
+    std::unique_ptr<int32_t[]> tmp(new int32_t[(size_t)std::max<int64_t>(m, 1)]);   // every entry is written before use
     std::vector<int32_t> newdeg((size_t)n + 1, 0);
     parallel_chunks(threads, n, 4096, [&](int64_t lo, int64_t hi) {
         for (int64_t u = lo; u < hi; ++u) {
-            int32_t* a = tmp.data() + row_ptr[u];
+            int32_t* a = tmp.get() + row_ptr[u];
             int64_t len = row_ptr[u + 1] - row_ptr[u];
             if (len > 0) std::memcpy(a, col_idx + row_ptr[u], (size_t)len * sizeof(int32_t));
-            std::sort(a, a + len);
+            if (!std::is_sorted(a, a + len)) std::sort(a, a + len);
             int64_t w = 0;
             for (int64_t i = 0; i < len; ++i)
                 if (a[i] != (int32_t)u && (w == 0 || a[w - 1] != a[i])) a[w++] = a[i];
@@ -78,7 +79,7 @@ int clean_csr(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int thr
     parallel_chunks(threads, n, 4096, [&](int64_t lo, int64_t hi) {
         for (int64_t u = lo; u < hi; ++u)
             if (newdeg[u] > 0)
-                std::memcpy(out.ci.data() + out.rp[u], tmp.data() + row_ptr[u], (size_t)newdeg[u] * sizeof(int32_t));
+                std::memcpy(out.ci.data() + out.rp[u], tmp.get() + row_ptr[u], (size_t)newdeg[u] * sizeof(int32_t));
     });
     return BLEST_OK;
 }
