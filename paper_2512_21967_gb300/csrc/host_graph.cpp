@@ -368,6 +368,7 @@ void order_gorder(const Csr& g, int w, int32_t hub_cap, std::vector<int32_t>& ne
 namespace {
 struct JaccardWorker {
     const Csr& g;
+    const int32_t* row_at;   // window position -> row of g (NULL: the identity)
     int sigma;
     std::vector<int32_t> c, cstamp;
     std::vector<uint8_t> inq;
@@ -381,7 +382,10 @@ struct JaccardWorker {
     int hshift = 60;
     int32_t stamp = 0;
 
-    JaccardWorker(const Csr& gr, int s) : g(gr), sigma(s) {}
+    JaccardWorker(const Csr& gr, const int32_t* at, int s) : g(gr), row_at(at), sigma(s) {}
+
+    int32_t row(int32_t pos) const { return row_at ? row_at[pos] : pos; }
+    int32_t deg(int32_t pos) const { const int32_t r = row(pos); return g.rp[r + 1] - g.rp[r]; }
 
     // Fibonacci hashing: the high bits of x times 2^64 / golden ratio
     size_t slot0(int32_t x) const { return (size_t)(((uint64_t)(uint32_t)x * 0x9E3779B97F4A7C15ull) >> hshift); }
@@ -396,8 +400,9 @@ struct JaccardWorker {
     }
 
     void build_index(int32_t s_k, int32_t L) {
-        const int32_t e0 = g.rp[s_k], e1 = g.rp[s_k + L];
-        const int64_t distinct_max = std::min<int64_t>((int64_t)e1 - e0, g.n);
+        int64_t nnz = 0;
+        for (int32_t jl = 0; jl < L; ++jl) nnz += deg(s_k + jl);
+        const int64_t distinct_max = std::min<int64_t>(nnz, g.n);
         size_t cap = 16;
         hshift = 60;
         while ((int64_t)cap < 2 * distinct_max) { cap <<= 1; --hshift; }   // load factor <= 1/2
@@ -406,23 +411,28 @@ struct JaccardWorker {
         hlen.assign(cap, 0);
         ustamp.assign(cap, 0);
         hoff.resize(cap);
-        for (int32_t e = e0; e < e1; ++e) {
-            const int32_t x = g.ci[e];
-            size_t h = slot0(x);
-            while (hkey[h] >= 0 && hkey[h] != x) h = (h + 1) & mask;
-            hkey[h] = x;
-            ++hlen[h];
+        for (int32_t jl = 0; jl < L; ++jl) {
+            const int32_t r = row(s_k + jl);
+            for (int32_t e = g.rp[r]; e < g.rp[r + 1]; ++e) {
+                const int32_t x = g.ci[e];
+                size_t h = slot0(x);
+                while (hkey[h] >= 0 && hkey[h] != x) h = (h + 1) & mask;
+                hkey[h] = x;
+                ++hlen[h];
+            }
         }
         int32_t run = 0;
         for (size_t h = 0; h < cap; ++h) { hoff[h] = run; run += hlen[h]; }
-        revj.resize((size_t)(e1 - e0));
+        revj.resize((size_t)nnz);
         std::vector<int32_t>& fill = c;   // scratch: per-slot fill position (c is reset by window())
         fill.assign(cap, 0);
-        for (int32_t jl = 0; jl < L; ++jl)
-            for (int32_t e = g.rp[s_k + jl]; e < g.rp[s_k + jl + 1]; ++e) {
+        for (int32_t jl = 0; jl < L; ++jl) {
+            const int32_t r = row(s_k + jl);
+            for (int32_t e = g.rp[r]; e < g.rp[r + 1]; ++e) {
                 const size_t h = (size_t)find(g.ci[e]);
                 revj[(size_t)(hoff[h] + fill[h]++)] = jl;   // rows in ascending order per x
             }
+        }
     }
 
     void window(int32_t s_k, int32_t e_k, int32_t* new_id) {
@@ -455,7 +465,7 @@ struct JaccardWorker {
                 for (int32_t jl : touched) {
                     if (!inq[jl]) continue;
                     int64_t num = c[jl];
-                    int64_t den = (int64_t)(g.rp[s_k + jl + 1] - g.rp[s_k + jl]) + usize - num;
+                    int64_t den = (int64_t)deg(s_k + jl) + usize - num;
                     // num > 0 here, so den >= 1
                     bool better = best < 0 || num * bden > bnum * den || (num * bden == bnum * den && jl < best);
                     if (better) { best = jl; bnum = num; bden = den; }
@@ -474,7 +484,8 @@ struct JaccardWorker {
     // U gains j's neighbours; every unplaced row sharing a new one gets c += 1.
     // The pick above is the best ratio with ties to the smallest row, so it does
     // not depend on the order in which rows are touched or listed.
-    void add_to_u(int32_t j, int64_t& usize) {
+    void add_to_u(int32_t pos, int64_t& usize) {
+        const int32_t j = row(pos);
         for (int32_t e = g.rp[j]; e < g.rp[j + 1]; ++e) {
             const size_t h = (size_t)find(g.ci[e]);   // j is a window row, so x has a slot
             if (ustamp[h] == stamp) continue;
@@ -494,7 +505,8 @@ struct JaccardWorker {
 };
 }  // namespace
 
-void order_jaccard_windows(const Csr& g, int sigma, int32_t window, int threads, std::vector<int32_t>& new_id) {
+void order_jaccard_windows(const Csr& g, int sigma, int32_t window, int threads, std::vector<int32_t>& new_id,
+                           const int32_t* row_at) {
     int32_t n = g.n;
     new_id.assign((size_t)n, 0);
     if (n == 0) return;
@@ -503,7 +515,7 @@ void order_jaccard_windows(const Csr& g, int sigma, int32_t window, int threads,
     if (nt < 1) nt = 1;
     std::atomic<int64_t> next(0);
     auto work = [&]() {
-        JaccardWorker wk(g, sigma);
+        JaccardWorker wk(g, row_at, sigma);
         for (;;) {
             int64_t k = next.fetch_add(1);
             if (k >= nwin) break;
@@ -523,10 +535,13 @@ void order_compress(const Csr& g, int sigma, int32_t window, int threads, std::v
     std::vector<int32_t> pre;
     if (prepass == 1) order_gorder(g, 5, 64, pre);
     else order_hub_prepass(g, pre);
-    Csr g2;
-    relabel_csr(g, pre, threads, g2);
+    // Algorithm 1 over the pre-pass order, reading g's rows through the
+    // permutation: neighbours only need to compare equal, and ties go to the
+    // smaller window position, so no relabelled copy of g is needed
+    std::vector<int32_t> at((size_t)g.n);
+    for (int32_t v = 0; v < g.n; ++v) at[(size_t)pre[v]] = v;
     std::vector<int32_t> jw;
-    order_jaccard_windows(g2, sigma, window, threads, jw);
+    order_jaccard_windows(g, sigma, window, threads, jw, at.data());
     new_id.resize((size_t)g.n);
     for (int32_t v = 0; v < g.n; ++v) new_id[v] = jw[pre[v]];
 }

@@ -29,8 +29,10 @@ bool is_symmetric(const Csr& g, int threads, int64_t* bad_u, int64_t* bad_v);
 // Orderings; all return new_id[old].
 void order_rcm(const Csr& g, std::vector<int32_t>& new_id);
 void order_hub_prepass(const Csr& g, std::vector<int32_t>& new_id);
+// row_at (optional, n entries): window position p holds row row_at[p] of g
+// (the identity when NULL); new_id is indexed by position.
 void order_jaccard_windows(const Csr& g, int sigma, int32_t window, int threads,
-                           std::vector<int32_t>& new_id);
+                           std::vector<int32_t>& new_id, const int32_t* row_at = nullptr);
 // Gorder (the pre-pass Section 3.2 names): window w, common neighbours of degree <= hub_cap.
 void order_gorder(const Csr& g, int w, int32_t hub_cap, std::vector<int32_t>& new_id);
 // The compression-oriented ordering: a pre-pass (0: BFS from the hubs, 1: Gorder with
