@@ -492,6 +492,9 @@ def run_ours_msbfs(args, torch, blest, h, g, srcs, k, dev, stream, flush, st, t_
     loop_ms = float(sum(a_.elapsed_time(b_) for a_, b_ in le))
     loop_rate = len(loop_srcs) / (loop_ms / 1e3)
     batched_rate = k * args.steps / (ms / 1e3)
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline_parallel(g, srcs[:k], 2 * (os.cpu_count() or 1))
     hbm, peak_kind = peaks()
     achieved = ms_bytes / (ms / args.steps / 1e3) / 1e9
     if rank == 0:
@@ -510,6 +513,7 @@ def run_ours_msbfs(args, torch, blest, h, g, srcs, k, dev, stream, flush, st, t_
                              "kernel": "msbfs_kernel (one launch per call; the event pair also covers the "
                                        "call's clears and source upload)",
                              "bytes_per_launch": ms_bytes, "avg_launch_ms": round(ms / args.steps, 5)},
+                "cpu_baseline": cpu,
                 "gpu_launches": args.steps, "clocks": clocks,
                 "bvss": {kk: st[kk] for kk in ("num_vss", "unpadded_slices", "compression_ratio")},
                 "preprocess_s": {"generate": round(t_gen, 2), "create_total": round(t_create, 2)}}
@@ -750,6 +754,24 @@ def cpu_baseline(g, srcs, nsrc, edges_of=None):
             "seconds": round(tot_t, 2)}
 
 
+def cpu_baseline_parallel(g, srcs, nsrc, threads=None):
+    """The oracle over all host cores, one source per thread (every run is the
+    plain queue BFS; threads only split the list of sources): the host baseline
+    of the multi-source workloads, on the first ``nsrc`` sources."""
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    sample = np.ascontiguousarray(srcs[:nsrc], dtype=np.int32)
+    t0 = time.perf_counter()
+    lv = oracle.msbfs_levels(g.n, g.row_ptr, g.col_idx, sample, threads=threads)
+    secs = time.perf_counter() - t0
+    edges = sum(oracle.reached_edges(g.row_ptr, lv[i]) for i in range(len(sample)))
+    return {"value": round(edges / secs / 1e9, 5), "unit": "GTEPS", "cores": int(min(threads, len(sample))),
+            "kind": "oracle", "source_bfs_per_s": round(len(sample) / secs, 3),
+            "sample": f"{len(sample)} of the {len(srcs)} sources, one source per thread on {threads} threads, "
+                      f"nproc={os.cpu_count()}",
+            "seconds": round(secs, 2)}
+
+
 def reference_jobs(args):
     """The workload of --impl reference as oracle jobs (graph, its sources), with
     the same workload string, unit and size as our arm's line for it."""
@@ -772,13 +794,18 @@ def reference_jobs(args):
         g, srcs = synth.rmat_workload(size, nsrc, seed_graph=sg, seed_src=ss)
     else:
         g, srcs = synth.grid_workload(size, nsrc, seed_graph=sg, seed_src=ss)
+    conf = {"n": g.n, "directed_edges": g.nnz}
     if kind == "wsweep":
         label = f"window sweep, {g.name}, {len(srcs)} sources"
     elif k:
+        # the multi-source baseline: one source per host thread
+        t = os.cpu_count() or 1
         label = f"multi-source BFS k={k}, {g.name}"
+        return ([(g, [int(x) for x in srcs[i:i + t]]) for i in range(0, k, t)], label, "GTEPS",
+                dict(conf, k=k, threads=t))
     else:
         label = f"single-source BFS, {g.name}, {len(srcs)} seeded sources, {order} order"
-    return [(g, [int(x)]) for x in srcs], label, "GTEPS", {"n": g.n, "directed_edges": g.nnz}
+    return [(g, [int(x)]) for x in srcs], label, "GTEPS", conf
 
 
 def run_reference(args):
@@ -789,11 +816,15 @@ def run_reference(args):
         return
     import oracle
     jobs, label, unit, conf = reference_jobs(args)
-    # serving queries carry up to 32 sources each: one query per step keeps a step bounded
-    per_step = 1 if unit == "queries/s" else max(1, args.ref_sources)
+    threads = conf.get("threads", 1)
+    # one serving query, or one source per thread of a multi-source job, per step keeps a step bounded
+    per_step = 1 if unit == "queries/s" or threads > 1 else max(1, args.ref_sources)
 
     def run_job(job):
         g, sources = job
+        if threads > 1:
+            lv = oracle.msbfs_levels(g.n, g.row_ptr, g.col_idx, np.asarray(sources, np.int32), threads=threads)
+            return sum(oracle.reached_edges(g.row_ptr, lv[i]) for i in range(len(sources)))
         e = 0
         for s_ in sources:
             e += oracle.reached_edges(g.row_ptr, oracle.bfs_levels(g.n, g.row_ptr, g.col_idx, s_))
@@ -809,15 +840,20 @@ def run_reference(args):
             tot_t += time.perf_counter() - t0
             done += 1
     value = tot_e / tot_t / 1e9 if unit == "GTEPS" else done / tot_t
-    what = "query" if unit == "queries/s" else "source"
-    sample = (f"{per_step} {what}(s) per step, one thread, nproc={os.cpu_count()}; "
-              "the oracle runs on the original vertex order, one source at a time")
+    if threads > 1:
+        sample = (f"{len(jobs[0][1])} sources per step, one source per thread on {threads} threads, "
+                  f"nproc={os.cpu_count()}; the oracle runs on the original vertex order")
+    else:
+        what = "query" if unit == "queries/s" else "source"
+        sample = (f"{per_step} {what}(s) per step, one thread, nproc={os.cpu_count()}; "
+                  "the oracle runs on the original vertex order, one source at a time")
     line = {"metric": METRIC, "value": round(value, 5), "unit": unit, "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_t / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
             "config": dict({"workload": label, "per_step": per_step}, **conf),
-            "cpu_baseline": {"value": round(value, 5), "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": round(value, 5), "unit": unit, "cores": threads, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": round(value, 5), "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

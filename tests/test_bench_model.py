@@ -54,3 +54,18 @@ def test_ms_byte_model_matches_plain_definition(case):
     got = bench.ms_traversal_bytes(torch.from_numpy(levels), torch.from_numpy(new_id), torch.from_numpy(w_s),
                                    torch.from_numpy(nvss), nss, g.n, torch)
     assert got == plain_ms_bytes(levels, new_id, w_s, nvss, g.n)
+
+
+def test_parallel_cpu_baseline_counts_the_oracle_work():
+    """The multi-source host baseline reports the oracle's reached edges over its
+    wall time, with the threads it used."""
+    import bench
+    g = synth.rmat_graph(10, 8, seed=8)
+    srcs = synth.pick_sources(g, 6, seed=9)
+    out = bench.cpu_baseline_parallel(g, srcs, 4, threads=3)
+    assert out["kind"] == "oracle" and out["cores"] == 3 and out["unit"] == "GTEPS"
+    edges = sum(oracle.reached_edges(g.row_ptr, oracle.bfs_levels(g.n, g.row_ptr, g.col_idx, int(s)))
+                for s in srcs[:4])
+    assert out["value"] > 0 and out["source_bfs_per_s"] > 0
+    secs = 4 / out["source_bfs_per_s"]                  # the reported rate gives the wall time back
+    assert abs(out["value"] * 1e9 * secs - edges) <= 0.01 * edges
