@@ -274,7 +274,7 @@ blest_status prepare_graph(int32_t n, const int32_t* row_ptr, const int32_t* col
     new_id.clear();
     if (ord == BLEST_ORDER_COMPRESS)
         blest::order_compress(clean, 8, window, threads, new_id, params && params->prepass == 1 ? 1 : 0);
-    else if (ord == BLEST_ORDER_BANDWIDTH) blest::order_rcm(clean, new_id);
+    else if (ord == BLEST_ORDER_BANDWIDTH) blest::order_rcm(clean, new_id, threads);
     *order_used = ord;
     *t_order = now_s() - t0;
     return BLEST_OK;

@@ -160,28 +160,130 @@ void relabel_csr(const Csr& g, const std::vector<int32_t>& new_id, int threads, 
 // Cuthill-McKee sequence is reversed at the end.
 
 namespace {
+// Spin barrier for a fixed set of host threads (sense by generation count).
+class SpinBarrier {
+  public:
+    explicit SpinBarrier(int n) : n_(n) {}
+    void wait() {
+        const unsigned gen = gen_.load(std::memory_order_acquire);
+        if (arrived_.fetch_add(1, std::memory_order_acq_rel) + 1 == n_) {
+            arrived_.store(0, std::memory_order_relaxed);
+            gen_.fetch_add(1, std::memory_order_acq_rel);
+            return;
+        }
+        for (unsigned spins = 0; gen_.load(std::memory_order_acquire) == gen; ++spins)
+            if (spins > 1024) std::this_thread::yield();
+    }
+
+  private:
+    const int n_;
+    std::atomic<int> arrived_{0};
+    std::atomic<unsigned> gen_{0};
+};
+
+// BFS that only needs the set of vertices on each level (the eccentricity and
+// the last level), not a visit order: levels are expanded sequentially while the
+// frontier is small and by `threads` host threads, each claiming vertices with a
+// compare-and-swap on their stamp, once a frontier holds kParallelFrontier
+// vertices.  queue[0..count) holds the vertices level by level.
 struct LevelBfs {
-    std::vector<int32_t> stamp, level, queue;
+    static constexpr int64_t kParallelFrontier = 1024;
+    struct Mark {
+        int32_t stamp, level;
+    };
+    std::vector<Mark> mark;
+    std::vector<int32_t> queue;
     int32_t cur = 0;
-    explicit LevelBfs(int32_t n) : stamp((size_t)n, 0), level((size_t)n, 0), queue((size_t)std::max(n, 1)) {}
-    // BFS from root over its component; returns eccentricity; queue[0..count) holds the visit order.
+    int threads = 1;
+    LevelBfs(int32_t n, int t) : mark((size_t)n, Mark{0, 0}), queue((size_t)std::max(n, 1)), threads(t) {}
+    int32_t level(int32_t v) const { return mark[(size_t)v].level; }
+
+    // returns the eccentricity of root
     int32_t run(const Csr& g, int32_t root, int64_t& count) {
         ++cur;
-        int64_t head = 0, tail = 0;
-        stamp[root] = cur; level[root] = 0; queue[tail++] = root;
-        int32_t ecc = 0;
+        int64_t head = 0, tail = 0, lvl_end = 1;
+        int32_t lvl = 0;
+        mark[root] = Mark{cur, 0};
+        queue[tail++] = root;
         while (head < tail) {
-            int32_t u = queue[head++];
+            if (head == lvl_end) {   // a level boundary
+                ++lvl;
+                lvl_end = tail;
+                if (threads > 1 && lvl_end - head >= kParallelFrontier) {
+                    tail = parallel_levels(g, head, tail, lvl);
+                    break;
+                }
+            }
+            const int32_t u = queue[head++];
             for (int32_t e = g.rp[u]; e < g.rp[u + 1]; ++e) {
-                int32_t v = g.ci[e];
-                if (stamp[v] != cur) {
-                    stamp[v] = cur; level[v] = level[u] + 1; queue[tail++] = v;
-                    if (level[v] > ecc) ecc = level[v];
+                const int32_t v = g.ci[e];
+                if (mark[v].stamp != cur) {
+                    mark[v] = Mark{cur, lvl + 1};
+                    queue[tail++] = v;
                 }
             }
         }
         count = tail;
-        return ecc;
+        return mark[queue[tail - 1]].level;
+    }
+
+    // Expands the frontier queue[lo, hi) (level lvl) and every later level with
+    // all threads; returns the new tail.
+    int64_t parallel_levels(const Csr& g, int64_t lo, int64_t hi, int32_t lvl) {
+        const int T = threads;
+        std::vector<std::vector<int32_t>> found((size_t)T);
+        std::vector<int64_t> sizes((size_t)T, 0);
+        std::atomic<int64_t> next(0);
+        int64_t end = hi;
+        SpinBarrier bar(T);
+        auto worker = [&](int t) {
+            int64_t fs = lo, fe = hi;   // the current frontier (each thread keeps its own copy)
+            int32_t l = lvl;
+            std::vector<int32_t>& out = found[(size_t)t];
+            for (;;) {
+                out.clear();
+                for (;;) {
+                    const int64_t c = fs + next.fetch_add(256, std::memory_order_relaxed);
+                    if (c >= fe) break;
+                    const int64_t c_end = std::min<int64_t>(c + 256, fe);
+                    for (int64_t i = c; i < c_end; ++i) {
+                        const int32_t u = queue[(size_t)i];
+                        for (int32_t e = g.rp[u]; e < g.rp[u + 1]; ++e) {
+                            const int32_t v = g.ci[e];
+                            int32_t seen = __atomic_load_n(&mark[v].stamp, __ATOMIC_RELAXED);
+                            if (seen == cur) continue;
+                            if (__atomic_compare_exchange_n(&mark[v].stamp, &seen, cur, false, __ATOMIC_RELAXED,
+                                                            __ATOMIC_RELAXED)) {
+                                mark[v].level = l + 1;
+                                out.push_back(v);
+                            }
+                        }
+                    }
+                }
+                sizes[(size_t)t] = (int64_t)out.size();
+                bar.wait();   // every thread's share of the next level is in `found`
+                int64_t off = fe, total = 0;
+                for (int i = 0; i < T; ++i) {
+                    if (i < t) off += sizes[(size_t)i];
+                    total += sizes[(size_t)i];
+                }
+                if (!out.empty()) std::memcpy(&queue[(size_t)off], out.data(), out.size() * sizeof(int32_t));
+                if (t == 0) next.store(0, std::memory_order_relaxed);
+                bar.wait();   // the next level is in the queue and the chunk counter is reset
+                if (total == 0) {
+                    if (t == 0) end = fe;
+                    return;
+                }
+                fs = fe;
+                fe += total;
+                ++l;
+            }
+        };
+        std::vector<std::thread> pool;
+        for (int t = 1; t < T; ++t) pool.emplace_back(worker, t);
+        worker(0);
+        for (auto& th : pool) th.join();
+        return end;
     }
 };
 }  // namespace
@@ -194,7 +296,7 @@ static int32_t pseudo_peripheral(const Csr& g, LevelBfs& bfs, int32_t start) {
         int32_t y = -1;
         for (int64_t i = 0; i < cnt; ++i) {
             int32_t v = bfs.queue[i];
-            if (bfs.level[v] != ex) continue;
+            if (bfs.level(v) != ex) continue;
             if (y < 0) { y = v; continue; }
             int32_t dv = g.rp[v + 1] - g.rp[v], dy = g.rp[y + 1] - g.rp[y];
             if (dv < dy || (dv == dy && v < y)) y = v;
@@ -209,17 +311,22 @@ static int32_t pseudo_peripheral(const Csr& g, LevelBfs& bfs, int32_t start) {
     }
 }
 
-void order_rcm(const Csr& g, std::vector<int32_t>& new_id) {
+void order_rcm(const Csr& g, std::vector<int32_t>& new_id, int threads) {
     int32_t n = g.n;
     new_id.assign((size_t)n, 0);
     if (n == 0) return;
-    LevelBfs bfs(n);
+    LevelBfs bfs(n, threads);
     std::vector<uint8_t> seen((size_t)n, 0);
     std::vector<int32_t> order;
     order.reserve((size_t)n);
     std::vector<int32_t> nb;
     for (int32_t v0 = 0; v0 < n; ++v0) {
         if (seen[v0]) continue;
+        if (g.rp[v0 + 1] == g.rp[v0]) {   // an isolated vertex is its own component and its own order
+            seen[v0] = 1;
+            order.push_back(v0);
+            continue;
+        }
         int32_t r = pseudo_peripheral(g, bfs, v0);
         size_t head = order.size();
         seen[r] = 1;

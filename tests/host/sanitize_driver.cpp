@@ -123,6 +123,23 @@ int main() {
             }
         }
     }
+    // the pseudo-peripheral search of RCM expands large levels on several threads:
+    // the order must not depend on the thread count
+    {
+        const int32_t n = 30000;
+        std::vector<int32_t> rp, ci;
+        make_graph(n, 8 * (int64_t)n, 4242, true, rp, ci);
+        blest::Csr g;
+        std::string err;
+        if (blest::clean_csr(n, rp.data(), ci.data(), 4, g, err) != 0) {
+            ++failures;
+        } else {
+            std::vector<int32_t> one, four;
+            blest::order_rcm(g, one, 1);
+            blest::order_rcm(g, four, 4);
+            if (!is_perm(one, n) || one != four) { std::printf("RCM differs across thread counts\n"); ++failures; }
+        }
+    }
     // a lower edge without its reverse, next to a symmetric pair: only the edge count shows it
     {
         blest::Csr g;

@@ -55,3 +55,26 @@ def test_multi_source_chunk_sizing(tmp_path):
     assert build.returncode == 0, build.stderr[-3000:]
     run = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert run.returncode == 0 and "failures=0" in run.stdout, run.stdout[-2000:]
+
+
+def test_host_preprocessing_under_tsan(tmp_path):
+    """The same driver built with ThreadSanitizer: the threaded parts (cleaning,
+    symmetry check, relabelling, JaccardWithWindows, the parallel levels of the
+    RCM pseudo-peripheral search) run without data races."""
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no g++")
+    exe = str(tmp_path / "sanitize_driver_tsan")
+    cmd = [gxx, "-std=c++17", "-O1", "-g", "-fsanitize=thread", "-I", CSRC, os.path.join(CSRC, "host_graph.cpp"),
+           DRIVER, "-o", exe, "-pthread"]
+    build = subprocess.run(cmd, capture_output=True, text=True)
+    if build.returncode != 0 and "sanitize" in build.stderr and "cannot find" in build.stderr:
+        pytest.skip("sanitizer runtime not installed")
+    assert build.returncode == 0, build.stderr[-3000:]
+    env = dict(os.environ, TSAN_OPTIONS="halt_on_error=1")
+    run = subprocess.run([exe], capture_output=True, text=True, env=env, timeout=600)
+    if run.returncode != 0 and "unexpected memory mapping" in run.stderr:
+        pytest.skip("ThreadSanitizer cannot run under this kernel's address layout")
+    assert run.returncode == 0, (run.stdout[-2000:], run.stderr[-4000:])
+    assert "ThreadSanitizer" not in run.stderr
+    assert "failures=0" in run.stdout
