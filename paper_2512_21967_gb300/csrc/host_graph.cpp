@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -288,6 +289,75 @@ struct LevelBfs {
 };
 }  // namespace
 
+// One level of a FIFO-order BFS: appends to queue[tail..), for i = fs .. fe-1 in
+// order, the neighbours of queue[i] that are not yet seen and not taken by an
+// earlier position, each group in the order arrange(u, first, last) leaves it,
+// and marks them seen.  Returns the new tail.  Large levels run on `threads`
+// threads with the same result: every such neighbour belongs to the smallest
+// position that reaches it (an atomic minimum in owner[], which must hold
+// INT32_MAX for unseen vertices), and each position writes its group at an
+// offset from a prefix sum of group sizes.
+template <class Arrange>
+static int64_t expand_level_fifo(const Csr& g, int32_t* queue, int64_t fs, int64_t fe, int64_t tail,
+                                 std::vector<uint8_t>& seen, std::vector<int32_t>& owner, int threads,
+                                 Arrange arrange) {
+    constexpr int64_t kParallelLevel = 65536;   // three thread launches per level must pay off
+    if (threads <= 1 || fe - fs < kParallelLevel) {
+        for (int64_t i = fs; i < fe; ++i) {
+            const int32_t u = queue[i];
+            const int64_t first = tail;
+            for (int32_t e = g.rp[u]; e < g.rp[u + 1]; ++e) {
+                const int32_t v = g.ci[e];
+                if (!seen[(size_t)v]) { seen[(size_t)v] = 1; queue[tail++] = v; }
+            }
+            arrange(u, queue + first, queue + tail);
+        }
+        return tail;
+    }
+    // owners: the smallest frontier position with an edge to each unseen neighbour
+    parallel_chunks(threads, fe - fs, 256, [&](int64_t lo, int64_t hi) {
+        for (int64_t i = fs + lo; i < fs + hi; ++i) {
+            const int32_t u = queue[i];
+            for (int32_t e = g.rp[u]; e < g.rp[u + 1]; ++e) {
+                const int32_t v = g.ci[e];
+                if (seen[(size_t)v]) continue;
+                int32_t cur = __atomic_load_n(&owner[(size_t)v], __ATOMIC_RELAXED);
+                while ((int32_t)i < cur && !__atomic_compare_exchange_n(&owner[(size_t)v], &cur, (int32_t)i, true,
+                                                                          __ATOMIC_RELAXED, __ATOMIC_RELAXED)) {
+                }
+            }
+        }
+    });
+    std::vector<int64_t> off((size_t)(fe - fs) + 1, 0);
+    parallel_chunks(threads, fe - fs, 256, [&](int64_t lo, int64_t hi) {
+        for (int64_t i = fs + lo; i < fs + hi; ++i) {
+            const int32_t u = queue[i];
+            int64_t c = 0;
+            for (int32_t e = g.rp[u]; e < g.rp[u + 1]; ++e) {
+                const int32_t v = g.ci[e];
+                c += !seen[(size_t)v] && owner[(size_t)v] == (int32_t)i;
+            }
+            off[(size_t)(i - fs) + 1] = c;
+        }
+    });
+    for (size_t k = 1; k < off.size(); ++k) off[k] += off[k - 1];
+    parallel_chunks(threads, fe - fs, 256, [&](int64_t lo, int64_t hi) {
+        for (int64_t i = fs + lo; i < fs + hi; ++i) {
+            const int32_t u = queue[i];
+            int32_t* first = queue + tail + off[(size_t)(i - fs)];
+            int32_t* w = first;
+            for (int32_t e = g.rp[u]; e < g.rp[u + 1]; ++e) {
+                const int32_t v = g.ci[e];
+                if (!seen[(size_t)v] && owner[(size_t)v] == (int32_t)i) *w++ = v;
+            }
+            arrange(u, first, w);
+        }
+    });
+    const int64_t new_tail = tail + off.back();
+    for (int64_t k = tail; k < new_tail; ++k) seen[(size_t)queue[k]] = 1;
+    return new_tail;
+}
+
 static int32_t pseudo_peripheral(const Csr& g, LevelBfs& bfs, int32_t start) {
     int32_t x = start;
     int64_t cnt = 0;
@@ -317,30 +387,30 @@ void order_rcm(const Csr& g, std::vector<int32_t>& new_id, int threads) {
     if (n == 0) return;
     LevelBfs bfs(n, threads);
     std::vector<uint8_t> seen((size_t)n, 0);
-    std::vector<int32_t> order;
-    order.reserve((size_t)n);
-    std::vector<int32_t> nb;
+    std::vector<int32_t> order((size_t)n), owner((size_t)n, INT32_MAX);
+    int64_t tail = 0;
+    // each vertex's unvisited neighbours join the queue by ascending (degree, id)
+    auto by_degree = [&](int32_t, int32_t* first, int32_t* last) {
+        std::sort(first, last, [&](int32_t a, int32_t b) {
+            int32_t da = g.rp[a + 1] - g.rp[a], db = g.rp[b + 1] - g.rp[b];
+            return da != db ? da < db : a < b;
+        });
+    };
     for (int32_t v0 = 0; v0 < n; ++v0) {
         if (seen[v0]) continue;
         if (g.rp[v0 + 1] == g.rp[v0]) {   // an isolated vertex is its own component and its own order
             seen[v0] = 1;
-            order.push_back(v0);
+            order[(size_t)tail++] = v0;
             continue;
         }
         int32_t r = pseudo_peripheral(g, bfs, v0);
-        size_t head = order.size();
         seen[r] = 1;
-        order.push_back(r);
-        while (head < order.size()) {
-            int32_t u = order[head++];
-            nb.clear();
-            for (int32_t e = g.rp[u]; e < g.rp[u + 1]; ++e)
-                if (!seen[g.ci[e]]) nb.push_back(g.ci[e]);
-            std::sort(nb.begin(), nb.end(), [&](int32_t a, int32_t b) {
-                int32_t da = g.rp[a + 1] - g.rp[a], db = g.rp[b + 1] - g.rp[b];
-                return da != db ? da < db : a < b;
-            });
-            for (int32_t v : nb) { seen[v] = 1; order.push_back(v); }
+        int64_t fs = tail;
+        order[(size_t)tail++] = r;
+        while (fs < tail) {   // one BFS level at a time, in the FIFO order of the sequential method
+            const int64_t fe = tail;
+            tail = expand_level_fifo(g, order.data(), fs, fe, tail, seen, owner, threads, by_degree);
+            fs = fe;
         }
     }
     for (int64_t pos = 0; pos < n; ++pos) new_id[order[pos]] = (int32_t)(n - 1 - pos);
@@ -352,7 +422,7 @@ void order_rcm(const Csr& g, std::vector<int32_t>& new_id, int threads) {
 // ties), neighbours scanned in ascending id.  Neighbours of the same hub land
 // in the same window of Algorithm 1.
 
-void order_hub_prepass(const Csr& g, std::vector<int32_t>& new_id) {
+void order_hub_prepass(const Csr& g, std::vector<int32_t>& new_id, int threads) {
     int32_t n = g.n;
     new_id.assign((size_t)n, 0);
     // roots by descending degree, ascending id within a degree (a counting sort)
@@ -364,19 +434,18 @@ void order_hub_prepass(const Csr& g, std::vector<int32_t>& new_id) {
     std::vector<int32_t> cand((size_t)n);
     for (int32_t v = 0; v < n; ++v) cand[(size_t)start[(size_t)(dmax - (g.rp[v + 1] - g.rp[v]))]++] = v;
     std::vector<uint8_t> seen((size_t)n, 0);
-    std::vector<int32_t> order;
-    order.reserve((size_t)n);
+    std::vector<int32_t> order((size_t)n), owner((size_t)n, INT32_MAX);
+    int64_t tail = 0;
+    auto as_listed = [](int32_t, int32_t*, int32_t*) {};   // neighbours in ascending id, as stored
     for (int32_t r : cand) {
         if (seen[r]) continue;
-        size_t head = order.size();
         seen[r] = 1;
-        order.push_back(r);
-        while (head < order.size()) {
-            int32_t u = order[head++];
-            for (int32_t e = g.rp[u]; e < g.rp[u + 1]; ++e) {
-                int32_t v = g.ci[e];
-                if (!seen[v]) { seen[v] = 1; order.push_back(v); }
-            }
+        int64_t fs = tail;
+        order[(size_t)tail++] = r;
+        while (fs < tail) {
+            const int64_t fe = tail;
+            tail = expand_level_fifo(g, order.data(), fs, fe, tail, seen, owner, threads, as_listed);
+            fs = fe;
         }
     }
     for (int32_t pos = 0; pos < n; ++pos) new_id[order[pos]] = pos;
@@ -641,7 +710,7 @@ void order_compress(const Csr& g, int sigma, int32_t window, int threads, std::v
                     int prepass) {
     std::vector<int32_t> pre;
     if (prepass == 1) order_gorder(g, 5, 64, pre);
-    else order_hub_prepass(g, pre);
+    else order_hub_prepass(g, pre, threads);
     // Algorithm 1 over the pre-pass order, reading g's rows through the
     // permutation: neighbours only need to compare equal, and ties go to the
     // smaller window position, so no relabelled copy of g is needed

@@ -27,10 +27,11 @@ int clean_csr(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int thr
 bool is_symmetric(const Csr& g, int threads, int64_t* bad_u, int64_t* bad_v);
 
 // Orderings; all return new_id[old].
-// threads > 1: the BFS runs of the pseudo-peripheral search expand large levels in
-// parallel (the order is the same for every thread count).
+// threads > 1: the BFS runs of the pseudo-peripheral search and large levels of
+// the Cuthill-McKee pass are expanded in parallel (the same order).
 void order_rcm(const Csr& g, std::vector<int32_t>& new_id, int threads = 1);
-void order_hub_prepass(const Csr& g, std::vector<int32_t>& new_id);
+// threads > 1: large BFS levels are expanded in parallel (the same order).
+void order_hub_prepass(const Csr& g, std::vector<int32_t>& new_id, int threads = 1);
 // row_at (optional, n entries): window position p holds row row_at[p] of g
 // (the identity when NULL); new_id is indexed by position.
 void order_jaccard_windows(const Csr& g, int sigma, int32_t window, int threads,

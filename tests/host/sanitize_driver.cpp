@@ -123,10 +123,11 @@ int main() {
             }
         }
     }
-    // the pseudo-peripheral search of RCM expands large levels on several threads:
-    // the order must not depend on the thread count
+    // RCM (its pseudo-peripheral search and its Cuthill-McKee levels) and the hub
+    // pre-pass expand large levels on several threads: the order must not depend
+    // on the thread count.  Levels of this graph exceed the parallel thresholds.
     {
-        const int32_t n = 30000;
+        const int32_t n = 200000;
         std::vector<int32_t> rp, ci;
         make_graph(n, 8 * (int64_t)n, 4242, true, rp, ci);
         blest::Csr g;
@@ -138,6 +139,9 @@ int main() {
             blest::order_rcm(g, one, 1);
             blest::order_rcm(g, four, 4);
             if (!is_perm(one, n) || one != four) { std::printf("RCM differs across thread counts\n"); ++failures; }
+            blest::order_hub_prepass(g, one, 1);
+            blest::order_hub_prepass(g, four, 4);
+            if (!is_perm(one, n) || one != four) { std::printf("pre-pass differs across thread counts\n"); ++failures; }
         }
     }
     // a lower edge without its reverse, next to a symmetric pair: only the edge count shows it
