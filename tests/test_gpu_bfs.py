@@ -575,3 +575,52 @@ def test_checkpoint_batch_handle(gpu, tmp_path):
             off += g.n
     finally:
         blest.blest_destroy(h2)
+
+
+# ------------------------------------------------------------ full sizes
+# The benchmark's own workloads at their full sizes, built and tuned as bench.py
+# builds and tunes them.  Sampled sources are compared element by element with
+# the oracle's single-source BFS, which takes a second or two at these sizes.
+
+def _bench_like_handle(g, order, tune_srcs):
+    h = blest.blest_graph_create_ex(g.n, g.row_ptr, g.col_idx, order, window=4096)
+    for key, val in ((blest.BLEST_OPT_UNROLL, 2), (blest.BLEST_OPT_MIN_BLOCKS, 2),
+                     (blest.BLEST_OPT_VISITED_FILTER, 3), (blest.BLEST_OPT_STAGE_DEPTH, 2)):
+        blest.blest_set_option(h, key, val)
+    blest.blest_autotune(h, tune_srcs)
+    return h
+
+
+@pytest.mark.parametrize("workload", ["rmat23", "grid4096"])
+def test_full_size_single_source_sampled(gpu, workload):
+    """R-MAT scale 23 (compression order) and the 4096 x 4096 grid (RCM), the
+    autotuned variant the benchmark times, three sampled sources each."""
+    if workload == "rmat23":
+        g, srcs = synth.rmat_workload(23, 64, seed_graph=2, seed_src=1002)
+        order = blest.BLEST_ORDER_COMPRESS
+    else:
+        g, srcs = synth.grid_workload(4096, 64, seed_graph=3, seed_src=1003)
+        order = blest.BLEST_ORDER_BANDWIDTH
+    h = _bench_like_handle(g, order, srcs[:4])
+    try:
+        check_levels(g, h, [srcs[0], srcs[37], srcs[-1]])
+    finally:
+        blest.blest_destroy(h)
+
+
+def test_full_size_multi_source_sampled(torch_cuda):
+    """R-MAT scale 22, k = 64 sources in one launch into device memory, as the
+    benchmark runs it; three sampled rows against the oracle."""
+    torch = torch_cuda
+    g, srcs = synth.rmat_workload(22, 64, seed_graph=4, seed_src=1004)
+    h = blest.blest_graph_create_ex(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_COMPRESS, window=4096)
+    try:
+        s = torch.cuda.Stream()
+        out = torch.empty((64, g.n), dtype=torch.int32, device="cuda")
+        blest.blest_msbfs_device(h, srcs[:64], out, stream=s)
+        blest.blest_sync(h)
+        for i in (0, 29, 63):
+            exp = oracle.bfs_levels(g.n, g.row_ptr, g.col_idx, int(srcs[i]))
+            assert np.array_equal(out[i].cpu().numpy(), exp), f"row {i} (source {srcs[i]}) differs"
+    finally:
+        blest.blest_destroy(h)
