@@ -550,11 +550,15 @@ struct JaccardWorker {
     std::vector<uint8_t> inq;
     std::vector<int32_t> touched;
     // Reverse index of the window: neighbour x -> the window rows that hold x.
-    // An open-addressing table keyed by x gives each x its list in revj
+    // An open-addressing table keyed by x (built once per window) gives each x its list in revj
     // (hoff, hlen); rows already placed are dropped from a list as it is walked.
     // Every neighbour of a window row has a slot, so the slot also records
     // (ustamp) the cluster whose U holds x: no per-vertex array per thread.
     std::vector<int32_t> hkey, hoff, hlen, ustamp, revj;
+    // eslot[eoff[jl] + k]: the slot of the k-th neighbour of window row jl, found
+    // once while the table is built
+    std::vector<int32_t> eslot;
+    std::vector<int64_t> eoff;
     int hshift = 60;
     int32_t stamp = 0;
 
@@ -565,15 +569,6 @@ struct JaccardWorker {
 
     // Fibonacci hashing: the high bits of x times 2^64 / golden ratio
     size_t slot0(int32_t x) const { return (size_t)(((uint64_t)(uint32_t)x * 0x9E3779B97F4A7C15ull) >> hshift); }
-
-    // slot of x, or -1 if no row of the window holds x
-    int64_t find(int32_t x) const {
-        const size_t mask = hkey.size() - 1;
-        for (size_t h = slot0(x);; h = (h + 1) & mask) {
-            if (hkey[h] == x) return (int64_t)h;
-            if (hkey[h] < 0) return -1;
-        }
-    }
 
     void build_index(int32_t s_k, int32_t L) {
         int64_t nnz = 0;
@@ -587,7 +582,11 @@ struct JaccardWorker {
         hlen.assign(cap, 0);
         ustamp.assign(cap, 0);
         hoff.resize(cap);
+        eslot.resize((size_t)nnz);
+        eoff.resize((size_t)L + 1);
+        int64_t k = 0;
         for (int32_t jl = 0; jl < L; ++jl) {
+            eoff[(size_t)jl] = k;
             const int32_t r = row(s_k + jl);
             for (int32_t e = g.rp[r]; e < g.rp[r + 1]; ++e) {
                 const int32_t x = g.ci[e];
@@ -595,24 +594,27 @@ struct JaccardWorker {
                 while (hkey[h] >= 0 && hkey[h] != x) h = (h + 1) & mask;
                 hkey[h] = x;
                 ++hlen[h];
+                eslot[(size_t)k++] = (int32_t)h;
             }
         }
+        eoff[(size_t)L] = k;
         int32_t run = 0;
         for (size_t h = 0; h < cap; ++h) { hoff[h] = run; run += hlen[h]; }
         revj.resize((size_t)nnz);
         std::vector<int32_t>& fill = c;   // scratch: per-slot fill position (c is reset by window())
         fill.assign(cap, 0);
-        for (int32_t jl = 0; jl < L; ++jl) {
-            const int32_t r = row(s_k + jl);
-            for (int32_t e = g.rp[r]; e < g.rp[r + 1]; ++e) {
-                const size_t h = (size_t)find(g.ci[e]);
+        for (int32_t jl = 0; jl < L; ++jl)
+            for (int64_t i = eoff[(size_t)jl]; i < eoff[(size_t)jl + 1]; ++i) {
+                const size_t h = (size_t)eslot[(size_t)i];
                 revj[(size_t)(hoff[h] + fill[h]++)] = jl;   // rows in ascending order per x
             }
-        }
     }
+
+    int32_t s_k_ = 0;   // first position of the current window
 
     void window(int32_t s_k, int32_t e_k, int32_t* new_id) {
         int32_t L = e_k - s_k;
+        s_k_ = s_k;
         build_index(s_k, L);
         c.assign((size_t)L, 0);
         cstamp.assign((size_t)L, 0);
@@ -661,9 +663,9 @@ struct JaccardWorker {
     // The pick above is the best ratio with ties to the smallest row, so it does
     // not depend on the order in which rows are touched or listed.
     void add_to_u(int32_t pos, int64_t& usize) {
-        const int32_t j = row(pos);
-        for (int32_t e = g.rp[j]; e < g.rp[j + 1]; ++e) {
-            const size_t h = (size_t)find(g.ci[e]);   // j is a window row, so x has a slot
+        const int32_t jl0 = pos - s_k_;
+        for (int64_t i = eoff[(size_t)jl0]; i < eoff[(size_t)jl0 + 1]; ++i) {
+            const size_t h = (size_t)eslot[(size_t)i];
             if (ustamp[h] == stamp) continue;
             ustamp[h] = stamp;
             ++usize;
