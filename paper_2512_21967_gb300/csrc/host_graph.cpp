@@ -542,6 +542,7 @@ void order_gorder(const Csr& g, int w, int32_t hub_cap, std::vector<int32_t>& ne
 // remaining id is chosen, as the argmax tie rule says.
 
 namespace {
+template <class Pos>   // type of a window position in the reverse lists (uint16_t when windows fit)
 struct JaccardWorker {
     const Csr& g;
     const int32_t* row_at;   // window position -> row of g (NULL: the identity)
@@ -554,7 +555,8 @@ struct JaccardWorker {
     // (hoff, hlen); rows already placed are dropped from a list as it is walked.
     // Every neighbour of a window row has a slot, so the slot also records
     // (ustamp) the cluster whose U holds x: no per-vertex array per thread.
-    std::vector<int32_t> hkey, hoff, hlen, ustamp, revj;
+    std::vector<int32_t> hkey, hoff, hlen, ustamp;
+    std::vector<Pos> revj;
     // eslot[eoff[jl] + k]: the slot of the k-th neighbour of window row jl, found
     // once while the table is built
     std::vector<int32_t> eslot;
@@ -606,7 +608,7 @@ struct JaccardWorker {
         for (int32_t jl = 0; jl < L; ++jl)
             for (int64_t i = eoff[(size_t)jl]; i < eoff[(size_t)jl + 1]; ++i) {
                 const size_t h = (size_t)eslot[(size_t)i];
-                revj[(size_t)(hoff[h] + fill[h]++)] = jl;   // rows in ascending order per x
+                revj[(size_t)(hoff[h] + fill[h]++)] = (Pos)jl;   // rows in ascending order per x
             }
     }
 
@@ -671,9 +673,9 @@ struct JaccardWorker {
             ++usize;
             int32_t w = hoff[h];
             for (int32_t i = hoff[h], end = hoff[h] + hlen[h]; i < end; ++i) {
-                int32_t jl = revj[i];
+                const int32_t jl = revj[i];
                 if (!inq[jl]) continue;   // placed rows leave the list
-                revj[w++] = jl;
+                revj[w++] = (Pos)jl;
                 if (cstamp[jl] != stamp) { cstamp[jl] = stamp; c[jl] = 0; touched.push_back(jl); }
                 ++c[jl];
             }
@@ -692,14 +694,22 @@ void order_jaccard_windows(const Csr& g, int sigma, int32_t window, int threads,
     int nt = (int)std::min<int64_t>(threads, nwin);
     if (nt < 1) nt = 1;
     std::atomic<int64_t> next(0);
-    auto work = [&]() {
-        JaccardWorker wk(g, row_at, sigma);
+    auto run = [&](auto& wk) {
         for (;;) {
             int64_t k = next.fetch_add(1);
             if (k >= nwin) break;
             int32_t s_k = (int32_t)(k * window);
             int32_t e_k = (int32_t)std::min<int64_t>((int64_t)s_k + window, n);
             wk.window(s_k, e_k, new_id.data());
+        }
+    };
+    auto work = [&]() {
+        if (window <= 65536) {   // positions fit 16 bits: half the bytes in every list walk
+            JaccardWorker<uint16_t> wk(g, row_at, sigma);
+            run(wk);
+        } else {
+            JaccardWorker<int32_t> wk(g, row_at, sigma);
+            run(wk);
         }
     };
     std::vector<std::thread> pool;

@@ -48,7 +48,8 @@ def test_rcm_matches_oracle_rmat_with_isolated():
     assert np.array_equal(got, oo.rcm(g.n, g.row_ptr, g.col_idx))
 
 
-@pytest.mark.parametrize("scale,w", [(8, 16), (9, 64), (10, 1024)])
+# windows up to 65536 store window positions in 16 bits, wider ones in 32 (the last case)
+@pytest.mark.parametrize("scale,w", [(8, 16), (9, 64), (10, 1024), (9, 131072)])
 def test_compress_order_matches_oracle(scale, w):
     g = synth.rmat_graph(scale, 16, seed=scale)
     got = blest.blest_compute_order(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_COMPRESS, window=w, threads=3)
