@@ -132,6 +132,27 @@ bool is_symmetric(const Csr& g, int threads, int64_t* bad_u, int64_t* bad_v) {
     return true;
 }
 
+// Sorts non-negative ids below 2^30: an LSD radix sort in three 10-bit passes
+// (counts stay in L1) for long rows, std::sort for short ones.
+static void sort_ids(int32_t* a, int64_t len, std::vector<int32_t>& tmp) {
+    if (len <= 1024) {
+        std::sort(a, a + len);
+        return;
+    }
+    tmp.resize((size_t)len);
+    int32_t* src = a;
+    int32_t* dst = tmp.data();
+    for (int shift = 0; shift < 30; shift += 10) {
+        int64_t cnt[1025] = {0};
+        for (int64_t i = 0; i < len; ++i) ++cnt[((uint32_t)src[i] >> shift & 1023u) + 1];
+        for (int d = 0; d < 1024; ++d) cnt[d + 1] += cnt[d];
+        for (int64_t i = 0; i < len; ++i) dst[cnt[(uint32_t)src[i] >> shift & 1023u]++] = src[i];
+        std::swap(src, dst);
+    }
+    // after three passes (an odd count) the sorted ids are in tmp, where src points
+    std::memcpy(a, src, (size_t)len * sizeof(int32_t));
+}
+
 void relabel_csr(const Csr& g, const std::vector<int32_t>& new_id, int threads, Csr& out) {
     int32_t n = g.n;
     std::vector<int32_t> old_of((size_t)n);
@@ -144,12 +165,13 @@ void relabel_csr(const Csr& g, const std::vector<int32_t>& new_id, int threads, 
     }
     out.ci.resize((size_t)out.rp[n]);
     parallel_chunks(threads, n, 4096, [&](int64_t lo, int64_t hi) {
+        std::vector<int32_t> tmp;
         for (int64_t w = lo; w < hi; ++w) {
             int32_t v = old_of[w];
             int32_t* dst = out.ci.data() + out.rp[w];
             int64_t len = g.rp[v + 1] - g.rp[v];
             for (int64_t i = 0; i < len; ++i) dst[i] = new_id[g.ci[g.rp[v] + i]];
-            std::sort(dst, dst + len);
+            sort_ids(dst, len, tmp);
         }
     });
 }
