@@ -3,6 +3,7 @@
 // with AddressSanitizer and UndefinedBehaviorSanitizer can check every path.
 // Exit code 0 when every ordering is a permutation and every relabelled graph
 // keeps its edge count; sanitizer reports abort the run by themselves.
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -142,6 +143,17 @@ int main() {
             blest::order_hub_prepass(g, one, 1);
             blest::order_hub_prepass(g, four, 4);
             if (!is_perm(one, n) || one != four) { std::printf("pre-pass differs across thread counts\n"); ++failures; }
+            // relabelling sorts the long hub rows by radix: rows sorted, duplicate-free, edges kept
+            blest::Csr r;
+            blest::relabel_csr(g, four, 4, r);
+            int64_t longest = 0;
+            bool sorted = r.nnz() == g.nnz();
+            for (int32_t u = 0; u < n && sorted; ++u) {
+                longest = std::max<int64_t>(longest, r.rp[(size_t)u + 1] - r.rp[(size_t)u]);
+                for (int64_t e = r.rp[(size_t)u] + 1; e < r.rp[(size_t)u + 1]; ++e)
+                    if (r.ci[(size_t)e - 1] >= r.ci[(size_t)e]) sorted = false;
+            }
+            if (!sorted || longest <= 1024) { std::printf("relabelled rows: sorted %d longest %lld\n", sorted, (long long)longest); ++failures; }
         }
     }
     // a lower edge without its reverse, next to a symmetric pair: only the edge count shows it
