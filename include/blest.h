@@ -108,7 +108,10 @@ typedef enum {
 /* Creation parameters; pass NULL to blest_graph_create_ex for the defaults. */
 typedef struct {
     int32_t window;          /* JaccardWithWindows window w, a multiple of 8 (default 65536, Section 5) */
-    int32_t threads;         /* host threads for reordering and cleaning; 0 = all cores */
+    int32_t threads;         /* host threads for cleaning, the symmetry check, every ordering
+                                (windows of JaccardWithWindows, large BFS levels of the pre-pass
+                                and of RCM) and relabelling; 0 = all cores.  The result does
+                                not depend on it. */
     int32_t skip_symmetry_check; /* 1 = trust the caller that the input is symmetric */
     int32_t prepass;         /* BLEST_ORDER_COMPRESS pre-pass before Algorithm 1: 0 = BFS from the
                                 highest-degree vertices (default), 1 = Gorder (window 5, common
