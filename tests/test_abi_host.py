@@ -157,3 +157,15 @@ def test_gorder_prepass_matches_oracle(scale, seed):
                                     prepass="gorder")
     exp = oo.compress_order(g.n, g.row_ptr, g.col_idx, 8, 64, prepass="gorder")
     assert np.array_equal(got, exp)
+
+
+@pytest.mark.parametrize("order", ["compress", "bandwidth"])
+def test_orders_do_not_depend_on_host_threads(order):
+    """Scale 19 has BFS levels above both parallel thresholds (1024 vertices in the
+    pseudo-peripheral search, 65536 in the order-preserving expansion)."""
+    g = synth.rmat_graph(19, 16, seed=12)
+    o = blest.BLEST_ORDER_COMPRESS if order == "compress" else blest.BLEST_ORDER_BANDWIDTH
+    one = blest.blest_compute_order(g.n, g.row_ptr, g.col_idx, o, window=4096, threads=1)
+    many = blest.blest_compute_order(g.n, g.row_ptr, g.col_idx, o, window=4096, threads=6)
+    assert np.array_equal(one, many)
+    assert np.array_equal(np.sort(one), np.arange(g.n))
