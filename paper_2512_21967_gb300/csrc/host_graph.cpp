@@ -573,10 +573,11 @@ struct JaccardWorker {
     std::vector<uint8_t> inq;
     std::vector<int32_t> touched;
     // Reverse index of the window: neighbour x -> the window rows that hold x.
-    // An open-addressing table keyed by x (built once per window) gives each x its list in revj
-    // (hoff, hlen); rows already placed are dropped from a list as it is walked.
-    // Every neighbour of a window row has a slot, so the slot also records
-    // (ustamp) the cluster whose U holds x: no per-vertex array per thread.
+    // An open-addressing table keyed by x, built once per window, gives each x
+    // its list in revj (hoff, hlen); rows already placed are dropped from a list
+    // as it is walked.  Every neighbour of a window row has a slot, so the slot
+    // also records (ustamp) the cluster whose U holds x: no per-vertex array per
+    // thread.
     std::vector<int32_t> hkey, hoff, hlen, ustamp;
     std::vector<Pos> revj;
     // eslot[eoff[jl] + k]: the slot of the k-th neighbour of window row jl, found
