@@ -156,6 +156,31 @@ int main() {
             if (!sorted || longest <= 1024) { std::printf("relabelled rows: sorted %d longest %lld\n", sorted, (long long)longest); ++failures; }
         }
     }
+    // a long row whose relabelled ids fill all three 10-bit radix digits (ids up to 2^23)
+    {
+        const int32_t n = 1 << 23, hub = 12345, deg = 5000;
+        blest::Csr g;
+        g.n = n;
+        std::vector<int32_t> nb;
+        for (int32_t i = 0; i < deg; ++i) nb.push_back((int32_t)(mix(777 + (uint64_t)i) % (uint64_t)n));
+        std::sort(nb.begin(), nb.end());
+        nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+        nb.erase(std::remove(nb.begin(), nb.end(), hub), nb.end());
+        g.rp.assign((size_t)n + 1, 0);
+        for (int32_t v = 0; v < n; ++v) g.rp[(size_t)v + 1] = g.rp[(size_t)v] + (v == hub ? (int32_t)nb.size() : 0);
+        g.ci = nb;
+        std::vector<int32_t> perm((size_t)n);
+        for (int32_t v = 0; v < n; ++v) perm[(size_t)v] = v;
+        for (int32_t v = n - 1; v > 0; --v) std::swap(perm[(size_t)v], perm[(size_t)(mix(31 + (uint64_t)v) % (uint64_t)(v + 1))]);
+        blest::Csr r;
+        blest::relabel_csr(g, perm, 2, r);
+        std::vector<int32_t> expect;
+        for (int32_t x : nb) expect.push_back(perm[(size_t)x]);
+        std::sort(expect.begin(), expect.end());
+        const int32_t w = perm[(size_t)hub];
+        std::vector<int32_t> got(r.ci.begin() + r.rp[(size_t)w], r.ci.begin() + r.rp[(size_t)w + 1]);
+        if (got != expect || expect.back() < (1 << 20)) { std::printf("radix row differs\n"); ++failures; }
+    }
     // a lower edge without its reverse, next to a symmetric pair: only the edge count shows it
     {
         blest::Csr g;
