@@ -43,6 +43,27 @@ static void parallel_chunks(int threads, int64_t n, int64_t chunk, F fn) {
 
 // ------------------------------------------------------------------ cleaning
 
+// Sorts ids in [0, bound): an LSD radix sort in three 10-bit passes (counts stay
+// in L1) for long rows when bound <= 2^30, std::sort otherwise.
+static void sort_ids(int32_t* a, int64_t len, int64_t bound, std::vector<int32_t>& tmp) {
+    if (len <= 1024 || bound > ((int64_t)1 << 30)) {
+        std::sort(a, a + len);
+        return;
+    }
+    tmp.resize((size_t)len);
+    int32_t* src = a;
+    int32_t* dst = tmp.data();
+    for (int shift = 0; shift < 30; shift += 10) {
+        int64_t cnt[1025] = {0};
+        for (int64_t i = 0; i < len; ++i) ++cnt[((uint32_t)src[i] >> shift & 1023u) + 1];
+        for (int d = 0; d < 1024; ++d) cnt[d + 1] += cnt[d];
+        for (int64_t i = 0; i < len; ++i) dst[cnt[(uint32_t)src[i] >> shift & 1023u]++] = src[i];
+        std::swap(src, dst);
+    }
+    // after three passes (an odd count) the sorted ids are in tmp, where src points
+    std::memcpy(a, src, (size_t)len * sizeof(int32_t));
+}
+
 int clean_csr(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int threads, Csr& out,
               std::string& err) {
     if (n < 0) { err = "n must be >= 0"; return BLEST_ERR_INVALID_ARG; }
@@ -64,11 +85,12 @@ int clean_csr(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int thr
     std::unique_ptr<int32_t[]> tmp(new int32_t[(size_t)std::max<int64_t>(m, 1)]);   // every entry is written before use
     std::vector<int32_t> newdeg((size_t)n + 1, 0);
     parallel_chunks(threads, n, 4096, [&](int64_t lo, int64_t hi) {
+        std::vector<int32_t> scratch;
         for (int64_t u = lo; u < hi; ++u) {
             int32_t* a = tmp.get() + row_ptr[u];
             int64_t len = row_ptr[u + 1] - row_ptr[u];
             if (len > 0) std::memcpy(a, col_idx + row_ptr[u], (size_t)len * sizeof(int32_t));
-            if (!std::is_sorted(a, a + len)) std::sort(a, a + len);
+            if (!std::is_sorted(a, a + len)) sort_ids(a, len, n, scratch);
             int64_t w = 0;
             for (int64_t i = 0; i < len; ++i)
                 if (a[i] != (int32_t)u && (w == 0 || a[w - 1] != a[i])) a[w++] = a[i];
@@ -132,27 +154,6 @@ bool is_symmetric(const Csr& g, int threads, int64_t* bad_u, int64_t* bad_v) {
     return true;
 }
 
-// Sorts non-negative ids below 2^30: an LSD radix sort in three 10-bit passes
-// (counts stay in L1) for long rows, std::sort for short ones.
-static void sort_ids(int32_t* a, int64_t len, std::vector<int32_t>& tmp) {
-    if (len <= 1024) {
-        std::sort(a, a + len);
-        return;
-    }
-    tmp.resize((size_t)len);
-    int32_t* src = a;
-    int32_t* dst = tmp.data();
-    for (int shift = 0; shift < 30; shift += 10) {
-        int64_t cnt[1025] = {0};
-        for (int64_t i = 0; i < len; ++i) ++cnt[((uint32_t)src[i] >> shift & 1023u) + 1];
-        for (int d = 0; d < 1024; ++d) cnt[d + 1] += cnt[d];
-        for (int64_t i = 0; i < len; ++i) dst[cnt[(uint32_t)src[i] >> shift & 1023u]++] = src[i];
-        std::swap(src, dst);
-    }
-    // after three passes (an odd count) the sorted ids are in tmp, where src points
-    std::memcpy(a, src, (size_t)len * sizeof(int32_t));
-}
-
 void relabel_csr(const Csr& g, const std::vector<int32_t>& new_id, int threads, Csr& out) {
     int32_t n = g.n;
     std::vector<int32_t> old_of((size_t)n);
@@ -171,7 +172,7 @@ void relabel_csr(const Csr& g, const std::vector<int32_t>& new_id, int threads, 
             int32_t* dst = out.ci.data() + out.rp[w];
             int64_t len = g.rp[v + 1] - g.rp[v];
             for (int64_t i = 0; i < len; ++i) dst[i] = new_id[g.ci[g.rp[v] + i]];
-            sort_ids(dst, len, tmp);
+            sort_ids(dst, len, n, tmp);
         }
     });
 }
