@@ -498,12 +498,16 @@ void order_gorder(const Csr& g, int w, int32_t hub_cap, std::vector<int32_t>& ne
         if (b < 0) return true;
         return key[a] != key[b] ? key[a] > key[b] : a < b;
     };
+    // point update after v's key or placement changed; a node whose winner stays
+    // the same and is not v leaves every ancestor's comparison as it was
     auto fix = [&](int32_t v) {
         size_t i = (size_t)size + (size_t)v;
         tree[i] = placed[v] ? -1 : v;
         for (i >>= 1; i >= 1; i >>= 1) {
             const int32_t l = tree[2 * i], r = tree[2 * i + 1];
-            tree[i] = better(l, r) ? l : (r >= 0 ? r : l);
+            const int32_t win = better(l, r) ? l : (r >= 0 ? r : l);
+            if (win == tree[i] && win != v) break;
+            tree[i] = win;
         }
     };
     for (int32_t v = 0; v < n; ++v) { key[v] = g.rp[v + 1] - g.rp[v]; tree[(size_t)size + v] = v; }
@@ -522,14 +526,19 @@ void order_gorder(const Csr& g, int w, int32_t hub_cap, std::vector<int32_t>& ne
     std::vector<int32_t> order;
     order.reserve((size_t)n);
     std::vector<int32_t> touched;
+    std::vector<int32_t> seen_at((size_t)n, -1);   // the step that last listed a vertex in touched
+    int32_t step = 0;
+    auto touch = [&](int32_t u) {
+        if (seen_at[(size_t)u] != step) { seen_at[(size_t)u] = step; touched.push_back(u); }
+    };
     auto contribute = [&](int32_t v, int64_t sign) {
         for (int32_t e = g.rp[v]; e < g.rp[v + 1]; ++e) {
             const int32_t x = g.ci[e];
-            if (!placed[x]) { key[x] += 2 * sign; touched.push_back(x); }
+            if (!placed[x]) { key[x] += 2 * sign; touch(x); }
             if (g.rp[x + 1] - g.rp[x] > hub_cap) continue;
             for (int32_t f = g.rp[x]; f < g.rp[x + 1]; ++f) {
                 const int32_t u = g.ci[f];
-                if (u != v && !placed[u]) { key[u] += sign; touched.push_back(u); }
+                if (u != v && !placed[u]) { key[u] += sign; touch(u); }
             }
         }
     };
@@ -541,10 +550,9 @@ void order_gorder(const Csr& g, int w, int32_t hub_cap, std::vector<int32_t>& ne
     place(first);
     while ((int32_t)order.size() < n) {
         touched.clear();
+        ++step;
         contribute(order.back(), +1);
         if ((int)order.size() > w) contribute(order[order.size() - 1 - (size_t)w], -1);
-        std::sort(touched.begin(), touched.end());
-        touched.erase(std::unique(touched.begin(), touched.end()), touched.end());
         for (int32_t u : touched) fix(u);
         place(tree[1]);
     }
