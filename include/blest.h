@@ -133,7 +133,8 @@ typedef struct {
     int64_t state_bytes;         /* device bytes of queues, bitmaps and levels */
     int32_t order;               /* blest_order actually used */
     int32_t update;              /* blest_update the AUTO rule picks for this graph */
-    double  order_seconds;       /* host reordering time */
+    double  order_seconds;       /* host reordering time (batch handles: the per-graph cleaning,
+                                    checks, reordering and relabelling, graphs run concurrently) */
     double  build_seconds;       /* everything else in create (cleaning, upload, device BVSS build) */
 } blest_stats;
 

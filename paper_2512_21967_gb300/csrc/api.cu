@@ -5,11 +5,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
 #include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/blest.h"
@@ -680,22 +682,50 @@ blest_status blest_batch_create(int32_t num_graphs, const int32_t* n_each, const
     uni.n = N;
     uni.rp.assign((size_t)N + 1, 0);
     std::vector<int32_t> new_id((size_t)N);
-    double t_order = 0, t_clean = 0;
     std::vector<Csr> parts((size_t)num_graphs);
     std::vector<std::vector<int32_t>> ids((size_t)num_graphs);
+    // Graphs are cleaned, checked, reordered and relabelled concurrently, largest
+    // first, each with its share of the host threads; an order does not depend on
+    // the thread count, so neither does the handle.  The first failing graph (by
+    // index) is reported.
+    std::vector<blest_status> status((size_t)num_graphs, BLEST_OK);
+    std::vector<std::string> errors((size_t)num_graphs);
+    std::vector<int32_t> by_size((size_t)num_graphs);
+    for (int32_t g = 0; g < num_graphs; ++g) by_size[(size_t)g] = g;
+    auto entries = [&](int32_t g) -> int64_t { return n_each[g] > 0 && row_ptrs[g] ? row_ptrs[g][n_each[g]] : 0; };
+    std::stable_sort(by_size.begin(), by_size.end(), [&](int32_t a, int32_t b) { return entries(a) > entries(b); });
+    const int workers = std::max(1, std::min(threads, num_graphs));
+    const int inner = std::max(1, threads / workers);
+    std::atomic<int32_t> next(0);
+    const double t0 = now_s();
+    auto work = [&]() {
+        for (;;) {
+            const int32_t k = next.fetch_add(1);
+            if (k >= num_graphs) break;
+            const int32_t g = by_size[(size_t)k];
+            int32_t used = 0;
+            double to = 0, tc = 0;
+            Csr clean;
+            blest_status s = prepare_graph(n_each[g], row_ptrs[g], col_idxs[g], (blest_order)orders[g], params, inner,
+                                           clean, ids[(size_t)g], &used, &to, &tc);
+            if (s) {
+                status[(size_t)g] = s;
+                errors[(size_t)g] = g_last_error;   // this worker's own message
+                continue;
+            }
+            if (!ids[(size_t)g].empty()) blest::relabel_csr(clean, ids[(size_t)g], inner, parts[(size_t)g]);
+            else parts[(size_t)g] = std::move(clean);
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < workers; ++t) pool.emplace_back(work);
+    work();
+    for (auto& th : pool) th.join();
+    const double t_order = now_s() - t0, t_clean = 0;
     int64_t total = 0;
     for (int32_t g = 0; g < num_graphs; ++g) {
-        int32_t used = 0;
-        double to = 0, tc = 0;
-        Csr clean;
-        blest_status s = prepare_graph(n_each[g], row_ptrs[g], col_idxs[g], (blest_order)orders[g], params, threads, clean,
-                                       ids[g], &used, &to, &tc);
-        if (s) return fail(s, "graph " + std::to_string(g) + ": " + g_last_error);
-        t_order += to;
-        t_clean += tc;
-        if (!ids[g].empty()) blest::relabel_csr(clean, ids[g], threads, parts[g]);
-        else parts[g] = std::move(clean);
-        total += parts[g].nnz();
+        if (status[(size_t)g]) return fail(status[(size_t)g], "graph " + std::to_string(g) + ": " + errors[(size_t)g]);
+        total += parts[(size_t)g].nnz();
         if (total >= ((int64_t)1 << 31)) return fail(BLEST_ERR_TOO_LARGE, "batch has 2^31 or more entries");
     }
     uni.ci.resize((size_t)total);

@@ -169,3 +169,36 @@ def test_orders_do_not_depend_on_host_threads(order):
     many = blest.blest_compute_order(g.n, g.row_ptr, g.col_idx, o, window=4096, threads=6)
     assert np.array_equal(one, many)
     assert np.array_equal(np.sort(one), np.arange(g.n))
+
+
+@pytest.mark.parametrize("threads", [1, 4])
+def test_batch_create_reports_the_first_bad_graph(threads):
+    """Batch graphs are prepared concurrently; the lowest-numbered invalid graph is
+    the one reported, whatever the thread count (this fails before any GPU call)."""
+    graphs = [synth.rmat_graph(8, 8, seed=40 + i) for i in range(12)]
+    items = [(g.n, g.row_ptr, g.col_idx) for g in graphs]
+    for b in (9, 5):   # an out-of-range column in graphs 9 and 5
+        ci = graphs[b].col_idx.copy()
+        ci[0] = graphs[b].n + 3
+        items[b] = (graphs[b].n, graphs[b].row_ptr, ci)
+    with pytest.raises(blest.BlestError) as e:
+        blest.blest_batch_create(items, [blest.BLEST_ORDER_COMPRESS] * 6 + [blest.BLEST_ORDER_BANDWIDTH] * 6,
+                                 threads=threads)
+    assert e.value.name == "BLEST_ERR_INVALID_ARG"
+    assert "graph 5:" in str(e.value) and "graph 9:" not in str(e.value)
+
+
+def test_batch_preparation_runs_to_the_device_step():
+    """Every graph of a valid batch is cleaned, reordered and relabelled on 4
+    threads; without a GPU creation then stops at the first device call, with a
+    GPU it returns a handle."""
+    graphs = [synth.rmat_graph(9, 8, seed=60 + i) for i in range(6)] + \
+             [synth.grid_graph(24 + i, 0.9, seed=70 + i)[0] for i in range(6)]
+    items = [(g.n, g.row_ptr, g.col_idx) for g in graphs]
+    orders = [blest.BLEST_ORDER_COMPRESS] * 6 + [blest.BLEST_ORDER_BANDWIDTH] * 6
+    try:
+        h = blest.blest_batch_create(items, orders, threads=4)
+    except blest.BlestError as e:
+        assert e.name == "BLEST_ERR_CUDA", str(e)
+    else:
+        blest.blest_destroy(h)
