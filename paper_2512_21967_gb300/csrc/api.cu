@@ -684,10 +684,11 @@ blest_status blest_batch_create(int32_t num_graphs, const int32_t* n_each, const
     std::vector<int32_t> new_id((size_t)N);
     std::vector<Csr> parts((size_t)num_graphs);
     std::vector<std::vector<int32_t>> ids((size_t)num_graphs);
-    // Graphs are cleaned, checked, reordered and relabelled concurrently, largest
-    // first, each with its share of the host threads; an order does not depend on
-    // the thread count, so neither does the handle.  The first failing graph (by
-    // index) is reported.
+    // Graphs are cleaned, checked, reordered and relabelled on the host threads:
+    // a graph holding more than an even share of the batch's entries alone with
+    // all threads, the others concurrently with one thread each, largest first.
+    // An order does not depend on the thread count, so neither does the handle.
+    // The first failing graph (by index) is reported.
     std::vector<blest_status> status((size_t)num_graphs, BLEST_OK);
     std::vector<std::string> errors((size_t)num_graphs);
     std::vector<int32_t> by_size((size_t)num_graphs);
@@ -695,26 +696,35 @@ blest_status blest_batch_create(int32_t num_graphs, const int32_t* n_each, const
     auto entries = [&](int32_t g) -> int64_t { return n_each[g] > 0 && row_ptrs[g] ? row_ptrs[g][n_each[g]] : 0; };
     std::stable_sort(by_size.begin(), by_size.end(), [&](int32_t a, int32_t b) { return entries(a) > entries(b); });
     const int workers = std::max(1, std::min(threads, num_graphs));
-    const int inner = std::max(1, threads / workers);
-    std::atomic<int32_t> next(0);
+    auto prepare_one = [&](int32_t g, int inner) {
+        int32_t used = 0;
+        double to = 0, tc = 0;
+        Csr clean;
+        blest_status s = prepare_graph(n_each[g], row_ptrs[g], col_idxs[g], (blest_order)orders[g], params, inner,
+                                       clean, ids[(size_t)g], &used, &to, &tc);
+        if (s) {
+            status[(size_t)g] = s;
+            errors[(size_t)g] = g_last_error;   // this thread's own message
+            return;
+        }
+        if (!ids[(size_t)g].empty()) blest::relabel_csr(clean, ids[(size_t)g], inner, parts[(size_t)g]);
+        else parts[(size_t)g] = std::move(clean);
+    };
     const double t0 = now_s();
+    // graphs above an even share of the batch's entries take all threads, one at a time
+    int64_t all_entries = 0;
+    for (int32_t g = 0; g < num_graphs; ++g) all_entries += entries(g);
+    int32_t first_small = 0;
+    while (first_small < num_graphs && workers > 1 &&
+           entries(by_size[(size_t)first_small]) * workers > all_entries)
+        prepare_one(by_size[(size_t)first_small++], threads);
+    // the rest run concurrently, one thread each
+    std::atomic<int32_t> next(first_small);
     auto work = [&]() {
         for (;;) {
             const int32_t k = next.fetch_add(1);
             if (k >= num_graphs) break;
-            const int32_t g = by_size[(size_t)k];
-            int32_t used = 0;
-            double to = 0, tc = 0;
-            Csr clean;
-            blest_status s = prepare_graph(n_each[g], row_ptrs[g], col_idxs[g], (blest_order)orders[g], params, inner,
-                                           clean, ids[(size_t)g], &used, &to, &tc);
-            if (s) {
-                status[(size_t)g] = s;
-                errors[(size_t)g] = g_last_error;   // this worker's own message
-                continue;
-            }
-            if (!ids[(size_t)g].empty()) blest::relabel_csr(clean, ids[(size_t)g], inner, parts[(size_t)g]);
-            else parts[(size_t)g] = std::move(clean);
+            prepare_one(by_size[(size_t)k], 1);
         }
     };
     std::vector<std::thread> pool;
