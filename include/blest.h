@@ -171,7 +171,10 @@ blest_status blest_graph_create_ex(int32_t n, const int32_t* row_ptr, const int3
  * traversal of many graphs in one persistent launch.  Graph g has n_each[g]
  * vertices and CSR (row_ptrs[g], col_idxs[g]) in its own local ids, and is
  * reordered with orders[g] inside its own id range; in the union, graph g's
- * vertices follow those of graphs 0..g-1.  Errors as blest_graph_create. */
+ * vertices follow those of graphs 0..g-1.  The graphs are cleaned, checked and
+ * reordered concurrently on the host threads of params (the handle does not
+ * depend on their number).  Errors as blest_graph_create; the message names
+ * the lowest-numbered graph that failed. */
 blest_status blest_batch_create(int32_t num_graphs, const int32_t* n_each,
                                 const int32_t* const* row_ptrs, const int32_t* const* col_idxs,
                                 const int32_t* orders, const blest_create_params* params,
