@@ -69,3 +69,29 @@ def test_parallel_cpu_baseline_counts_the_oracle_work():
     assert out["value"] > 0 and out["source_bfs_per_s"] > 0
     secs = 4 / out["source_bfs_per_s"]                  # the reported rate gives the wall time back
     assert abs(out["value"] * 1e9 * secs - edges) <= 0.01 * edges
+
+
+def plain_ss_bytes(levels, new_id, w_s, n, lazy):
+    pairs = {(int(levels[v]), int(new_id[v]) // 8) for v in range(n) if levels[v] >= 0}
+    stage1 = sum(int(w_s[s]) for _, s in pairs)
+    reached = int((levels >= 0).sum())
+    nlevels = int(levels.max()) + 1
+    sweeps = nlevels + 1 if lazy else 1
+    return stage1 + sweeps * ((n + 31) // 32) * 8 + 4 * reached + 12 * n, reached
+
+
+@pytest.mark.parametrize("lazy", [False, True])
+@pytest.mark.parametrize("case", ["rmat", "grid"])
+def test_single_source_byte_model_matches_plain_definition(case, lazy):
+    """The byte model behind the headline roofline, on oracle levels."""
+    import bench
+    g = synth.rmat_graph(9, 8, seed=2) if case == "rmat" else synth.grid_graph(30, 0.85, seed=3)[0]
+    src = int(synth.pick_sources(g, 1, seed=4)[0])
+    levels = oracle.bfs_levels(g.n, g.row_ptr, g.col_idx, src)
+    rng = np.random.default_rng(5)
+    new_id = rng.permutation(g.n).astype(np.int64)
+    nss = (g.n + 7) // 8
+    w_s = rng.integers(20, 2000, nss)
+    got = bench.traversal_bytes(torch.from_numpy(levels), torch.from_numpy(new_id), torch.from_numpy(w_s), nss,
+                                g.n, lazy, torch)
+    assert got == plain_ss_bytes(levels, new_id, w_s, g.n, lazy)
