@@ -717,7 +717,9 @@ def run_ours_window_sweep(args, torch, blest, dev, rank, world):
         h = blest.blest_graph_create_ex(g.n, g.row_ptr, g.col_idx, order, window=max(w, 8), prepass=prepass)
         st = blest.blest_get_stats(h)
         blest.blest_autotune(h, srcs[:4])
-        edges, ms = 0, 0.0
+        w_s, new_id, _ = byte_model(h, g, g.n)
+        w_s_t, new_id_t = torch.from_numpy(w_s).to(dev), torch.from_numpy(new_id).to(dev)
+        edges, ms, nbytes = 0, 0.0, 0
         for s_ in srcs:
             blest.blest_bfs_device(h, int(s_), out, stream=stream)
         blest.blest_sync(h)
@@ -730,11 +732,15 @@ def run_ours_window_sweep(args, torch, blest, dev, rank, world):
             torch.cuda.synchronize(dev)
             ms += e0.elapsed_time(e1)
             edges += int(deg_t[out >= 0].sum().item()) // 2
+            info, _ = blest.blest_get_run_info(h)
+            nbytes += traversal_bytes(out, new_id_t, w_s_t, (g.n + 7) // 8, g.n,
+                                      info["update"] == blest.BLEST_UPDATE_LAZY, torch)[0]
         blest.blest_sync(h)
         rows.append({"window": w if w else "none", "prepass": prepass if w else None,
                      "order_s": round(st["order_seconds"], 3),
                      "compression_ratio": round(st["compression_ratio"], 4), "num_vss": st["num_vss"],
-                     "bfs_ms_mean": round(ms / len(srcs), 4), "gteps": round(edges / (ms / 1e3) / 1e9, 2)})
+                     "bfs_ms_mean": round(ms / len(srcs), 4), "gteps": round(edges / (ms / 1e3) / 1e9, 2),
+                     "roofline_frac": round(nbytes / (ms / 1e3) / 1e9 / peaks()[0], 4)})
         blest.blest_destroy(h)
     if rank == 0:
         best = max(r["gteps"] for r in rows)
