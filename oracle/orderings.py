@@ -244,20 +244,25 @@ def bandwidth(n: int, row_ptr, col_idx) -> int:
     return int(np.abs(rows - ci).max()) if len(ci) else 0
 
 
-def is_social_like(n: int, row_ptr, col_idx) -> bool:
-    """Section 3.2.1 classifier.  Heavy-tail sharing: the top 1% of vertices by
-    degree (ceil(n/100) of them) hold more than 5% of the edges and the top 10%
-    (ceil(n/10)) more than 40%.  Power law (the paper gives no numbers; this
-    reading's band): a least-squares line through (log d, log #vertices of degree
-    d) over degrees d >= 1 with at least 5 points has slope in [-3.5, -1.5] and
+def social_like_degrees(deg) -> bool:
+    """Section 3.2.1 classifier on a degree sequence (reading 11).
+
+    Heavy-tail sharing: the ceil(n/100) highest-degree vertices hold more than
+    5% of all edge endpoints and the ceil(n/10) highest more than 40%.  "More
+    than" is strict and exact: 20 * top1 > total and 5 * top10 > 2 * total.
+    Power law (the paper gives no numbers; this reading's band): a least-squares
+    line through (log d, log #vertices of degree d), over the degrees d >= 1
+    that occur, with at least 5 such points, has slope in [-3.5, -1.5] and
     R^2 >= 0.8.  Social-like = either property."""
-    deg = np.diff(np.asarray(row_ptr, dtype=np.int64))
+    deg = np.asarray(deg, dtype=np.int64)
+    n = len(deg)
     total = int(deg.sum())
     if n == 0 or total == 0:
         return False
     srt = np.sort(deg)[::-1]
     k1, k10 = max(1, -(-n // 100)), max(1, -(-n // 10))
-    if srt[:k1].sum() > 0.05 * total and srt[:k10].sum() > 0.40 * total:
+    top1, top10 = int(srt[:k1].sum()), int(srt[:k10].sum())
+    if 20 * top1 > total and 5 * top10 > 2 * total:
         return True
     ds, cnt = np.unique(deg[deg >= 1], return_counts=True)
     if len(ds) < 5:
@@ -270,3 +275,11 @@ def is_social_like(n: int, row_ptr, col_idx) -> bool:
         return False
     slope, r2 = cxy / vx, cxy * cxy / (vx * vy)
     return bool(-3.5 <= slope <= -1.5 and r2 >= 0.8)
+
+
+def is_social_like(n: int, row_ptr, col_idx) -> bool:
+    """Section 3.2.1 classifier of a CSR graph: its degree sequence (row
+    lengths) through social_like_degrees."""
+    deg = np.diff(np.asarray(row_ptr, dtype=np.int64))
+    assert len(deg) == n
+    return social_like_degrees(deg)

@@ -780,7 +780,8 @@ bool is_social_like(const Csr& g) {
     int64_t k1 = std::max<int64_t>(1, (n + 99) / 100), k10 = std::max<int64_t>(1, (n + 9) / 10);
     int64_t s1 = 0, s10 = 0;
     for (int64_t i = 0; i < k10; ++i) { if (i < k1) s1 += sorted[i]; s10 += sorted[i]; }
-    bool heavy = (double)s1 > 0.05 * (double)total && (double)s10 > 0.40 * (double)total;
+    // "more than 5% / 40%" as exact integer comparisons
+    bool heavy = 20 * s1 > total && 5 * s10 > 2 * total;
     if (heavy) return true;
     // log-log degree histogram, least-squares line over degrees >= 1
     int64_t dmax = sorted[0];
