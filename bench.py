@@ -179,19 +179,51 @@ def byte_model(h, g, n):
     return w_s, new_id, rp[1:] - rp[:-1]
 
 
-def traversal_bytes(levels_t, new_id_t, w_s_t, nss, n, lazy, torch):
-    """Algorithmic bytes of one traversal from its (device) level array."""
+def traversal_bytes(levels_t, new_id_t, w_s_t, nvss_t, nss, n, lazy, direct, nroots, torch):
+    """Algorithmic bytes of one single-source (or multi-root) traversal, from its
+    level array in original ids, under the model of the fused kernel:
+      init: the level array cleared to -1 (4 B per vertex) and the visited
+        bitmaps cleared (V_curr and V_next; eager also its 3 frontier bitmaps);
+      stage 1: per level l and slice set s holding a vertex at level l-1, the
+        visit bytes of s (5 B per unpadded slice + 16 B per VSS);
+      sweeps (level 0, and every processed level when lazy): a dense sweep reads
+        V_next and V_curr (8 B per word); a sparse one (queue of at most n/2048
+        VSSs, or at most n/2048 roots at level 0) reads only the dirty bitmap
+        (4 B per 32 words) and the words holding a newly reached vertex; every
+        word holding a newly reached vertex is written back (4 B; eager level 0
+        also writes its frontier word);
+      level writes: 4 B per reached vertex, plus 4 B for its original id when
+        the sweeps write levels straight to the output (direct);
+      unpermute (not direct): read the order, gather L, write the output, 12 B
+        per vertex.
+    Returns (bytes, reached vertices, bytes under the survey's formula with the
+    unpermute counted, the same without)."""
     reached = levels_t >= 0
     nreached = int(reached.sum().item())
     lv = levels_t[reached].long()
-    s = new_id_t[reached] >> 3
+    r = new_id_t[reached].long()
+    s = r >> 3
+    nwords = (n + 31) // 32
+    cap = nwords >> 6                            # a queue this short takes the sparse sweep
+    dirty_read = 4 * ((nwords + 31) // 32)
     key = torch.unique(lv * nss + s)
     stage1 = int(w_s_t[key % nss].sum().item())
-    nlevels = int(lv.max().item()) + 1          # levels 1..max+1 are processed
-    nwords = (n + 31) // 32
-    sweeps = (nlevels + 1) if lazy else 1       # level 0 plus one per lazy level
-    sweep = sweeps * nwords * 8
-    return stage1 + sweep + 4 * nreached + 12 * n, nreached
+    lmax = int(lv.max().item()) if nreached else -1
+    # words holding a vertex first reached at level l
+    wkey = torch.unique(lv * nwords + (r >> 5))
+    words_new = torch.bincount(wkey // nwords, minlength=lmax + 2).cpu().numpy()
+    # queue of processed level l = the VSSs of the slice sets holding a vertex at level l - 1
+    qn = torch.bincount(key // nss, weights=nvss_t[key % nss].double(), minlength=lmax + 2).cpu().numpy()
+    sweep = 0
+    for l in range(0, (lmax + 2) if lazy else 1):
+        q = nroots if l == 0 else float(qn[l - 1])
+        wn = int(words_new[l]) if l < len(words_new) else 0
+        sweep += (dirty_read + 8 * wn) if q <= cap else 8 * nwords
+        sweep += 4 * wn * (2 if (not lazy and l == 0) else 1)
+    init = 4 * n + 4 * nwords * (2 if lazy else 5)
+    body = stage1 + sweep + 4 * nreached
+    total = init + body + (4 * nreached if direct else 12 * n)
+    return total, nreached, body + 4 * n + 12 * n, body + 4 * n
 
 
 def ms_traversal_bytes(levels_t, new_id_t, w_s_t, nvss_t, nss, n, torch):
@@ -329,6 +361,8 @@ def run_ours(args):
     out = torch.empty(n, dtype=torch.int32, device=dev)
     edges = np.zeros(len(srcs), np.int64)
     abytes = np.zeros(len(srcs), np.int64)
+    abytes_survey = np.zeros((len(srcs), 2), np.int64)
+    nvss_t = torch.from_numpy(nvss).to(dev)
     lazy = None
     run_info = None
 
@@ -351,7 +385,8 @@ def run_ours(args):
                 if lazy is None:
                     run_info, _ = blest.blest_get_run_info(h)
                     lazy = run_info["update"] == blest.BLEST_UPDATE_LAZY
-                abytes[i], _ = traversal_bytes(out, new_id_t, w_s_t, nss, n, lazy, torch)
+                abytes[i], _, abytes_survey[i, 0], abytes_survey[i, 1] = traversal_bytes(
+                    out, new_id_t, w_s_t, nvss_t, nss, n, lazy, run_info["output_path"] == 1, 1, torch)
         else:
             one_step()
     blest.blest_sync(h)
@@ -433,6 +468,11 @@ def run_ours(args):
                          "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
                          "traffic": round(tr_ratio * avg_bytes) if tr_ratio else None, "traffic_note": tr_note,
                          "kernel": "bfs_kernel (fused persistent traversal)",
+                         "bytes_model": "init + stage-1 visits + dense/sparse sweeps + level writes"
+                                        + (" (direct, no unpermute)" if run_info["output_path"] == 1
+                                           else " + unpermute"),
+                         "bytes_survey_with_unpermute": float(abytes_survey[:, 0].mean()),
+                         "bytes_survey_without_unpermute": float(abytes_survey[:, 1].mean()),
                          "bytes_per_launch": avg_bytes, "avg_launch_ms": round(avg_launch_ms, 5)},
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -558,9 +598,11 @@ def run_ours_batch(args, torch, blest, dev, rank, world):
     edges = int(deg[out >= 0].sum().item()) // 2
     info, _ = blest.blest_get_run_info(h)
     # one multi-root traversal of the union: the single-source byte model applies as it is
-    w_s, new_id, _ = byte_model(h, None, n)
-    batch_bytes, _ = traversal_bytes(out, torch.from_numpy(new_id).to(dev), torch.from_numpy(w_s).to(dev),
-                                     (n + 7) // 8, n, info["update"] == blest.BLEST_UPDATE_LAZY, torch)
+    w_s, new_id, nvss = byte_model(h, None, n)
+    batch_bytes, _, _, _ = traversal_bytes(out, torch.from_numpy(new_id).to(dev), torch.from_numpy(w_s).to(dev),
+                                           torch.from_numpy(nvss).to(dev), (n + 7) // 8, n,
+                                           info["update"] == blest.BLEST_UPDATE_LAZY, info["output_path"] == 1,
+                                           len(srcs), torch)
     torch.cuda.synchronize(dev)
     sampler = ClockSampler() if rank == 0 else None
     evs = [[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(args.steps)]
@@ -717,8 +759,9 @@ def run_ours_window_sweep(args, torch, blest, dev, rank, world):
         h = blest.blest_graph_create_ex(g.n, g.row_ptr, g.col_idx, order, window=max(w, 8), prepass=prepass)
         st = blest.blest_get_stats(h)
         blest.blest_autotune(h, srcs[:4])
-        w_s, new_id, _ = byte_model(h, g, g.n)
+        w_s, new_id, nvss = byte_model(h, g, g.n)
         w_s_t, new_id_t = torch.from_numpy(w_s).to(dev), torch.from_numpy(new_id).to(dev)
+        nvss_t = torch.from_numpy(nvss).to(dev)
         edges, ms, nbytes = 0, 0.0, 0
         for s_ in srcs:
             blest.blest_bfs_device(h, int(s_), out, stream=stream)
@@ -733,8 +776,9 @@ def run_ours_window_sweep(args, torch, blest, dev, rank, world):
             ms += e0.elapsed_time(e1)
             edges += int(deg_t[out >= 0].sum().item()) // 2
             info, _ = blest.blest_get_run_info(h)
-            nbytes += traversal_bytes(out, new_id_t, w_s_t, (g.n + 7) // 8, g.n,
-                                      info["update"] == blest.BLEST_UPDATE_LAZY, torch)[0]
+            nbytes += traversal_bytes(out, new_id_t, w_s_t, nvss_t, (g.n + 7) // 8, g.n,
+                                      info["update"] == blest.BLEST_UPDATE_LAZY, info["output_path"] == 1, 1,
+                                      torch)[0]
         blest.blest_sync(h)
         rows.append({"window": w if w else "none", "prepass": prepass if w else None,
                      "order_s": round(st["order_seconds"], 3),

@@ -146,6 +146,10 @@ typedef struct {
     int32_t grid_blocks;         /* persistent-grid blocks */
     int32_t threads_per_block;
     int32_t recorded;            /* entries of the queue-size record below that are valid */
+    int32_t output_path;         /* how levels reached the output: 0 written in place (no
+                                    reordering), 1 written by the sweeps straight to their
+                                    original ids (lazy with a reordering), 2 kept in BVSS ids
+                                    and gathered by an unpermute pass */
 } blest_run_info;
 
 /* ---------------------------------------------------------------- graphs */

@@ -106,7 +106,8 @@ class ServerStats(ctypes.Structure):
 
 class RunInfo(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int32), ("update", ctypes.c_int32), ("pull", ctypes.c_int32),
-                ("grid_blocks", ctypes.c_int32), ("threads_per_block", ctypes.c_int32), ("recorded", ctypes.c_int32)]
+                ("grid_blocks", ctypes.c_int32), ("threads_per_block", ctypes.c_int32), ("recorded", ctypes.c_int32),
+                ("output_path", ctypes.c_int32)]
 
 
 _lock = threading.Lock()

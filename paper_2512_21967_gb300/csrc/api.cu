@@ -389,6 +389,7 @@ blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots
     h->info.grid_blocks = L.grid;
     h->info.threads_per_block = blest::bfs_threads_per_block();
     h->info.recorded = -1;  // resolved in blest_get_run_info
+    h->info.output_path = !h->d_new_id ? 0 : (L.direct ? 1 : 2);
     return BLEST_OK;
 }
 

@@ -71,27 +71,60 @@ def test_parallel_cpu_baseline_counts_the_oracle_work():
     assert abs(out["value"] * 1e9 * secs - edges) <= 0.01 * edges
 
 
-def plain_ss_bytes(levels, new_id, w_s, n, lazy):
-    pairs = {(int(levels[v]), int(new_id[v]) // 8) for v in range(n) if levels[v] >= 0}
-    stage1 = sum(int(w_s[s]) for _, s in pairs)
-    reached = int((levels >= 0).sum())
-    nlevels = int(levels.max()) + 1
-    sweeps = nlevels + 1 if lazy else 1
-    return stage1 + sweeps * ((n + 31) // 32) * 8 + 4 * reached + 12 * n, reached
+def plain_ss_bytes(levels, new_id, w_s, nvss, n, lazy, direct, nroots):
+    """The single-source model written as loops over levels and vertices."""
+    nwords = (n + 31) // 32
+    sets_at, words_at = {}, {}
+    reached = 0
+    for v in range(n):
+        if levels[v] >= 0:
+            reached += 1
+            sets_at.setdefault(int(levels[v]), set()).add(int(new_id[v]) // 8)
+            words_at.setdefault(int(levels[v]), set()).add(int(new_id[v]) // 32)
+    stage1 = sum(int(w_s[s]) for ss in sets_at.values() for s in ss)
+    lmax = max(sets_at) if sets_at else -1
+    sweep = 0
+    for l in range(0, lmax + 2 if lazy else 1):
+        queue = nroots if l == 0 else sum(int(nvss[s]) for s in sets_at.get(l - 1, ()))
+        new_words = len(words_at.get(l, ()))
+        if queue <= nwords // 64:                      # sparse: dirty bitmap + touched words only
+            sweep += 4 * ((nwords + 31) // 32) + 8 * new_words
+        else:
+            sweep += 8 * nwords
+        sweep += 4 * new_words * (1 if lazy or l > 0 else 2)
+    init = 4 * n + 4 * nwords * (2 if lazy else 5)
+    body = stage1 + sweep + 4 * reached
+    out = 4 * reached if direct else 12 * n
+    return init + body + out, reached, body + 16 * n, body + 4 * n
 
 
+@pytest.mark.parametrize("direct", [False, True])
 @pytest.mark.parametrize("lazy", [False, True])
-@pytest.mark.parametrize("case", ["rmat", "grid"])
-def test_single_source_byte_model_matches_plain_definition(case, lazy):
-    """The byte model behind the headline roofline, on oracle levels."""
+@pytest.mark.parametrize("case", ["rmat", "grid", "fullgrid"])
+def test_single_source_byte_model_matches_plain_definition(case, lazy, direct):
+    """The byte model behind the headline roofline, on oracle levels; the grid
+    cases have levels whose queue is short enough for the sparse sweep."""
     import bench
-    g = synth.rmat_graph(9, 8, seed=2) if case == "rmat" else synth.grid_graph(30, 0.85, seed=3)[0]
+    if case == "rmat":
+        g = synth.rmat_graph(9, 8, seed=2)
+    elif case == "grid":
+        g = synth.grid_graph(30, 0.85, seed=3)[0]
+    else:
+        g = synth.grid_graph(160, 1.0, seed=3)[0]   # n = 25600: queues of <= 12 VSSs are sparse
     src = int(synth.pick_sources(g, 1, seed=4)[0])
     levels = oracle.bfs_levels(g.n, g.row_ptr, g.col_idx, src)
     rng = np.random.default_rng(5)
-    new_id = rng.permutation(g.n).astype(np.int64)
+    new_id = rng.permutation(g.n).astype(np.int64) if case != "fullgrid" else np.arange(g.n, dtype=np.int64)
     nss = (g.n + 7) // 8
     w_s = rng.integers(20, 2000, nss)
-    got = bench.traversal_bytes(torch.from_numpy(levels), torch.from_numpy(new_id), torch.from_numpy(w_s), nss,
-                                g.n, lazy, torch)
-    assert got == plain_ss_bytes(levels, new_id, w_s, g.n, lazy)
+    nvss = rng.integers(1, 3, nss)
+    got = bench.traversal_bytes(torch.from_numpy(levels), torch.from_numpy(new_id), torch.from_numpy(w_s),
+                                torch.from_numpy(nvss), nss, g.n, lazy, direct, 1, torch)
+    want = plain_ss_bytes(levels, new_id, w_s, nvss, g.n, lazy, direct, 1)
+    assert got == want
+    if case == "fullgrid":
+        # some processed levels take the sparse sweep and some the dense one
+        cap = ((g.n + 31) // 32) // 64
+        queues = [sum(int(nvss[s]) for s in {int(new_id[v]) // 8 for v in np.flatnonzero(levels == l)})
+                  for l in range(int(levels.max()) + 1)]
+        assert min(queues) <= cap < max(queues)
