@@ -450,10 +450,11 @@ void blest_server_destroy(blest_server_handle s);
 /* ------------------------------------------------- allocation-free traversal */
 
 /* Single-source BFS that allocates nothing, for callers that may not call
- * cudaMalloc: work captured into a CUDA graph whose capture mode forbids
- * allocation, plugins and embedded runtimes whose host application owns every
- * device allocation, and services whose device memory is budgeted up front.
- * The paper has no counterpart; this is a deployment variant of blest_bfs_device.
+ * cudaMalloc: plugins and embedded runtimes whose host application owns every
+ * device allocation and lends them only their input and output buffers, and
+ * services whose device memory is budgeted up front so that no request can
+ * fail or stall on an allocation.  The paper has no counterpart; this is a
+ * deployment variant of blest_bfs_device.
  *
  * Inputs are the BVSS arrays of a graph in device memory, as blest_export gives
  * them: d_real_ptrs (int32[ceil(n/8)+1]), d_row_ids (int32[128*num_vss]),
@@ -461,8 +462,9 @@ void blest_server_destroy(blest_server_handle s);
  * NULL if the BVSS uses the original order).  src_bvss is the source in BVSS
  * ids (new_id[src]).  d_levels (int32[n], device) receives the levels in
  * ORIGINAL ids.  update is BLEST_UPDATE_EAGER or BLEST_UPDATE_LAZY.  stream is a
- * cudaStream_t (NULL = the legacy default stream).  The call blocks until the
- * traversal is done and returns its status.
+ * cudaStream_t (NULL = the legacy default stream).  The call is blocking: it
+ * enqueues the clears and the traversal on the stream, then waits for the
+ * stream to finish them before it reads the traversal's status and returns.
  *
  * Working memory comes from one fixed device array inside the library (about
  * 21 MiB), which every GPU that loads the library keeps until the process

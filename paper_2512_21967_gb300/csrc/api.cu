@@ -10,6 +10,8 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <thread>
 #include <vector>
@@ -698,18 +700,28 @@ blest_status blest_batch_create(int32_t num_graphs, const int32_t* n_each, const
     std::stable_sort(by_size.begin(), by_size.end(), [&](int32_t a, int32_t b) { return entries(a) > entries(b); });
     const int workers = std::max(1, std::min(threads, num_graphs));
     auto prepare_one = [&](int32_t g, int inner) {
-        int32_t used = 0;
-        double to = 0, tc = 0;
-        Csr clean;
-        blest_status s = prepare_graph(n_each[g], row_ptrs[g], col_idxs[g], (blest_order)orders[g], params, inner,
-                                       clean, ids[(size_t)g], &used, &to, &tc);
-        if (s) {
-            status[(size_t)g] = s;
-            errors[(size_t)g] = g_last_error;   // this thread's own message
-            return;
+        // runs on worker threads: an exception escaping here would terminate the process,
+        // so a failed host allocation becomes this graph's error status
+        try {
+            int32_t used = 0;
+            double to = 0, tc = 0;
+            Csr clean;
+            blest_status s = prepare_graph(n_each[g], row_ptrs[g], col_idxs[g], (blest_order)orders[g], params,
+                                           inner, clean, ids[(size_t)g], &used, &to, &tc);
+            if (s) {
+                status[(size_t)g] = s;
+                errors[(size_t)g] = g_last_error;   // this thread's own message
+                return;
+            }
+            if (!ids[(size_t)g].empty()) blest::relabel_csr(clean, ids[(size_t)g], inner, parts[(size_t)g]);
+            else parts[(size_t)g] = std::move(clean);
+        } catch (const std::bad_alloc&) {
+            status[(size_t)g] = BLEST_ERR_OOM;
+            errors[(size_t)g] = "host memory exhausted while preparing the graph";
+        } catch (const std::exception& ex) {
+            status[(size_t)g] = BLEST_ERR_INTERNAL;
+            errors[(size_t)g] = std::string("host preparation failed: ") + ex.what();
         }
-        if (!ids[(size_t)g].empty()) blest::relabel_csr(clean, ids[(size_t)g], inner, parts[(size_t)g]);
-        else parts[(size_t)g] = std::move(clean);
     };
     const double t0 = now_s();
     // graphs above an even share of the batch's entries take all threads, one at a time

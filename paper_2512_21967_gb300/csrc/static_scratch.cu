@@ -1,15 +1,16 @@
 // Single-source traversal for callers that cannot allocate device memory.
 //
-// Some callers must not call cudaMalloc at all: code running inside a CUDA
-// stream capture that may not allocate, embedded runtimes and plugins whose host
-// application owns every device allocation, and real-time services whose memory
-// is budgeted up front.  For them, blest_bfs_static_scratch runs the same fused
-// traversal kernel as blest_bfs_device, but every working buffer it needs --
-// control block, internal levels, visited bitmaps, eager frontier bitmaps and
-// the three VSS queues -- lives in the file-scope device array g_scratch below.
-// Its size is fixed at compile time (about 21 MiB) and every GPU that loads this
-// library holds it until the process exits.  The caller passes the BVSS arrays
-// and the output; nothing here allocates.
+// Some callers must never call cudaMalloc: plugins and embedded runtimes whose
+// host application owns every device allocation and hands them only the
+// buffers they work on, and services whose device memory is budgeted up front
+// so that no request can fail or stall on an allocation.  For them,
+// blest_bfs_static_scratch runs the same fused traversal kernel as
+// blest_bfs_device, but every working buffer it needs -- control block,
+// internal levels, visited bitmaps, eager frontier bitmaps and the three VSS
+// queues -- lives in the file-scope device array g_scratch below.  Its size is
+// fixed at compile time (about 21 MiB) and every GPU that loads this library
+// holds it until the process exits.  The caller passes the BVSS arrays and the
+// output; nothing here allocates.
 //
 // Host code must not take the address of g_scratch directly: in host code that
 // name is only a host-side stand-in for the device variable.  The device
