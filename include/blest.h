@@ -467,7 +467,7 @@ void blest_server_destroy(blest_server_handle s);
  * stream to finish them before it reads the traversal's status and returns.
  *
  * Working memory comes from one fixed device array inside the library (about
- * 21 MiB), which every GPU that loads the library keeps until the process
+ * 21.5 MiB), which every GPU that loads the library keeps until the process
  * exits.  Limits: n <= 2,097,152 vertices and num_vss <= 524,288 virtual slice
  * sets; larger graphs get BLEST_ERR_TOO_LARGE.  The first call on a device looks
  * up the array's device address (once per device, with that device current);

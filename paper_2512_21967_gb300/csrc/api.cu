@@ -24,10 +24,13 @@
 namespace blest {
 constexpr int kCtrlBytes = 256;        // layout in device_common.cuh
 constexpr int kCtrlClearBytes = 192;
+// bitmaps of a handle's traversal state: 3 eager frontiers, the V_curr/V_next pairs (2), the V_curr copy
+constexpr size_t kStateBitmaps = 6;
 constexpr int kStickyWord = 48;
 }  // namespace blest
 using blest::kCtrlBytes;
 using blest::kCtrlClearBytes;
+using blest::kStateBitmaps;
 using blest::kStickyWord;
 
 using blest::Csr;
@@ -71,13 +74,13 @@ struct blest_graph {
     int32_t* d_new_id = nullptr;
     int32_t* d_L = nullptr;              // internal levels (BVSS ids)
     int32_t* d_out = nullptr;            // staging for host-output calls (original ids)
-    // [F0 F1 F2 | V_curr | V_next | dirty | control block] in one allocation, so that
+    // [F0 F1 F2 | V_curr/V_next pairs (2 bitmaps) | V_curr copy | dirty | control block] in one allocation, so that
     // one memset clears the bitmaps a traversal needs and the control block's counters
     unsigned char* d_state = nullptr;
     size_t bitmap_bytes = 0;             // each bitmap, rounded up to 256 B
     size_t dirty_bytes = 0;              // 1 bit per bitmap word, rounded up to 256 B
-    uint32_t* d_vcur = nullptr;
-    uint32_t* d_vnext = nullptr;
+    uint2* d_vis = nullptr;              // V_curr / V_next word pairs (two bitmaps' worth of bytes)
+    uint32_t* d_vcur = nullptr;          // dense copy of V_curr
     uint32_t* d_dirty = nullptr;
     uint32_t* d_F = nullptr;             // 3 bitmaps, bitmap_bytes apart (eager frontier)
     unsigned long long* d_Q = nullptr;   // 3 * qcap
@@ -181,12 +184,12 @@ blest_status alloc_state(blest_graph* h, const std::vector<int32_t>& new_id) {
     BLEST_ALLOC(h->d_out, sizeof(int32_t) * std::max<size_t>(h->n, 1), "cudaMalloc(out)");
     h->bitmap_bytes = (sizeof(uint32_t) * std::max<size_t>(nw, 1) + 255) / 256 * 256;
     h->dirty_bytes = (sizeof(uint32_t) * ((std::max<size_t>(nw, 1) + 31) / 32) + 255) / 256 * 256;
-    BLEST_ALLOC(h->d_state, 5 * h->bitmap_bytes + h->dirty_bytes + kCtrlBytes, "cudaMalloc(bitmaps)");
+    BLEST_ALLOC(h->d_state, kStateBitmaps * h->bitmap_bytes + h->dirty_bytes + kCtrlBytes, "cudaMalloc(bitmaps)");
     h->d_F = reinterpret_cast<uint32_t*>(h->d_state);
-    h->d_vcur = reinterpret_cast<uint32_t*>(h->d_state + 3 * h->bitmap_bytes);
-    h->d_vnext = reinterpret_cast<uint32_t*>(h->d_state + 4 * h->bitmap_bytes);
-    h->d_dirty = reinterpret_cast<uint32_t*>(h->d_state + 5 * h->bitmap_bytes);
-    h->d_ctrl = reinterpret_cast<unsigned int*>(h->d_state + 5 * h->bitmap_bytes + h->dirty_bytes);
+    h->d_vis = reinterpret_cast<uint2*>(h->d_state + 3 * h->bitmap_bytes);
+    h->d_vcur = reinterpret_cast<uint32_t*>(h->d_state + 5 * h->bitmap_bytes);
+    h->d_dirty = reinterpret_cast<uint32_t*>(h->d_state + kStateBitmaps * h->bitmap_bytes);
+    h->d_ctrl = reinterpret_cast<unsigned int*>(h->d_state + kStateBitmaps * h->bitmap_bytes + h->dirty_bytes);
     BLEST_ALLOC(h->d_Q, sizeof(unsigned long long) * 3 * (size_t)h->qcap, "cudaMalloc(queues)");
     BLEST_ALLOC(h->d_level_sizes, sizeof(int32_t) * kLevelRecordCap, "cudaMalloc(level record)");
     BLEST_ALLOC(h->d_level_times, sizeof(unsigned long long) * (2 * (size_t)kLevelRecordCap + 2), "cudaMalloc(level times)");
@@ -337,8 +340,8 @@ blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots
     // -1 before the launch) and needs no unpermute; the parent pass needs L
     L.direct = (L.update == 2 && h->d_new_id && h->d_old_of && !h->need_internal_levels) ? 1 : 0;
     L.old_of = h->d_old_of;
+    L.vis = h->d_vis;
     L.vcur = h->d_vcur;
-    L.vnext = h->d_vnext;
     L.dirty = h->d_dirty;
     for (int i = 0; i < 3; ++i) {
         L.F[i] = reinterpret_cast<uint32_t*>(h->d_state + i * h->bitmap_bytes);
@@ -376,9 +379,9 @@ blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots
     L.out = d_out;
     L.timeout_ns = (uint64_t)h->timeout_us * 1000ull;
     L.phantom = h->phantom ? 1u : 0u;
-    // [F (eager only) | V_curr | V_next | dirty | control block up to the sticky status word]
+    // [F (eager only) | V_curr/V_next pairs | V_curr copy | dirty | control block up to the sticky status word]
     const size_t skip = L.update == 1 ? 0 : 3 * h->bitmap_bytes;
-    cudaMemsetAsync(h->d_state + skip, 0, 5 * h->bitmap_bytes + h->dirty_bytes - skip + kCtrlClearBytes, st);
+    cudaMemsetAsync(h->d_state + skip, 0, kStateBitmaps * h->bitmap_bytes + h->dirty_bytes - skip + kCtrlClearBytes, st);
     cudaMemsetAsync(L.direct ? d_out : L.levels_internal, 0xFF, sizeof(int32_t) * (size_t)h->n, st);
     if (L.level_sizes) {
         cudaMemsetAsync(L.arrive_first, 0xFF, sizeof(unsigned long long) * 2 * kLevelRecordCap, st);

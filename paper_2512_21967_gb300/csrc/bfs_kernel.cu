@@ -47,8 +47,13 @@ struct BfsArgs {
     const uint32_t* __restrict__ masks_c; // compact layout: 4 packed masks per group
     const int32_t* __restrict__ new_id;  // NULL: identity, L is the output
     int32_t* L;
+    // V_curr and V_next interleaved word by word (x = V_curr, y = V_next), so that a
+    // hit row's test against both bitmaps is one 8-byte load and the sweep reads a
+    // word pair with one.  vcur is a dense copy of V_curr for the tests that need
+    // only V_curr (lazy levels after a quarter of the rows are visited, eager
+    // levels): it keeps half the footprint in L1.  The sweeps keep both equal.
+    uint2* vis;
     uint32_t* vcur;
-    uint32_t* vnext;
     uint32_t* dirty;                      // 1 bit per V_next word touched on a sparse level (NULL = never sparse)
     uint32_t* F[3];
     unsigned long long* Q[3];
@@ -141,8 +146,9 @@ __device__ __forceinline__ void sweep(const BfsArgs& a, int lvl, unsigned long l
         uint32_t diff = 0;
         int rp[5] = {0, 0, 0, 0, 0};   // VSS (or group) offsets of the word's 4 slice sets and the next
         if (t < a.nwords && ((live >> lane) & 1u)) {
-            const uint32_t nx = ld_cg(&a.vnext[t]);
-            const uint32_t cu = ld_cg(&a.vcur[t]);
+            const uint2 vv = ld_cg(&a.vis[t]);
+            const uint32_t nx = vv.y;
+            const uint32_t cu = vv.x;
             // issued with the bitmap loads, not after them: their addresses do not depend on diff
             const int32_t* ptrs = LAYOUT == 1 ? a.goff : a.real_ptrs;
 #pragma unroll
@@ -150,6 +156,7 @@ __device__ __forceinline__ void sweep(const BfsArgs& a, int lvl, unsigned long l
                 if (4 * t + q <= a.nss) rp[q] = __ldg(&ptrs[4 * t + q]);
             diff = nx ^ cu;
             if (diff) {
+                a.vis[t].x = nx;
                 a.vcur[t] = nx;
                 if (UPDATE == 1) Fout[t] = diff;
                 fresh += (unsigned int)__popc(diff);
@@ -262,10 +269,22 @@ __device__ __forceinline__ void mark_rows(const BfsArgs& a, const int4 (&rows)[N
     }
     if (filt == 2) {
 #pragma unroll
-        for (int k = 0; k < 4 * NV; ++k) w[k] = (hm >> k) & 1u ? a.vcur[u[k] >> 5] | ld_cg(&a.vnext[u[k] >> 5]) : 0u;
+        for (int k = 0; k < 4 * NV; ++k) {
+            w[k] = 0u;
+            if ((hm >> k) & 1u) {
+                const uint2 vv = ld_cg(&a.vis[u[k] >> 5]);
+                w[k] = vv.x | vv.y;
+            }
+        }
     } else if (filt == 3) {   // V_next through L1: staler, so more redundant marks, but cheaper loads
 #pragma unroll
-        for (int k = 0; k < 4 * NV; ++k) w[k] = (hm >> k) & 1u ? a.vcur[u[k] >> 5] | a.vnext[u[k] >> 5] : 0u;
+        for (int k = 0; k < 4 * NV; ++k) {
+            w[k] = 0u;
+            if ((hm >> k) & 1u) {
+                const uint2 vv = a.vis[u[k] >> 5];
+                w[k] = vv.x | vv.y;
+            }
+        }
     } else if (filt) {
 #pragma unroll
         for (int k = 0; k < 4 * NV; ++k) w[k] = (hm >> k) & 1u ? a.vcur[u[k] >> 5] : 0u;
@@ -277,7 +296,7 @@ __device__ __forceinline__ void mark_rows(const BfsArgs& a, const int4 (&rows)[N
     for (int k = 0; k < 4 * NV; ++k) {
         const uint32_t bit = 1u << (u[k] & 31);
         if (((hm >> k) & 1u) && !(w[k] & bit)) {
-            atomicOr(&a.vnext[u[k] >> 5], bit);
+            atomicOr(&a.vis[u[k] >> 5].y, bit);
             if (dirty) atomicOr(&dirty[u[k] >> 10], 1u << ((u[k] >> 5) & 31));
         }
     }
@@ -637,7 +656,7 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
     const bool sparse0 = a.dirty != nullptr && (unsigned int)a.nroots <= sparse_cap;
     for (int i = gtid; i < a.nroots; i += nthreads) {
         const int r = a.nroots <= kInlineRoots ? a.inline_roots[i] : a.roots[i];
-        atomicOr(&a.vnext[r >> 5], 1u << (r & 31));
+        atomicOr(&a.vis[r >> 5].y, 1u << (r & 31));
         if (sparse0) atomicOr(&a.dirty[r >> 10], 1u << ((r >> 5) & 31));
     }
     if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns)) return;
@@ -863,8 +882,8 @@ cudaError_t launch_bfs_kernel(const BfsLaunch& L, cudaStream_t stream) {
     a.masks_c = L.masks_c;
     a.new_id = L.new_id;
     a.L = L.levels_internal;
+    a.vis = L.vis;
     a.vcur = L.vcur;
-    a.vnext = L.vnext;
     a.dirty = L.dirty;
     for (int i = 0; i < 3; ++i) { a.F[i] = L.F[i]; a.Q[i] = L.Q[i]; }
     a.ctrl = reinterpret_cast<Ctrl*>(L.ctrl);
