@@ -501,6 +501,13 @@ def run_ours_msbfs(args, torch, blest, h, g, srcs, k, dev, stream, flush, st, t_
     n = g.n
     out = torch.empty((k, n), dtype=torch.int32, device=dev)
     deg_t = torch.from_numpy(g.degrees()).to(dev)
+    ms_tune = None
+    if not args.no_tune:
+        # untimed: pull back-end (CUDA-core / tensor-core), sources per launch, blocks per SM
+        t0 = time.time()
+        ms_tune = blest.blest_autotune_msbfs(h, srcs[:k])
+        ms_tune["seconds"] = round(time.time() - t0, 2)
+        ms_tune["pull"] = ["popc", "mma"][ms_tune["pull"]]
     for _ in range(args.warmup):
         blest.blest_msbfs_device(h, srcs[:k], out, stream=stream)
     blest.blest_sync(h)
@@ -553,6 +560,7 @@ def run_ours_msbfs(args, torch, blest, h, g, srcs, k, dev, stream, flush, st, t_
                            "k": k, "source_bfs_per_s": round(batched_rate, 2),
                            "single_source_loop_bfs_per_s": round(loop_rate, 2),
                            "batched_over_loop": round(batched_rate / loop_rate, 2),
+                           "autotune": ms_tune,
                            "single_source_variant": {kk: tune[kk] for kk in ("update", "unroll", "stage_depth",
                                                                               "visited_filter", "blocks_per_sm")}},
                 "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",

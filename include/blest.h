@@ -97,12 +97,19 @@ typedef enum {
                                         3.1.2, default); 1 = compact groups of 4 slices, only the last
                                         group of a slice set padded (built from the padded layout on
                                         first use: about 5 B per slice more device memory) */
-    BLEST_OPT_SCHEDULE = 11          /* stage-1 work split of the register pipelines (stage depth 2, 3):
+    BLEST_OPT_SCHEDULE = 11,         /* stage-1 work split of the register pipelines (stage depth 2, 3):
                                         0 = static, warp w takes queue entries w, w + W, ...;
                                         1 = on levels with at least 16 queue entries per warp, static
                                         for the first 7/8 of the queue, then warps take chunks of the
                                         rest from a per-level counter, sized (entries left) /
                                         (2 x warps) within [2 x unroll, 64] (guided); else as 0 (default) */
+    BLEST_OPT_MS_PULL = 12,          /* multi-source pull: BLEST_PULL_POPC (default) ORs the frontier words
+                                        the masks select on the CUDA cores; BLEST_PULL_MMA computes the
+                                        same Boolean product with m16n8k128 b1 AND+POPC tensor-core MMAs */
+    BLEST_OPT_MS_CHUNK = 13,         /* sources per multi-source launch (the k-tile): 64, 128 or 256
+                                        (default); a call with more sources runs several launches */
+    BLEST_OPT_MS_BLOCKS_PER_SM = 14  /* multi-source persistent-grid blocks per SM; 0 (default) = the
+                                        value of BLEST_OPT_BLOCKS_PER_SM (0 = as many as fit) */
 } blest_option;
 
 /* Creation parameters; pass NULL to blest_graph_create_ex for the defaults. */
@@ -340,6 +347,26 @@ typedef struct {
  * SM, prefetch depth, layout, schedule).  out may be NULL.
  * Errors: INVALID_ARG (k < 1, bad source), TIMEOUT, INTERNAL, CUDA. */
 blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, blest_tune_result* out);
+
+/* Result of blest_autotune_msbfs. */
+typedef struct {
+    int32_t pull;                /* BLEST_OPT_MS_PULL kept */
+    int32_t chunk;               /* BLEST_OPT_MS_CHUNK kept (sources per launch) */
+    int32_t blocks_per_sm;       /* BLEST_OPT_MS_BLOCKS_PER_SM kept (0 = as many as fit) */
+    int32_t candidates;          /* variants timed */
+    double  best_ms;             /* device time of one call over all k sources, kept variant */
+    double  popc_ms;             /* best time with the CUDA-core pull */
+    double  mma_ms;              /* best time with the tensor-core pull */
+} blest_ms_tune_result;
+
+/* Time multi-source traversal variants on one call over the k host sources
+ * srcs[0..k) (Section 2's multi-source form) with CUDA events, each variant
+ * after one untimed pass, and keep the fastest as the handle's options: pull
+ * back-end (CUDA-core OR or b1 tensor-core MMA), sources per launch (64, 128,
+ * 256; only sizes that change the launches of k sources) and blocks per SM.
+ * Allocates a k x n device level buffer for the duration of the call.  out may
+ * be NULL.  Errors: INVALID_ARG (k < 1, bad source), OOM, TIMEOUT, INTERNAL, CUDA. */
+blest_status blest_autotune_msbfs(blest_handle h, const int32_t* srcs, int32_t k, blest_ms_tune_result* out);
 
 /* ----------------------------------------------------------------- export */
 

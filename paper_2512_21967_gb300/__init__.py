@@ -28,7 +28,8 @@ __all__ = [
     "blest_msbfs_device", "blest_bfs_multiroot_device", "blest_sync", "blest_get_run_info", "blest_get_level_times",
     "blest_get_level_arrivals", "blest_distance_stats", "blest_graph_save", "blest_graph_load",
     "blest_export",
-    "blest_autotune", "blest_export_size", "blest_compute_order", "blest_is_social", "blest_debug_pull",
+    "blest_autotune", "blest_autotune_msbfs", "blest_export_size", "blest_compute_order", "blest_is_social",
+    "blest_debug_pull",
     "blest_bfs_static_scratch", "blest_server_create", "blest_server_submit", "blest_server_wait",
     "blest_server_pause", "blest_server_get_stats", "blest_server_destroy", "lib", "EXPORTED_SYMBOLS",
 ]
@@ -45,6 +46,7 @@ BLEST_OPT_UPDATE, BLEST_OPT_PULL, BLEST_OPT_BLOCKS_PER_SM, BLEST_OPT_BARRIER_TIM
 BLEST_OPT_RECORD_LEVELS, BLEST_OPT_UNROLL, BLEST_OPT_TEST_PHANTOM_BLOCK = 4, 5, 6
 BLEST_OPT_VISITED_FILTER, BLEST_OPT_MIN_BLOCKS, BLEST_OPT_STAGE_DEPTH, BLEST_OPT_LAYOUT = 7, 8, 9, 10
 BLEST_OPT_SCHEDULE = 11
+BLEST_OPT_MS_PULL, BLEST_OPT_MS_CHUNK, BLEST_OPT_MS_BLOCKS_PER_SM = 12, 13, 14
 BLEST_ARRAY_REAL_PTRS, BLEST_ARRAY_VIRTUAL_TO_REAL, BLEST_ARRAY_ROW_IDS = 0, 1, 2
 BLEST_ARRAY_MASKS, BLEST_ARRAY_NEW_ID, BLEST_ARRAY_VSS_COUNT = 3, 4, 5
 BLEST_ARRAY_COMPACT_OFFSETS, BLEST_ARRAY_COMPACT_ROWS, BLEST_ARRAY_COMPACT_MASKS = 6, 7, 8
@@ -55,7 +57,7 @@ EXPORTED_SYMBOLS = [
     "blest_batch_graph_capture",
     "blest_batch_graph_launch", "blest_bfs_device", "blest_msbfs_device", "blest_bfs_multiroot_device", "blest_sync",
     "blest_get_run_info", "blest_get_level_times", "blest_get_level_arrivals", "blest_distance_stats", "blest_graph_save", "blest_graph_load",
-    "blest_autotune",
+    "blest_autotune", "blest_autotune_msbfs",
     "blest_export_size", "blest_export", "blest_compute_order", "blest_is_social", "blest_debug_pull",
     "blest_server_create", "blest_server_submit", "blest_server_wait", "blest_server_pause", "blest_server_get_stats",
     "blest_server_destroy", "blest_bfs_static_scratch", "blest_status_string", "blest_last_error",
@@ -91,6 +93,12 @@ class TuneResult(ctypes.Structure):
                 ("min_blocks", ctypes.c_int32), ("visited_filter", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("stage_depth", ctypes.c_int32), ("layout", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_double), ("rule_ms", ctypes.c_double)]
+
+
+class MsTuneResult(ctypes.Structure):
+    _fields_ = [("pull", ctypes.c_int32), ("chunk", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_double), ("popc_ms", ctypes.c_double),
+                ("mma_ms", ctypes.c_double)]
 
 
 class ServerParams(ctypes.Structure):
@@ -146,6 +154,7 @@ def lib():
             "blest_sync": (ctypes.c_int, [_vp]),
             "blest_get_run_info": (ctypes.c_int, [_vp, ctypes.POINTER(RunInfo), _i32p, ctypes.c_int32]),
             "blest_autotune": (ctypes.c_int, [_vp, _i32p, ctypes.c_int32, ctypes.POINTER(TuneResult)]),
+            "blest_autotune_msbfs": (ctypes.c_int, [_vp, _i32p, ctypes.c_int32, ctypes.POINTER(MsTuneResult)]),
             "blest_get_level_times": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32]),
             "blest_get_level_arrivals": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64),
                                                         ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32]),
@@ -371,6 +380,13 @@ def blest_autotune(h: int, srcs) -> dict:
     s = _i32(srcs)
     r = TuneResult()
     _check(lib().blest_autotune(h, _ptr(s), len(s), ctypes.byref(r)), "blest_autotune")
+    return {f: getattr(r, f) for f, _ in r._fields_}
+
+
+def blest_autotune_msbfs(h: int, srcs) -> dict:
+    s = _i32(srcs)
+    r = MsTuneResult()
+    _check(lib().blest_autotune_msbfs(h, _ptr(s), len(s), ctypes.byref(r)), "blest_autotune_msbfs")
     return {f: getattr(r, f) for f, _ in r._fields_}
 
 

@@ -101,6 +101,9 @@ struct blest_graph {
     // options
     int update_opt = BLEST_UPDATE_AUTO;
     int pull = BLEST_PULL_POPC;
+    int ms_pull = BLEST_PULL_POPC;       // multi-source pull back-end
+    int ms_chunk = blest::kMsbfsChunk;   // sources per multi-source launch
+    int ms_blocks_per_sm = 0;            // 0 = blocks_per_sm
     int blocks_per_sm = 0;
     int64_t timeout_us = 2000000;
     int record = 0;
@@ -839,6 +842,18 @@ blest_status blest_set_option(blest_handle h, int32_t key, int64_t value) {
             if (value != 0 && value != 1) break;
             h->phantom = (int)value;
             return BLEST_OK;
+        case BLEST_OPT_MS_PULL:
+            if (value != BLEST_PULL_POPC && value != BLEST_PULL_MMA) break;
+            h->ms_pull = (int)value;
+            return BLEST_OK;
+        case BLEST_OPT_MS_CHUNK:
+            if (value != 64 && value != 128 && value != 256) break;
+            h->ms_chunk = (int)value;
+            return BLEST_OK;
+        case BLEST_OPT_MS_BLOCKS_PER_SM:
+            if (value < 0 || value > 64) break;
+            h->ms_blocks_per_sm = (int)value;
+            return BLEST_OK;
         default:
             return fail(BLEST_ERR_INVALID_ARG, "unknown option key");
     }
@@ -1037,17 +1052,19 @@ blest_status blest_msbfs_device(blest_handle h, const int32_t* srcs, int32_t k, 
     c.new_id = h->d_new_id;
     c.ctrl = h->d_ctrl;
     c.sms = h->sms;
-    c.blocks_per_sm = h->blocks_per_sm;
+    c.blocks_per_sm = h->ms_blocks_per_sm ? h->ms_blocks_per_sm : h->blocks_per_sm;
     c.timeout_ns = (uint64_t)h->timeout_us * 1000ull;
     c.phantom = h->phantom ? 1u : 0u;
     c.level_sizes = h->record ? h->d_level_sizes : nullptr;
     c.level_cap = kLevelRecordCap;
+    c.pull = h->ms_pull;
+    c.chunk = h->ms_chunk;
     const char* err = nullptr;
     int rc = blest::run_msbfs(h->ms, c, roots, d_levels, st, &err);
     if (rc) return fail((blest_status)rc, std::string("msbfs: ") + (err ? err : "?"));
     h->last_stream = st;
     h->info.update = BLEST_UPDATE_LAZY;
-    h->info.pull = BLEST_PULL_POPC;
+    h->info.pull = h->ms_pull;
     h->info.recorded = -1;
     return BLEST_OK;
 }
@@ -1131,6 +1148,64 @@ blest_status blest_get_run_info(blest_handle h, blest_run_info* info, int32_t* q
         int32_t m = std::min(cap, h->info.recorded);
         e = cudaMemcpy(queue_sizes, h->d_level_sizes, sizeof(int32_t) * (size_t)m, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "read level record");
+    }
+    return BLEST_OK;
+}
+
+blest_status blest_autotune_msbfs(blest_handle h, const int32_t* srcs, int32_t k, blest_ms_tune_result* out) {
+    if (!h) return fail(BLEST_ERR_INVALID_ARG, "NULL handle");
+    if (k < 1 || !srcs) return fail(BLEST_ERR_INVALID_ARG, "autotune needs at least one source");
+    if (h->n == 0) return fail(BLEST_ERR_INVALID_ARG, "empty graph");
+    std::vector<int32_t> roots;
+    blest_status s = map_sources(h, srcs, k, roots);
+    if (s) return s;
+    // launch sizes that give different launches for k sources
+    std::vector<int> chunks{blest::kMsbfsChunk};
+    if (k > 64) chunks.push_back(64);
+    if (k > 128) chunks.push_back(128);
+    int32_t* d_out = nullptr;
+    cudaError_t e = cudaMalloc(&d_out, sizeof(int32_t) * (size_t)k * (size_t)h->n);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(autotune levels)");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaFree(d_out);
+        return cuda_fail(e, "cudaEventCreate");
+    }
+    const int saved_pull = h->ms_pull, saved_chunk = h->ms_chunk, saved_bps = h->ms_blocks_per_sm;
+    double best = 1e300, best_pull[2] = {-1.0, -1.0};
+    int bp = saved_pull, bc = saved_chunk, bb = saved_bps, timed = 0;
+    for (int pull : {BLEST_PULL_POPC, BLEST_PULL_MMA})
+        for (int chunk : chunks)
+            for (int bps : {0, 1, 2}) {   // blocks per SM above what fits run as many as fit
+                if (s) break;
+                h->ms_pull = pull;
+                h->ms_chunk = chunk;
+                h->ms_blocks_per_sm = bps;
+                for (int pass = 0; pass < 2 && !s; ++pass) {
+                    if (pass == 1) cudaEventRecord(e0, h->stream);
+                    s = blest_msbfs_device(h, srcs, k, d_out, h->stream);
+                }
+                if (s) break;
+                cudaEventRecord(e1, h->stream);
+                if ((s = sync_status(h)) != BLEST_OK) break;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ++timed;
+                if (best_pull[pull] < 0 || ms < best_pull[pull]) best_pull[pull] = ms;
+                if (ms < best) { best = ms; bp = pull; bc = chunk; bb = bps; }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d_out);
+    if (s) {
+        h->ms_pull = saved_pull; h->ms_chunk = saved_chunk; h->ms_blocks_per_sm = saved_bps;
+        return s;
+    }
+    h->ms_pull = bp; h->ms_chunk = bc; h->ms_blocks_per_sm = bb;
+    if (out) {
+        out->pull = bp; out->chunk = bc; out->blocks_per_sm = bb; out->candidates = timed;
+        out->best_ms = best; out->popc_ms = best_pull[0]; out->mma_ms = best_pull[1];
     }
     return BLEST_OK;
 }

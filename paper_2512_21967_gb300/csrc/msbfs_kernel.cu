@@ -17,9 +17,11 @@
 // writes them one vertex at a time across the warp, and a final warp-level
 // transpose turns them into the source-major output in original ids, so that
 // neither side gathers one 4-byte entry per memory sector.
-// The tensor-core form of this product would need the 8-bit masks unpacked to
-// an f16/b1 operand per VSS; with K = 8 columns per slice set the work is
-// memory-bound, so it stays on the CUDA cores.
+// Two back-ends compute the pull.  PULL 0 (default) ORs the selected frontier
+// words on the CUDA cores.  PULL 1 runs the same product as b1 AND+POPC
+// tensor-core MMAs (m16n8k128): VSS slots along M, sources along N, the slice
+// set's 8 columns along K, so a VSS of k sources takes k MMAs (for k <= 64;
+// 64 per word of 64 sources) and its counts are turned back into hit bits.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -203,9 +205,63 @@ __device__ __forceinline__ MsTile<W> ms_load_tile(const MsArgs& a, unsigned long
     return t;
 }
 
+// The tensor-core product of one VSS and one 64-source word w of its slice set's
+// frontier tile: y[q] = the sources (bits) reaching this lane's sub-slot q.
+//   M (16 rows per MMA, 8 MMA row tiles): slot (tile m, row r) is sub-slot
+//     2 (m / 4) + r / 8 of lane 4 (r % 8) + m % 4, so an MMA group's rows are the
+//     sub-slots of its own 4 lanes and the results come back to their owners;
+//   N (8 per MMA, 8 column tiles): source 64 w + 8 n + c;
+//   K (bits 0..7 of the 128; the rest zero): the slice set's 8 columns.
+// D[r][c] = popc(mask byte of slot r & column bits of source c) > 0 is the hit.
+// Fragments (m16n8k128, b1): lane 4 g + t holds A rows g and g + 8 and B column
+// g, each over K bits 32 t .. 32 t + 31 (so only t = 0 carries data), and D
+// rows g and g + 8 at columns 2 t, 2 t + 1.
+template <int W>
+__device__ __forceinline__ void ms_mma_word(const MsTile<W>& t, int lane, int w, unsigned long long (&y)[4][W]) {
+    const int g = lane >> 2, tq = lane & 3;
+    // column bits of sources 64 w + 8 n + g, byte n: a transpose of the 8 x 64 tile
+    unsigned long long bt = 0ull;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const unsigned long long x = __shfl_sync(0xffffffffu, t.fw, j * W + w);
+        bt |= ((x >> g) & 0x0101010101010101ull) << j;
+    }
+    uint32_t mw[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) mw[i] = __shfl_sync(0xffffffffu, t.m, 4 * g + i);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const uint32_t a0 = tq == 0 ? (mw[m & 3] >> (8 * (2 * (m >> 2)))) & 0xFFu : 0u;
+        const uint32_t a1 = tq == 0 ? (mw[m & 3] >> (8 * (2 * (m >> 2) + 1))) & 0xFFu : 0u;
+        unsigned long long pg = 0ull, pg8 = 0ull;   // this lane's columns of rows g and g + 8
+#pragma unroll
+        for (int n = 0; n < 8; ++n) {
+            const uint32_t b0 = tq == 0 ? (uint32_t)(bt >> (8 * n)) & 0xFFu : 0u;
+            int d0, d1, d2, d3;
+            asm volatile(
+                "mma.sync.aligned.m16n8k128.row.col.s32.b1.b1.s32.and.popc {%0,%1,%2,%3}, {%4,%5}, {%6}, "
+                "{%7,%7,%7,%7};\n"
+                : "=r"(d0), "=r"(d1), "=r"(d2), "=r"(d3)
+                : "r"(a0), "r"(a1), "r"(b0), "r"(0));
+            const int sh = 8 * n + 2 * tq;
+            pg |= (unsigned long long)((d0 > 0 ? 1u : 0u) | (d1 > 0 ? 2u : 0u)) << sh;
+            pg8 |= (unsigned long long)((d2 > 0 ? 1u : 0u) | (d3 > 0 ? 2u : 0u)) << sh;
+        }
+        // the 4 lanes of the group hold 16 of the 64 columns each
+        pg |= __shfl_xor_sync(0xffffffffu, pg, 1);
+        pg |= __shfl_xor_sync(0xffffffffu, pg, 2);
+        pg8 |= __shfl_xor_sync(0xffffffffu, pg8, 1);
+        pg8 |= __shfl_xor_sync(0xffffffffu, pg8, 2);
+        if (tq == (m & 3)) {   // the owner of slots (m, g) and (m, g + 8)
+            y[2 * (m >> 2)][w] = pg;
+            y[2 * (m >> 2) + 1][w] = pg8;
+        }
+    }
+}
+
 // y_u |= OR over the columns j of u's mask of the frontier word X[8s + j], then
 // the returnless marks of the fresh bits in V_next (Algorithm 3, k bits at a time).
-template <int W>
+template <int W, int PULL>
 __device__ __forceinline__ void ms_pull_tile(const MsArgs& a, const MsTile<W>& t, int lane, bool sparse) {
     const unsigned int nzb = __ballot_sync(0xffffffffu, t.fw != 0ull);
     uint32_t alpha = 0;
@@ -213,21 +269,26 @@ __device__ __forceinline__ void ms_pull_tile(const MsArgs& a, const MsTile<W>& t
     for (int j = 0; j < 8; ++j)
         if ((nzb >> (j * W)) & ((1u << W) - 1u)) alpha |= 1u << j;
     if (!alpha) return;   // warp-uniform: no column of this slice set is in the frontier
-    const uint32_t m = t.m & (alpha * 0x01010101u);
     unsigned long long y[4][W];
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
         for (int w = 0; w < W; ++w) y[q][w] = 0ull;
+    if (PULL == 1) {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        if (!((alpha >> j) & 1u)) continue;   // warp-uniform
+        for (int w = 0; w < W; ++w) ms_mma_word<W>(t, lane, w, y);
+    } else {
+        const uint32_t m = t.m & (alpha * 0x01010101u);
 #pragma unroll
-        for (int w = 0; w < W; ++w) {
-            const unsigned long long v = __shfl_sync(0xffffffffu, t.fw, j * W + w);
+        for (int j = 0; j < 8; ++j) {
+            if (!((alpha >> j) & 1u)) continue;   // warp-uniform
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if ((m >> (8 * q + j)) & 1u) y[q][w] |= v;
+            for (int w = 0; w < W; ++w) {
+                const unsigned long long v = __shfl_sync(0xffffffffu, t.fw, j * W + w);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if ((m >> (8 * q + j)) & 1u) y[q][w] |= v;
+            }
         }
     }
     const int r4[4] = {t.r.x, t.r.y, t.r.z, t.r.w};
@@ -246,7 +307,7 @@ __device__ __forceinline__ void ms_pull_tile(const MsArgs& a, const MsTile<W>& t
         }
 }
 
-template <int W>
+template <int W, int PULL>
 __device__ __forceinline__ void ms_body(const MsArgs& a) {
     const int lane = threadIdx.x & 31;
     const int gtid = (int)(blockIdx.x * blockDim.x + threadIdx.x);
@@ -288,7 +349,7 @@ __device__ __forceinline__ void ms_body(const MsArgs& a) {
         for (; p < qn; p += nw) {
             const unsigned long long e_after = p + 2u * nw < qn ? ld_cg(&Qin[p + 2u * nw]) : kNoEntry;
             const MsTile<W> t_next = ms_load_tile<W>(a, e_next, lane, pol);
-            ms_pull_tile<W>(a, t, lane, sparse);
+            ms_pull_tile<W, PULL>(a, t, lane, sparse);
             t = t_next;
             e_next = e_after;
         }
@@ -331,9 +392,9 @@ __device__ __forceinline__ void ms_body(const MsArgs& a) {
     }
 }
 
-template <int W>
+template <int W, int PULL>
 __global__ void __launch_bounds__(kMsBlock) msbfs_kernel(MsArgs a) {
-    ms_body<W>(a);
+    ms_body<W, PULL>(a);
     fold_status(a.ctrl);
 }
 
@@ -368,9 +429,10 @@ int run_msbfs(MsbfsState& s, const MsbfsLaunchCommon& c, const std::vector<int32
     if (k_all == 0 || c.n == 0) return 0;
     cudaError_t e = cudaSuccess;
     const bool own = s.caller_owned;
-    for (int64_t i0 = 0; i0 < k_all; i0 += kMsbfsChunk) {
-        const int k = (int)std::min<int64_t>(kMsbfsChunk, k_all - i0);
-        const int W = msbfs_words(k);
+    const int chunk = c.chunk == 64 || c.chunk == 128 ? c.chunk : kMsbfsChunk;
+    for (int64_t i0 = 0; i0 < k_all; i0 += chunk) {
+        const int k = (int)std::min<int64_t>(chunk, k_all - i0);
+        const int W = msbfs_words(k, chunk);
         const int64_t words = (int64_t)c.n * W;
         int64_t cap_v = s.words_cap, cap_n = s.words_cap, cap_f = s.words_cap;
         if ((e = grow(s.vcur, cap_v, words, own)) != cudaSuccess) break;
@@ -379,7 +441,7 @@ int run_msbfs(MsbfsState& s, const MsbfsLaunchCommon& c, const std::vector<int32
         s.words_cap = std::min(cap_v, std::min(cap_n, cap_f));
         if ((e = grow(s.Q, s.qcap, std::max<int64_t>(c.nvss, 1), own, 3)) != cudaSuccess) break;
         const int32_t kst = (k + 7) & ~7;
-        if ((e = grow(s.lint, s.lint_cap, msbfs_level_entries(c.n, k), own)) != cudaSuccess) break;
+        if ((e = grow(s.lint, s.lint_cap, msbfs_level_entries(c.n, k, chunk), own)) != cudaSuccess) break;
         if ((e = grow(s.roots, s.roots_cap, k, own)) != cudaSuccess) break;
         const int64_t dwords = ((int64_t)c.nss + 31) / 32;
         if ((e = grow(s.dirty, s.dirty_cap, dwords, own)) != cudaSuccess) break;
@@ -411,7 +473,9 @@ int run_msbfs(MsbfsState& s, const MsbfsLaunchCommon& c, const std::vector<int32
         a.level_cap = c.level_cap;
         a.timeout_ns = c.timeout_ns;
         a.phantom = c.phantom;
-        void* kfn = W == 1 ? (void*)&msbfs_kernel<1> : (W == 2 ? (void*)&msbfs_kernel<2> : (void*)&msbfs_kernel<4>);
+        void* kfn = c.pull == 1
+                        ? (W == 1 ? (void*)&msbfs_kernel<1, 1> : (W == 2 ? (void*)&msbfs_kernel<2, 1> : (void*)&msbfs_kernel<4, 1>))
+                        : (W == 1 ? (void*)&msbfs_kernel<1, 0> : (W == 2 ? (void*)&msbfs_kernel<2, 0> : (void*)&msbfs_kernel<4, 0>));
         int nb = 0;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn, kMsBlock, 0)) != cudaSuccess) break;
         if (nb <= 0) { *err = "msbfs kernel cannot be resident"; return 5; }

@@ -8,18 +8,19 @@
 
 namespace blest {
 
-constexpr int kMsbfsChunk = 256;   // sources per launch
+constexpr int kMsbfsChunk = 256;   // most sources per launch (the default launch size)
 
-// 64-bit words per vertex of each bit matrix for a launch of k sources.
-inline int msbfs_words(int64_t k) {
-    const int64_t kc = std::min<int64_t>(k, kMsbfsChunk);
+// 64-bit words per vertex of each bit matrix for a launch of k sources, with
+// launches of at most `chunk` sources (64, 128 or 256).
+inline int msbfs_words(int64_t k, int chunk = kMsbfsChunk) {
+    const int64_t kc = std::min<int64_t>(k, chunk);
     return kc <= 64 ? 1 : (kc <= 128 ? 2 : 4);
 }
 
 // int32 entries of the vertex-major internal level buffer for k sources: n rows
-// of the largest chunk's source count rounded up to a multiple of 8.
-inline int64_t msbfs_level_entries(int32_t n, int64_t k) {
-    const int64_t kc = std::min<int64_t>(k, kMsbfsChunk);
+// of the largest launch's source count rounded up to a multiple of 8.
+inline int64_t msbfs_level_entries(int32_t n, int64_t k, int chunk = kMsbfsChunk) {
+    const int64_t kc = std::min<int64_t>(k, chunk);
     return ((kc + 7) & ~int64_t(7)) * (int64_t)n;
 }
 
@@ -56,10 +57,12 @@ struct MsbfsLaunchCommon {
     unsigned int phantom = 0;
     int32_t* level_sizes = nullptr;
     int32_t level_cap = 0;
+    int pull = 0;                       // 0 CUDA-core OR of frontier words, 1 b1 tensor-core MMAs
+    int chunk = kMsbfsChunk;            // sources per launch: 64, 128 or 256
 };
 
-// Runs k = roots.size() traversals (sources already in BVSS ids) in batches of
-// at most 256 sources, writing out[i*n + v] in original ids.  Returns a
+// Runs k = roots.size() traversals (sources already in BVSS ids) in launches of
+// at most c.chunk sources, writing out[i*n + v] in original ids.  Returns a
 // blest_status code (device-side status is folded into the sticky word).
 int run_msbfs(MsbfsState& s, const MsbfsLaunchCommon& c, const std::vector<int32_t>& roots, int32_t* d_out,
               cudaStream_t st, const char** err);

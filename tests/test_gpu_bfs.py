@@ -244,6 +244,42 @@ def test_msbfs_matches_k_oracle_runs(gpu, k):
             blest.blest_destroy(h)
 
 
+@pytest.mark.parametrize("pull", [blest.BLEST_PULL_POPC, blest.BLEST_PULL_MMA])
+@pytest.mark.parametrize("chunk", [64, 128, 256])
+def test_msbfs_pull_backends_and_launch_sizes(gpu, pull, chunk):
+    """Both multi-source pull back-ends (CUDA-core OR, b1 tensor-core MMA) and every
+    launch size give the oracle's levels, for source counts across word and launch
+    boundaries, on a power-law graph and on a ragged grid."""
+    g = synth.rmat_graph(11, 16, seed=5)
+    gg, _ = synth.grid_graph(37, 0.9, seed=6)
+    for graph, order in ((g, blest.BLEST_ORDER_COMPRESS), (gg, blest.BLEST_ORDER_BANDWIDTH)):
+        h = blest.blest_graph_create(graph.n, graph.row_ptr, graph.col_idx, order)
+        try:
+            blest.blest_set_option(h, blest.BLEST_OPT_MS_PULL, pull)
+            blest.blest_set_option(h, blest.BLEST_OPT_MS_CHUNK, chunk)
+            for k in (3, 64, 65, 130, 300):
+                srcs = synth.pick_sources(graph, k, seed=31 + k)
+                exp = oracle.msbfs_levels(graph.n, graph.row_ptr, graph.col_idx, srcs, threads=8)
+                assert np.array_equal(blest.blest_msbfs(h, srcs), exp), (k, pull, chunk)
+        finally:
+            blest.blest_destroy(h)
+
+
+def test_msbfs_autotune_keeps_levels_exact(gpu):
+    g = synth.rmat_graph(12, 16, seed=9)
+    srcs = synth.pick_sources(g, 150, seed=3)
+    exp = oracle.msbfs_levels(g.n, g.row_ptr, g.col_idx, srcs, threads=8)
+    h = blest.blest_graph_create(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_COMPRESS)
+    try:
+        r = blest.blest_autotune_msbfs(h, srcs)
+        assert r["candidates"] == 2 * 3 * 3                 # 2 back-ends x 3 launch sizes x 3 grid sizes
+        assert r["popc_ms"] > 0 and r["mma_ms"] > 0 and r["best_ms"] == min(r["popc_ms"], r["mma_ms"])
+        assert r["chunk"] in (64, 128, 256) and r["pull"] in (blest.BLEST_PULL_POPC, blest.BLEST_PULL_MMA)
+        assert np.array_equal(blest.blest_msbfs(h, srcs), exp)
+    finally:
+        blest.blest_destroy(h)
+
+
 def test_msbfs_grid_and_isolated(gpu):
     g, srcs = synth.grid_workload(96, 20, seed_graph=4, seed_src=9)
     srcs = np.concatenate([srcs, [int(np.argmin(g.degrees()))]]).astype(np.int32)
