@@ -502,7 +502,10 @@ def run_ours_msbfs(args, torch, blest, h, g, srcs, k, dev, stream, flush, st, t_
     out = torch.empty((k, n), dtype=torch.int32, device=dev)
     deg_t = torch.from_numpy(g.degrees()).to(dev)
     ms_tune = None
-    if not args.no_tune:
+    if args.ms_pull != "auto":
+        blest.blest_set_option(h, blest.BLEST_OPT_MS_PULL,
+                               blest.BLEST_PULL_MMA if args.ms_pull == "mma" else blest.BLEST_PULL_POPC)
+    elif not args.no_tune:
         # untimed: pull back-end (CUDA-core / tensor-core), sources per launch, blocks per SM
         t0 = time.time()
         ms_tune = blest.blest_autotune_msbfs(h, srcs[:k])
@@ -594,6 +597,13 @@ def run_ours_batch(args, torch, blest, dev, rank, world):
                                blest.BLEST_UPDATE_EAGER if args.update == "eager" else blest.BLEST_UPDATE_LAZY)
     blest.blest_set_option(h, blest.BLEST_OPT_STAGE_DEPTH, args.depth)
     n = sum(g.n for g in graphs)
+    tune = None
+    if not args.no_tune:
+        # untimed: every kernel variant timed as the one multi-root launch the batch runs
+        offs = np.concatenate([[0], np.cumsum([g.n for g in graphs])[:-1]]).astype(np.int64)
+        t0 = time.time()
+        tune = blest.blest_autotune_multiroot(h, (offs + np.asarray(srcs, np.int64)).astype(np.int32))
+        tune["seconds"] = round(time.time() - t0, 2)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -638,7 +648,8 @@ def run_ours_batch(args, torch, blest, dev, rank, world):
                 "config": {"workload": f"{len(graphs)} graphs of uneven size (R-MAT scale 10..18, grids 64..1024), "
                                        "one source each, one persistent launch replayed as a CUDA graph",
                            "n": n, "directed_edges": int(sum(g.nnz for g in graphs)), "graphs": len(graphs),
-                           "levels": info["levels"], "update": ["auto", "eager", "lazy"][info["update"]]},
+                           "levels": info["levels"], "update": ["auto", "eager", "lazy"][info["update"]],
+                           "autotune": tune},
                 "gpu_launches": args.steps, "clocks": clocks,
                 "preprocess_s": {"generate": round(t_gen, 2), "create_total": round(t_create, 2),
                                  "order": round(st["order_seconds"], 2)}}
@@ -714,6 +725,10 @@ def run_ours_serve(args, torch, blest, dev, rank, world):
         stream = synth_query_stream(args.queries, len(graphs), rate, 55, pools)
         row = {"rate_qps": rate, "queries": len(stream)}
         for mode in ("batched", "one_at_a_time"):
+            if mode == "one_at_a_time":
+                # the same stream's first queries: one query per launch saturates far below
+                # these rates, so the full stream would take many minutes per rate
+                stream = stream[:min(len(stream), args.oaat_queries)]
             if mode == "batched":
                 srv = blest.blest_server_create(handles, memory_cap_bytes=40 << 30, max_batch_sources=64,
                                                 max_inflight=4, blocks_per_sm=1)
@@ -725,7 +740,7 @@ def run_ours_serve(args, torch, blest, dev, rank, world):
                 st = blest.blest_server_get_stats(srv)
             finally:
                 blest.blest_server_destroy(srv)
-            row[mode] = {"p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
+            row[mode] = {"queries": len(stream), "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
                          "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
                          "throughput_qps": round(len(stream) / wall, 2), "launches": st["launches"],
                          "mean_sources_per_launch": round(st["sources_launched"] / max(1, st["launches"]), 2),
@@ -945,6 +960,8 @@ def main():
     ap.add_argument("--window", type=int, default=4096)
     ap.add_argument("--update", choices=["auto", "eager", "lazy"], default="auto")
     ap.add_argument("--pull", choices=["popc", "mma"], default="popc")
+    ap.add_argument("--ms-pull", choices=["auto", "popc", "mma"], default="auto",
+                    help="multi-source pull back-end; auto = the multi-source autotuner's choice")
     ap.add_argument("--unroll", type=int, default=2)
     ap.add_argument("--minb", type=int, default=2)
     ap.add_argument("--filter", type=int, default=3,
@@ -955,6 +972,8 @@ def main():
                     help="lazy stage-1 prefetch: 0 none, 2 register double buffer, 4 or 8 TMA ring stages")
     ap.add_argument("--queries", type=int, default=2000, help="serving: queries per arrival rate")
     ap.add_argument("--rates", default="100,400,1600", help="serving: arrival rates in queries/s")
+    ap.add_argument("--oaat-queries", type=int, default=2000,
+                    help="serving: queries per rate for the one-query-per-launch comparison")
     ap.add_argument("--windows", default="0,8,64,512,4096,16384,65536,g4096",
                     help="window sweep: JaccardWithWindows windows (0 = no reordering; g<w> = Gorder pre-pass)")
     ap.add_argument("--sched", type=int, default=0, help="stage-1 schedule of depth 2: 0 static, 1 static + dynamic tail")

@@ -348,6 +348,14 @@ typedef struct {
  * Errors: INVALID_ARG (k < 1, bad source), TIMEOUT, INTERNAL, CUDA. */
 blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, blest_tune_result* out);
 
+/* As blest_autotune, but every timing is ONE traversal from all k roots at once
+ * (the multi-root form: level = distance to the nearest root), which is the
+ * launch a batch handle runs for its graphs (blest_batch_bfs and the captured
+ * blest_batch_graph_launch; srcs are then union ids, one per graph).  best_ms
+ * and rule_ms are per multi-root traversal.  A batch handle captured before the
+ * call keeps the variant it was captured with: capture again afterwards. */
+blest_status blest_autotune_multiroot(blest_handle h, const int32_t* srcs, int32_t k, blest_tune_result* out);
+
 /* Result of blest_autotune_msbfs. */
 typedef struct {
     int32_t pull;                /* BLEST_OPT_MS_PULL kept */

@@ -28,7 +28,7 @@ __all__ = [
     "blest_msbfs_device", "blest_bfs_multiroot_device", "blest_sync", "blest_get_run_info", "blest_get_level_times",
     "blest_get_level_arrivals", "blest_distance_stats", "blest_graph_save", "blest_graph_load",
     "blest_export",
-    "blest_autotune", "blest_autotune_msbfs", "blest_export_size", "blest_compute_order", "blest_is_social",
+    "blest_autotune", "blest_autotune_msbfs", "blest_autotune_multiroot", "blest_export_size", "blest_compute_order", "blest_is_social",
     "blest_debug_pull",
     "blest_bfs_static_scratch", "blest_server_create", "blest_server_submit", "blest_server_wait",
     "blest_server_pause", "blest_server_get_stats", "blest_server_destroy", "lib", "EXPORTED_SYMBOLS",
@@ -57,7 +57,7 @@ EXPORTED_SYMBOLS = [
     "blest_batch_graph_capture",
     "blest_batch_graph_launch", "blest_bfs_device", "blest_msbfs_device", "blest_bfs_multiroot_device", "blest_sync",
     "blest_get_run_info", "blest_get_level_times", "blest_get_level_arrivals", "blest_distance_stats", "blest_graph_save", "blest_graph_load",
-    "blest_autotune", "blest_autotune_msbfs",
+    "blest_autotune", "blest_autotune_msbfs", "blest_autotune_multiroot",
     "blest_export_size", "blest_export", "blest_compute_order", "blest_is_social", "blest_debug_pull",
     "blest_server_create", "blest_server_submit", "blest_server_wait", "blest_server_pause", "blest_server_get_stats",
     "blest_server_destroy", "blest_bfs_static_scratch", "blest_status_string", "blest_last_error",
@@ -155,6 +155,7 @@ def lib():
             "blest_get_run_info": (ctypes.c_int, [_vp, ctypes.POINTER(RunInfo), _i32p, ctypes.c_int32]),
             "blest_autotune": (ctypes.c_int, [_vp, _i32p, ctypes.c_int32, ctypes.POINTER(TuneResult)]),
             "blest_autotune_msbfs": (ctypes.c_int, [_vp, _i32p, ctypes.c_int32, ctypes.POINTER(MsTuneResult)]),
+            "blest_autotune_multiroot": (ctypes.c_int, [_vp, _i32p, ctypes.c_int32, ctypes.POINTER(TuneResult)]),
             "blest_get_level_times": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32]),
             "blest_get_level_arrivals": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64),
                                                         ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32]),
@@ -380,6 +381,13 @@ def blest_autotune(h: int, srcs) -> dict:
     s = _i32(srcs)
     r = TuneResult()
     _check(lib().blest_autotune(h, _ptr(s), len(s), ctypes.byref(r)), "blest_autotune")
+    return {f: getattr(r, f) for f, _ in r._fields_}
+
+
+def blest_autotune_multiroot(h: int, srcs) -> dict:
+    s = _i32(srcs)
+    r = TuneResult()
+    _check(lib().blest_autotune_multiroot(h, _ptr(s), len(s), ctypes.byref(r)), "blest_autotune_multiroot")
     return {f: getattr(r, f) for f, _ in r._fields_}
 
 

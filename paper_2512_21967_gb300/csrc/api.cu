@@ -1210,7 +1210,10 @@ blest_status blest_autotune_msbfs(blest_handle h, const int32_t* srcs, int32_t k
     return BLEST_OK;
 }
 
-blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, blest_tune_result* out) {
+// Shared by blest_autotune (k single-source traversals per timing) and
+// blest_autotune_multiroot (one traversal from all k roots per timing).
+static blest_status autotune_impl(blest_handle h, const int32_t* srcs, int32_t k, bool multiroot,
+                                  blest_tune_result* out) {
     if (!h) return fail(BLEST_ERR_INVALID_ARG, "NULL handle");
     if (k < 1 || !srcs) return fail(BLEST_ERR_INVALID_ARG, "autotune needs at least one source");
     if (h->n == 0) return fail(BLEST_ERR_INVALID_ARG, "empty graph");
@@ -1270,6 +1273,10 @@ blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, bles
         std::vector<int32_t> one(1);
         for (int pass = 0; pass < 2 && !s; ++pass) {
             if (pass == 1) cudaEventRecord(e0, h->stream);
+            if (multiroot) {
+                s = enqueue_traversal(h, roots, h->d_out, h->stream);
+                continue;
+            }
             for (int32_t i = 0; i < k && !s; ++i) {
                 one[0] = roots[i];
                 s = enqueue_traversal(h, one, h->d_out, h->stream);
@@ -1281,7 +1288,7 @@ blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, bles
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         ++timed;
-        const double per = (double)ms / k;
+        const double per = multiroot ? (double)ms : (double)ms / k;
         if (per < best) { best = per; bestc = c; }
         return per;
     };
@@ -1321,6 +1328,14 @@ blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, bles
         out->best_ms = best; out->rule_ms = rule;
     }
     return BLEST_OK;
+}
+
+blest_status blest_autotune(blest_handle h, const int32_t* srcs, int32_t k, blest_tune_result* out) {
+    return autotune_impl(h, srcs, k, false, out);
+}
+
+blest_status blest_autotune_multiroot(blest_handle h, const int32_t* srcs, int32_t k, blest_tune_result* out) {
+    return autotune_impl(h, srcs, k, true, out);
 }
 
 blest_status blest_get_level_arrivals(blest_handle h, int32_t phase, uint64_t* first_ns, uint64_t* last_ns,

@@ -351,6 +351,31 @@ def test_batch_of_uneven_graphs(gpu):
         blest.blest_destroy(h)
 
 
+def test_batch_multiroot_autotune_keeps_levels_exact(gpu):
+    """The multi-root autotuner times variants of the batch's own launch (all
+    graphs' roots at once) and the kept variant gives every graph its levels."""
+    graphs, srcs, orders = [], [], []
+    for i in range(10):
+        if i % 2 == 0:
+            g = synth.rmat_graph(8 + i % 4, 16, seed=600 + i)
+            orders.append(blest.BLEST_ORDER_COMPRESS)
+        else:
+            g, _ = synth.grid_graph(20 + 7 * i, 0.9, seed=700 + i)
+            orders.append(blest.BLEST_ORDER_BANDWIDTH)
+        graphs.append(g)
+        srcs.append(int(synth.pick_sources(g, 1, seed=800 + i)[0]))
+    offs = np.concatenate([[0], np.cumsum([g.n for g in graphs])[:-1]])
+    h = blest.blest_batch_create([(g.n, g.row_ptr, g.col_idx) for g in graphs], orders)
+    try:
+        r = blest.blest_autotune_multiroot(h, (offs + np.asarray(srcs)).astype(np.int32))
+        assert r["candidates"] > 20 and r["best_ms"] > 0
+        got = blest.blest_batch_bfs(h, srcs)
+        for g, s, o in zip(graphs, srcs, offs):
+            assert np.array_equal(got[o:o + g.n], oracle.bfs_levels(g.n, g.row_ptr, g.col_idx, s))
+    finally:
+        blest.blest_destroy(h)
+
+
 @pytest.mark.parametrize("update", ["eager", "lazy"])
 def test_device_api_with_torch_stream(torch_cuda, update):
     """Device output into rows of a caller's tensor on the caller's stream
