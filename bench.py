@@ -236,9 +236,10 @@ def ms_traversal_bytes(levels_t, new_id_t, w_s_t, nvss_t, nss, n, torch):
       sweeps: level 0 and every processed level read V_next, V_curr and write the
         frontier (24 W B per vertex); a level whose queue has at most n/128 VSSs
         sweeps only the slice sets holding a newly reached vertex (8 vertices each);
-      levels: 4 B written and 4 B read back per (source, reached vertex), 4 B
-        written per (source, vertex) of the output, 8 W + 4 B per vertex read by
-        the final transpose (visited words, vertex order).
+      levels: 4 B written per (source, vertex) of the output, 8 W + 4 B per
+        vertex read by the final pass (visited words, vertex order).  How the
+        kernel keeps levels during the traversal (bit planes) is its own
+        overhead and is not counted.
     Returns (bytes, reached pairs)."""
     k_all = int(levels_t.shape[0])
     total, pairs_all = 0, 0
@@ -271,7 +272,7 @@ def ms_traversal_bytes(levels_t, new_id_t, w_s_t, nvss_t, nss, n, torch):
                     sweep += 24 * W * 8 * int(sets[l])
                 else:
                     sweep += 24 * W * n
-        total += stage1 + sweep + 8 * pairs + 4 * k * n + (8 * W + 4) * n
+        total += stage1 + sweep + 4 * k * n + (8 * W + 4) * n
         pairs_all += pairs
     return total, pairs_all
 
@@ -569,7 +570,8 @@ def run_ours_msbfs(args, torch, blest, h, g, srcs, k, dev, stream, flush, st, t_
                 "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                              "frac": round(achieved / hbm, 4), "peak_kind": peak_kind, "traffic": None,
                              "traffic_note": "no capture of this kernel revision",
-                             "kernel": "msbfs_kernel (one launch per call; the event pair also covers the "
+                             "kernel": "msbfs_kernel + msbfs_output_kernel (one traversal launch and one "
+                                       "output launch per 64-256 sources; the event pair also covers the "
                                        "call's clears and source upload)",
                              "bytes_per_launch": ms_bytes, "avg_launch_ms": round(ms / args.steps, 5)},
                 "cpu_baseline": cpu,

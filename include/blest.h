@@ -411,6 +411,48 @@ blest_status blest_compute_order(int32_t n, const int32_t* row_ptr, const int32_
  * negative blest_status on bad input. */
 int32_t blest_is_social(int32_t n, const int32_t* row_ptr, const int32_t* col_idx);
 
+/* ------------------------------------------------------ sharded traversal */
+
+/* One rank's share of a single-source BFS whose pull is split over `world` ranks
+ * (one GPU each) by slice set: rank r pulls only the queued VSSs of the slice
+ * sets s with s mod world = r.  Between the pull and the finalisation sweep of
+ * every level, the ranks combine their V_next words (the lazy marks of
+ * Algorithm 3) with a bitwise OR; every rank then runs the same sweep on the
+ * combined words, so all of them end with the full level array.  The paper
+ * names multi-GPU BFS as future work (Section 6); this is that exchange step,
+ * one n/32-word OR per level.  The caller owns the collective: an all-gather of
+ * every rank's words followed by blest_shard_merge, or any all-reduce with
+ * bitwise OR.  Every rank's handle holds the same graph in the same order.
+ *
+ * A traversal is: blest_shard_begin, then per level blest_shard_pull, the
+ * exchange, and blest_shard_finish, until finish reports *more == 0.  Steps are
+ * enqueued on `stream` (NULL = the handle's stream); finish waits for it.  The
+ * steps use the lazy update on the padded layout whatever the handle's
+ * options, and the handle runs no other traversal until finish reports the end.
+ *
+ * blest_shard_begin: src is an original id; d_levels (device int32[n]) receives
+ * the levels in original ids (-1 unreached) as the levels are finished, complete
+ * once *more == 0.  Runs level 0 (the root).  Errors: INVALID_ARG (rank outside
+ * [0, world), bad source, batch handle, empty graph), CUDA. */
+blest_status blest_shard_begin(blest_handle h, int32_t rank, int32_t world, int32_t src, int32_t* d_levels,
+                               void* stream);
+
+/* Stage 1 of the current level over this rank's queue; d_words (device
+ * uint32[ceil(n/32)]) receives the rank's V_next words (bit u % 32 of word u / 32
+ * = row u, in BVSS order, marked at this or an earlier level). */
+blest_status blest_shard_pull(blest_handle h, uint32_t* d_words, void* stream);
+
+/* d_dst[i] = OR over j < count of d_src[j * words + i] (device arrays): merges
+ * all-gathered word arrays.  Errors: INVALID_ARG, CUDA. */
+blest_status blest_shard_merge(uint32_t* d_dst, const uint32_t* d_src, int64_t words, int32_t count, void* stream);
+
+/* The level's finalisation sweep on d_merged (the OR of every rank's words):
+ * newly reached rows get the level, and the rank's own slice sets holding them
+ * are queued for the next level.  Waits for the stream; *more = 1 if the level
+ * reached a row (the traversal goes on), 0 when it is over.
+ * Errors: INVALID_ARG, TIMEOUT, INTERNAL, CUDA. */
+blest_status blest_shard_finish(blest_handle h, const uint32_t* d_merged, int32_t* more, void* stream);
+
 /* ---------------------------------------------------------------- testing */
 
 /* The stage-1 pull of one virtual slice set, on the device, for every tile:

@@ -28,7 +28,8 @@ __all__ = [
     "blest_msbfs_device", "blest_bfs_multiroot_device", "blest_sync", "blest_get_run_info", "blest_get_level_times",
     "blest_get_level_arrivals", "blest_distance_stats", "blest_graph_save", "blest_graph_load",
     "blest_export",
-    "blest_autotune", "blest_autotune_msbfs", "blest_autotune_multiroot", "blest_export_size", "blest_compute_order", "blest_is_social",
+    "blest_autotune", "blest_autotune_msbfs", "blest_autotune_multiroot", "blest_shard_begin", "blest_shard_pull",
+    "blest_shard_merge", "blest_shard_finish", "blest_export_size", "blest_compute_order", "blest_is_social",
     "blest_debug_pull",
     "blest_bfs_static_scratch", "blest_server_create", "blest_server_submit", "blest_server_wait",
     "blest_server_pause", "blest_server_get_stats", "blest_server_destroy", "lib", "EXPORTED_SYMBOLS",
@@ -57,7 +58,8 @@ EXPORTED_SYMBOLS = [
     "blest_batch_graph_capture",
     "blest_batch_graph_launch", "blest_bfs_device", "blest_msbfs_device", "blest_bfs_multiroot_device", "blest_sync",
     "blest_get_run_info", "blest_get_level_times", "blest_get_level_arrivals", "blest_distance_stats", "blest_graph_save", "blest_graph_load",
-    "blest_autotune", "blest_autotune_msbfs", "blest_autotune_multiroot",
+    "blest_autotune", "blest_autotune_msbfs", "blest_autotune_multiroot", "blest_shard_begin",
+    "blest_shard_pull", "blest_shard_merge", "blest_shard_finish",
     "blest_export_size", "blest_export", "blest_compute_order", "blest_is_social", "blest_debug_pull",
     "blest_server_create", "blest_server_submit", "blest_server_wait", "blest_server_pause", "blest_server_get_stats",
     "blest_server_destroy", "blest_bfs_static_scratch", "blest_status_string", "blest_last_error",
@@ -156,6 +158,10 @@ def lib():
             "blest_autotune": (ctypes.c_int, [_vp, _i32p, ctypes.c_int32, ctypes.POINTER(TuneResult)]),
             "blest_autotune_msbfs": (ctypes.c_int, [_vp, _i32p, ctypes.c_int32, ctypes.POINTER(MsTuneResult)]),
             "blest_autotune_multiroot": (ctypes.c_int, [_vp, _i32p, ctypes.c_int32, ctypes.POINTER(TuneResult)]),
+            "blest_shard_begin": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp]),
+            "blest_shard_pull": (ctypes.c_int, [_vp, _vp, _vp]),
+            "blest_shard_merge": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_int32, _vp]),
+            "blest_shard_finish": (ctypes.c_int, [_vp, _vp, _i32p, _vp]),
             "blest_get_level_times": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32]),
             "blest_get_level_arrivals": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64),
                                                         ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32]),
@@ -382,6 +388,27 @@ def blest_autotune(h: int, srcs) -> dict:
     r = TuneResult()
     _check(lib().blest_autotune(h, _ptr(s), len(s), ctypes.byref(r)), "blest_autotune")
     return {f: getattr(r, f) for f, _ in r._fields_}
+
+
+def blest_shard_begin(h: int, rank: int, world: int, src: int, d_levels, stream=None) -> None:
+    _check(lib().blest_shard_begin(h, int(rank), int(world), int(src), _dev_ptr(d_levels), _stream_ptr(stream)),
+           "blest_shard_begin")
+
+
+def blest_shard_pull(h: int, d_words, stream=None) -> None:
+    _check(lib().blest_shard_pull(h, _dev_ptr(d_words), _stream_ptr(stream)), "blest_shard_pull")
+
+
+def blest_shard_merge(d_dst, d_src, words: int, count: int, stream=None) -> None:
+    _check(lib().blest_shard_merge(_dev_ptr(d_dst), _dev_ptr(d_src), int(words), int(count), _stream_ptr(stream)),
+           "blest_shard_merge")
+
+
+def blest_shard_finish(h: int, d_merged, stream=None) -> bool:
+    more = ctypes.c_int32(0)
+    _check(lib().blest_shard_finish(h, _dev_ptr(d_merged), ctypes.byref(more), _stream_ptr(stream)),
+           "blest_shard_finish")
+    return bool(more.value)
 
 
 def blest_autotune_multiroot(h: int, srcs) -> dict:

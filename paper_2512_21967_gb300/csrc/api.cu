@@ -104,6 +104,10 @@ struct blest_graph {
     int ms_pull = BLEST_PULL_POPC;       // multi-source pull back-end
     int ms_chunk = blest::kMsbfsChunk;   // sources per multi-source launch
     int ms_blocks_per_sm = 0;            // 0 = blocks_per_sm
+    // sharded traversal in progress (blest_shard_*): rank, ranks, next level, output, rows reached
+    int32_t shard_rank = -1, shard_world = 0, shard_level = 0;
+    int32_t* shard_out = nullptr;
+    unsigned int shard_reached = 0;
     int blocks_per_sm = 0;
     int64_t timeout_us = 2000000;
     int record = 0;
@@ -399,6 +403,35 @@ blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots
     h->info.recorded = -1;  // resolved in blest_get_run_info
     h->info.output_path = !h->d_new_id ? 0 : (L.direct ? 1 : 2);
     return BLEST_OK;
+}
+
+// Launch description of one step of a sharded traversal (lazy update, padded
+// layout, register double buffer, 2 blocks per SM; the steps are separate launches).
+blest::BfsLaunch shard_launch(blest_graph* h) {
+    blest::BfsLaunch L;
+    L.update = 2;
+    L.filter = h->filter;
+    L.depth = 2;
+    L.n = h->n;
+    L.qcap = h->qcap;
+    L.real_ptrs = h->bvss.real_ptrs;
+    L.row_ids = h->bvss.row_ids;
+    L.masks = h->bvss.masks;
+    L.new_id = h->d_new_id;
+    L.direct = h->d_new_id && h->d_old_of ? 1 : 0;
+    L.old_of = h->d_old_of;
+    L.levels_internal = h->d_new_id ? h->d_L : h->shard_out;
+    L.out = h->shard_out;
+    L.vis = h->d_vis;
+    L.vcur = h->d_vcur;
+    for (int i = 0; i < 3; ++i) {
+        L.F[i] = reinterpret_cast<uint32_t*>(h->d_state + i * h->bitmap_bytes);
+        L.Q[i] = h->d_Q + i * (size_t)h->qcap;
+    }
+    L.ctrl = h->d_ctrl;
+    L.timeout_ns = (uint64_t)h->timeout_us * 1000ull;
+    L.grid = 2 * h->sms;
+    return L;
 }
 
 blest_status map_sources(blest_graph* h, const int32_t* srcs, int32_t k, std::vector<int32_t>& roots) {
@@ -1453,6 +1486,87 @@ int32_t blest_is_social(int32_t n, const int32_t* row_ptr, const int32_t* col_id
         return -rc;
     }
     return blest::is_social_like(clean) ? 1 : 0;
+}
+
+blest_status blest_shard_begin(blest_handle h, int32_t rank, int32_t world, int32_t src, int32_t* d_levels,
+                               void* stream) {
+    if (!h) return fail(BLEST_ERR_INVALID_ARG, "NULL handle");
+    if (world < 1 || rank < 0 || rank >= world) return fail(BLEST_ERR_INVALID_ARG, "rank must be in [0, world)");
+    if (!h->offsets.empty()) return fail(BLEST_ERR_INVALID_ARG, "a batch handle has no sharded traversal");
+    if (h->n == 0) return fail(BLEST_ERR_INVALID_ARG, "empty graph");
+    if (!d_levels) return fail(BLEST_ERR_INVALID_ARG, "levels is NULL");
+    std::vector<int32_t> roots;
+    blest_status s = map_sources(h, &src, 1, roots);
+    if (s) return s;
+    cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
+    h->shard_rank = rank;
+    h->shard_world = world;
+    h->shard_out = d_levels;
+    h->shard_level = 1;
+    h->shard_reached = 1;   // the level-0 sweep gives the root its level
+    blest::BfsLaunch L = shard_launch(h);
+    cudaError_t e;
+    // [V_curr/V_next pairs | V_curr copy | dirty | control block up to the sticky status word]
+    const size_t skip = 3 * h->bitmap_bytes;
+    if ((e = cudaMemsetAsync(h->d_state + skip, 0, kStateBitmaps * h->bitmap_bytes + h->dirty_bytes - skip +
+                                                       kCtrlClearBytes, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(L.direct ? d_levels : L.levels_internal, 0xFF, sizeof(int32_t) * (size_t)h->n, st)) !=
+            cudaSuccess ||
+        (e = blest::launch_shard_step(L, blest::kShardRoot, 0, world, rank, roots[0], nullptr, st)) != cudaSuccess ||
+        (e = blest::launch_shard_step(L, blest::kShardSweep, 0, world, rank, 0, nullptr, st)) != cudaSuccess)
+        return cuda_fail(e, "shard: level 0");
+    h->last_stream = st;
+    return BLEST_OK;
+}
+
+blest_status blest_shard_pull(blest_handle h, uint32_t* d_words, void* stream) {
+    if (!h) return fail(BLEST_ERR_INVALID_ARG, "NULL handle");
+    if (h->shard_rank < 0) return fail(BLEST_ERR_INVALID_ARG, "no sharded traversal begun on this handle");
+    if (!d_words) return fail(BLEST_ERR_INVALID_ARG, "words is NULL");
+    cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
+    blest::BfsLaunch L = shard_launch(h);
+    cudaError_t e;
+    if ((e = blest::launch_shard_step(L, blest::kShardPull, h->shard_level, h->shard_world, h->shard_rank, 0,
+                                      nullptr, st)) != cudaSuccess ||
+        (e = blest::launch_shard_step(L, blest::kShardWordsOut, h->shard_level, h->shard_world, h->shard_rank, 0,
+                                      d_words, st)) != cudaSuccess)
+        return cuda_fail(e, "shard: pull");
+    h->last_stream = st;
+    return BLEST_OK;
+}
+
+blest_status blest_shard_merge(uint32_t* d_dst, const uint32_t* d_src, int64_t words, int32_t count, void* stream) {
+    if (words < 0 || count < 1 || (words > 0 && (!d_dst || !d_src))) return fail(BLEST_ERR_INVALID_ARG, "bad arguments");
+    if (words == 0) return BLEST_OK;
+    cudaError_t e = blest::launch_or_words(d_dst, d_src, words, count, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "shard: merge");
+    return BLEST_OK;
+}
+
+blest_status blest_shard_finish(blest_handle h, const uint32_t* d_merged, int32_t* more, void* stream) {
+    if (!h) return fail(BLEST_ERR_INVALID_ARG, "NULL handle");
+    if (h->shard_rank < 0) return fail(BLEST_ERR_INVALID_ARG, "no sharded traversal begun on this handle");
+    if (!d_merged || !more) return fail(BLEST_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
+    blest::BfsLaunch L = shard_launch(h);
+    cudaError_t e;
+    if ((e = blest::launch_shard_step(L, blest::kShardWordsIn, h->shard_level, h->shard_world, h->shard_rank, 0,
+                                      const_cast<uint32_t*>(d_merged), st)) != cudaSuccess ||
+        (e = blest::launch_shard_step(L, blest::kShardSweep, h->shard_level, h->shard_world, h->shard_rank, 0,
+                                      nullptr, st)) != cudaSuccess)
+        return cuda_fail(e, "shard: sweep");
+    h->last_stream = st;
+    blest_status s = sync_status(h);
+    if (s) return s;
+    unsigned int ctrl[16];
+    if ((e = cudaMemcpy(ctrl, h->d_ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "shard: read counters");
+    const unsigned int reached = ctrl[7];   // Ctrl::reached
+    *more = reached > h->shard_reached ? 1 : 0;
+    h->shard_reached = reached;
+    h->shard_level += 1;
+    if (!*more) h->shard_rank = -1;   // the traversal is over; d_levels holds every level
+    return BLEST_OK;
 }
 
 blest_status blest_debug_pull(const uint32_t* d_masks, const uint8_t* d_alpha, int32_t tiles, int32_t pull,

@@ -115,9 +115,13 @@ __device__ __forceinline__ unsigned int pull_hits(uint32_t mask, uint32_t alpha,
 // Sparse levels (stage 1 set a dirty bit per touched V_next word): the warp
 // visits only the 32-word blocks whose dirty word is nonzero, clears it, and
 // treats the other words of the block as unchanged.
-template <int UPDATE, int LAYOUT>
+//
+// SHARD (sharded traversal): every rank sweeps every word, so all ranks finalise
+// the same level, but a rank enqueues only the slice sets it owns (s mod world =
+// rank), and the number of newly reached rows is always counted.
+template <int UPDATE, int LAYOUT, bool SHARD = false>
 __device__ __forceinline__ void sweep(const BfsArgs& a, int lvl, unsigned long long* Qout, unsigned int* qcount,
-                                      uint32_t* Fout, bool sparse) {
+                                      uint32_t* Fout, bool sparse, int world = 1, int rank = 0) {
     // Work split: in round k, warp w of block B takes the block of 32 words
     // B + (w + 16 k) gridDim.x, so consecutive 32-word blocks go to consecutive
     // thread blocks: the orderings put the hubs, whose slice sets carry most of
@@ -199,7 +203,8 @@ __device__ __forceinline__ void sweep(const BfsArgs& a, int lvl, unsigned long l
         for (int q = 0; q < 4; ++q) {
             const uint32_t byte = (diff >> (8 * q)) & 0xFFu;
             st[q] = 0; ln[q] = 0; tot[q] = 0; pay[q] = 0;
-            if (byte) {   // a row of slice set s exists, so s < nss and rp[q + 1] was loaded
+            if (byte && (!SHARD || (4 * t + q) % world == rank)) {
+                // a row of slice set s exists, so s < nss and rp[q + 1] was loaded
                 const int s = 4 * t + q;
                 st[q] = rp[q];
                 if (LAYOUT == 1) {
@@ -238,7 +243,7 @@ __device__ __forceinline__ void sweep(const BfsArgs& a, int lvl, unsigned long l
         if (base != 0xFFFFFFFFu && __shfl_sync(0xffffffffu, incl, 31) != 0u)
             warp_write_entries<4, LAYOUT == 1>(Qout, base + s_off[warp] + incl - cnt, cnt, st, ln, pay, tot, lane);
     }
-    if (UPDATE == 2 && a.filter >= 2) {
+    if (UPDATE == 2 && (SHARD || a.filter >= 2)) {
         fresh = __reduce_add_sync(0xffffffffu, fresh);
         if (lane == 0 && fresh) atomicAdd(&a.ctrl->reached, fresh);
     }
@@ -780,6 +785,56 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
     }
 }
 
+// ------------------------------------------------------- sharded traversal
+// One rank's share of a single-source traversal whose pull is partitioned by
+// slice set (rank r owns the slice sets s with s mod world = r), one launch per
+// step so that the ranks' exchange of V_next words sits between the steps of a
+// level: pull (stage 1 over the rank's own queue), then, after the exchange, the
+// finalisation sweep of the merged words, identical on every rank.  Lazy update,
+// padded layout, queues Q[level & 1].
+
+// Level 0: mark the root in V_next, then the level-0 sweep.
+__global__ void shard_root_kernel(BfsArgs a, int32_t root) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.vis[root >> 5].y, 1u << (root & 31));
+}
+
+__global__ void __launch_bounds__(kBfsBlock, 2) shard_pull_kernel(BfsArgs a, int lvl) {
+    const int lane = threadIdx.x & 31;
+    const int gtid = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int gwarp = gtid >> 5;
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    Ctrl* ctrl = a.ctrl;
+    unsigned int qn = ld_cg(&ctrl->qcount[lvl & 1]);
+    if (qn > a.qcap) qn = a.qcap;   // only after an overflow, which already raised an error
+    if (gtid == 0) ctrl->qcount[(lvl + 1) & 1] = 0u;   // written by this level's sweep
+    const int filt = (a.filter >= 2 && ld_cg(&ctrl->reached) >= (unsigned int)a.n / 4u) ? 1 : a.filter;
+    stage1_pipelined<0, 2, 0, 1>(a, a.Q[lvl & 1], qn, l2_evict_first_policy(), lane, gwarp, nwarps, filt, nullptr,
+                                 nullptr);
+    fold_status(ctrl);
+}
+
+__global__ void __launch_bounds__(kBfsBlock, 2) shard_sweep_kernel(BfsArgs a, int lvl, int world, int rank) {
+    sweep<2, 0, true>(a, lvl, a.Q[(lvl + 1) & 1], &a.ctrl->qcount[(lvl + 1) & 1], nullptr, false, world, rank);
+    fold_status(a.ctrl);
+}
+
+// The rank's V_next words out (to_vis = 0) or the merged words in (to_vis = 1).
+__global__ void shard_words_kernel(uint2* vis, uint32_t* words, int nwords, int to_vis) {
+    for (int t = (int)(blockIdx.x * blockDim.x + threadIdx.x); t < nwords; t += (int)(gridDim.x * blockDim.x)) {
+        if (to_vis) vis[t].y = words[t];
+        else words[t] = vis[t].y;
+    }
+}
+
+// dst[i] = OR over j < count of src[j * words + i]: the merge of all-gathered words.
+__global__ void or_words_kernel(uint32_t* dst, const uint32_t* src, int64_t words, int count) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t v = 0u;
+        for (int j = 0; j < count; ++j) v |= __ldg(&src[(int64_t)j * words + i]);
+        dst[i] = v;
+    }
+}
+
 template <int UPDATE, int PULL, int UNROLL, int MINB, int DEPTH, int LAYOUT>
 __global__ void __launch_bounds__(kBfsBlock, MINB) bfs_kernel(BfsArgs a) {
     bfs_body<UPDATE, PULL, UNROLL, DEPTH, LAYOUT>(a);
@@ -865,10 +920,7 @@ cudaError_t launch_debug_pull(const uint32_t* d_masks, const uint8_t* d_alpha, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_bfs_kernel(const BfsLaunch& L, cudaStream_t stream) {
-    void* k = pick_kernel(L.update, L.pull, L.unroll, L.minb, L.depth, L.layout);
-    if (!k) return cudaErrorInvalidValue;
-    const size_t smem = ring_smem_bytes(L.depth);
+static BfsArgs make_args(const BfsLaunch& L) {
     BfsArgs a;
     a.n = L.n;
     a.nwords = (L.n + 31) / 32;
@@ -902,8 +954,49 @@ cudaError_t launch_bfs_kernel(const BfsLaunch& L, cudaStream_t stream) {
     a.old_of = L.old_of;
     a.direct = L.direct;
     a.sched = L.sched;
+    return a;
+}
+
+cudaError_t launch_bfs_kernel(const BfsLaunch& L, cudaStream_t stream) {
+    void* k = pick_kernel(L.update, L.pull, L.unroll, L.minb, L.depth, L.layout);
+    if (!k) return cudaErrorInvalidValue;
+    const size_t smem = ring_smem_bytes(L.depth);
+    BfsArgs a = make_args(L);
     void* args[] = {&a};
     return cudaLaunchCooperativeKernel(k, dim3((unsigned)L.grid), dim3(kBfsBlock), args, smem, stream);
+}
+
+cudaError_t launch_shard_step(const BfsLaunch& L, int step, int lvl, int world, int rank, int32_t root,
+                              uint32_t* words, cudaStream_t stream) {
+    const BfsArgs a = make_args(L);
+    const int nwords = (L.n + 31) / 32;
+    const int wblocks = (int)std::min<int64_t>(((int64_t)nwords + 255) / 256, 4096);
+    switch (step) {
+        case kShardRoot:
+            shard_root_kernel<<<1, 32, 0, stream>>>(a, root);
+            break;
+        case kShardPull:
+            shard_pull_kernel<<<L.grid, kBfsBlock, 0, stream>>>(a, lvl);
+            break;
+        case kShardWordsOut:
+            shard_words_kernel<<<std::max(wblocks, 1), 256, 0, stream>>>(a.vis, words, nwords, 0);
+            break;
+        case kShardWordsIn:
+            shard_words_kernel<<<std::max(wblocks, 1), 256, 0, stream>>>(a.vis, words, nwords, 1);
+            break;
+        case kShardSweep:
+            shard_sweep_kernel<<<L.grid, kBfsBlock, 0, stream>>>(a, lvl, world, rank);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_or_words(uint32_t* dst, const uint32_t* src, int64_t words, int count, cudaStream_t stream) {
+    const int blocks = (int)std::min<int64_t>((words + 255) / 256, 4096);
+    or_words_kernel<<<std::max(blocks, 1), 256, 0, stream>>>(dst, src, words, count);
+    return cudaGetLastError();
 }
 
 }  // namespace blest

@@ -51,6 +51,15 @@ struct BfsLaunch {
 };
 
 int bfs_max_blocks_per_sm(int update, int pull, int unroll, int minb, int depth, int layout);
+
+// Steps of the sharded single-source traversal (bfs_kernel.cu): mark the root,
+// pull this rank's queue, copy the rank's V_next words out, copy the merged
+// words in, and the finalisation sweep (which enqueues the rank's own slice sets).
+enum ShardStep { kShardRoot = 0, kShardPull = 1, kShardWordsOut = 2, kShardWordsIn = 3, kShardSweep = 4 };
+cudaError_t launch_shard_step(const BfsLaunch& L, int step, int lvl, int world, int rank, int32_t root,
+                              uint32_t* words, cudaStream_t stream);
+// dst[i] = OR over j < count of src[j * words + i].
+cudaError_t launch_or_words(uint32_t* dst, const uint32_t* src, int64_t words, int count, cudaStream_t stream);
 int bfs_threads_per_block();
 cudaError_t launch_bfs_kernel(const BfsLaunch& L, cudaStream_t stream);
 

@@ -13,10 +13,12 @@
 //   stage 2: a coalesced sweep over vertices: diff = V_next ^ V_curr becomes
 //     the next frontier, newly set bits give levels, and the slice sets of
 //     vertices with any new bit are enqueued with one atomicAdd per warp.
-// Levels are kept vertex-major (a vertex's k levels are contiguous).  The sweep
-// writes them one vertex at a time across the warp, and a final warp-level
-// transpose turns them into the source-major output in original ids, so that
-// neither side gathers one 4-byte entry per memory sector.
+// Levels are kept as bit planes during the traversal: bit i of plane p's word w
+// of vertex u is bit p of u's level from source 64 w + i.  A sweep ORs each
+// vertex's new-bit word into the planes of the bits set in the level number
+// (a coalesced read-modify-write per vertex and plane, no per-(source, vertex)
+// store), and a final pass rebuilds each vertex's levels, 8 sources at a time
+// with an 8 x 8 bit transpose, into the source-major output in original ids.
 // Two back-ends compute the pull.  PULL 0 (default) ORs the selected frontier
 // words on the CUDA cores.  PULL 1 runs the same product as b1 AND+POPC
 // tensor-core MMAs (m16n8k128): VSS slots along M, sources along N, the slice
@@ -48,8 +50,8 @@ struct MsArgs {
     unsigned long long* vnext;
     unsigned long long* front;
     unsigned long long* Q[3];
-    int32_t* lint;       // n x kst, vertex-major: lint[u * kst + i] = level of BVSS vertex u from source i
-    int32_t kst;         // row stride of lint: k rounded up to a multiple of 8 (rows start on 32-byte sectors)
+    unsigned long long* planes;   // nplanes x (n x W) words: plane p holds bit p of every level
+    int32_t nplanes;              // msbfs_planes(n): enough bits for level n - 1
     int32_t* out;        // k x n, source-major, original ids
     uint32_t* dirty;     // one bit per slice set touched by a mark in a sparse level (cleared by the sweep)
     const int32_t* roots;
@@ -60,21 +62,17 @@ struct MsArgs {
     unsigned int phantom;
 };
 
-// Levels of the new bits, vertex-major.  Lane j holds the new-bit word d (sources
-// 64 w .. 64 w + 63) of vertex u0 + stride * j; for each such vertex with a new
-// bit the warp writes that vertex's entries with two stores of 32 consecutive
-// sources, so a store touches one row instead of 32.
-__device__ __forceinline__ void ms_write_levels(const MsArgs& a, unsigned long long d, int u0, int stride, int w,
-                                                int lvl, int lane) {
-    unsigned int todo = __ballot_sync(0xffffffffu, d != 0ull);
-    while (todo) {
-        const int j = __ffs(todo) - 1;
-        todo &= todo - 1u;
-        const unsigned long long dj = __shfl_sync(0xffffffffu, d, j);
-        int32_t* row = a.lint + (size_t)(u0 + stride * j) * (size_t)a.kst + (size_t)(64 * w);
-        if ((dj >> lane) & 1ull) row[lane] = lvl;
-        if ((dj >> (32 + lane)) & 1ull) row[32 + lane] = lvl;
-    }
+// Level lvl for the new bits d of word w of vertex u: d is ORed into every plane
+// p with bit p set in lvl.  Only the calling lane writes u's words in a sweep, so
+// a plain read-modify-write suffices; plane p was cleared during stage 1 of level
+// 2^p, its first use.
+template <int W>
+__device__ __forceinline__ void ms_write_planes(const MsArgs& a, unsigned long long d, int u, int w, int lvl) {
+    if (!d) return;
+    const size_t stride = (size_t)a.n * W;
+    unsigned long long* q = a.planes + (size_t)u * W + w;
+    for (int p = 0; (lvl >> p) != 0; ++p)
+        if ((lvl >> p) & 1) q[(size_t)p * stride] |= d;
 }
 
 template <int W>
@@ -103,7 +101,7 @@ __device__ __forceinline__ void ms_sweep(const MsArgs& a, int lvl, unsigned long
                     any = true;
                 }
             }
-            ms_write_levels(a, d, c * kWarp, 1, w, lvl, lane);
+            ms_write_planes<W>(a, d, u, w, lvl);
         }
         const unsigned int ball = __ballot_sync(0xffffffffu, any);
         int st = 0, ln = 0;
@@ -157,7 +155,7 @@ __device__ __forceinline__ void ms_sweep_sparse(const MsArgs& a, int lvl, unsign
                             any = true;
                         }
                     }
-                    ms_write_levels(a, d, 8 * 32 * t + j, 8, w, lvl, lane);
+                    ms_write_planes<W>(a, d, u, w, lvl);
                 }
             }
         }
@@ -339,6 +337,15 @@ __device__ __forceinline__ void ms_body(const MsArgs& a) {
         const unsigned long long* Qin = a.Q[lvl % 3];
         unsigned long long* Qout = a.Q[(lvl + 1) % 3];
         unsigned int* qcount_next = &ctrl->qcount[(lvl + 1) & 3];
+        if ((lvl & (lvl - 1)) == 0) {
+            // lvl = 2^p: this level's sweep is the first to write plane p, so it is
+            // cleared now (stage 1 does not touch the planes; the barrier orders it)
+            const int p = __ffs(lvl) - 1;
+            if (p < a.nplanes) {
+                unsigned long long* pl = a.planes + (size_t)p * (size_t)a.n * W;
+                for (size_t i = (size_t)gtid; i < (size_t)a.n * W; i += (size_t)nthreads) pl[i] = 0ull;
+            }
+        }
         // software pipeline over this warp's items p, p + nwarps, ...: the entry two
         // items ahead and the tile and frontier words one item ahead are in flight
         // while the current item is pulled
@@ -362,31 +369,63 @@ __device__ __forceinline__ void ms_body(const MsArgs& a) {
         qn = qnext;
     }
     if (gtid == 0) ctrl->levels = (unsigned int)lvl;
-    // out[i*n + v] = level of v from source i (original ids), -1 if unreached: a
-    // warp-level transpose of the vertex-major buffer.  Lane j takes vertex
-    // v = 32 b + j and reads its levels 4 sources (16 bytes) at a time; the warp
-    // then stores them source by source, 32 consecutive vertices per store.
+}
+
+// out[i*n + v] = level of v from source i (original ids), -1 if unreached: a
+// separate launch after the traversal (ctrl->levels holds its level count), so
+// that the traversal kernel keeps its register budget.  Lane j takes vertex
+// v = 32 b + j, reads its visited word and its plane words (the planes that can
+// hold a bit of a level <= the level count: the ones the traversal cleared),
+// rebuilds its levels 8 sources at a time and stores them source by source, 32
+// consecutive vertices per store.
+template <int W>
+__global__ void __launch_bounds__(kMsBlock) msbfs_output_kernel(MsArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    const int lvl = (int)ld_cg(&a.ctrl->levels);
+    const int np = min(32 - __clz(lvl), a.nplanes);
+    const size_t pstride = (size_t)a.n * W;
     const int nvb = (a.n + kWarp - 1) / kWarp;
     for (int b = gwarp; b < nvb; b += nwarps) {
         const int v = b * kWarp + lane;
-        const bool ok = v < a.n;
-        const int u = ok ? (a.new_id ? __ldg(&a.new_id[v]) : v) : 0;
-        const int4* row = reinterpret_cast<const int4*>(a.lint + (size_t)u * (size_t)a.kst);
+        if (v >= a.n) continue;
+        const int u = a.new_id ? __ldg(&a.new_id[v]) : v;
         int32_t* o = a.out + v;
 #pragma unroll 1
         for (int w = 0; w < W; ++w) {
-            const unsigned long long vis = ok ? ld_cg(&a.vcur[(size_t)u * W + w]) : 0ull;
+            const size_t idx = (size_t)u * W + w;
+            const unsigned long long vis = ld_cg(&a.vcur[idx]);
             const int i_end = min(64 * w + 64, a.k);
+            if (np <= 8) {
+                uint64_t pw[8];
+#pragma unroll
+                for (int p = 0; p < 8; ++p) pw[p] = p < np ? ld_cg(&a.planes[(size_t)p * pstride + idx]) : 0ull;
 #pragma unroll 1
-            for (int i0 = 64 * w; i0 < i_end; i0 += 4) {
-                const uint32_t bits = (uint32_t)(vis >> (i0 - 64 * w)) & 0xFu;
-                // positions of sources that never reached u are never written, so never used
-                const int4 lv = bits ? ld_cg(&row[i0 >> 2]) : make_int4(-1, -1, -1, -1);
-                if (!ok) continue;
-                o[(size_t)i0 * (size_t)a.n] = bits & 1u ? lv.x : -1;
-                if (i0 + 1 < i_end) o[(size_t)(i0 + 1) * (size_t)a.n] = bits & 2u ? lv.y : -1;
-                if (i0 + 2 < i_end) o[(size_t)(i0 + 2) * (size_t)a.n] = bits & 4u ? lv.z : -1;
-                if (i0 + 3 < i_end) o[(size_t)(i0 + 3) * (size_t)a.n] = bits & 8u ? lv.w : -1;
+                for (int i0 = 64 * w; i0 < i_end; i0 += 8) {
+                    const int c = (i0 - 64 * w) >> 3;
+                    const unsigned long long lv8 = levels_of_8(pw, c);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int i = i0 + j;
+                        if (i < i_end)
+                            o[(size_t)i * (size_t)a.n] =
+                                (vis >> (8 * c + j)) & 1ull ? (int32_t)((lv8 >> (8 * j)) & 0xFFull) : -1;
+                    }
+                }
+            } else {
+                // levels of 256 and more (high-diameter graphs): plane by plane, per source
+#pragma unroll 1
+                for (int i = 64 * w; i < i_end; ++i) {
+                    const int bit = i - 64 * w;
+                    int32_t lv = -1;
+                    if ((vis >> bit) & 1ull) {
+                        lv = 0;
+                        for (int p = 0; p < np; ++p)
+                            lv |= (int32_t)((ld_cg(&a.planes[(size_t)p * pstride + idx]) >> bit) & 1ull) << p;
+                    }
+                    o[(size_t)i * (size_t)a.n] = lv;
+                }
             }
         }
     }
@@ -395,6 +434,13 @@ __device__ __forceinline__ void ms_body(const MsArgs& a) {
 template <int W, int PULL>
 __global__ void __launch_bounds__(kMsBlock) msbfs_kernel(MsArgs a) {
     ms_body<W, PULL>(a);
+    fold_status(a.ctrl);
+}
+
+// One word of sources (W = 1) on the CUDA cores, held to 3 resident blocks per SM:
+// as many warps in flight as the register file allows at that width.
+__global__ void __launch_bounds__(kMsBlock, 3) msbfs_kernel_w1(MsArgs a) {
+    ms_body<1, 0>(a);
     fold_status(a.ctrl);
 }
 
@@ -417,7 +463,7 @@ void free_msbfs_state(MsbfsState& s) {
     cudaFree(s.vnext);
     cudaFree(s.front);
     cudaFree(s.Q);
-    cudaFree(s.lint);
+    cudaFree(s.planes);
     cudaFree(s.roots);
     cudaFree(s.dirty);
     s = MsbfsState();
@@ -440,8 +486,7 @@ int run_msbfs(MsbfsState& s, const MsbfsLaunchCommon& c, const std::vector<int32
         if ((e = grow(s.front, cap_f, words, own)) != cudaSuccess) break;
         s.words_cap = std::min(cap_v, std::min(cap_n, cap_f));
         if ((e = grow(s.Q, s.qcap, std::max<int64_t>(c.nvss, 1), own, 3)) != cudaSuccess) break;
-        const int32_t kst = (k + 7) & ~7;
-        if ((e = grow(s.lint, s.lint_cap, msbfs_level_entries(c.n, k, chunk), own)) != cudaSuccess) break;
+        if ((e = grow(s.planes, s.planes_cap, msbfs_plane_words(c.n, k, chunk), own)) != cudaSuccess) break;
         if ((e = grow(s.roots, s.roots_cap, k, own)) != cudaSuccess) break;
         const int64_t dwords = ((int64_t)c.nss + 31) / 32;
         if ((e = grow(s.dirty, s.dirty_cap, dwords, own)) != cudaSuccess) break;
@@ -463,8 +508,8 @@ int run_msbfs(MsbfsState& s, const MsbfsLaunchCommon& c, const std::vector<int32
         a.front = s.front;
         for (int i = 0; i < 3; ++i) a.Q[i] = s.Q + (size_t)i * (size_t)s.qcap;
         int32_t* out = d_out + (size_t)i0 * (size_t)c.n;
-        a.lint = s.lint;
-        a.kst = kst;
+        a.planes = s.planes;
+        a.nplanes = msbfs_planes(c.n);
         a.out = out;
         a.roots = s.roots;
         a.dirty = s.dirty;
@@ -475,13 +520,21 @@ int run_msbfs(MsbfsState& s, const MsbfsLaunchCommon& c, const std::vector<int32
         a.phantom = c.phantom;
         void* kfn = c.pull == 1
                         ? (W == 1 ? (void*)&msbfs_kernel<1, 1> : (W == 2 ? (void*)&msbfs_kernel<2, 1> : (void*)&msbfs_kernel<4, 1>))
-                        : (W == 1 ? (void*)&msbfs_kernel<1, 0> : (W == 2 ? (void*)&msbfs_kernel<2, 0> : (void*)&msbfs_kernel<4, 0>));
+                        : (W == 1 ? (void*)&msbfs_kernel_w1 : (W == 2 ? (void*)&msbfs_kernel<2, 0> : (void*)&msbfs_kernel<4, 0>));
         int nb = 0;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn, kMsBlock, 0)) != cudaSuccess) break;
         if (nb <= 0) { *err = "msbfs kernel cannot be resident"; return 5; }
         if (c.blocks_per_sm > 0) nb = std::min(nb, c.blocks_per_sm);
         void* args[] = {&a};
         if ((e = cudaLaunchCooperativeKernel(kfn, dim3((unsigned)(nb * c.sms)), dim3(kMsBlock), args, 0, st)) != cudaSuccess) break;
+        // the source-major output in original ids, from the level planes
+        const int64_t warps_needed = ((int64_t)c.n + kWarp - 1) / kWarp;
+        const int64_t blocks = std::min<int64_t>((warps_needed + kMsBlock / kWarp - 1) / (kMsBlock / kWarp),
+                                                 (int64_t)c.sms * 8);
+        void* ofn = W == 1 ? (void*)&msbfs_output_kernel<1> : (W == 2 ? (void*)&msbfs_output_kernel<2>
+                                                                     : (void*)&msbfs_output_kernel<4>);
+        if ((e = cudaLaunchKernel(ofn, dim3((unsigned)std::max<int64_t>(blocks, 1)), dim3(kMsBlock), args, 0, st)) != cudaSuccess)
+            break;
     }
     if (e != cudaSuccess) {
         *err = own && e == cudaErrorInvalidValue ? "caller-owned multi-source state is smaller than the launch"

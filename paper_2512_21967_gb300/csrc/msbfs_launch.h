@@ -6,6 +6,8 @@
 #include <cstdint>
 #include <vector>
 
+#include "msbfs_bits.h"
+
 namespace blest {
 
 constexpr int kMsbfsChunk = 256;   // most sources per launch (the default launch size)
@@ -17,11 +19,10 @@ inline int msbfs_words(int64_t k, int chunk = kMsbfsChunk) {
     return kc <= 64 ? 1 : (kc <= 128 ? 2 : 4);
 }
 
-// int32 entries of the vertex-major internal level buffer for k sources: n rows
-// of the largest launch's source count rounded up to a multiple of 8.
-inline int64_t msbfs_level_entries(int32_t n, int64_t k, int chunk = kMsbfsChunk) {
-    const int64_t kc = std::min<int64_t>(k, chunk);
-    return ((kc + 7) & ~int64_t(7)) * (int64_t)n;
+// 64-bit words of the level bit planes for k sources: msbfs_planes(n) planes of
+// n vertices x W words (plane p holds bit p of every (vertex, source) level).
+inline int64_t msbfs_plane_words(int32_t n, int64_t k, int chunk = kMsbfsChunk) {
+    return (int64_t)msbfs_planes(n) * (int64_t)n * msbfs_words(k, chunk);
 }
 
 // Device buffers of a multi-source traversal, grown on demand and kept with
@@ -35,8 +36,8 @@ struct MsbfsState {
     unsigned long long* front = nullptr;
     int64_t qcap = 0;
     unsigned long long* Q = nullptr;   // 3 * qcap
-    int64_t lint_cap = 0;              // int32 entries of the internal level buffer
-    int32_t* lint = nullptr;
+    int64_t planes_cap = 0;            // u64 words of the level bit planes
+    unsigned long long* planes = nullptr;
     int64_t roots_cap = 0;
     int32_t* roots = nullptr;
     int64_t dirty_cap = 0;             // words of the dirty-slice-set bitmap

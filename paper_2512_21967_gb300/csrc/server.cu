@@ -144,7 +144,7 @@ int64_t launch_bytes(const blest::HandleView& v, int k) {
     int64_t b = (int64_t)k * v.n * 4;                          // levels
     b += 3 * (int64_t)v.n * W * 8;                            // V_curr, V_next, frontier
     b += 3 * std::max<int64_t>(v.nvss, 1) * 8;                // queues
-    b += blest::msbfs_level_entries(v.n, k) * 4;              // vertex-major levels in BVSS ids
+    b += blest::msbfs_plane_words(v.n, k) * 8;                // level bit planes in BVSS ids
     b += (int64_t)k * 4 + 4 * 256;                             // roots, alignment slack
     b += ((int64_t)v.nss + 31) / 32 * 4;                       // dirty slice sets
     return b;
@@ -168,9 +168,9 @@ cudaError_t alloc_launch(Slot& s, const blest::HandleView& v, int k) {
     m.words_cap = words;
     if ((e = alloc_async(m.Q, 3 * std::max<int64_t>(v.nvss, 1), s.stream)) != cudaSuccess) return e;
     m.qcap = std::max<int64_t>(v.nvss, 1);
-    const int64_t lev = blest::msbfs_level_entries(v.n, k);
-    if ((e = alloc_async(m.lint, lev, s.stream)) != cudaSuccess) return e;
-    m.lint_cap = lev;
+    const int64_t pw = blest::msbfs_plane_words(v.n, k);
+    if ((e = alloc_async(m.planes, pw, s.stream)) != cudaSuccess) return e;
+    m.planes_cap = pw;
     if ((e = alloc_async(m.roots, k, s.stream)) != cudaSuccess) return e;
     m.roots_cap = k;
     const int64_t dwords = ((int64_t)v.nss + 31) / 32;
@@ -181,7 +181,7 @@ cudaError_t alloc_launch(Slot& s, const blest::HandleView& v, int k) {
 
 void free_launch(Slot& s) {
     blest::MsbfsState& m = s.ms;
-    for (void* p : {(void*)s.d_levels, (void*)m.vcur, (void*)m.vnext, (void*)m.front, (void*)m.Q, (void*)m.lint,
+    for (void* p : {(void*)s.d_levels, (void*)m.vcur, (void*)m.vnext, (void*)m.front, (void*)m.Q, (void*)m.planes,
                     (void*)m.roots, (void*)m.dirty})
         if (p) cudaFreeAsync(p, s.stream);
     s.d_levels = nullptr;

@@ -29,7 +29,7 @@ def plain_ms_bytes(levels, new_id, w_s, nvss, n):
         for l in range(1, lmax + 2):
             q = sum(int(nvss[s]) for s in sets_at.get(l - 1, ()))
             sweep += 24 * W * n if q * 128 > n else 24 * W * 8 * len(sets_at.get(l, ()))
-        total += stage1 + sweep + 8 * pairs + 4 * k * n + (8 * W + 4) * n
+        total += stage1 + sweep + 4 * k * n + (8 * W + 4) * n
         pairs_all += pairs
     return total, pairs_all
 

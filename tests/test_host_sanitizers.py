@@ -57,6 +57,24 @@ def test_multi_source_chunk_sizing(tmp_path):
     assert run.returncode == 0 and "failures=0" in run.stdout, run.stdout[-2000:]
 
 
+def test_msbfs_bit_plane_helpers(tmp_path):
+    """The multi-source level bit planes: the 8 x 8 bit transpose and the
+    per-source level extraction against their loop definitions, and the plane
+    count against the largest level an n-vertex graph can have."""
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no g++")
+    exe = str(tmp_path / "msbfs_bits_check")
+    cmd = [gxx, "-std=c++17", "-O1", "-fsanitize=undefined", "-fno-sanitize-recover=undefined", "-I", CSRC,
+           os.path.join(ROOT, "tests", "host", "msbfs_bits_check.cpp"), "-o", exe]
+    build = subprocess.run(cmd, capture_output=True, text=True)
+    if build.returncode != 0 and "sanitize" in build.stderr and "cannot find" in build.stderr:
+        pytest.skip("sanitizer runtime not installed")
+    assert build.returncode == 0, build.stderr[-3000:]
+    run = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert run.returncode == 0 and "failures=0" in run.stdout, run.stdout[-2000:]
+
+
 def test_host_preprocessing_under_tsan(tmp_path):
     """The same driver built with ThreadSanitizer: the threaded parts (cleaning,
     symmetry check, relabelling, JaccardWithWindows, the parallel levels of the
