@@ -733,7 +733,8 @@ def run_ours_serve(args, torch, blest, dev, rank, world):
                 stream = stream[:min(len(stream), args.oaat_queries)]
             if mode == "batched":
                 srv = blest.blest_server_create(handles, memory_cap_bytes=40 << 30, max_batch_sources=64,
-                                                max_inflight=4, blocks_per_sm=1)
+                                                max_inflight=args.serve_inflight, blocks_per_sm=1,
+                                                narrow_sms=args.serve_narrow_sms, narrow_levels=256)
             else:
                 srv = blest.blest_server_create(handles, memory_cap_bytes=40 << 30, max_batch_sources=32,
                                                 max_inflight=1, blocks_per_sm=0, max_queries_per_launch=1)
@@ -757,6 +758,8 @@ def run_ours_serve(args, torch, blest, dev, rank, world):
                 "dtype": "u64", "data": "synthetic",
                 "config": {"workload": "serving: 16 resident graphs (8 R-MAT s16..22, 8 grids 256..2048, p=0.9), "
                                        f"Poisson queries with 1..32 sources, {args.queries} per rate, 40 GB cap",
+                           "server": {"max_inflight": args.serve_inflight, "max_batch_sources": 64,
+                                      "narrow_sms": args.serve_narrow_sms, "narrow_levels": 256},
                            "results_copied": "no (levels stay in device memory)"},
                 "serving": results, "preprocess_s": {"create_total": round(t_create, 2)}}
         print(json.dumps(line), flush=True)
@@ -974,6 +977,9 @@ def main():
                     help="lazy stage-1 prefetch: 0 none, 2 register double buffer, 4 or 8 TMA ring stages")
     ap.add_argument("--queries", type=int, default=2000, help="serving: queries per arrival rate")
     ap.add_argument("--rates", default="100,400,1600", help="serving: arrival rates in queries/s")
+    ap.add_argument("--serve-inflight", type=int, default=8, help="serving: launches in flight at once")
+    ap.add_argument("--serve-narrow-sms", type=int, default=19,
+                    help="serving: SMs of a launch on a graph whose last launch ran more than 256 levels (0 = all)")
     ap.add_argument("--oaat-queries", type=int, default=2000,
                     help="serving: queries per rate for the one-query-per-launch comparison")
     ap.add_argument("--windows", default="0,8,64,512,4096,16384,65536,g4096",

@@ -108,8 +108,14 @@ typedef enum {
                                         same Boolean product with m16n8k128 b1 AND+POPC tensor-core MMAs */
     BLEST_OPT_MS_CHUNK = 13,         /* sources per multi-source launch (the k-tile): 64, 128 or 256
                                         (default); a call with more sources runs several launches */
-    BLEST_OPT_MS_BLOCKS_PER_SM = 14  /* multi-source persistent-grid blocks per SM; 0 (default) = the
+    BLEST_OPT_MS_BLOCKS_PER_SM = 14, /* multi-source persistent-grid blocks per SM; 0 (default) = the
                                         value of BLEST_OPT_BLOCKS_PER_SM (0 = as many as fit) */
+    BLEST_OPT_MS_LEVELS = 15         /* how the multi-source traversal keeps levels until its output pass:
+                                        1 = vertex-major (one entry per reached (vertex, source)), 2 = bit
+                                        planes (plane p = bit p of every level; updated once per plane
+                                        and distinct level at which a vertex gains bits), 0 (default) =
+                                        planes on graphs the Section 5 rule updates lazily, else
+                                        vertex-major */
 } blest_option;
 
 /* Creation parameters; pass NULL to blest_graph_create_ex for the defaults. */
@@ -361,6 +367,7 @@ typedef struct {
     int32_t pull;                /* BLEST_OPT_MS_PULL kept */
     int32_t chunk;               /* BLEST_OPT_MS_CHUNK kept (sources per launch) */
     int32_t blocks_per_sm;       /* BLEST_OPT_MS_BLOCKS_PER_SM kept (0 = as many as fit) */
+    int32_t levels;              /* BLEST_OPT_MS_LEVELS kept (1 vertex-major, 2 bit planes) */
     int32_t candidates;          /* variants timed */
     double  best_ms;             /* device time of one call over all k sources, kept variant */
     double  popc_ms;             /* best time with the CUDA-core pull */
@@ -371,7 +378,8 @@ typedef struct {
  * srcs[0..k) (Section 2's multi-source form) with CUDA events, each variant
  * after one untimed pass, and keep the fastest as the handle's options: pull
  * back-end (CUDA-core OR or b1 tensor-core MMA), sources per launch (64, 128,
- * 256; only sizes that change the launches of k sources) and blocks per SM.
+ * 256; only sizes that change the launches of k sources), blocks per SM and
+ * level layout (the MMA back-end is timed with bit planes only).
  * Allocates a k x n device level buffer for the duration of the call.  out may
  * be NULL.  Errors: INVALID_ARG (k < 1, bad source), OOM, TIMEOUT, INTERNAL, CUDA. */
 blest_status blest_autotune_msbfs(blest_handle h, const int32_t* srcs, int32_t k, blest_ms_tune_result* out);
@@ -483,6 +491,12 @@ typedef struct {
     int32_t max_inflight;        /* launches in flight at once (default 4, at most 64) */
     int32_t blocks_per_sm;       /* persistent-grid blocks per SM of each launch (default 1) */
     int32_t max_queries_per_launch; /* 0 = no limit (default); 1 = one query per launch (no coalescing) */
+    int32_t narrow_sms;          /* SMs of the persistent grid of a launch on a graph whose previous
+                                    launch ran more than narrow_levels levels (0 = every launch uses all
+                                    SMs, default): high-diameter graphs have small levels, and a narrow
+                                    grid crosses each level barrier faster and leaves the other SMs to
+                                    the launches of other graphs */
+    int32_t narrow_levels;       /* level count above which a graph's launches turn narrow (default 256) */
 } blest_server_params;
 
 typedef struct {

@@ -47,7 +47,7 @@ BLEST_OPT_UPDATE, BLEST_OPT_PULL, BLEST_OPT_BLOCKS_PER_SM, BLEST_OPT_BARRIER_TIM
 BLEST_OPT_RECORD_LEVELS, BLEST_OPT_UNROLL, BLEST_OPT_TEST_PHANTOM_BLOCK = 4, 5, 6
 BLEST_OPT_VISITED_FILTER, BLEST_OPT_MIN_BLOCKS, BLEST_OPT_STAGE_DEPTH, BLEST_OPT_LAYOUT = 7, 8, 9, 10
 BLEST_OPT_SCHEDULE = 11
-BLEST_OPT_MS_PULL, BLEST_OPT_MS_CHUNK, BLEST_OPT_MS_BLOCKS_PER_SM = 12, 13, 14
+BLEST_OPT_MS_PULL, BLEST_OPT_MS_CHUNK, BLEST_OPT_MS_BLOCKS_PER_SM, BLEST_OPT_MS_LEVELS = 12, 13, 14, 15
 BLEST_ARRAY_REAL_PTRS, BLEST_ARRAY_VIRTUAL_TO_REAL, BLEST_ARRAY_ROW_IDS = 0, 1, 2
 BLEST_ARRAY_MASKS, BLEST_ARRAY_NEW_ID, BLEST_ARRAY_VSS_COUNT = 3, 4, 5
 BLEST_ARRAY_COMPACT_OFFSETS, BLEST_ARRAY_COMPACT_ROWS, BLEST_ARRAY_COMPACT_MASKS = 6, 7, 8
@@ -99,14 +99,15 @@ class TuneResult(ctypes.Structure):
 
 class MsTuneResult(ctypes.Structure):
     _fields_ = [("pull", ctypes.c_int32), ("chunk", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_double), ("popc_ms", ctypes.c_double),
+                ("levels", ctypes.c_int32), ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_double), ("popc_ms", ctypes.c_double),
                 ("mma_ms", ctypes.c_double)]
 
 
 class ServerParams(ctypes.Structure):
     _fields_ = [("memory_cap_bytes", ctypes.c_int64), ("max_batch_sources", ctypes.c_int32),
                 ("max_inflight", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("max_queries_per_launch", ctypes.c_int32)]
+                ("max_queries_per_launch", ctypes.c_int32), ("narrow_sms", ctypes.c_int32),
+                ("narrow_levels", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -521,10 +522,10 @@ def blest_bfs_static_scratch(n: int, num_vss: int, d_real_ptrs, d_row_ids, d_mas
 
 
 def blest_server_create(handles, memory_cap_bytes=0, max_batch_sources=0, max_inflight=0, blocks_per_sm=0,
-                        max_queries_per_launch=0) -> int:
+                        max_queries_per_launch=0, narrow_sms=0, narrow_levels=0) -> int:
     arr = (_vp * len(handles))(*handles)
     p = ServerParams(int(memory_cap_bytes), int(max_batch_sources), int(max_inflight), int(blocks_per_sm),
-                     int(max_queries_per_launch))
+                     int(max_queries_per_launch), int(narrow_sms), int(narrow_levels))
     s = _vp()
     _check(lib().blest_server_create(arr, len(handles), ctypes.byref(p), ctypes.byref(s)), "blest_server_create")
     return s.value

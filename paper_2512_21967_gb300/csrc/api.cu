@@ -104,6 +104,7 @@ struct blest_graph {
     int ms_pull = BLEST_PULL_POPC;       // multi-source pull back-end
     int ms_chunk = blest::kMsbfsChunk;   // sources per multi-source launch
     int ms_blocks_per_sm = 0;            // 0 = blocks_per_sm
+    int ms_levels = 0;                   // BLEST_OPT_MS_LEVELS: 0 auto, 1 vertex-major, 2 bit planes
     // sharded traversal in progress (blest_shard_*): rank, ranks, next level, output, rows reached
     int32_t shard_rank = -1, shard_world = 0, shard_level = 0;
     int32_t* shard_out = nullptr;
@@ -137,6 +138,14 @@ struct blest_graph {
     int resolved_update() const {
         if (update_opt == BLEST_UPDATE_EAGER || update_opt == BLEST_UPDATE_LAZY) return update_opt;
         return stats.update;
+    }
+    // multi-source level layout: 1 = bit planes, 0 = vertex-major; AUTO takes planes
+    // on graphs the Section 5 rule updates lazily (U_div > 25,000: low diameter,
+    // where a vertex gains bits at few distinct levels)
+    int ms_levels_layout() const {
+        if (ms_levels == 1) return 0;
+        if (ms_levels == 2) return 1;
+        return stats.update == BLEST_UPDATE_LAZY ? 1 : 0;
     }
 };
 
@@ -481,6 +490,7 @@ struct HandleView {
     const int32_t* new_id_dev;
     const int32_t* new_id_host;
     int sms;
+    int levels_layout;
 };
 bool handle_view(blest_handle h, HandleView* v) {
     if (!h || !v || h->n == 0) return false;
@@ -493,6 +503,7 @@ bool handle_view(blest_handle h, HandleView* v) {
     v->new_id_dev = h->d_new_id;
     v->new_id_host = h->h_new_id.empty() ? nullptr : h->h_new_id.data();
     v->sms = h->sms;
+    v->levels_layout = h->ms_levels_layout();
     return true;
 }
 }  // namespace blest
@@ -887,6 +898,10 @@ blest_status blest_set_option(blest_handle h, int32_t key, int64_t value) {
             if (value < 0 || value > 64) break;
             h->ms_blocks_per_sm = (int)value;
             return BLEST_OK;
+        case BLEST_OPT_MS_LEVELS:
+            if (value < 0 || value > 2) break;
+            h->ms_levels = (int)value;
+            return BLEST_OK;
         default:
             return fail(BLEST_ERR_INVALID_ARG, "unknown option key");
     }
@@ -1092,6 +1107,7 @@ blest_status blest_msbfs_device(blest_handle h, const int32_t* srcs, int32_t k, 
     c.level_cap = kLevelRecordCap;
     c.pull = h->ms_pull;
     c.chunk = h->ms_chunk;
+    c.levels_layout = h->ms_levels_layout();
     const char* err = nullptr;
     int rc = blest::run_msbfs(h->ms, c, roots, d_levels, st, &err);
     if (rc) return fail((blest_status)rc, std::string("msbfs: ") + (err ? err : "?"));
@@ -1206,15 +1222,19 @@ blest_status blest_autotune_msbfs(blest_handle h, const int32_t* srcs, int32_t k
         return cuda_fail(e, "cudaEventCreate");
     }
     const int saved_pull = h->ms_pull, saved_chunk = h->ms_chunk, saved_bps = h->ms_blocks_per_sm;
+    const int saved_levels = h->ms_levels;
     double best = 1e300, best_pull[2] = {-1.0, -1.0};
-    int bp = saved_pull, bc = saved_chunk, bb = saved_bps, timed = 0;
+    int bp = saved_pull, bc = saved_chunk, bb = saved_bps, bl = saved_levels, timed = 0;
     for (int pull : {BLEST_PULL_POPC, BLEST_PULL_MMA})
         for (int chunk : chunks)
-            for (int bps : {0, 1, 2}) {   // blocks per SM above what fits run as many as fit
+            for (int bps : {0, 1, 2})   // blocks per SM above what fits run as many as fit
+            for (int levels : {1, 2}) {  // vertex-major, bit planes
                 if (s) break;
+                if (pull == BLEST_PULL_MMA && levels != 2) continue;   // one layout is enough to time the MMA
                 h->ms_pull = pull;
                 h->ms_chunk = chunk;
                 h->ms_blocks_per_sm = bps;
+                h->ms_levels = levels;
                 for (int pass = 0; pass < 2 && !s; ++pass) {
                     if (pass == 1) cudaEventRecord(e0, h->stream);
                     s = blest_msbfs_device(h, srcs, k, d_out, h->stream);
@@ -1226,18 +1246,19 @@ blest_status blest_autotune_msbfs(blest_handle h, const int32_t* srcs, int32_t k
                 cudaEventElapsedTime(&ms, e0, e1);
                 ++timed;
                 if (best_pull[pull] < 0 || ms < best_pull[pull]) best_pull[pull] = ms;
-                if (ms < best) { best = ms; bp = pull; bc = chunk; bb = bps; }
+                if (ms < best) { best = ms; bp = pull; bc = chunk; bb = bps; bl = levels; }
             }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(d_out);
     if (s) {
         h->ms_pull = saved_pull; h->ms_chunk = saved_chunk; h->ms_blocks_per_sm = saved_bps;
+        h->ms_levels = saved_levels;
         return s;
     }
-    h->ms_pull = bp; h->ms_chunk = bc; h->ms_blocks_per_sm = bb;
+    h->ms_pull = bp; h->ms_chunk = bc; h->ms_blocks_per_sm = bb; h->ms_levels = bl;
     if (out) {
-        out->pull = bp; out->chunk = bc; out->blocks_per_sm = bb; out->candidates = timed;
+        out->pull = bp; out->chunk = bc; out->blocks_per_sm = bb; out->levels = bl; out->candidates = timed;
         out->best_ms = best; out->popc_ms = best_pull[0]; out->mma_ms = best_pull[1];
     }
     return BLEST_OK;

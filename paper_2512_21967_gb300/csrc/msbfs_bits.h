@@ -45,4 +45,19 @@ BLEST_HD uint64_t levels_of_8(const uint64_t (&pw)[8], int c) {
     return transpose8x8(rows);
 }
 
+// Levels of 8 sources from up to 16 planes (levels below 65536): byte j of lo
+// and of hi hold bits 0..7 and 8..15 of the level of source 8 c + j.
+BLEST_HD void levels_of_8x16(const uint64_t (&pw)[16], int c, uint64_t& lo, uint64_t& hi) {
+    uint64_t r0 = 0, r1 = 0;
+#ifdef __CUDACC__
+#pragma unroll
+#endif
+    for (int p = 0; p < 8; ++p) {
+        r0 |= ((pw[p] >> (8 * c)) & 0xFFull) << (8 * p);
+        r1 |= ((pw[8 + p] >> (8 * c)) & 0xFFull) << (8 * p);
+    }
+    lo = transpose8x8(r0);
+    hi = transpose8x8(r1);
+}
+
 }  // namespace blest

@@ -13,12 +13,18 @@
 //   stage 2: a coalesced sweep over vertices: diff = V_next ^ V_curr becomes
 //     the next frontier, newly set bits give levels, and the slice sets of
 //     vertices with any new bit are enqueued with one atomicAdd per warp.
-// Levels are kept as bit planes during the traversal: bit i of plane p's word w
-// of vertex u is bit p of u's level from source 64 w + i.  A sweep ORs each
-// vertex's new-bit word into the planes of the bits set in the level number
-// (a coalesced read-modify-write per vertex and plane, no per-(source, vertex)
-// store), and a final pass rebuilds each vertex's levels, 8 sources at a time
-// with an 8 x 8 bit transpose, into the source-major output in original ids.
+// Two layouts keep the levels during the traversal (LV):
+//   LV 0, vertex-major: a vertex's k levels are contiguous; the sweep writes a
+//     vertex's new levels with one warp store per 32 sources, and the output
+//     kernel transposes them to the source-major output in original ids;
+//   LV 1, bit planes: bit i of plane p's word w of vertex u is bit p of u's level
+//     from source 64 w + i; a sweep ORs each vertex's new-bit word into the planes
+//     of the bits set in the level number (a coalesced read-modify-write per vertex
+//     and plane), and the output kernel rebuilds the levels 8 sources at a time
+//     with 8 x 8 bit transposes.
+// Planes cost popc(level) updates per distinct level at which a vertex gains bits:
+// few on low-diameter graphs (most sources reach a vertex within a few levels),
+// many on high-diameter ones, where the vertex-major layout is cheaper.
 // Two back-ends compute the pull.  PULL 0 (default) ORs the selected frontier
 // words on the CUDA cores.  PULL 1 runs the same product as b1 AND+POPC
 // tensor-core MMAs (m16n8k128): VSS slots along M, sources along N, the slice
@@ -50,7 +56,9 @@ struct MsArgs {
     unsigned long long* vnext;
     unsigned long long* front;
     unsigned long long* Q[3];
-    unsigned long long* planes;   // nplanes x (n x W) words: plane p holds bit p of every level
+    int32_t* lint;                // LV 0: n x kst, lint[u * kst + i] = level of BVSS vertex u from source i
+    int32_t kst;                  // row stride of lint: k rounded up to a multiple of 8
+    unsigned long long* planes;   // LV 1: nplanes x (n x W) words: plane p holds bit p of every level
     int32_t nplanes;              // msbfs_planes(n): enough bits for level n - 1
     int32_t* out;        // k x n, source-major, original ids
     uint32_t* dirty;     // one bit per slice set touched by a mark in a sparse level (cleared by the sweep)
@@ -62,10 +70,27 @@ struct MsArgs {
     unsigned int phantom;
 };
 
-// Level lvl for the new bits d of word w of vertex u: d is ORed into every plane
-// p with bit p set in lvl.  Only the calling lane writes u's words in a sweep, so
-// a plain read-modify-write suffices; plane p was cleared during stage 1 of level
-// 2^p, its first use.
+// LV 0: levels of the new bits, vertex-major.  Lane j holds the new-bit word d
+// (sources 64 w .. 64 w + 63) of vertex u0 + stride * j; for each such vertex with
+// a new bit the warp writes that vertex's entries with two stores of 32
+// consecutive sources, so a store touches one row instead of 32.
+__device__ __forceinline__ void ms_write_levels(const MsArgs& a, unsigned long long d, int u0, int stride, int w,
+                                                int lvl, int lane) {
+    unsigned int todo = __ballot_sync(0xffffffffu, d != 0ull);
+    while (todo) {
+        const int j = __ffs(todo) - 1;
+        todo &= todo - 1u;
+        const unsigned long long dj = __shfl_sync(0xffffffffu, d, j);
+        int32_t* row = a.lint + (size_t)(u0 + stride * j) * (size_t)a.kst + (size_t)(64 * w);
+        if ((dj >> lane) & 1ull) row[lane] = lvl;
+        if ((dj >> (32 + lane)) & 1ull) row[32 + lane] = lvl;
+    }
+}
+
+// LV 1: level lvl for the new bits d of word w of vertex u: d is ORed into every
+// plane p with bit p set in lvl.  Only the calling lane writes u's words in a
+// sweep, so a plain read-modify-write suffices (measured faster than returnless
+// atomic ORs); plane p was cleared during stage 1 of level 2^p, its first use.
 template <int W>
 __device__ __forceinline__ void ms_write_planes(const MsArgs& a, unsigned long long d, int u, int w, int lvl) {
     if (!d) return;
@@ -75,7 +100,7 @@ __device__ __forceinline__ void ms_write_planes(const MsArgs& a, unsigned long l
         if ((lvl >> p) & 1) q[(size_t)p * stride] |= d;
 }
 
-template <int W>
+template <int W, int LV>
 __device__ __forceinline__ void ms_sweep(const MsArgs& a, int lvl, unsigned long long* Qout, unsigned int* qcount) {
     const int lane = threadIdx.x & 31;
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
@@ -101,7 +126,8 @@ __device__ __forceinline__ void ms_sweep(const MsArgs& a, int lvl, unsigned long
                     any = true;
                 }
             }
-            ms_write_planes<W>(a, d, u, w, lvl);
+            if (LV == 1) ms_write_planes<W>(a, d, u, w, lvl);
+            else ms_write_levels(a, d, c * kWarp, 1, w, lvl, lane);
         }
         const unsigned int ball = __ballot_sync(0xffffffffu, any);
         int st = 0, ln = 0;
@@ -123,7 +149,7 @@ __device__ __forceinline__ void ms_sweep(const MsArgs& a, int lvl, unsigned long
 // has a current frontier word), levels, and the enqueue.  Slice sets outside
 // the dirty set keep stale frontier words, but they are not queued, so stage 1
 // never reads them.
-template <int W>
+template <int W, int LV>
 __device__ __forceinline__ void ms_sweep_sparse(const MsArgs& a, int lvl, unsigned long long* Qout,
                                                 unsigned int* qcount) {
     const int lane = threadIdx.x & 31;
@@ -155,7 +181,8 @@ __device__ __forceinline__ void ms_sweep_sparse(const MsArgs& a, int lvl, unsign
                             any = true;
                         }
                     }
-                    ms_write_planes<W>(a, d, u, w, lvl);
+                    if (LV == 1) ms_write_planes<W>(a, d, u, w, lvl);
+                    else ms_write_levels(a, d, 8 * 32 * t + j, 8, w, lvl, lane);
                 }
             }
         }
@@ -305,7 +332,7 @@ __device__ __forceinline__ void ms_pull_tile(const MsArgs& a, const MsTile<W>& t
         }
 }
 
-template <int W, int PULL>
+template <int W, int PULL, int LV>
 __device__ __forceinline__ void ms_body(const MsArgs& a) {
     const int lane = threadIdx.x & 31;
     const int gtid = (int)(blockIdx.x * blockDim.x + threadIdx.x);
@@ -321,7 +348,7 @@ __device__ __forceinline__ void ms_body(const MsArgs& a) {
         atomicOr(&a.vnext[(size_t)r * W + (i >> 6)], 1ull << (i & 63));
     }
     if (!grid_barrier(ctrl, gridDim.x, a.phantom, gen, a.timeout_ns)) return;
-    ms_sweep<W>(a, 0, a.Q[1], &ctrl->qcount[1]);
+    ms_sweep<W, LV>(a, 0, a.Q[1], &ctrl->qcount[1]);
     unsigned int qn = 0;
     if (!grid_barrier(ctrl, gridDim.x, a.phantom, gen, a.timeout_ns, &ctrl->qcount[1], &qn)) return;
 
@@ -337,7 +364,7 @@ __device__ __forceinline__ void ms_body(const MsArgs& a) {
         const unsigned long long* Qin = a.Q[lvl % 3];
         unsigned long long* Qout = a.Q[(lvl + 1) % 3];
         unsigned int* qcount_next = &ctrl->qcount[(lvl + 1) & 3];
-        if ((lvl & (lvl - 1)) == 0) {
+        if (LV == 1 && (lvl & (lvl - 1)) == 0) {
             // lvl = 2^p: this level's sweep is the first to write plane p, so it is
             // cleared now (stage 1 does not touch the planes; the barrier orders it)
             const int p = __ffs(lvl) - 1;
@@ -361,8 +388,8 @@ __device__ __forceinline__ void ms_body(const MsArgs& a) {
             e_next = e_after;
         }
         if (!grid_barrier(ctrl, gridDim.x, a.phantom, gen, a.timeout_ns)) return;
-        if (sparse) ms_sweep_sparse<W>(a, lvl, Qout, qcount_next);
-        else ms_sweep<W>(a, lvl, Qout, qcount_next);
+        if (sparse) ms_sweep_sparse<W, LV>(a, lvl, Qout, qcount_next);
+        else ms_sweep<W, LV>(a, lvl, Qout, qcount_next);
         unsigned int qnext = 0;
         if (!grid_barrier(ctrl, gridDim.x, a.phantom, gen, a.timeout_ns, qcount_next, &qnext)) return;
         if (qnext == 0) break;
@@ -371,13 +398,46 @@ __device__ __forceinline__ void ms_body(const MsArgs& a) {
     if (gtid == 0) ctrl->levels = (unsigned int)lvl;
 }
 
-// out[i*n + v] = level of v from source i (original ids), -1 if unreached: a
-// separate launch after the traversal (ctrl->levels holds its level count), so
-// that the traversal kernel keeps its register budget.  Lane j takes vertex
-// v = 32 b + j, reads its visited word and its plane words (the planes that can
-// hold a bit of a level <= the level count: the ones the traversal cleared),
-// rebuilds its levels 8 sources at a time and stores them source by source, 32
+// Output kernels: out[i*n + v] = level of v from source i (original ids), -1 if
+// unreached, as a separate launch after the traversal (ctrl->levels holds its
+// level count) so that the traversal kernel keeps its register budget.  Lane j
+// takes vertex v = 32 b + j and stores the levels source by source, 32
 // consecutive vertices per store.
+
+// LV 0: the vertex's levels are read 4 sources (16 bytes) at a time.
+template <int W>
+__global__ void __launch_bounds__(kMsBlock) msbfs_output_rows_kernel(MsArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    const int nvb = (a.n + kWarp - 1) / kWarp;
+    for (int b = gwarp; b < nvb; b += nwarps) {
+        const int v = b * kWarp + lane;
+        if (v >= a.n) continue;
+        const int u = a.new_id ? __ldg(&a.new_id[v]) : v;
+        const int4* row = reinterpret_cast<const int4*>(a.lint + (size_t)u * (size_t)a.kst);
+        int32_t* o = a.out + v;
+#pragma unroll 1
+        for (int w = 0; w < W; ++w) {
+            const unsigned long long vis = ld_cg(&a.vcur[(size_t)u * W + w]);
+            const int i_end = min(64 * w + 64, a.k);
+#pragma unroll 1
+            for (int i0 = 64 * w; i0 < i_end; i0 += 4) {
+                const uint32_t bits = (uint32_t)(vis >> (i0 - 64 * w)) & 0xFu;
+                // positions of sources that never reached u are never written, so never used
+                const int4 lv = bits ? ld_cg(&row[i0 >> 2]) : make_int4(-1, -1, -1, -1);
+                o[(size_t)i0 * (size_t)a.n] = bits & 1u ? lv.x : -1;
+                if (i0 + 1 < i_end) o[(size_t)(i0 + 1) * (size_t)a.n] = bits & 2u ? lv.y : -1;
+                if (i0 + 2 < i_end) o[(size_t)(i0 + 2) * (size_t)a.n] = bits & 4u ? lv.z : -1;
+                if (i0 + 3 < i_end) o[(size_t)(i0 + 3) * (size_t)a.n] = bits & 8u ? lv.w : -1;
+            }
+        }
+    }
+}
+
+// LV 1: the vertex's plane words (the planes that can hold a bit of a level <= the
+// level count: the ones the traversal cleared) are read once, and the levels are
+// rebuilt 8 sources at a time.
 template <int W>
 __global__ void __launch_bounds__(kMsBlock) msbfs_output_kernel(MsArgs a) {
     const int lane = threadIdx.x & 31;
@@ -414,34 +474,64 @@ __global__ void __launch_bounds__(kMsBlock) msbfs_output_kernel(MsArgs a) {
                     }
                 }
             } else {
-                // levels of 256 and more (high-diameter graphs): plane by plane, per source
+                // levels of 256 and more (high-diameter graphs): planes 0..15 in registers, two
+                // transposes per 8 sources; planes 16.. (levels of 65536 and more) read per source
+                uint64_t pw[16];
+#pragma unroll
+                for (int p = 0; p < 16; ++p) pw[p] = p < np ? ld_cg(&a.planes[(size_t)p * pstride + idx]) : 0ull;
 #pragma unroll 1
-                for (int i = 64 * w; i < i_end; ++i) {
-                    const int bit = i - 64 * w;
-                    int32_t lv = -1;
-                    if ((vis >> bit) & 1ull) {
-                        lv = 0;
-                        for (int p = 0; p < np; ++p)
-                            lv |= (int32_t)((ld_cg(&a.planes[(size_t)p * pstride + idx]) >> bit) & 1ull) << p;
+                for (int i0 = 64 * w; i0 < i_end; i0 += 8) {
+                    const int c = (i0 - 64 * w) >> 3;
+                    uint64_t lo, hi;
+                    levels_of_8x16(pw, c, lo, hi);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int i = i0 + j;
+                        if (i >= i_end) continue;
+                        const int bit = 8 * c + j;
+                        int32_t lv = -1;
+                        if ((vis >> bit) & 1ull) {
+                            lv = (int32_t)((lo >> (8 * j)) & 0xFFull) | ((int32_t)((hi >> (8 * j)) & 0xFFull) << 8);
+                            for (int p = 16; p < np; ++p)
+                                lv |= (int32_t)((ld_cg(&a.planes[(size_t)p * pstride + idx]) >> bit) & 1ull) << p;
+                        }
+                        o[(size_t)i * (size_t)a.n] = lv;
                     }
-                    o[(size_t)i * (size_t)a.n] = lv;
                 }
             }
         }
     }
 }
 
-template <int W, int PULL>
+template <int W, int PULL, int LV>
 __global__ void __launch_bounds__(kMsBlock) msbfs_kernel(MsArgs a) {
-    ms_body<W, PULL>(a);
+    ms_body<W, PULL, LV>(a);
     fold_status(a.ctrl);
 }
 
 // One word of sources (W = 1) on the CUDA cores, held to 3 resident blocks per SM:
 // as many warps in flight as the register file allows at that width.
+template <int LV>
 __global__ void __launch_bounds__(kMsBlock, 3) msbfs_kernel_w1(MsArgs a) {
-    ms_body<1, 0>(a);
+    ms_body<1, 0, LV>(a);
     fold_status(a.ctrl);
+}
+
+template <int LV>
+void* ms_kernel_ptr(int W, int pull) {
+    if (pull == 1)
+        return W == 1 ? (void*)&msbfs_kernel<1, 1, LV> : (W == 2 ? (void*)&msbfs_kernel<2, 1, LV>
+                                                                  : (void*)&msbfs_kernel<4, 1, LV>);
+    return W == 1 ? (void*)&msbfs_kernel_w1<LV> : (W == 2 ? (void*)&msbfs_kernel<2, 0, LV>
+                                                           : (void*)&msbfs_kernel<4, 0, LV>);
+}
+
+void* ms_output_ptr(int W, int lv) {
+    if (lv == 1)
+        return W == 1 ? (void*)&msbfs_output_kernel<1> : (W == 2 ? (void*)&msbfs_output_kernel<2>
+                                                                 : (void*)&msbfs_output_kernel<4>);
+    return W == 1 ? (void*)&msbfs_output_rows_kernel<1> : (W == 2 ? (void*)&msbfs_output_rows_kernel<2>
+                                                                   : (void*)&msbfs_output_rows_kernel<4>);
 }
 
 template <class T>
@@ -463,6 +553,7 @@ void free_msbfs_state(MsbfsState& s) {
     cudaFree(s.vnext);
     cudaFree(s.front);
     cudaFree(s.Q);
+    cudaFree(s.lint);
     cudaFree(s.planes);
     cudaFree(s.roots);
     cudaFree(s.dirty);
@@ -486,7 +577,13 @@ int run_msbfs(MsbfsState& s, const MsbfsLaunchCommon& c, const std::vector<int32
         if ((e = grow(s.front, cap_f, words, own)) != cudaSuccess) break;
         s.words_cap = std::min(cap_v, std::min(cap_n, cap_f));
         if ((e = grow(s.Q, s.qcap, std::max<int64_t>(c.nvss, 1), own, 3)) != cudaSuccess) break;
-        if ((e = grow(s.planes, s.planes_cap, msbfs_plane_words(c.n, k, chunk), own)) != cudaSuccess) break;
+        const int lv = c.levels_layout == 1 ? 1 : 0;
+        const int32_t kst = (k + 7) & ~7;
+        if (lv == 1) {
+            if ((e = grow(s.planes, s.planes_cap, msbfs_plane_words(c.n, k, chunk), own)) != cudaSuccess) break;
+        } else {
+            if ((e = grow(s.lint, s.lint_cap, msbfs_level_entries(c.n, k, chunk), own)) != cudaSuccess) break;
+        }
         if ((e = grow(s.roots, s.roots_cap, k, own)) != cudaSuccess) break;
         const int64_t dwords = ((int64_t)c.nss + 31) / 32;
         if ((e = grow(s.dirty, s.dirty_cap, dwords, own)) != cudaSuccess) break;
@@ -508,6 +605,8 @@ int run_msbfs(MsbfsState& s, const MsbfsLaunchCommon& c, const std::vector<int32
         a.front = s.front;
         for (int i = 0; i < 3; ++i) a.Q[i] = s.Q + (size_t)i * (size_t)s.qcap;
         int32_t* out = d_out + (size_t)i0 * (size_t)c.n;
+        a.lint = s.lint;
+        a.kst = kst;
         a.planes = s.planes;
         a.nplanes = msbfs_planes(c.n);
         a.out = out;
@@ -518,9 +617,7 @@ int run_msbfs(MsbfsState& s, const MsbfsLaunchCommon& c, const std::vector<int32
         a.level_cap = c.level_cap;
         a.timeout_ns = c.timeout_ns;
         a.phantom = c.phantom;
-        void* kfn = c.pull == 1
-                        ? (W == 1 ? (void*)&msbfs_kernel<1, 1> : (W == 2 ? (void*)&msbfs_kernel<2, 1> : (void*)&msbfs_kernel<4, 1>))
-                        : (W == 1 ? (void*)&msbfs_kernel_w1 : (W == 2 ? (void*)&msbfs_kernel<2, 0> : (void*)&msbfs_kernel<4, 0>));
+        void* kfn = lv == 1 ? ms_kernel_ptr<1>(W, c.pull) : ms_kernel_ptr<0>(W, c.pull);
         int nb = 0;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn, kMsBlock, 0)) != cudaSuccess) break;
         if (nb <= 0) { *err = "msbfs kernel cannot be resident"; return 5; }
@@ -531,8 +628,7 @@ int run_msbfs(MsbfsState& s, const MsbfsLaunchCommon& c, const std::vector<int32
         const int64_t warps_needed = ((int64_t)c.n + kWarp - 1) / kWarp;
         const int64_t blocks = std::min<int64_t>((warps_needed + kMsBlock / kWarp - 1) / (kMsBlock / kWarp),
                                                  (int64_t)c.sms * 8);
-        void* ofn = W == 1 ? (void*)&msbfs_output_kernel<1> : (W == 2 ? (void*)&msbfs_output_kernel<2>
-                                                                     : (void*)&msbfs_output_kernel<4>);
+        void* ofn = ms_output_ptr(W, lv);
         if ((e = cudaLaunchKernel(ofn, dim3((unsigned)std::max<int64_t>(blocks, 1)), dim3(kMsBlock), args, 0, st)) != cudaSuccess)
             break;
     }

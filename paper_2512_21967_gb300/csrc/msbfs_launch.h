@@ -19,6 +19,13 @@ inline int msbfs_words(int64_t k, int chunk = kMsbfsChunk) {
     return kc <= 64 ? 1 : (kc <= 128 ? 2 : 4);
 }
 
+// int32 entries of the vertex-major level buffer for k sources: n rows of the
+// largest launch's source count rounded up to a multiple of 8.
+inline int64_t msbfs_level_entries(int32_t n, int64_t k, int chunk = kMsbfsChunk) {
+    const int64_t kc = std::min<int64_t>(k, chunk);
+    return ((kc + 7) & ~int64_t(7)) * (int64_t)n;
+}
+
 // 64-bit words of the level bit planes for k sources: msbfs_planes(n) planes of
 // n vertices x W words (plane p holds bit p of every (vertex, source) level).
 inline int64_t msbfs_plane_words(int32_t n, int64_t k, int chunk = kMsbfsChunk) {
@@ -36,6 +43,8 @@ struct MsbfsState {
     unsigned long long* front = nullptr;
     int64_t qcap = 0;
     unsigned long long* Q = nullptr;   // 3 * qcap
+    int64_t lint_cap = 0;              // int32 entries of the vertex-major level buffer
+    int32_t* lint = nullptr;
     int64_t planes_cap = 0;            // u64 words of the level bit planes
     unsigned long long* planes = nullptr;
     int64_t roots_cap = 0;
@@ -60,6 +69,7 @@ struct MsbfsLaunchCommon {
     int32_t level_cap = 0;
     int pull = 0;                       // 0 CUDA-core OR of frontier words, 1 b1 tensor-core MMAs
     int chunk = kMsbfsChunk;            // sources per launch: 64, 128 or 256
+    int levels_layout = 0;              // 0 vertex-major levels, 1 bit planes
 };
 
 // Runs k = roots.size() traversals (sources already in BVSS ids) in launches of

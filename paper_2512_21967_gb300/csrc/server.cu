@@ -48,6 +48,7 @@ struct HandleView {
     const int32_t* new_id_dev;
     const int32_t* new_id_host;   // NULL = identity
     int sms;
+    int levels_layout;            // multi-source level layout (0 vertex-major, 1 bit planes)
 };
 bool handle_view(blest_handle h, HandleView* v);
 }  // namespace blest
@@ -76,7 +77,8 @@ struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     unsigned int* d_ctrl = nullptr;  // 256-byte control block of the launch
-    unsigned int* h_status = nullptr;  // pinned copy of the sticky status word
+    unsigned int* h_status = nullptr;  // pinned: [0] the sticky status word, [1] the launch's level count
+    int32_t graph = -1;                // graph of the launch in flight
     bool busy = false;
     std::vector<Query*> batch;
     int32_t* d_levels = nullptr;
@@ -97,6 +99,7 @@ struct blest_server {
     std::condition_variable cv_work;   // new queries or shutdown
     std::condition_variable cv_done;   // a query finished
     std::vector<std::deque<Query*>> pending;
+    std::vector<int32_t> last_levels;  // per graph: levels of its last finished launch (0 = none yet)
     std::unordered_map<uint64_t, std::unique_ptr<Query>> queries;
     uint64_t next_ticket = 1;
     int64_t mem_used = 0, mem_peak = 0;
@@ -144,7 +147,8 @@ int64_t launch_bytes(const blest::HandleView& v, int k) {
     int64_t b = (int64_t)k * v.n * 4;                          // levels
     b += 3 * (int64_t)v.n * W * 8;                            // V_curr, V_next, frontier
     b += 3 * std::max<int64_t>(v.nvss, 1) * 8;                // queues
-    b += blest::msbfs_plane_words(v.n, k) * 8;                // level bit planes in BVSS ids
+    if (v.levels_layout == 1) b += blest::msbfs_plane_words(v.n, k) * 8;   // level bit planes in BVSS ids
+    else b += blest::msbfs_level_entries(v.n, k) * 4;                   // vertex-major levels in BVSS ids
     b += (int64_t)k * 4 + 4 * 256;                             // roots, alignment slack
     b += ((int64_t)v.nss + 31) / 32 * 4;                       // dirty slice sets
     return b;
@@ -168,9 +172,15 @@ cudaError_t alloc_launch(Slot& s, const blest::HandleView& v, int k) {
     m.words_cap = words;
     if ((e = alloc_async(m.Q, 3 * std::max<int64_t>(v.nvss, 1), s.stream)) != cudaSuccess) return e;
     m.qcap = std::max<int64_t>(v.nvss, 1);
-    const int64_t pw = blest::msbfs_plane_words(v.n, k);
-    if ((e = alloc_async(m.planes, pw, s.stream)) != cudaSuccess) return e;
-    m.planes_cap = pw;
+    if (v.levels_layout == 1) {
+        const int64_t pw = blest::msbfs_plane_words(v.n, k);
+        if ((e = alloc_async(m.planes, pw, s.stream)) != cudaSuccess) return e;
+        m.planes_cap = pw;
+    } else {
+        const int64_t lev = blest::msbfs_level_entries(v.n, k);
+        if ((e = alloc_async(m.lint, lev, s.stream)) != cudaSuccess) return e;
+        m.lint_cap = lev;
+    }
     if ((e = alloc_async(m.roots, k, s.stream)) != cudaSuccess) return e;
     m.roots_cap = k;
     const int64_t dwords = ((int64_t)v.nss + 31) / 32;
@@ -181,7 +191,7 @@ cudaError_t alloc_launch(Slot& s, const blest::HandleView& v, int k) {
 
 void free_launch(Slot& s) {
     blest::MsbfsState& m = s.ms;
-    for (void* p : {(void*)s.d_levels, (void*)m.vcur, (void*)m.vnext, (void*)m.front, (void*)m.Q, (void*)m.planes,
+    for (void* p : {(void*)s.d_levels, (void*)m.vcur, (void*)m.vnext, (void*)m.front, (void*)m.Q, (void*)m.lint, (void*)m.planes,
                     (void*)m.roots, (void*)m.dirty})
         if (p) cudaFreeAsync(p, s.stream);
     s.d_levels = nullptr;
@@ -197,7 +207,8 @@ bool retire(blest_server* sv) {
         if (q == cudaErrorNotReady) continue;
         blest_status st = BLEST_OK;
         if (q != cudaSuccess) st = BLEST_ERR_CUDA;
-        else if (*s.h_status) st = (blest_status)*s.h_status;
+        else if (s.h_status[0]) st = (blest_status)s.h_status[0];
+        if (q == cudaSuccess && s.graph >= 0) sv->last_levels[(size_t)s.graph] = (int32_t)s.h_status[1];
         const auto now = clk::now();
         for (Query* r : s.batch) {
             r->status = st;
@@ -265,7 +276,11 @@ bool launch_more(blest_server* sv) {
         c.new_id = v.new_id_dev;
         c.ctrl = s.d_ctrl;
         c.sms = v.sms;
+        if (sv->p.narrow_sms > 0 && sv->last_levels[(size_t)g] > sv->p.narrow_levels)
+            c.sms = std::min(v.sms, sv->p.narrow_sms);
         c.blocks_per_sm = sv->p.blocks_per_sm;
+        c.levels_layout = v.levels_layout;
+        s.graph = g;
         int rc = 0;
         const char* err = nullptr;
         if (e == cudaSuccess) e = cudaMemsetAsync(s.d_ctrl + kStickyWord, 0, sizeof(unsigned int), s.stream);
@@ -279,6 +294,8 @@ bool launch_more(blest_server* sv) {
         }
         if (e == cudaSuccess && rc == 0)
             e = cudaMemcpyAsync(s.h_status, s.d_ctrl + kStickyWord, sizeof(unsigned int), cudaMemcpyDeviceToHost, s.stream);
+        if (e == cudaSuccess && rc == 0)   // Ctrl::levels of the (last) launch
+            e = cudaMemcpyAsync(s.h_status + 1, s.d_ctrl + 6, sizeof(unsigned int), cudaMemcpyDeviceToHost, s.stream);
         if (e == cudaSuccess && rc == 0) e = cudaEventRecord(s.done, s.stream);
         if (e != cudaSuccess || rc != 0) {
             // the launch could not be issued: fail its queries now
@@ -335,6 +352,8 @@ blest_status blest_server_create(const blest_handle* graphs, int32_t num_graphs,
     sv->p.max_inflight = params && params->max_inflight > 0 ? params->max_inflight : 4;
     sv->p.blocks_per_sm = params && params->blocks_per_sm > 0 ? params->blocks_per_sm : 1;
     sv->p.max_queries_per_launch = params && params->max_queries_per_launch > 0 ? params->max_queries_per_launch : 0;
+    sv->p.narrow_sms = params && params->narrow_sms > 0 ? params->narrow_sms : 0;
+    sv->p.narrow_levels = params && params->narrow_levels > 0 ? params->narrow_levels : 256;
     if (sv->p.max_batch_sources > 256) return fail(BLEST_ERR_INVALID_ARG, "max_batch_sources must be <= 256");
     if (sv->p.max_inflight > 64) return fail(BLEST_ERR_INVALID_ARG, "max_inflight must be <= 64");
     for (int32_t g = 0; g < num_graphs; ++g) {
@@ -344,13 +363,14 @@ blest_status blest_server_create(const blest_handle* graphs, int32_t num_graphs,
         sv->views.push_back(v);
     }
     sv->pending.resize((size_t)num_graphs);
+    sv->last_levels.assign((size_t)num_graphs, 0);
     sv->slots.resize((size_t)sv->p.max_inflight);
     cudaError_t e;
     for (Slot& s : sv->slots) {
         if ((e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming)) != cudaSuccess ||
             (e = cudaMalloc(&s.d_ctrl, 256)) != cudaSuccess || (e = cudaMemset(s.d_ctrl, 0, 256)) != cudaSuccess ||
-            (e = cudaHostAlloc(&s.h_status, sizeof(unsigned int), cudaHostAllocDefault)) != cudaSuccess) {
+            (e = cudaHostAlloc(&s.h_status, 2 * sizeof(unsigned int), cudaHostAllocDefault)) != cudaSuccess) {
             for (Slot& t : sv->slots) {
                 if (t.stream) cudaStreamDestroy(t.stream);
                 if (t.done) cudaEventDestroy(t.done);
@@ -359,7 +379,8 @@ blest_status blest_server_create(const blest_handle* graphs, int32_t num_graphs,
             }
             return fail(e == cudaErrorMemoryAllocation ? BLEST_ERR_OOM : BLEST_ERR_CUDA, cudaGetErrorString(e));
         }
-        *s.h_status = 0;
+        s.h_status[0] = 0;
+        s.h_status[1] = 0;
     }
     blest_server* raw = sv.get();
     int dev = 0;

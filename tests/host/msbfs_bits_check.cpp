@@ -37,6 +37,24 @@ int main() {
                                 lv[8 * c + j]);
         }
     }
+    for (int it = 0; it < 20000; ++it) {
+        uint64_t pw[16];
+        int lv[64];
+        for (int i = 0; i < 64; ++i) lv[i] = (int)(rng() & 0xFFFF);
+        for (int p = 0; p < 16; ++p) {
+            pw[p] = 0;
+            for (int i = 0; i < 64; ++i) pw[p] |= (uint64_t)((lv[i] >> p) & 1) << i;
+        }
+        for (int c = 0; c < 8; ++c) {
+            uint64_t lo, hi;
+            blest::levels_of_8x16(pw, c, lo, hi);
+            for (int j = 0; j < 8; ++j) {
+                const int got = (int)((lo >> (8 * j)) & 0xFF) | ((int)((hi >> (8 * j)) & 0xFF) << 8);
+                if (got != lv[8 * c + j] && failures++ < 10)
+                    std::printf("levels_of_8x16 c=%d j=%d got %d want %d\n", c, j, got, lv[8 * c + j]);
+            }
+        }
+    }
     const int32_t ns[] = {1, 2, 3, 4, 7, 8, 255, 256, 257, 4194304, 16777216, 2147483647};
     for (int32_t n : ns) {
         const int p = blest::msbfs_planes(n);

@@ -20,8 +20,12 @@ int main() {
                 const int w = blest::msbfs_words(kc);
                 const int64_t l = blest::msbfs_plane_words(n, kc);
                 const int planes = blest::msbfs_planes(n);
+                const int64_t rows = blest::msbfs_level_entries(n, kc);
+                const int64_t stride = rows / n;
                 const bool ok = w <= whole_w && l <= whole_l && 64 * w >= kc && (w == 1 || w == 2 || w == 4) &&
-                                l == (int64_t)planes * n * w && (int64_t)(n - 1) < ((int64_t)1 << planes);
+                                l == (int64_t)planes * n * w && (int64_t)(n - 1) < ((int64_t)1 << planes) &&
+                                rows <= blest::msbfs_level_entries(n, k) && rows % n == 0 && stride % 8 == 0 &&
+                                stride >= kc && stride < kc + 8;
                 if (!ok) {
                     if (failures < 10)
                         std::printf("n=%d k=%lld chunk at %lld: words %d/%d levels %lld/%lld\n", n, (long long)k,

@@ -244,12 +244,14 @@ def test_msbfs_matches_k_oracle_runs(gpu, k):
             blest.blest_destroy(h)
 
 
+@pytest.mark.parametrize("levels", [1, 2])
 @pytest.mark.parametrize("pull", [blest.BLEST_PULL_POPC, blest.BLEST_PULL_MMA])
 @pytest.mark.parametrize("chunk", [64, 128, 256])
-def test_msbfs_pull_backends_and_launch_sizes(gpu, pull, chunk):
-    """Both multi-source pull back-ends (CUDA-core OR, b1 tensor-core MMA) and every
-    launch size give the oracle's levels, for source counts across word and launch
-    boundaries, on a power-law graph and on a ragged grid."""
+def test_msbfs_pull_backends_and_launch_sizes(gpu, pull, chunk, levels):
+    """Both multi-source pull back-ends (CUDA-core OR, b1 tensor-core MMA), both
+    level layouts (vertex-major, bit planes) and every launch size give the
+    oracle's levels, for source counts across word and launch boundaries, on a
+    power-law graph and on a ragged grid."""
     g = synth.rmat_graph(11, 16, seed=5)
     gg, _ = synth.grid_graph(37, 0.9, seed=6)
     for graph, order in ((g, blest.BLEST_ORDER_COMPRESS), (gg, blest.BLEST_ORDER_BANDWIDTH)):
@@ -257,6 +259,7 @@ def test_msbfs_pull_backends_and_launch_sizes(gpu, pull, chunk):
         try:
             blest.blest_set_option(h, blest.BLEST_OPT_MS_PULL, pull)
             blest.blest_set_option(h, blest.BLEST_OPT_MS_CHUNK, chunk)
+            blest.blest_set_option(h, blest.BLEST_OPT_MS_LEVELS, levels)
             for k in (3, 64, 65, 130, 300):
                 srcs = synth.pick_sources(graph, k, seed=31 + k)
                 exp = oracle.msbfs_levels(graph.n, graph.row_ptr, graph.col_idx, srcs, threads=8)
@@ -272,12 +275,35 @@ def test_msbfs_autotune_keeps_levels_exact(gpu):
     h = blest.blest_graph_create(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_COMPRESS)
     try:
         r = blest.blest_autotune_msbfs(h, srcs)
-        assert r["candidates"] == 2 * 3 * 3                 # 2 back-ends x 3 launch sizes x 3 grid sizes
+        # CUDA-core pull: 3 launch sizes x 3 grid sizes x 2 level layouts; MMA: bit planes only
+        assert r["candidates"] == 3 * 3 * 2 + 3 * 3
+        assert r["levels"] in (1, 2)
         assert r["popc_ms"] > 0 and r["mma_ms"] > 0 and r["best_ms"] == min(r["popc_ms"], r["mma_ms"])
         assert r["chunk"] in (64, 128, 256) and r["pull"] in (blest.BLEST_PULL_POPC, blest.BLEST_PULL_MMA)
         assert np.array_equal(blest.blest_msbfs(h, srcs), exp)
     finally:
         blest.blest_destroy(h)
+
+
+@pytest.mark.parametrize("levels", [1, 2])
+def test_msbfs_more_than_256_levels(gpu, levels):
+    """A long thin grid: levels above 255 take the 16-plane path of the bit-plane
+    output (and the vertex-major layout stores them as they are)."""
+    rows, cols = 3, 400
+    edges = [(r * cols + c, r * cols + c + 1) for r in range(rows) for c in range(cols - 1)]
+    edges += [(r * cols + c, (r + 1) * cols + c) for r in range(rows - 1) for c in range(cols)]
+    src, dst = np.array(edges, np.int32).T
+    g = synth.csr_from_edges(rows * cols, src, dst)
+    srcs = np.array([0, cols - 1, rows * cols - 1, 600, 5], np.int32)
+    exp = oracle.msbfs_levels(g.n, g.row_ptr, g.col_idx, srcs)
+    assert exp.max() > 300
+    for order in (blest.BLEST_ORDER_NONE, blest.BLEST_ORDER_BANDWIDTH):
+        h = blest.blest_graph_create(g.n, g.row_ptr, g.col_idx, order)
+        try:
+            blest.blest_set_option(h, blest.BLEST_OPT_MS_LEVELS, levels)
+            assert np.array_equal(blest.blest_msbfs(h, srcs), exp)
+        finally:
+            blest.blest_destroy(h)
 
 
 def test_msbfs_grid_and_isolated(gpu):

@@ -62,6 +62,26 @@ def test_results_alone_and_in_the_mix(served):
         blest.blest_server_destroy(srv)
 
 
+def test_narrow_launches_keep_results(served):
+    """Graphs whose last launch ran more than narrow_levels levels (the grids here,
+    40 to 130 levels) launch on a narrow grid of 8 SMs; results stay the oracle's."""
+    graphs, handles, queries = served
+    srv = blest.blest_server_create(handles, max_batch_sources=16, max_inflight=4, narrow_sms=8, narrow_levels=10)
+    try:
+        for _ in range(2):                                 # the first pass learns each graph's level count
+            outs, tickets = [], []
+            for gi, srcs, exp in queries:
+                out = np.full((len(srcs), graphs[gi].n), 99, np.int32)
+                outs.append(out)
+                tickets.append(blest.blest_server_submit(srv, gi, srcs, out))
+            for t in tickets:
+                blest.blest_server_wait(srv, t, 60.0)
+            for out, (_, _, exp) in zip(outs, queries):
+                assert np.array_equal(out, exp)
+    finally:
+        blest.blest_server_destroy(srv)
+
+
 def test_memory_cap_admits_one_launch_at_a_time(served):
     graphs, handles, queries = served
     n_max = max(g.n for g in graphs)
