@@ -179,7 +179,7 @@ def byte_model(h, g, n):
     return w_s, new_id, rp[1:] - rp[:-1]
 
 
-def traversal_bytes(levels_t, new_id_t, w_s_t, nvss_t, nss, n, lazy, direct, nroots, torch):
+def traversal_bytes(levels_t, new_id_t, w_s_t, nvss_t, nss, n, lazy, output_path, nroots, torch):
     """Algorithmic bytes of one single-source (or multi-root) traversal, from its
     level array in original ids, under the model of the fused kernel:
       init: the level array cleared to -1 (4 B per vertex) and the visited
@@ -193,9 +193,10 @@ def traversal_bytes(levels_t, new_id_t, w_s_t, nvss_t, nss, n, lazy, direct, nro
         word holding a newly reached vertex is written back (4 B; eager level 0
         also writes its frontier word);
       level writes: 4 B per reached vertex, plus 4 B for its original id when
-        the sweeps write levels straight to the output (direct);
-      unpermute (not direct): read the order, gather L, write the output, 12 B
-        per vertex.
+        the sweeps write levels straight to the output (output_path 1);
+      unpermute (output_path 2: levels kept in BVSS ids): read the order, gather
+        L, write the output, 12 B per vertex; nothing when the graph keeps its
+        own order (output_path 0, levels written in place).
     Returns (bytes, reached vertices, bytes under the survey's formula with the
     unpermute counted, the same without)."""
     reached = levels_t >= 0
@@ -222,7 +223,7 @@ def traversal_bytes(levels_t, new_id_t, w_s_t, nvss_t, nss, n, lazy, direct, nro
         sweep += 4 * wn * (2 if (not lazy and l == 0) else 1)
     init = 4 * n + 4 * nwords * (2 if lazy else 5)
     body = stage1 + sweep + 4 * nreached
-    total = init + body + (4 * nreached if direct else 12 * n)
+    total = init + body + {0: 0, 1: 4 * nreached, 2: 12 * n}[int(output_path)]
     return total, nreached, body + 4 * n + 12 * n, body + 4 * n
 
 
@@ -387,7 +388,7 @@ def run_ours(args):
                     run_info, _ = blest.blest_get_run_info(h)
                     lazy = run_info["update"] == blest.BLEST_UPDATE_LAZY
                 abytes[i], _, abytes_survey[i, 0], abytes_survey[i, 1] = traversal_bytes(
-                    out, new_id_t, w_s_t, nvss_t, nss, n, lazy, run_info["output_path"] == 1, 1, torch)
+                    out, new_id_t, w_s_t, nvss_t, nss, n, lazy, run_info["output_path"], 1, torch)
         else:
             one_step()
     blest.blest_sync(h)
@@ -470,8 +471,8 @@ def run_ours(args):
                          "traffic": round(tr_ratio * avg_bytes) if tr_ratio else None, "traffic_note": tr_note,
                          "kernel": "bfs_kernel (fused persistent traversal)",
                          "bytes_model": "init + stage-1 visits + dense/sparse sweeps + level writes"
-                                        + (" (direct, no unpermute)" if run_info["output_path"] == 1
-                                           else " + unpermute"),
+                                        + {0: " (in place, no reordering)", 1: " (direct, no unpermute)",
+                                           2: " + unpermute"}[run_info["output_path"]],
                          "bytes_survey_with_unpermute": float(abytes_survey[:, 0].mean()),
                          "bytes_survey_without_unpermute": float(abytes_survey[:, 1].mean()),
                          "bytes_per_launch": avg_bytes, "avg_launch_ms": round(avg_launch_ms, 5)},
@@ -621,7 +622,7 @@ def run_ours_batch(args, torch, blest, dev, rank, world):
     w_s, new_id, nvss = byte_model(h, None, n)
     batch_bytes, _, _, _ = traversal_bytes(out, torch.from_numpy(new_id).to(dev), torch.from_numpy(w_s).to(dev),
                                            torch.from_numpy(nvss).to(dev), (n + 7) // 8, n,
-                                           info["update"] == blest.BLEST_UPDATE_LAZY, info["output_path"] == 1,
+                                           info["update"] == blest.BLEST_UPDATE_LAZY, info["output_path"],
                                            len(srcs), torch)
     torch.cuda.synchronize(dev)
     sampler = ClockSampler() if rank == 0 else None
@@ -805,7 +806,7 @@ def run_ours_window_sweep(args, torch, blest, dev, rank, world):
             edges += int(deg_t[out >= 0].sum().item()) // 2
             info, _ = blest.blest_get_run_info(h)
             nbytes += traversal_bytes(out, new_id_t, w_s_t, nvss_t, (g.n + 7) // 8, g.n,
-                                      info["update"] == blest.BLEST_UPDATE_LAZY, info["output_path"] == 1, 1,
+                                      info["update"] == blest.BLEST_UPDATE_LAZY, info["output_path"], 1,
                                       torch)[0]
         blest.blest_sync(h)
         rows.append({"window": w if w else "none", "prepass": prepass if w else None,

@@ -71,7 +71,7 @@ def test_parallel_cpu_baseline_counts_the_oracle_work():
     assert abs(out["value"] * 1e9 * secs - edges) <= 0.01 * edges
 
 
-def plain_ss_bytes(levels, new_id, w_s, nvss, n, lazy, direct, nroots):
+def plain_ss_bytes(levels, new_id, w_s, nvss, n, lazy, output_path, nroots):
     """The single-source model written as loops over levels and vertices."""
     nwords = (n + 31) // 32
     sets_at, words_at = {}, {}
@@ -94,14 +94,14 @@ def plain_ss_bytes(levels, new_id, w_s, nvss, n, lazy, direct, nroots):
         sweep += 4 * new_words * (1 if lazy or l > 0 else 2)
     init = 4 * n + 4 * nwords * (2 if lazy else 5)
     body = stage1 + sweep + 4 * reached
-    out = 4 * reached if direct else 12 * n
+    out = {0: 0, 1: 4 * reached, 2: 12 * n}[output_path]
     return init + body + out, reached, body + 16 * n, body + 4 * n
 
 
-@pytest.mark.parametrize("direct", [False, True])
+@pytest.mark.parametrize("output_path", [0, 1, 2])
 @pytest.mark.parametrize("lazy", [False, True])
 @pytest.mark.parametrize("case", ["rmat", "grid", "fullgrid"])
-def test_single_source_byte_model_matches_plain_definition(case, lazy, direct):
+def test_single_source_byte_model_matches_plain_definition(case, lazy, output_path):
     """The byte model behind the headline roofline, on oracle levels; the grid
     cases have levels whose queue is short enough for the sparse sweep."""
     import bench
@@ -119,8 +119,8 @@ def test_single_source_byte_model_matches_plain_definition(case, lazy, direct):
     w_s = rng.integers(20, 2000, nss)
     nvss = rng.integers(1, 3, nss)
     got = bench.traversal_bytes(torch.from_numpy(levels), torch.from_numpy(new_id), torch.from_numpy(w_s),
-                                torch.from_numpy(nvss), nss, g.n, lazy, direct, 1, torch)
-    want = plain_ss_bytes(levels, new_id, w_s, nvss, g.n, lazy, direct, 1)
+                                torch.from_numpy(nvss), nss, g.n, lazy, output_path, 1, torch)
+    want = plain_ss_bytes(levels, new_id, w_s, nvss, g.n, lazy, output_path, 1)
     assert got == want
     if case == "fullgrid":
         # some processed levels take the sparse sweep and some the dense one
