@@ -978,8 +978,8 @@ def main():
                     help="lazy stage-1 prefetch: 0 none, 2 register double buffer, 4 or 8 TMA ring stages")
     ap.add_argument("--queries", type=int, default=2000, help="serving: queries per arrival rate")
     ap.add_argument("--rates", default="100,400,1600", help="serving: arrival rates in queries/s")
-    ap.add_argument("--serve-inflight", type=int, default=8, help="serving: launches in flight at once")
-    ap.add_argument("--serve-narrow-sms", type=int, default=19,
+    ap.add_argument("--serve-inflight", type=int, default=4, help="serving: launches in flight at once")
+    ap.add_argument("--serve-narrow-sms", type=int, default=0,
                     help="serving: SMs of a launch on a graph whose last launch ran more than 256 levels (0 = all)")
     ap.add_argument("--oaat-queries", type=int, default=2000,
                     help="serving: queries per rate for the one-query-per-launch comparison")
