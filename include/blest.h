@@ -110,12 +110,16 @@ typedef enum {
                                         (default); a call with more sources runs several launches */
     BLEST_OPT_MS_BLOCKS_PER_SM = 14, /* multi-source persistent-grid blocks per SM; 0 (default) = the
                                         value of BLEST_OPT_BLOCKS_PER_SM (0 = as many as fit) */
-    BLEST_OPT_MS_LEVELS = 15         /* how the multi-source traversal keeps levels until its output pass:
+    BLEST_OPT_MS_LEVELS = 15,        /* how the multi-source traversal keeps levels until its output pass:
                                         1 = vertex-major (one entry per reached (vertex, source)), 2 = bit
                                         planes (plane p = bit p of every level; updated once per plane
                                         and distinct level at which a vertex gains bits), 0 (default) =
                                         planes on graphs the Section 5 rule updates lazily, else
                                         vertex-major */
+    BLEST_OPT_MS_VISITED_FILTER = 16 /* multi-source marks: 1 (default) = read the row's V_curr word and
+                                        mark only sources that have not reached it; 0 = mark every hit
+                                        word (no dependent read; V_next still contains V_curr, so the
+                                        levels are the same) */
 } blest_option;
 
 /* Creation parameters; pass NULL to blest_graph_create_ex for the defaults. */
@@ -368,6 +372,7 @@ typedef struct {
     int32_t chunk;               /* BLEST_OPT_MS_CHUNK kept (sources per launch) */
     int32_t blocks_per_sm;       /* BLEST_OPT_MS_BLOCKS_PER_SM kept (0 = as many as fit) */
     int32_t levels;              /* BLEST_OPT_MS_LEVELS kept (1 vertex-major, 2 bit planes) */
+    int32_t visited_filter;      /* BLEST_OPT_MS_VISITED_FILTER kept */
     int32_t candidates;          /* variants timed */
     double  best_ms;             /* device time of one call over all k sources, kept variant */
     double  popc_ms;             /* best time with the CUDA-core pull */
@@ -378,8 +383,9 @@ typedef struct {
  * srcs[0..k) (Section 2's multi-source form) with CUDA events, each variant
  * after one untimed pass, and keep the fastest as the handle's options: pull
  * back-end (CUDA-core OR or b1 tensor-core MMA), sources per launch (64, 128,
- * 256; only sizes that change the launches of k sources), blocks per SM and
- * level layout (the MMA back-end is timed with bit planes only).
+ * 256; only sizes that change the launches of k sources), blocks per SM, level
+ * layout and the visited test before the marks (the MMA back-end is timed with
+ * bit planes and the test only).
  * Allocates a k x n device level buffer for the duration of the call.  out may
  * be NULL.  Errors: INVALID_ARG (k < 1, bad source), OOM, TIMEOUT, INTERNAL, CUDA. */
 blest_status blest_autotune_msbfs(blest_handle h, const int32_t* srcs, int32_t k, blest_ms_tune_result* out);

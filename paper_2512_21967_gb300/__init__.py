@@ -48,6 +48,7 @@ BLEST_OPT_RECORD_LEVELS, BLEST_OPT_UNROLL, BLEST_OPT_TEST_PHANTOM_BLOCK = 4, 5, 
 BLEST_OPT_VISITED_FILTER, BLEST_OPT_MIN_BLOCKS, BLEST_OPT_STAGE_DEPTH, BLEST_OPT_LAYOUT = 7, 8, 9, 10
 BLEST_OPT_SCHEDULE = 11
 BLEST_OPT_MS_PULL, BLEST_OPT_MS_CHUNK, BLEST_OPT_MS_BLOCKS_PER_SM, BLEST_OPT_MS_LEVELS = 12, 13, 14, 15
+BLEST_OPT_MS_VISITED_FILTER = 16
 BLEST_ARRAY_REAL_PTRS, BLEST_ARRAY_VIRTUAL_TO_REAL, BLEST_ARRAY_ROW_IDS = 0, 1, 2
 BLEST_ARRAY_MASKS, BLEST_ARRAY_NEW_ID, BLEST_ARRAY_VSS_COUNT = 3, 4, 5
 BLEST_ARRAY_COMPACT_OFFSETS, BLEST_ARRAY_COMPACT_ROWS, BLEST_ARRAY_COMPACT_MASKS = 6, 7, 8
@@ -99,7 +100,7 @@ class TuneResult(ctypes.Structure):
 
 class MsTuneResult(ctypes.Structure):
     _fields_ = [("pull", ctypes.c_int32), ("chunk", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("levels", ctypes.c_int32), ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_double), ("popc_ms", ctypes.c_double),
+                ("levels", ctypes.c_int32), ("visited_filter", ctypes.c_int32), ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_double), ("popc_ms", ctypes.c_double),
                 ("mma_ms", ctypes.c_double)]
 
 

@@ -105,6 +105,7 @@ struct blest_graph {
     int ms_chunk = blest::kMsbfsChunk;   // sources per multi-source launch
     int ms_blocks_per_sm = 0;            // 0 = blocks_per_sm
     int ms_levels = 0;                   // BLEST_OPT_MS_LEVELS: 0 auto, 1 vertex-major, 2 bit planes
+    int ms_filter = 1;                   // BLEST_OPT_MS_VISITED_FILTER
     // sharded traversal in progress (blest_shard_*): rank, ranks, next level, output, rows reached
     int32_t shard_rank = -1, shard_world = 0, shard_level = 0;
     int32_t* shard_out = nullptr;
@@ -902,6 +903,10 @@ blest_status blest_set_option(blest_handle h, int32_t key, int64_t value) {
             if (value < 0 || value > 2) break;
             h->ms_levels = (int)value;
             return BLEST_OK;
+        case BLEST_OPT_MS_VISITED_FILTER:
+            if (value != 0 && value != 1) break;
+            h->ms_filter = (int)value;
+            return BLEST_OK;
         default:
             return fail(BLEST_ERR_INVALID_ARG, "unknown option key");
     }
@@ -1108,6 +1113,7 @@ blest_status blest_msbfs_device(blest_handle h, const int32_t* srcs, int32_t k, 
     c.pull = h->ms_pull;
     c.chunk = h->ms_chunk;
     c.levels_layout = h->ms_levels_layout();
+    c.visited_filter = h->ms_filter;
     const char* err = nullptr;
     int rc = blest::run_msbfs(h->ms, c, roots, d_levels, st, &err);
     if (rc) return fail((blest_status)rc, std::string("msbfs: ") + (err ? err : "?"));
@@ -1222,19 +1228,22 @@ blest_status blest_autotune_msbfs(blest_handle h, const int32_t* srcs, int32_t k
         return cuda_fail(e, "cudaEventCreate");
     }
     const int saved_pull = h->ms_pull, saved_chunk = h->ms_chunk, saved_bps = h->ms_blocks_per_sm;
-    const int saved_levels = h->ms_levels;
+    const int saved_levels = h->ms_levels, saved_filter = h->ms_filter;
     double best = 1e300, best_pull[2] = {-1.0, -1.0};
-    int bp = saved_pull, bc = saved_chunk, bb = saved_bps, bl = saved_levels, timed = 0;
+    int bp = saved_pull, bc = saved_chunk, bb = saved_bps, bl = saved_levels, bf = saved_filter, timed = 0;
     for (int pull : {BLEST_PULL_POPC, BLEST_PULL_MMA})
         for (int chunk : chunks)
             for (int bps : {0, 1, 2})   // blocks per SM above what fits run as many as fit
-            for (int levels : {1, 2}) {  // vertex-major, bit planes
+            for (int levels : {1, 2})    // vertex-major, bit planes
+            for (int filt : {1, 0}) {    // V_curr test before each mark, or none
                 if (s) break;
-                if (pull == BLEST_PULL_MMA && levels != 2) continue;   // one layout is enough to time the MMA
+                // one layout and the default test are enough to time the MMA
+                if (pull == BLEST_PULL_MMA && (levels != 2 || filt != 1)) continue;
                 h->ms_pull = pull;
                 h->ms_chunk = chunk;
                 h->ms_blocks_per_sm = bps;
                 h->ms_levels = levels;
+                h->ms_filter = filt;
                 for (int pass = 0; pass < 2 && !s; ++pass) {
                     if (pass == 1) cudaEventRecord(e0, h->stream);
                     s = blest_msbfs_device(h, srcs, k, d_out, h->stream);
@@ -1246,7 +1255,7 @@ blest_status blest_autotune_msbfs(blest_handle h, const int32_t* srcs, int32_t k
                 cudaEventElapsedTime(&ms, e0, e1);
                 ++timed;
                 if (best_pull[pull] < 0 || ms < best_pull[pull]) best_pull[pull] = ms;
-                if (ms < best) { best = ms; bp = pull; bc = chunk; bb = bps; bl = levels; }
+                if (ms < best) { best = ms; bp = pull; bc = chunk; bb = bps; bl = levels; bf = filt; }
             }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1254,11 +1263,13 @@ blest_status blest_autotune_msbfs(blest_handle h, const int32_t* srcs, int32_t k
     if (s) {
         h->ms_pull = saved_pull; h->ms_chunk = saved_chunk; h->ms_blocks_per_sm = saved_bps;
         h->ms_levels = saved_levels;
+        h->ms_filter = saved_filter;
         return s;
     }
-    h->ms_pull = bp; h->ms_chunk = bc; h->ms_blocks_per_sm = bb; h->ms_levels = bl;
+    h->ms_pull = bp; h->ms_chunk = bc; h->ms_blocks_per_sm = bb; h->ms_levels = bl; h->ms_filter = bf;
     if (out) {
-        out->pull = bp; out->chunk = bc; out->blocks_per_sm = bb; out->levels = bl; out->candidates = timed;
+        out->pull = bp; out->chunk = bc; out->blocks_per_sm = bb; out->levels = bl; out->visited_filter = bf;
+        out->candidates = timed;
         out->best_ms = best; out->popc_ms = best_pull[0]; out->mma_ms = best_pull[1];
     }
     return BLEST_OK;
