@@ -49,6 +49,8 @@ WORKLOADS = {
     "batch128": ("batch", 128, 128, "per-kind", 4, 0, 0),
     "serve": ("serve", 16, 0, "per-kind", 5, 0, 0),
     "window-sweep": ("wsweep", 20, 16, "compress", 6, 1006, 0),
+    # the sharded single-source traversal, 2 ranks emulated on one GPU (config 2's graph and sources)
+    "rmat23-shard2": ("shard", 23, 8, "compress", 2, 1002, 0),
 }
 
 
@@ -101,7 +103,7 @@ def build_workload(name, window):
     t0 = time.time()
     if kind == "batch":
         return synth.batch_workload(size, sg), None, order, k, time.time() - t0
-    if kind == "rmat":
+    if kind in ("rmat", "shard"):
         g, srcs = synth.rmat_workload(size, nsrc, seed_graph=sg, seed_src=ss)
     else:
         g, srcs = synth.grid_workload(size, nsrc, seed_graph=sg, seed_src=ss)
@@ -311,6 +313,8 @@ def run_ours(args):
         return run_ours_serve(args, torch, blest, dev, rank, world)
     if WORKLOADS[args.workload][0] == "wsweep":
         return run_ours_window_sweep(args, torch, blest, dev, rank, world)
+    if WORKLOADS[args.workload][0] == "shard":
+        return run_ours_shard(args, torch, blest, dev, rank, world)
     g, srcs, order_name, msk, t_gen = build_workload(args.workload, args.window)
     order = {"compress": blest.BLEST_ORDER_COMPRESS, "bandwidth": blest.BLEST_ORDER_BANDWIDTH,
              "none": blest.BLEST_ORDER_NONE}[order_name]
@@ -766,6 +770,116 @@ def run_ours_serve(args, torch, blest, dev, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def run_ours_shard(args, torch, blest, dev, rank, world):
+    """The sharded single-source traversal with 2 ranks emulated on one GPU:
+    each rank has its own handle of config 2's graph; every level runs rank 0's
+    pull, rank 1's pull, the OR merge and both ranks' sweeps in one stream, each
+    step timed with CUDA events.  No collective runs (one GPU): the line reports
+    the device time of every step, the words a collective would move, and, for
+    reference, the fused single-handle traversal of the same sources."""
+    from paper_2512_21967_gb300 import shard
+    g, srcs, _, _, t_gen = build_workload(args.workload, args.window)
+    W = 2
+    t0 = time.time()
+    h0 = blest.blest_graph_create_ex(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_COMPRESS, window=args.window)
+    path = os.path.join("/tmp", f"blest_shard_{os.getpid()}.bin")
+    blest.blest_graph_save(h0, path)
+    h1 = blest.blest_graph_load(path)             # the same BVSS and order without a second reordering
+    os.remove(path)
+    t_create = time.time() - t0
+    hs = [h0, h1]
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    outs = [torch.empty(g.n, dtype=torch.int32, device=dev) for _ in range(W)]
+    nw = (g.n + 31) // 32
+    merged = torch.empty(nw, dtype=torch.int32, device=dev)
+    gathered = torch.empty(W * nw, dtype=torch.int32, device=dev)
+    deg_t = torch.from_numpy(g.degrees()).to(dev)
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+
+    def traverse(src, timed):
+        steps = [shard.DeviceShard(h, r, W, int(src), outs[r], stream) for r, h in enumerate(hs)]
+        for st in steps:
+            st.begin()
+        t = {"pull": [0.0] * W, "merge": 0.0, "sweep": [0.0] * W}
+        levels = 0
+        while True:
+            for r, st in enumerate(steps):
+                a = ev()
+                words = st.pull()
+                gathered[r * nw:(r + 1) * nw].copy_(words)      # what the all-gather delivers
+                b = ev()
+                if timed:
+                    b.synchronize()
+                    t["pull"][r] += a.elapsed_time(b)
+            a = ev()
+            blest.blest_shard_merge(merged, gathered, nw, W, stream)
+            b = ev()
+            more = []
+            for r, st in enumerate(steps):
+                c = ev()
+                blest.blest_shard_sweep(hs[r], merged, stream)
+                d = ev()
+                more.append(blest.blest_shard_more(hs[r]))
+                if timed:
+                    t["sweep"][r] += c.elapsed_time(d)
+            if timed:
+                t["merge"] += a.elapsed_time(b)
+            levels += 1
+            assert len(set(more)) == 1, "ranks disagree on the end of the traversal"
+            if not more[0]:
+                return t, levels
+
+    for s_ in srcs[:2]:                                # warm-up
+        traverse(s_, False)
+    torch.cuda.synchronize(dev)
+    tot = {"pull0": 0.0, "pull1": 0.0, "merge": 0.0, "sweep": 0.0}
+    edges, nlev = 0, 0
+    for s_ in srcs:
+        flush.fill_(3)
+        t, levels = traverse(s_, True)
+        tot["pull0"] += t["pull"][0]
+        tot["pull1"] += t["pull"][1]
+        tot["merge"] += t["merge"]
+        tot["sweep"] += max(t["sweep"])
+        nlev += levels
+        assert torch.equal(outs[0], outs[1])
+        edges += int(deg_t[outs[0] >= 0].sum().item()) // 2
+    # the fused single-handle traversal of the same sources, for reference
+    fused = 0.0
+    for s_ in srcs:
+        flush.fill_(5)
+        a = ev()
+        blest.blest_bfs_device(h0, int(s_), outs[0], stream=stream)
+        b = ev()
+        b.synchronize()
+        fused += a.elapsed_time(b)
+    for h in hs:
+        blest.blest_destroy(h)
+    k = len(srcs)
+    emulated_ms = (tot["pull0"] + tot["pull1"] + tot["merge"] + tot["sweep"]) / k
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(edges / (emulated_ms * k / 1e3) / 1e9, 4), "unit": "GTEPS",
+                "n_gpus": world, "steps": 1, "warmup": 2, "ms_per_step": round(emulated_ms * k, 4),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+                "data": "synthetic",
+                "config": {"workload": f"sharded single-source BFS, {g.name}, {k} sources, 2 ranks emulated on one GPU "
+                                       "(steps in sequence, no collective)",
+                           "n": g.n, "directed_edges": g.nnz, "ranks": W, "levels_per_traversal": nlev / k,
+                           "value_is": "edges / the sum of every step's device time (both ranks' pulls in sequence)"},
+                "per_traversal_ms": {"pull_rank0": round(tot["pull0"] / k, 4), "pull_rank1": round(tot["pull1"] / k, 4),
+                                     "merge": round(tot["merge"] / k, 4), "sweep": round(tot["sweep"] / k, 4),
+                                     "fused_single_handle": round(fused / k, 4)},
+                "exchange_bytes_per_level_per_rank": nw * 4,
+                "gpu_launches": int(nlev * (2 * W + 1 + 2 * W)),
+                "preprocess_s": {"generate": round(t_gen, 2), "create_and_load": round(t_create, 2)}}
+        print(json.dumps(line), flush=True)
+
+
 def run_ours_window_sweep(args, torch, blest, dev, rank, world):
     """Effect of the JaccardWithWindows window w on compression and BFS time (the
     experiment of Fig. 3, here on an R-MAT graph of scale 20): for each w, the
@@ -888,7 +1002,7 @@ def reference_jobs(args):
         label = ("serving: 16 resident graphs (8 R-MAT s16..22, 8 grids 256..2048, p=0.9), "
                  f"Poisson queries with 1..32 sources, {args.queries} per rate, 40 GB cap")
         return [(graphs[gq], [int(x) for x in q]) for (_, gq, q) in stream], label, "queries/s", {}
-    if kind == "rmat" or kind == "wsweep":
+    if kind in ("rmat", "wsweep", "shard"):
         g, srcs = synth.rmat_workload(size, nsrc, seed_graph=sg, seed_src=ss)
     else:
         g, srcs = synth.grid_workload(size, nsrc, seed_graph=sg, seed_src=ss)

@@ -467,6 +467,13 @@ blest_status blest_shard_merge(uint32_t* d_dst, const uint32_t* d_src, int64_t w
  * Errors: INVALID_ARG, TIMEOUT, INTERNAL, CUDA. */
 blest_status blest_shard_finish(blest_handle h, const uint32_t* d_merged, int32_t* more, void* stream);
 
+/* blest_shard_finish in two calls, for callers that overlap or time the steps:
+ * blest_shard_sweep only enqueues the sweep on the stream; blest_shard_more then
+ * waits for the handle's work and sets *more as finish does.  Each sweep must be
+ * followed by one blest_shard_more before the next pull. */
+blest_status blest_shard_sweep(blest_handle h, const uint32_t* d_merged, void* stream);
+blest_status blest_shard_more(blest_handle h, int32_t* more);
+
 /* ---------------------------------------------------------------- testing */
 
 /* The stage-1 pull of one virtual slice set, on the device, for every tile:

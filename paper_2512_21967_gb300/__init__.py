@@ -29,7 +29,7 @@ __all__ = [
     "blest_get_level_arrivals", "blest_distance_stats", "blest_graph_save", "blest_graph_load",
     "blest_export",
     "blest_autotune", "blest_autotune_msbfs", "blest_autotune_multiroot", "blest_shard_begin", "blest_shard_pull",
-    "blest_shard_merge", "blest_shard_finish", "blest_export_size", "blest_compute_order", "blest_is_social",
+    "blest_shard_merge", "blest_shard_finish", "blest_shard_sweep", "blest_shard_more", "blest_export_size", "blest_compute_order", "blest_is_social",
     "blest_debug_pull",
     "blest_bfs_static_scratch", "blest_server_create", "blest_server_submit", "blest_server_wait",
     "blest_server_pause", "blest_server_get_stats", "blest_server_destroy", "lib", "EXPORTED_SYMBOLS",
@@ -60,7 +60,7 @@ EXPORTED_SYMBOLS = [
     "blest_batch_graph_launch", "blest_bfs_device", "blest_msbfs_device", "blest_bfs_multiroot_device", "blest_sync",
     "blest_get_run_info", "blest_get_level_times", "blest_get_level_arrivals", "blest_distance_stats", "blest_graph_save", "blest_graph_load",
     "blest_autotune", "blest_autotune_msbfs", "blest_autotune_multiroot", "blest_shard_begin",
-    "blest_shard_pull", "blest_shard_merge", "blest_shard_finish",
+    "blest_shard_pull", "blest_shard_merge", "blest_shard_finish", "blest_shard_sweep", "blest_shard_more",
     "blest_export_size", "blest_export", "blest_compute_order", "blest_is_social", "blest_debug_pull",
     "blest_server_create", "blest_server_submit", "blest_server_wait", "blest_server_pause", "blest_server_get_stats",
     "blest_server_destroy", "blest_bfs_static_scratch", "blest_status_string", "blest_last_error",
@@ -164,6 +164,8 @@ def lib():
             "blest_shard_pull": (ctypes.c_int, [_vp, _vp, _vp]),
             "blest_shard_merge": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_int32, _vp]),
             "blest_shard_finish": (ctypes.c_int, [_vp, _vp, _i32p, _vp]),
+            "blest_shard_sweep": (ctypes.c_int, [_vp, _vp, _vp]),
+            "blest_shard_more": (ctypes.c_int, [_vp, _i32p]),
             "blest_get_level_times": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32]),
             "blest_get_level_arrivals": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64),
                                                         ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32]),
@@ -410,6 +412,16 @@ def blest_shard_finish(h: int, d_merged, stream=None) -> bool:
     more = ctypes.c_int32(0)
     _check(lib().blest_shard_finish(h, _dev_ptr(d_merged), ctypes.byref(more), _stream_ptr(stream)),
            "blest_shard_finish")
+    return bool(more.value)
+
+
+def blest_shard_sweep(h: int, d_merged, stream=None) -> None:
+    _check(lib().blest_shard_sweep(h, _dev_ptr(d_merged), _stream_ptr(stream)), "blest_shard_sweep")
+
+
+def blest_shard_more(h: int) -> bool:
+    more = ctypes.c_int32(0)
+    _check(lib().blest_shard_more(h, ctypes.byref(more)), "blest_shard_more")
     return bool(more.value)
 
 

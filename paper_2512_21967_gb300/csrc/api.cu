@@ -1575,10 +1575,10 @@ blest_status blest_shard_merge(uint32_t* d_dst, const uint32_t* d_src, int64_t w
     return BLEST_OK;
 }
 
-blest_status blest_shard_finish(blest_handle h, const uint32_t* d_merged, int32_t* more, void* stream) {
+blest_status blest_shard_sweep(blest_handle h, const uint32_t* d_merged, void* stream) {
     if (!h) return fail(BLEST_ERR_INVALID_ARG, "NULL handle");
     if (h->shard_rank < 0) return fail(BLEST_ERR_INVALID_ARG, "no sharded traversal begun on this handle");
-    if (!d_merged || !more) return fail(BLEST_ERR_INVALID_ARG, "NULL argument");
+    if (!d_merged) return fail(BLEST_ERR_INVALID_ARG, "merged is NULL");
     cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
     blest::BfsLaunch L = shard_launch(h);
     cudaError_t e;
@@ -1588,9 +1588,17 @@ blest_status blest_shard_finish(blest_handle h, const uint32_t* d_merged, int32_
                                       nullptr, st)) != cudaSuccess)
         return cuda_fail(e, "shard: sweep");
     h->last_stream = st;
+    return BLEST_OK;
+}
+
+blest_status blest_shard_more(blest_handle h, int32_t* more) {
+    if (!h) return fail(BLEST_ERR_INVALID_ARG, "NULL handle");
+    if (h->shard_rank < 0) return fail(BLEST_ERR_INVALID_ARG, "no sharded traversal begun on this handle");
+    if (!more) return fail(BLEST_ERR_INVALID_ARG, "more is NULL");
     blest_status s = sync_status(h);
     if (s) return s;
     unsigned int ctrl[16];
+    cudaError_t e;
     if ((e = cudaMemcpy(ctrl, h->d_ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost)) != cudaSuccess)
         return cuda_fail(e, "shard: read counters");
     const unsigned int reached = ctrl[7];   // Ctrl::reached
@@ -1599,6 +1607,13 @@ blest_status blest_shard_finish(blest_handle h, const uint32_t* d_merged, int32_
     h->shard_level += 1;
     if (!*more) h->shard_rank = -1;   // the traversal is over; d_levels holds every level
     return BLEST_OK;
+}
+
+blest_status blest_shard_finish(blest_handle h, const uint32_t* d_merged, int32_t* more, void* stream) {
+    if (!more) return fail(BLEST_ERR_INVALID_ARG, "more is NULL");
+    blest_status s = blest_shard_sweep(h, d_merged, stream);
+    if (s) return s;
+    return blest_shard_more(h, more);
 }
 
 blest_status blest_debug_pull(const uint32_t* d_masks, const uint8_t* d_alpha, int32_t tiles, int32_t pull,
