@@ -875,7 +875,9 @@ def run_ours_shard(args, torch, blest, dev, rank, world):
                                      "merge": round(tot["merge"] / k, 4), "sweep": round(tot["sweep"] / k, 4),
                                      "fused_single_handle": round(fused / k, 4)},
                 "exchange_bytes_per_level_per_rank": nw * 4,
-                "gpu_launches": int(nlev * (2 * W + 1 + 2 * W)),
+                # per level: each rank's pull and words-out, the merge, each rank's words-in and sweep;
+                # per traversal: each rank's root mark and level-0 sweep
+                "gpu_launches": int(nlev * (2 * W + 1 + 2 * W) + k * 2 * W),
                 "preprocess_s": {"generate": round(t_gen, 2), "create_and_load": round(t_create, 2)}}
         print(json.dumps(line), flush=True)
 
