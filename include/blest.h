@@ -82,11 +82,12 @@ typedef enum {
                                         (4 only with the 8-stage TMA ring) */
     BLEST_OPT_TEST_PHANTOM_BLOCK = 6,/* testing: 1 = every barrier waits for one block that does not
                                         exist, so the next traversal must end in BLEST_ERR_TIMEOUT */
-    BLEST_OPT_VISITED_FILTER = 7,    /* 1 = test a visited bitmap before marking a row; 2 = lazy update
-                                        also skips rows already marked at this level (V_next read at L2),
-                                        on levels where fewer than n/4 rows have a level; 3 (default) = as
-                                        2 with V_next read through L1 (staler, cheaper); 0 = off; the eager
-                                        update uses 1 for 2 and 3 */
+    BLEST_OPT_VISITED_FILTER = 7,    /* 1 = test V_curr before marking a row; 2 = lazy update also skips
+                                        rows already marked at this level: it tests V_next (which contains
+                                        V_curr), read at L2, on levels where fewer than n/4 rows have a
+                                        level, V_curr after; 3 (default) = as 2 with V_next read through
+                                        L1 (staler, cheaper); 4 = V_next through L1 at every level; 0 = off;
+                                        the eager update uses 1 for 2, 3 and 4 */
     BLEST_OPT_MIN_BLOCKS = 8,        /* kernel variant compiled for 2 (default) or 3 blocks per SM */
     BLEST_OPT_STAGE_DEPTH = 9,       /* lazy stage 1 prefetch: 0 = none; 2 (default) = the next group's
                                         tiles in registers while the current group's hits are handled; 3 =
@@ -571,7 +572,7 @@ void blest_server_destroy(blest_server_handle s);
  * stream to finish them before it reads the traversal's status and returns.
  *
  * Working memory comes from one fixed device array inside the library (about
- * 21.5 MiB), which every GPU that loads the library keeps until the process
+ * 21 MiB), which every GPU that loads the library keeps until the process
  * exits.  Limits: n <= 2,097,152 vertices and num_vss <= 524,288 virtual slice
  * sets; larger graphs get BLEST_ERR_TOO_LARGE.  The first call on a device looks
  * up the array's device address (once per device, with that device current);

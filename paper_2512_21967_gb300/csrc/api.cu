@@ -24,8 +24,8 @@
 namespace blest {
 constexpr int kCtrlBytes = 256;        // layout in device_common.cuh
 constexpr int kCtrlClearBytes = 192;
-// bitmaps of a handle's traversal state: 3 eager frontiers, the V_curr/V_next pairs (2), the V_curr copy
-constexpr size_t kStateBitmaps = 6;
+// bitmaps of a handle's traversal state: 3 eager frontiers, V_curr, V_next
+constexpr size_t kStateBitmaps = 5;
 constexpr int kStickyWord = 48;
 }  // namespace blest
 using blest::kCtrlBytes;
@@ -74,13 +74,13 @@ struct blest_graph {
     int32_t* d_new_id = nullptr;
     int32_t* d_L = nullptr;              // internal levels (BVSS ids)
     int32_t* d_out = nullptr;            // staging for host-output calls (original ids)
-    // [F0 F1 F2 | V_curr/V_next pairs (2 bitmaps) | V_curr copy | dirty | control block] in one allocation, so that
+    // [F0 F1 F2 | V_curr | V_next | dirty | control block] in one allocation, so that
     // one memset clears the bitmaps a traversal needs and the control block's counters
     unsigned char* d_state = nullptr;
     size_t bitmap_bytes = 0;             // each bitmap, rounded up to 256 B
     size_t dirty_bytes = 0;              // 1 bit per bitmap word, rounded up to 256 B
-    uint2* d_vis = nullptr;              // V_curr / V_next word pairs (two bitmaps' worth of bytes)
-    uint32_t* d_vcur = nullptr;          // dense copy of V_curr
+    uint32_t* d_vcur = nullptr;          // V_curr
+    uint32_t* d_vnext = nullptr;         // V_next
     uint32_t* d_dirty = nullptr;
     uint32_t* d_F = nullptr;             // 3 bitmaps, bitmap_bytes apart (eager frontier)
     unsigned long long* d_Q = nullptr;   // 3 * qcap
@@ -203,8 +203,8 @@ blest_status alloc_state(blest_graph* h, const std::vector<int32_t>& new_id) {
     h->dirty_bytes = (sizeof(uint32_t) * ((std::max<size_t>(nw, 1) + 31) / 32) + 255) / 256 * 256;
     BLEST_ALLOC(h->d_state, kStateBitmaps * h->bitmap_bytes + h->dirty_bytes + kCtrlBytes, "cudaMalloc(bitmaps)");
     h->d_F = reinterpret_cast<uint32_t*>(h->d_state);
-    h->d_vis = reinterpret_cast<uint2*>(h->d_state + 3 * h->bitmap_bytes);
-    h->d_vcur = reinterpret_cast<uint32_t*>(h->d_state + 5 * h->bitmap_bytes);
+    h->d_vcur = reinterpret_cast<uint32_t*>(h->d_state + 3 * h->bitmap_bytes);
+    h->d_vnext = reinterpret_cast<uint32_t*>(h->d_state + 4 * h->bitmap_bytes);
     h->d_dirty = reinterpret_cast<uint32_t*>(h->d_state + kStateBitmaps * h->bitmap_bytes);
     h->d_ctrl = reinterpret_cast<unsigned int*>(h->d_state + kStateBitmaps * h->bitmap_bytes + h->dirty_bytes);
     BLEST_ALLOC(h->d_Q, sizeof(unsigned long long) * 3 * (size_t)h->qcap, "cudaMalloc(queues)");
@@ -357,8 +357,8 @@ blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots
     // -1 before the launch) and needs no unpermute; the parent pass needs L
     L.direct = (L.update == 2 && h->d_new_id && h->d_old_of && !h->need_internal_levels) ? 1 : 0;
     L.old_of = h->d_old_of;
-    L.vis = h->d_vis;
     L.vcur = h->d_vcur;
+    L.vnext = h->d_vnext;
     L.dirty = h->d_dirty;
     for (int i = 0; i < 3; ++i) {
         L.F[i] = reinterpret_cast<uint32_t*>(h->d_state + i * h->bitmap_bytes);
@@ -396,7 +396,7 @@ blest_status enqueue_traversal(blest_graph* h, const std::vector<int32_t>& roots
     L.out = d_out;
     L.timeout_ns = (uint64_t)h->timeout_us * 1000ull;
     L.phantom = h->phantom ? 1u : 0u;
-    // [F (eager only) | V_curr/V_next pairs | V_curr copy | dirty | control block up to the sticky status word]
+    // [F (eager only) | V_curr | V_next | dirty | control block up to the sticky status word]
     const size_t skip = L.update == 1 ? 0 : 3 * h->bitmap_bytes;
     cudaMemsetAsync(h->d_state + skip, 0, kStateBitmaps * h->bitmap_bytes + h->dirty_bytes - skip + kCtrlClearBytes, st);
     cudaMemsetAsync(L.direct ? d_out : L.levels_internal, 0xFF, sizeof(int32_t) * (size_t)h->n, st);
@@ -432,8 +432,8 @@ blest::BfsLaunch shard_launch(blest_graph* h) {
     L.old_of = h->d_old_of;
     L.levels_internal = h->d_new_id ? h->d_L : h->shard_out;
     L.out = h->shard_out;
-    L.vis = h->d_vis;
     L.vcur = h->d_vcur;
+    L.vnext = h->d_vnext;
     for (int i = 0; i < 3; ++i) {
         L.F[i] = reinterpret_cast<uint32_t*>(h->d_state + i * h->bitmap_bytes);
         L.Q[i] = h->d_Q + i * (size_t)h->qcap;
@@ -859,7 +859,7 @@ blest_status blest_set_option(blest_handle h, int32_t key, int64_t value) {
             h->unroll = (int)value;
             return BLEST_OK;
         case BLEST_OPT_VISITED_FILTER:
-            if (value < 0 || value > 3) break;
+            if (value < 0 || value > 4) break;
             h->filter = (int)value;
             return BLEST_OK;
         case BLEST_OPT_MIN_BLOCKS:
@@ -1291,9 +1291,9 @@ static blest_status autotune_impl(blest_handle h, const int32_t* srcs, int32_t k
         for (int p : {BLEST_PULL_POPC, BLEST_PULL_MMA})
             for (int r : {1, 2})
                 for (int m : {2, 3})
-                    for (int f = 0; f <= (u == BLEST_UPDATE_LAZY ? 3 : 1); ++f)
+                    for (int f = 0; f <= (u == BLEST_UPDATE_LAZY ? 4 : 1); ++f)
                         for (int b : {0, 1}) cands.push_back({u, p, r, m, f, b, 0});
-    for (int f : {0, 1, 2, 3})
+    for (int f : {0, 1, 2, 3, 4})
         for (int b : {0, 1}) {
             for (int p : {BLEST_PULL_POPC, BLEST_PULL_MMA})
                 for (int r : {1, 2}) {
@@ -1538,7 +1538,7 @@ blest_status blest_shard_begin(blest_handle h, int32_t rank, int32_t world, int3
     h->shard_reached = 1;   // the level-0 sweep gives the root its level
     blest::BfsLaunch L = shard_launch(h);
     cudaError_t e;
-    // [V_curr/V_next pairs | V_curr copy | dirty | control block up to the sticky status word]
+    // [V_curr | V_next | dirty | control block up to the sticky status word]
     const size_t skip = 3 * h->bitmap_bytes;
     if ((e = cudaMemsetAsync(h->d_state + skip, 0, kStateBitmaps * h->bitmap_bytes + h->dirty_bytes - skip +
                                                        kCtrlClearBytes, st)) != cudaSuccess ||

@@ -47,13 +47,11 @@ struct BfsArgs {
     const uint32_t* __restrict__ masks_c; // compact layout: 4 packed masks per group
     const int32_t* __restrict__ new_id;  // NULL: identity, L is the output
     int32_t* L;
-    // V_curr and V_next interleaved word by word (x = V_curr, y = V_next), so that a
-    // hit row's test against both bitmaps is one 8-byte load and the sweep reads a
-    // word pair with one.  vcur is a dense copy of V_curr for the tests that need
-    // only V_curr (lazy levels after a quarter of the rows are visited, eager
-    // levels): it keeps half the footprint in L1.  The sweeps keep both equal.
-    uint2* vis;
+    // V_curr and V_next, dense bitmaps.  V_next always contains V_curr (stage 1 only
+    // adds marks; the sweep copies V_next into V_curr), so a hit row's test against
+    // both is one 4-byte load of its V_next word.
     uint32_t* vcur;
+    uint32_t* vnext;
     uint32_t* dirty;                      // 1 bit per V_next word touched on a sparse level (NULL = never sparse)
     uint32_t* F[3];
     unsigned long long* Q[3];
@@ -150,9 +148,8 @@ __device__ __forceinline__ void sweep(const BfsArgs& a, int lvl, unsigned long l
         uint32_t diff = 0;
         int rp[5] = {0, 0, 0, 0, 0};   // VSS (or group) offsets of the word's 4 slice sets and the next
         if (t < a.nwords && ((live >> lane) & 1u)) {
-            const uint2 vv = ld_cg(&a.vis[t]);
-            const uint32_t nx = vv.y;
-            const uint32_t cu = vv.x;
+            const uint32_t nx = ld_cg(&a.vnext[t]);
+            const uint32_t cu = ld_cg(&a.vcur[t]);
             // issued with the bitmap loads, not after them: their addresses do not depend on diff
             const int32_t* ptrs = LAYOUT == 1 ? a.goff : a.real_ptrs;
 #pragma unroll
@@ -160,7 +157,6 @@ __device__ __forceinline__ void sweep(const BfsArgs& a, int lvl, unsigned long l
                 if (4 * t + q <= a.nss) rp[q] = __ldg(&ptrs[4 * t + q]);
             diff = nx ^ cu;
             if (diff) {
-                a.vis[t].x = nx;
                 a.vcur[t] = nx;
                 if (UPDATE == 1) Fout[t] = diff;
                 fresh += (unsigned int)__popc(diff);
@@ -277,8 +273,7 @@ __device__ __forceinline__ void mark_rows(const BfsArgs& a, const int4 (&rows)[N
         for (int k = 0; k < 4 * NV; ++k) {
             w[k] = 0u;
             if ((hm >> k) & 1u) {
-                const uint2 vv = ld_cg(&a.vis[u[k] >> 5]);
-                w[k] = vv.x | vv.y;
+                w[k] = ld_cg(&a.vnext[u[k] >> 5]);   // V_next contains V_curr
             }
         }
     } else if (filt == 3) {   // V_next through L1: staler, so more redundant marks, but cheaper loads
@@ -286,8 +281,7 @@ __device__ __forceinline__ void mark_rows(const BfsArgs& a, const int4 (&rows)[N
         for (int k = 0; k < 4 * NV; ++k) {
             w[k] = 0u;
             if ((hm >> k) & 1u) {
-                const uint2 vv = a.vis[u[k] >> 5];
-                w[k] = vv.x | vv.y;
+                w[k] = a.vnext[u[k] >> 5];
             }
         }
     } else if (filt) {
@@ -301,7 +295,7 @@ __device__ __forceinline__ void mark_rows(const BfsArgs& a, const int4 (&rows)[N
     for (int k = 0; k < 4 * NV; ++k) {
         const uint32_t bit = 1u << (u[k] & 31);
         if (((hm >> k) & 1u) && !(w[k] & bit)) {
-            atomicOr(&a.vis[u[k] >> 5].y, bit);
+            atomicOr(&a.vnext[u[k] >> 5], bit);
             if (dirty) atomicOr(&dirty[u[k] >> 10], 1u << ((u[k] >> 5) & 31));
         }
     }
@@ -661,7 +655,7 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
     const bool sparse0 = a.dirty != nullptr && (unsigned int)a.nroots <= sparse_cap;
     for (int i = gtid; i < a.nroots; i += nthreads) {
         const int r = a.nroots <= kInlineRoots ? a.inline_roots[i] : a.roots[i];
-        atomicOr(&a.vis[r >> 5].y, 1u << (r & 31));
+        atomicOr(&a.vnext[r >> 5], 1u << (r & 31));
         if (sparse0) atomicOr(&a.dirty[r >> 10], 1u << ((r >> 5) & 31));
     }
     if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns)) return;
@@ -696,7 +690,11 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
 
         // stage 1: pull the queued virtual slice sets, round-robin over warps
         // the lazy filter of this level: the V_next test only while few rows are visited
-        const int filt = (a.filter >= 2 && ld_cg(&ctrl->reached) >= (unsigned int)a.n / 4u) ? 1 : a.filter;
+        // filters 2 and 3 test V_next while fewer than n/4 rows are visited, then V_curr;
+        // filter 4 tests V_next (through L1) at every level
+        const int filt = a.filter == 4 ? 3
+                                       : ((a.filter >= 2 && ld_cg(&ctrl->reached) >= (unsigned int)a.n / 4u) ? 1
+                                                                                                          : a.filter);
         const bool sparse = UPDATE == 2 && a.dirty != nullptr && qn <= sparse_cap;
         uint32_t* dirty = sparse ? a.dirty : nullptr;
         if (DEPTH == 2 || DEPTH == 3) {
@@ -795,7 +793,7 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
 
 // Level 0: mark the root in V_next, then the level-0 sweep.
 __global__ void shard_root_kernel(BfsArgs a, int32_t root) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.vis[root >> 5].y, 1u << (root & 31));
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.vnext[root >> 5], 1u << (root & 31));
 }
 
 __global__ void __launch_bounds__(kBfsBlock, 2) shard_pull_kernel(BfsArgs a, int lvl) {
@@ -807,7 +805,9 @@ __global__ void __launch_bounds__(kBfsBlock, 2) shard_pull_kernel(BfsArgs a, int
     unsigned int qn = ld_cg(&ctrl->qcount[lvl & 1]);
     if (qn > a.qcap) qn = a.qcap;   // only after an overflow, which already raised an error
     if (gtid == 0) ctrl->qcount[(lvl + 1) & 1] = 0u;   // written by this level's sweep
-    const int filt = (a.filter >= 2 && ld_cg(&ctrl->reached) >= (unsigned int)a.n / 4u) ? 1 : a.filter;
+    const int filt = a.filter == 4 ? 3
+                                   : ((a.filter >= 2 && ld_cg(&ctrl->reached) >= (unsigned int)a.n / 4u) ? 1
+                                                                                                      : a.filter);
     stage1_pipelined<0, 2, 0, 1>(a, a.Q[lvl & 1], qn, l2_evict_first_policy(), lane, gwarp, nwarps, filt, nullptr,
                                  nullptr);
     fold_status(ctrl);
@@ -819,10 +819,10 @@ __global__ void __launch_bounds__(kBfsBlock, 2) shard_sweep_kernel(BfsArgs a, in
 }
 
 // The rank's V_next words out (to_vis = 0) or the merged words in (to_vis = 1).
-__global__ void shard_words_kernel(uint2* vis, uint32_t* words, int nwords, int to_vis) {
+__global__ void shard_words_kernel(uint32_t* vnext, uint32_t* words, int nwords, int to_vis) {
     for (int t = (int)(blockIdx.x * blockDim.x + threadIdx.x); t < nwords; t += (int)(gridDim.x * blockDim.x)) {
-        if (to_vis) vis[t].y = words[t];
-        else words[t] = vis[t].y;
+        if (to_vis) vnext[t] = words[t];
+        else words[t] = vnext[t];
     }
 }
 
@@ -934,8 +934,8 @@ static BfsArgs make_args(const BfsLaunch& L) {
     a.masks_c = L.masks_c;
     a.new_id = L.new_id;
     a.L = L.levels_internal;
-    a.vis = L.vis;
     a.vcur = L.vcur;
+    a.vnext = L.vnext;
     a.dirty = L.dirty;
     for (int i = 0; i < 3; ++i) { a.F[i] = L.F[i]; a.Q[i] = L.Q[i]; }
     a.ctrl = reinterpret_cast<Ctrl*>(L.ctrl);
@@ -979,10 +979,10 @@ cudaError_t launch_shard_step(const BfsLaunch& L, int step, int lvl, int world, 
             shard_pull_kernel<<<L.grid, kBfsBlock, 0, stream>>>(a, lvl);
             break;
         case kShardWordsOut:
-            shard_words_kernel<<<std::max(wblocks, 1), 256, 0, stream>>>(a.vis, words, nwords, 0);
+            shard_words_kernel<<<std::max(wblocks, 1), 256, 0, stream>>>(a.vnext, words, nwords, 0);
             break;
         case kShardWordsIn:
-            shard_words_kernel<<<std::max(wblocks, 1), 256, 0, stream>>>(a.vis, words, nwords, 1);
+            shard_words_kernel<<<std::max(wblocks, 1), 256, 0, stream>>>(a.vnext, words, nwords, 1);
             break;
         case kShardSweep:
             shard_sweep_kernel<<<L.grid, kBfsBlock, 0, stream>>>(a, lvl, world, rank);

@@ -31,8 +31,8 @@ struct BfsLaunch {
     const uint32_t* masks_c = nullptr;
     const int32_t* new_id = nullptr;
     int32_t* levels_internal = nullptr;
-    uint2* vis = nullptr;               // ceil(n/32) visited pairs: x = V_curr word, y = V_next word
-    uint32_t* vcur = nullptr;           // ceil(n/32) words: a dense copy of V_curr
+    uint32_t* vcur = nullptr;           // ceil(n/32) words: V_curr
+    uint32_t* vnext = nullptr;          // ceil(n/32) words: V_next (always contains V_curr)
     uint32_t* dirty = nullptr;          // ceil(nwords / 32) words, zero before launch (NULL: no sparse levels)
     uint32_t* F[3] = {nullptr, nullptr, nullptr};
     unsigned long long* Q[3] = {nullptr, nullptr, nullptr};

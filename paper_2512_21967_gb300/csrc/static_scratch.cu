@@ -8,7 +8,7 @@
 // blest_bfs_device, but every working buffer it needs -- control block,
 // internal levels, visited bitmaps, eager frontier bitmaps and the three VSS
 // queues -- lives in the file-scope device array g_scratch below.  Its size is
-// fixed at compile time (about 21.5 MiB) and every GPU that loads this library
+// fixed at compile time (about 21 MiB) and every GPU that loads this library
 // holds it until the process exits.  The caller passes the BVSS arrays and the
 // output; nothing here allocates.
 //
@@ -36,14 +36,14 @@ constexpr int64_t kScratchMaxVss = 1 << 19;               // 524,288 virtual sli
 constexpr size_t kWordsMax = kScratchMaxVertices / 32;
 constexpr size_t kOffCtrl = 0;
 constexpr size_t kOffLevels = 256;
-constexpr size_t kOffVis = kOffLevels + sizeof(int32_t) * kScratchMaxVertices;   // V_curr / V_next word pairs
-constexpr size_t kOffVcur = kOffVis + sizeof(uint2) * kWordsMax;                 // dense V_curr copy
-constexpr size_t kOffF = kOffVcur + sizeof(uint32_t) * kWordsMax;
+constexpr size_t kOffVcur = kOffLevels + sizeof(int32_t) * kScratchMaxVertices;
+constexpr size_t kOffVnext = kOffVcur + sizeof(uint32_t) * kWordsMax;
+constexpr size_t kOffF = kOffVnext + sizeof(uint32_t) * kWordsMax;
 constexpr size_t kOffQ = kOffF + 3 * sizeof(uint32_t) * kWordsMax;
 constexpr size_t kScratchBytes = kOffQ + 3 * sizeof(unsigned long long) * (size_t)kScratchMaxVss;
 constexpr int kStickyWord = 48;        // control-block layout of device_common.cuh
 
-static_assert(kOffVis % 16 == 0 && kOffVcur % 16 == 0 && kOffF % 16 == 0 && kOffQ % 16 == 0, "scratch sub-arrays stay 16-byte aligned");
+static_assert(kOffVcur % 16 == 0 && kOffVnext % 16 == 0 && kOffF % 16 == 0 && kOffQ % 16 == 0, "scratch sub-arrays stay 16-byte aligned");
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -109,8 +109,8 @@ extern "C" blest_status blest_bfs_static_scratch(int32_t n, int64_t num_vss, con
     L.masks = d_masks;
     L.new_id = d_new_id;
     L.levels_internal = d_new_id ? reinterpret_cast<int32_t*>(base + kOffLevels) : d_levels;
-    L.vis = reinterpret_cast<uint2*>(base + kOffVis);
     L.vcur = reinterpret_cast<uint32_t*>(base + kOffVcur);
+    L.vnext = reinterpret_cast<uint32_t*>(base + kOffVnext);
     for (int i = 0; i < 3; ++i) {
         L.F[i] = reinterpret_cast<uint32_t*>(base + kOffF) + i * words;
         L.Q[i] = reinterpret_cast<unsigned long long*>(base + kOffQ) + (size_t)i * (size_t)L.qcap;
@@ -125,8 +125,8 @@ extern "C" blest_status blest_bfs_static_scratch(int32_t n, int64_t num_vss, con
     unsigned int* ctrl = reinterpret_cast<unsigned int*>(base + kOffCtrl);
     if ((e = cudaMemsetAsync(ctrl, 0, 256, st)) != cudaSuccess ||
         (e = cudaMemsetAsync(L.levels_internal, 0xFF, sizeof(int32_t) * (size_t)n, st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(L.vis, 0, sizeof(uint2) * words, st)) != cudaSuccess ||
         (e = cudaMemsetAsync(L.vcur, 0, sizeof(uint32_t) * words, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(L.vnext, 0, sizeof(uint32_t) * words, st)) != cudaSuccess ||
         (L.update == 1 && (e = cudaMemsetAsync(L.F[0], 0, 3 * sizeof(uint32_t) * words, st)) != cudaSuccess))
         return fail(BLEST_ERR_CUDA, std::string("clearing scratch: ") + cudaGetErrorString(e));
     if ((e = blest::launch_bfs_kernel(L, st)) != cudaSuccess)

@@ -111,7 +111,8 @@ def test_rmat16_all_sources_all_modes(cfg1, order):
                              (2, 2, 2, 8, 0, 0), (1, 2, 1, 0, 1, 0), (2, 2, 2, 0, 1, 0), (1, 2, 0, 2, 1, 0),
                              (2, 2, 2, 2, 1, 0), (2, 2, 2, 2, 0, 1), (1, 2, 1, 2, 0, 1), (2, 2, 2, 2, 1, 1),
                              (2, 2, 2, 3, 0, 0), (1, 2, 1, 3, 0, 1), (2, 2, 2, 3, 0, 1),
-                             (2, 2, 3, 2, 0, 1), (1, 2, 3, 0, 0, 0), (2, 2, 3, 8, 0, 0), (2, 2, 3, 2, 1, 1)]
+                             (2, 2, 3, 2, 0, 1), (1, 2, 3, 0, 0, 0), (2, 2, 3, 8, 0, 0), (2, 2, 3, 2, 1, 1),
+                             (2, 2, 4, 2, 0, 1), (1, 2, 4, 0, 0, 0), (2, 2, 4, 2, 1, 0), (2, 3, 4, 0, 0, 0)]
             for unroll, minb, filt, depth, layout, sched in variants:
                 blest.blest_set_option(h, blest.BLEST_OPT_SCHEDULE, sched)
                 blest.blest_set_option(h, blest.BLEST_OPT_UNROLL, unroll)
