@@ -1086,8 +1086,9 @@ def main():
                     help="multi-source pull back-end; auto = the multi-source autotuner's choice")
     ap.add_argument("--unroll", type=int, default=2)
     ap.add_argument("--minb", type=int, default=2)
-    ap.add_argument("--filter", type=int, default=3,
-                    help="visited filter: 0 off, 1 V_curr, 2/3 V_curr + V_next (L2/L1) while few rows are visited")
+    ap.add_argument("--filter", type=int, default=4,
+                    help="visited filter: 0 off, 1 V_curr, 2/3 V_next (L2/L1) while few rows are visited, "
+                         "4 V_next (L1) at every level")
     ap.add_argument("--sources", type=int, default=0, help="use only the first N sources of the workload")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner, use the flags as given")
     ap.add_argument("--depth", type=int, default=2,

@@ -85,8 +85,8 @@ typedef enum {
     BLEST_OPT_VISITED_FILTER = 7,    /* 1 = test V_curr before marking a row; 2 = lazy update also skips
                                         rows already marked at this level: it tests V_next (which contains
                                         V_curr), read at L2, on levels where fewer than n/4 rows have a
-                                        level, V_curr after; 3 (default) = as 2 with V_next read through
-                                        L1 (staler, cheaper); 4 = V_next through L1 at every level; 0 = off;
+                                        level, V_curr after; 3 = as 2 with V_next read through L1 (staler,
+                                        cheaper); 4 (default) = V_next through L1 at every level; 0 = off;
                                         the eager update uses 1 for 2, 3 and 4 */
     BLEST_OPT_MIN_BLOCKS = 8,        /* kernel variant compiled for 2 (default) or 3 blocks per SM */
     BLEST_OPT_STAGE_DEPTH = 9,       /* lazy stage 1 prefetch: 0 = none; 2 (default) = the next group's

@@ -117,7 +117,7 @@ struct blest_graph {
     int minb = 2;
     // defaults: the variant the autotuner picks on social-like graphs (lazy levels);
     // eager levels ignore the lazy-only ones
-    int filter = 3;
+    int filter = 4;
     int depth = 2;
     int layout = 0;
     int sched = 1;
