@@ -117,10 +117,11 @@ typedef enum {
                                         and distinct level at which a vertex gains bits), 0 (default) =
                                         planes on graphs the Section 5 rule updates lazily, else
                                         vertex-major */
-    BLEST_OPT_MS_VISITED_FILTER = 16 /* multi-source marks: 1 (default) = read the row's V_curr word and
-                                        mark only sources that have not reached it; 0 = mark every hit
-                                        word (no dependent read; V_next still contains V_curr, so the
-                                        levels are the same) */
+    BLEST_OPT_MS_VISITED_FILTER = 16 /* multi-source marks: 1 = read the row's V_curr word and mark only
+                                        sources that have not reached it; 2 (default) = read its V_next
+                                        word instead (V_next contains V_curr: also skips sources marked
+                                        at this level); 0 = mark every hit word (no dependent read; V_next
+                                        still contains V_curr, so the levels are the same) */
 } blest_option;
 
 /* Creation parameters; pass NULL to blest_graph_create_ex for the defaults. */

@@ -105,7 +105,7 @@ struct blest_graph {
     int ms_chunk = blest::kMsbfsChunk;   // sources per multi-source launch
     int ms_blocks_per_sm = 0;            // 0 = blocks_per_sm
     int ms_levels = 0;                   // BLEST_OPT_MS_LEVELS: 0 auto, 1 vertex-major, 2 bit planes
-    int ms_filter = 1;                   // BLEST_OPT_MS_VISITED_FILTER
+    int ms_filter = 2;                   // BLEST_OPT_MS_VISITED_FILTER
     // sharded traversal in progress (blest_shard_*): rank, ranks, next level, output, rows reached
     int32_t shard_rank = -1, shard_world = 0, shard_level = 0;
     int32_t* shard_out = nullptr;
@@ -904,7 +904,7 @@ blest_status blest_set_option(blest_handle h, int32_t key, int64_t value) {
             h->ms_levels = (int)value;
             return BLEST_OK;
         case BLEST_OPT_MS_VISITED_FILTER:
-            if (value != 0 && value != 1) break;
+            if (value < 0 || value > 2) break;
             h->ms_filter = (int)value;
             return BLEST_OK;
         default:
@@ -1235,7 +1235,7 @@ blest_status blest_autotune_msbfs(blest_handle h, const int32_t* srcs, int32_t k
         for (int chunk : chunks)
             for (int bps : {0, 1, 2})   // blocks per SM above what fits run as many as fit
             for (int levels : {1, 2})    // vertex-major, bit planes
-            for (int filt : {1, 0}) {    // V_curr test before each mark, or none
+            for (int filt : {1, 2, 0}) { // V_curr or V_next test before each mark, or none
                 if (s) break;
                 // one layout and the default test are enough to time the MMA
                 if (pull == BLEST_PULL_MMA && (levels != 2 || filt != 1)) continue;

@@ -60,7 +60,7 @@ struct MsArgs {
     int32_t kst;                  // row stride of lint: k rounded up to a multiple of 8
     unsigned long long* planes;   // LV 1: nplanes x (n x W) words: plane p holds bit p of every level
     int32_t nplanes;              // msbfs_planes(n): enough bits for level n - 1
-    int32_t vfilter;              // 1: test V_curr before each mark; 0: mark every hit row's word
+    int32_t vfilter;              // 1: test V_curr before each mark; 2: test V_next; 0: mark every hit word
     int32_t* out;        // k x n, source-major, original ids
     uint32_t* dirty;     // one bit per slice set touched by a mark in a sparse level (cleared by the sweep)
     const int32_t* roots;
@@ -327,7 +327,11 @@ __device__ __forceinline__ void ms_pull_tile(const MsArgs& a, const MsTile<W>& t
             // bits during a traversal, so a stale word can only let a mark through.
             // Without the test every hit word is marked: V_next keeps containing V_curr,
             // so the sweep's diff is the same, and the gather (a dependent load) is gone.
-            const unsigned long long fresh = a.vfilter ? y[q][w] & ~a.vcur[(size_t)r4[q] * W + w] : y[q][w];
+            // V_next contains V_curr, so testing it also skips sources already marked at
+            // this level (a stale word again only lets a mark through).
+            const size_t vi = (size_t)r4[q] * W + w;
+            const unsigned long long fresh =
+                a.vfilter == 0 ? y[q][w] : y[q][w] & ~(a.vfilter == 2 ? a.vnext[vi] : a.vcur[vi]);
             if (fresh) {
                 atomicOr(&a.vnext[(size_t)r4[q] * W + w], fresh);
                 if (sparse) atomicOr(&a.dirty[r4[q] >> 8], 1u << ((r4[q] >> 3) & 31));
@@ -612,7 +616,7 @@ int run_msbfs(MsbfsState& s, const MsbfsLaunchCommon& c, const std::vector<int32
         a.kst = kst;
         a.planes = s.planes;
         a.nplanes = msbfs_planes(c.n);
-        a.vfilter = c.visited_filter ? 1 : 0;
+        a.vfilter = c.visited_filter;
         a.out = out;
         a.roots = s.roots;
         a.dirty = s.dirty;

@@ -70,7 +70,7 @@ struct MsbfsLaunchCommon {
     int pull = 0;                       // 0 CUDA-core OR of frontier words, 1 b1 tensor-core MMAs
     int chunk = kMsbfsChunk;            // sources per launch: 64, 128 or 256
     int levels_layout = 0;              // 0 vertex-major levels, 1 bit planes
-    int visited_filter = 1;             // 1: test V_curr before each mark, 0: mark every hit word
+    int visited_filter = 2;             // 1: test V_curr before each mark, 2: V_next, 0: mark every hit word
 };
 
 // Runs k = roots.size() traversals (sources already in BVSS ids) in launches of

@@ -264,7 +264,7 @@ def test_msbfs_pull_backends_and_launch_sizes(gpu, pull, chunk, levels):
             for k in (3, 64, 65, 130, 300):
                 srcs = synth.pick_sources(graph, k, seed=31 + k)
                 exp = oracle.msbfs_levels(graph.n, graph.row_ptr, graph.col_idx, srcs, threads=8)
-                for filt in (1, 0):
+                for filt in (1, 2, 0):
                     blest.blest_set_option(h, blest.BLEST_OPT_MS_VISITED_FILTER, filt)
                     assert np.array_equal(blest.blest_msbfs(h, srcs), exp), (k, pull, chunk, filt)
         finally:
@@ -278,9 +278,9 @@ def test_msbfs_autotune_keeps_levels_exact(gpu):
     h = blest.blest_graph_create(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_COMPRESS)
     try:
         r = blest.blest_autotune_msbfs(h, srcs)
-        # CUDA-core pull: 3 launch sizes x 3 grid sizes x 2 level layouts x 2 visited tests;
-        # MMA: bit planes with the test only
-        assert r["candidates"] == 3 * 3 * 2 * 2 + 3 * 3
+        # CUDA-core pull: 3 launch sizes x 3 grid sizes x 2 level layouts x 3 visited tests;
+        # MMA: bit planes with the V_curr test only
+        assert r["candidates"] == 3 * 3 * 2 * 3 + 3 * 3
         assert r["levels"] in (1, 2)
         assert r["popc_ms"] > 0 and r["mma_ms"] > 0 and r["best_ms"] == min(r["popc_ms"], r["mma_ms"])
         assert r["chunk"] in (64, 128, 256) and r["pull"] in (blest.BLEST_PULL_POPC, blest.BLEST_PULL_MMA)
