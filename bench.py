@@ -782,10 +782,14 @@ def run_ours_shard(args, torch, blest, dev, rank, world):
     W = 2
     t0 = time.time()
     h0 = blest.blest_graph_create_ex(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_COMPRESS, window=args.window)
-    path = os.path.join("/tmp", f"blest_shard_{os.getpid()}.bin")
-    blest.blest_graph_save(h0, path)
-    h1 = blest.blest_graph_load(path)             # the same BVSS and order without a second reordering
-    os.remove(path)
+    import tempfile
+    fd, path = tempfile.mkstemp(suffix=".blest")
+    os.close(fd)
+    try:
+        blest.blest_graph_save(h0, path)
+        h1 = blest.blest_graph_load(path)         # the same BVSS and order without a second reordering
+    finally:
+        os.remove(path)
     t_create = time.time() - t0
     hs = [h0, h1]
     stream = torch.cuda.current_stream(dev)
