@@ -60,28 +60,31 @@ WORKLOADS = {
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "bfs_kernel_traffic.txt")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2512_21967_gb300", "csrc", f)
                   for f in ("bfs_kernel.cu", "device_common.cuh", "bfs_launch.h")]
+MS_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "msbfs_kernel_traffic.txt")
+MS_KERNEL_SOURCES = [os.path.join(ROOT, "paper_2512_21967_gb300", "csrc", f)
+                     for f in ("msbfs_kernel.cu", "msbfs_launch.h", "msbfs_bits.h", "device_common.cuh")]
 
 
-def kernel_sources_sha256():
+def kernel_sources_sha256(sources=None):
     import hashlib
     d = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources or KERNEL_SOURCES:
         with open(f, "rb") as fh:
             d.update(fh.read())
     return d.hexdigest()
 
 
-def traffic_ratio():
+def traffic_ratio(path=None, sources=None):
     """(DRAM bytes per algorithmic byte, note), or (None, why) when the kernel
     changed since the capture or no capture is committed."""
     try:
         kv = {}
-        with open(TRAFFIC_FILE) as f:
+        with open(path or TRAFFIC_FILE) as f:
             for line in f:
                 if ":" in line and not line.startswith("#"):
                     k, v = line.split(":", 1)
                     kv[k.strip()] = v.strip()
-        if kv.get("kernel_sources_sha256") != kernel_sources_sha256():
+        if kv.get("kernel_sources_sha256") != kernel_sources_sha256(sources):
             return None, "kernel sources changed since the ncu capture"
         return float(kv["dram_bytes_per_algorithmic_byte"]), kv.get("capture", "")
     except (OSError, KeyError, ValueError):
@@ -561,6 +564,7 @@ def run_ours_msbfs(args, torch, blest, h, g, srcs, k, dev, stream, flush, st, t_
         cpu = cpu_baseline_parallel(g, srcs[:k], 2 * (os.cpu_count() or 1))
     hbm, peak_kind = peaks()
     achieved = ms_bytes / (ms / args.steps / 1e3) / 1e9
+    ms_ratio, ms_note = traffic_ratio(MS_TRAFFIC_FILE, MS_KERNEL_SOURCES)
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
@@ -573,8 +577,9 @@ def run_ours_msbfs(args, torch, blest, h, g, srcs, k, dev, stream, flush, st, t_
                            "single_source_variant": {kk: tune[kk] for kk in ("update", "unroll", "stage_depth",
                                                                               "visited_filter", "blocks_per_sm")}},
                 "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                             "frac": round(achieved / hbm, 4), "peak_kind": peak_kind, "traffic": None,
-                             "traffic_note": "no capture of this kernel revision",
+                             "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
+                             "traffic": round(ms_ratio * ms_bytes) if ms_ratio else None,
+                             "traffic_note": ms_note,
                              "kernel": "msbfs_kernel + msbfs_output_kernel (one traversal launch and one "
                                        "output launch per 64-256 sources; the event pair also covers the "
                                        "call's clears and source upload)",
