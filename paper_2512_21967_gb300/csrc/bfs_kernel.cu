@@ -118,7 +118,7 @@ __device__ __forceinline__ unsigned int pull_hits(uint32_t mask, uint32_t alpha,
 // the same level, but a rank enqueues only the slice sets it owns (s mod world =
 // rank), and the number of newly reached rows is always counted.
 template <int UPDATE, int LAYOUT, bool SHARD = false>
-__device__ __forceinline__ void sweep(const BfsArgs& a, int lvl, unsigned long long* Qout, unsigned int* qcount,
+__device__ __forceinline__ void sweep(const BfsArgs& a, int lvl, unsigned long long* Qout, unsigned long long* qcount,
                                       uint32_t* Fout, bool sparse, int world = 1, int rank = 0) {
     // Work split: in round k, warp w of block B takes the block of 32 words
     // B + (w + 16 k) gridDim.x, so consecutive 32-word blocks go to consecutive
@@ -225,7 +225,7 @@ __device__ __forceinline__ void sweep(const BfsArgs& a, int lvl, unsigned long l
             }
             unsigned int base = 0;
             if (run) {
-                base = atomicAdd(qcount, run);
+                base = (unsigned int)atomicAdd(qcount, (unsigned long long)run);
                 if (base + run > a.qcap || base + run < base) {
                     raise_error(a.ctrl, 7u);
                     base = 0xFFFFFFFFu;
@@ -306,7 +306,7 @@ __device__ __forceinline__ void mark_rows(const BfsArgs& a, const int4 (&rows)[N
 // bit of a slice set's frontier byte enqueues that slice set's VSS range.
 template <int NV>
 __device__ __forceinline__ void eager_update(const BfsArgs& a, const int4 (&rows)[NV], unsigned int hm, int lvl,
-                                             uint32_t* Fnext, unsigned long long* Qout, unsigned int* qcount_next,
+                                             uint32_t* Fnext, unsigned long long* Qout, unsigned long long* qcount_next,
                                              int lane) {
     constexpr int K = 4 * NV;
     int u[K];
@@ -631,7 +631,7 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
     const int gwarp = gtid >> 5;
     const int nwarps = nthreads >> 5;
     const unsigned int nblocks = gridDim.x;
-    unsigned int gen = 0;
+    unsigned int bar = 0;   // barriers passed; the next one is number bar
     Ctrl* ctrl = a.ctrl;
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     // DEPTH 4 or 8: a shared-memory ring per warp; DEPTH 2 and 3 keep their stages in registers
@@ -658,17 +658,16 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
         atomicOr(&a.vnext[r >> 5], 1u << (r & 31));
         if (sparse0) atomicOr(&a.dirty[r >> 10], 1u << ((r >> 5) & 31));
     }
-    if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns)) return;
+    if (!grid_barrier(ctrl, nblocks, a.phantom, bar, a.timeout_ns)) return;
     if (gtid == 0 && a.level_sizes) a.level_times[0] = global_timer_ns();
-    sweep<UPDATE, LAYOUT>(a, 0, a.Q[1], &ctrl->qcount[1], a.F[1], sparse0);
+    sweep<UPDATE, LAYOUT>(a, 0, a.Q[1], ring_word(ctrl, bar), a.F[1], sparse0);
     unsigned int qn = 0, qprev = 0;
-    if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns, &ctrl->qcount[1], &qn)) return;
+    if (!grid_barrier(ctrl, nblocks, a.phantom, bar, a.timeout_ns, &qn)) return;
 
     int lvl = 1;
     for (;; ++lvl) {
         if (qn > a.qcap) qn = a.qcap;   // only after an overflow, which already raised an error
         if (gtid == 0) {
-            ctrl->qcount[(lvl + 2) & 3] = 0;
             ctrl->work[(lvl + 1) & 1] = 0;   // counter of the next level (this level's is work[lvl & 1])
             if (a.level_sizes && lvl - 1 < a.level_cap) {
                 a.level_sizes[lvl - 1] = (int32_t)qn;
@@ -686,7 +685,9 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
         const uint32_t* Fcur = a.F[lvl % 3];
         uint32_t* Fnext = a.F[(lvl + 1) % 3];
         unsigned long long* Qout = a.Q[(lvl + 1) % 3];
-        unsigned int* qcount_next = &ctrl->qcount[(lvl + 1) & 3];
+        // the next queue's size: the word of the barrier that ends this level
+        // (the lazy update passes one barrier between stage 1 and its sweep)
+        unsigned long long* qcount_next = ring_word(ctrl, bar + (UPDATE == 2 ? 1u : 0u));
 
         // stage 1: pull the queued virtual slice sets, round-robin over warps
         // the lazy filter of this level: the V_next test only while few rows are visited
@@ -753,7 +754,7 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
             }
         }
         if (UPDATE == 2) {
-            if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns)) return;
+            if (!grid_barrier(ctrl, nblocks, a.phantom, bar, a.timeout_ns)) return;
             if (gtid == 0 && a.level_sizes && lvl - 1 < a.level_cap) a.level_times[2 * lvl + 1] = global_timer_ns();
             sweep<UPDATE, LAYOUT>(a, lvl, Qout, qcount_next, nullptr, sparse);
             if (a.level_sizes && lvl - 1 < a.level_cap) {
@@ -766,7 +767,7 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
             }
         }
         unsigned int qnext = 0;
-        if (!grid_barrier(ctrl, nblocks, a.phantom, gen, a.timeout_ns, qcount_next, &qnext)) return;
+        if (!grid_barrier(ctrl, nblocks, a.phantom, bar, a.timeout_ns, &qnext)) return;
         if (qnext == 0) break;
         qprev = qn;
         qn = qnext;
@@ -802,9 +803,10 @@ __global__ void __launch_bounds__(kBfsBlock, 2) shard_pull_kernel(BfsArgs a, int
     const int gwarp = gtid >> 5;
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
     Ctrl* ctrl = a.ctrl;
-    unsigned int qn = ld_cg(&ctrl->qcount[lvl & 1]);
+    // the queue sizes are ring words 0 and 1 (no grid barrier runs in these launches)
+    unsigned int qn = (unsigned int)ld_cg(ring_word(ctrl, (unsigned int)lvl & 1u));
     if (qn > a.qcap) qn = a.qcap;   // only after an overflow, which already raised an error
-    if (gtid == 0) ctrl->qcount[(lvl + 1) & 1] = 0u;   // written by this level's sweep
+    if (gtid == 0) *ring_word(ctrl, (unsigned int)(lvl + 1) & 1u) = 0ull;   // written by this level's sweep
     const int filt = a.filter == 4 ? 3
                                    : ((a.filter >= 2 && ld_cg(&ctrl->reached) >= (unsigned int)a.n / 4u) ? 1
                                                                                                       : a.filter);
@@ -814,7 +816,8 @@ __global__ void __launch_bounds__(kBfsBlock, 2) shard_pull_kernel(BfsArgs a, int
 }
 
 __global__ void __launch_bounds__(kBfsBlock, 2) shard_sweep_kernel(BfsArgs a, int lvl, int world, int rank) {
-    sweep<2, 0, true>(a, lvl, a.Q[(lvl + 1) & 1], &a.ctrl->qcount[(lvl + 1) & 1], nullptr, false, world, rank);
+    sweep<2, 0, true>(a, lvl, a.Q[(lvl + 1) & 1], ring_word(a.ctrl, (unsigned int)(lvl + 1) & 1u), nullptr, false,
+                      world, rank);
     fold_status(a.ctrl);
 }
 

@@ -11,9 +11,9 @@ constexpr int kWarp = 32;
 
 // Control block (device memory, zeroed before every traversal).
 struct Ctrl {
-    unsigned int barrier;      // monotonically increasing arrival counter
+    unsigned int spare0;
     unsigned int error;        // first blest_status raised on the device (0 = none)
-    unsigned int qcount[4];    // queue sizes, index = level & 3
+    unsigned int spare1[4];
     unsigned int levels;       // levels processed
     unsigned int reached;      // rows given a level so far (counted only when a filter needs it)
     unsigned int work[2];      // dynamic stage-1 schedule: next queue position, index = level & 1
@@ -27,12 +27,6 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
     return t;
 }
 
-__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 __device__ __forceinline__ unsigned int ld_volatile_u32(const unsigned int* p) {
     return *(const volatile unsigned int*)p;
 }
@@ -42,12 +36,23 @@ template <class T>
 __device__ __forceinline__ T ld_cg(const T* p) { return __ldcg(p); }
 
 // Control words live in one 256-byte device block: the Ctrl struct at byte 0,
-// the barrier release flag alone on the cache line at byte 128, and the sticky
-// status word at byte 192.  Bytes [0, 192) are cleared before every traversal.
+// the grid barrier's ring of four 64-bit words alone on the cache line at byte
+// 128, and the sticky status word at byte 192.  Bytes [0, 192) are cleared
+// before every traversal.
 constexpr int kCtrlBytes = 256;
 constexpr int kCtrlClearBytes = 192;
-constexpr int kFlagWord = 32;     // unsigned-int index of the 64-bit release flag
+constexpr int kRingWord = 32;     // unsigned-int index of the barrier ring
 constexpr int kStickyWord = 48;   // unsigned-int index of the sticky status
+
+// Word i of the barrier ring.  Barrier number b of a launch uses word b & 3: its
+// high half counts the blocks that arrived, its low half is the size of the
+// queue that the phase ending at barrier b fills (the queue appends add to it),
+// so the next level's queue size comes back with the load that sees the last
+// arrival.  The low half never carries into the high half: a phase appends each
+// VSS at most once and VSS indices are 32-bit.
+__device__ __forceinline__ unsigned long long* ring_word(void* ctrl, unsigned int i) {
+    return reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned int*>(ctrl) + kRingWord) + (i & 3u);
+}
 
 __device__ __forceinline__ unsigned long long ld_acquire_gpu_u64(const unsigned long long* p) {
     unsigned long long v;
@@ -55,78 +60,67 @@ __device__ __forceinline__ unsigned long long ld_acquire_gpu_u64(const unsigned 
     return v;
 }
 
-__device__ __forceinline__ void st_release_gpu_u64(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+// Reduction with release semantics at GPU scope: it releases the calling
+// thread's earlier writes (and, through a preceding __syncthreads, its block's).
+__device__ __forceinline__ void red_release_gpu_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// atomicAdd with acquire-release semantics at GPU scope: it releases the
-// calling thread's earlier writes (and, through a preceding __syncthreads, its
-// block's) and acquires those released by earlier RMWs on the same address.
-__device__ __forceinline__ unsigned int atom_add_acq_rel_gpu(unsigned int* p, unsigned int v) {
-    unsigned int old;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
+__device__ __forceinline__ void st_relaxed_gpu_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Grid barrier for a cooperative launch (all blocks co-resident).  Thread 0 of
-// each block arrives with an acquire-release atomic add on the arrival counter,
-// which releases its block's writes.  The block that arrives last has thereby
-// acquired every block's writes; it reads *pub and releases the others by storing
-// (generation << 32 | *pub) into a flag on its own cache line; the waiting
-// blocks spin on that flag with acquire loads.  Every block returns the
-// published word through *published (the next queue size, so the level loop
-// needs no separate read of it).  The last block also reads ctrl->error and
-// publishes it as bit 63 of the flag, so that no waiting block needs a second
-// round trip to L2 after the release: the generation takes bits 32..62.
-// The wait is bounded: after timeout_ns it records BLEST_ERR_TIMEOUT (6) in
-// ctrl->error and returns false, as it does when another block has already
-// recorded an error (checked every 32 polls, with the clock).  `extra` adds
-// phantom participants (test hook: a barrier that can never complete).  `gen`
-// is this block's barrier count.
+// Grid barrier for a cooperative launch (all blocks co-resident).  `count` is
+// the number of barriers this block has passed (the same in every block and
+// every thread); barrier number b uses ring word b & 3 (see ring_word).  Thread
+// 0 of each block arrives by adding 1 << 32 to the word with a release
+// reduction, which releases its block's writes (ordered before it by
+// __syncthreads), and polls the word with acquire loads until all
+// nblocks + extra arrivals are counted.  The load that sees the last arrival has
+// acquired every block's writes and carries the low half, which every block
+// returns through *published (the next queue size).  Block 0 then clears word
+// (b + 2) & 3: every block has arrived at barrier b, so none still polls barrier
+// b - 2, the word's previous use; and the clear is released with block 0's
+// arrival at barrier b + 1, before which no block adds to the word or arrives on
+// it.  The wait is bounded: after timeout_ns it records BLEST_ERR_TIMEOUT (6) in
+// ctrl->error and returns false, as it does when an error has been recorded (read
+// with the first poll and every 32 polls; an error recorded by a block arriving
+// late is seen at the next barrier).  `extra` adds phantom participants (test
+// hook: a barrier that can never complete).
 __device__ __forceinline__ bool grid_barrier(Ctrl* ctrl, unsigned int nblocks, unsigned int extra,
-                                             unsigned int& gen, uint64_t timeout_ns,
-                                             const unsigned int* pub = nullptr,
+                                             unsigned int& count, uint64_t timeout_ns,
                                              unsigned int* published = nullptr) {
     __shared__ int s_ok;
     __shared__ unsigned int s_pub;
     __syncthreads();
     if (threadIdx.x == 0) {
-        gen += 1;
-        unsigned long long* flag = reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned int*>(ctrl) + kFlagWord);
-        const unsigned int target = gen * (nblocks + extra);
-        const unsigned int old = atom_add_acq_rel_gpu(&ctrl->barrier, 1u);
-        int ok = 1;
-        unsigned int value = 0;
-        if (old + 1u == target) {
-            value = pub ? atomicOr(const_cast<unsigned int*>(pub), 0u) : 0u;   // coherent reads at L2
-            const unsigned long long err = atomicOr(&ctrl->error, 0u) != 0u ? 1ull : 0ull;
-            st_release_gpu_u64(flag, (err << 63) | ((unsigned long long)gen << 32) | value);
-            if (err) ok = 0;
-        } else {
-            const uint64_t t0 = global_timer_ns();
-            unsigned int spins = 0;
-            for (;;) {
-                const unsigned long long f = ld_acquire_gpu_u64(flag);
-                if (((unsigned int)(f >> 32) & 0x7FFFFFFFu) >= gen) {
-                    value = (unsigned int)f;
-                    if (f >> 63) ok = 0;
+        unsigned long long* w = ring_word(ctrl, count);
+        const unsigned int need = nblocks + extra;
+        red_release_gpu_u64(w, 1ull << 32);
+        unsigned int err = ld_volatile_u32(&ctrl->error);   // in flight with the first poll
+        unsigned long long f = 0;
+        const uint64_t t0 = global_timer_ns();
+        unsigned int spins = 0;
+        for (;;) {
+            f = ld_acquire_gpu_u64(w);
+            if ((unsigned int)(f >> 32) >= need) break;
+            if ((++spins & 31u) == 0) {
+                err |= ld_volatile_u32(&ctrl->error);
+                if (err) break;
+                if (global_timer_ns() - t0 > timeout_ns) {
+                    atomicCAS(&ctrl->error, 0u, 6u);
+                    err = 6u;
                     break;
                 }
-                if ((++spins & 31u) == 0) {
-                    if (ld_volatile_u32(&ctrl->error) != 0) { ok = 0; break; }
-                    if (global_timer_ns() - t0 > timeout_ns) {
-                        atomicCAS(&ctrl->error, 0u, 6u);
-                        ok = 0;
-                        break;
-                    }
-                }
-                if (spins > 64) __nanosleep(32);
             }
+            if (spins > 64) __nanosleep(32);
         }
-        s_ok = ok;   // the flag's acquire load (or the acq_rel add) orders what follows
-        s_pub = value;
+        if (err == 0u && blockIdx.x == 0) st_relaxed_gpu_u64(ring_word(ctrl, count + 2u), 0ull);
+        s_ok = err == 0u;
+        s_pub = (unsigned int)f;
     }
     __syncthreads();
+    count += 1u;
     if (published) *published = s_pub;
     return s_ok != 0;
 }
@@ -268,7 +262,7 @@ __device__ __forceinline__ void warp_write_entries(unsigned long long* Qout, uns
 // writing past qcap.
 template <int NS, bool GROUPS = false>
 __device__ __forceinline__ void warp_enqueue(unsigned int qcap, Ctrl* ctrl, unsigned long long* Qout,
-                                             unsigned int* qcount, const int (&st)[NS], const int (&ln)[NS],
+                                             unsigned long long* qcount, const int (&st)[NS], const int (&ln)[NS],
                                              const uint32_t (&pay)[NS], int lane, const int (&tot)[NS]) {
     unsigned int cnt = 0;
 #pragma unroll
@@ -277,7 +271,7 @@ __device__ __forceinline__ void warp_enqueue(unsigned int qcap, Ctrl* ctrl, unsi
     const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
     if (total == 0) return;
     unsigned int base = 0;
-    if (lane == 31) base = atomicAdd(qcount, total);
+    if (lane == 31) base = (unsigned int)atomicAdd(qcount, (unsigned long long)total);
     base = __shfl_sync(0xffffffffu, base, 31);
     if (base + total > qcap || base + total < base) {
         if (lane == 0) raise_error(ctrl, 7u);
@@ -293,13 +287,13 @@ __device__ __forceinline__ void warp_enqueue(unsigned int qcap, Ctrl* ctrl, unsi
 // over the warp's exclusive prefix of ln (5 shuffle steps), so every store
 // instruction writes 32 consecutive entries (256 contiguous bytes).
 __device__ __forceinline__ void warp_enqueue_coalesced(unsigned int qcap, Ctrl* ctrl, unsigned long long* Qout,
-                                                       unsigned int* qcount, int st, int ln, uint32_t pay,
+                                                       unsigned long long* qcount, int st, int ln, uint32_t pay,
                                                        int lane) {
     const unsigned int incl = warp_inclusive_scan((unsigned int)ln, lane);
     const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
     if (total == 0) return;
     unsigned int base = 0;
-    if (lane == 31) base = atomicAdd(qcount, total);
+    if (lane == 31) base = (unsigned int)atomicAdd(qcount, (unsigned long long)total);
     base = __shfl_sync(0xffffffffu, base, 31);
     if (base + total > qcap || base + total < base) {
         if (lane == 0) raise_error(ctrl, 7u);

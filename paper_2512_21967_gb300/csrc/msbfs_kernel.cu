@@ -102,7 +102,7 @@ __device__ __forceinline__ void ms_write_planes(const MsArgs& a, unsigned long l
 }
 
 template <int W, int LV>
-__device__ __forceinline__ void ms_sweep(const MsArgs& a, int lvl, unsigned long long* Qout, unsigned int* qcount) {
+__device__ __forceinline__ void ms_sweep(const MsArgs& a, int lvl, unsigned long long* Qout, unsigned long long* qcount) {
     const int lane = threadIdx.x & 31;
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
     const int nchunks = (a.n + kWarp - 1) / kWarp;
@@ -152,7 +152,7 @@ __device__ __forceinline__ void ms_sweep(const MsArgs& a, int lvl, unsigned long
 // never reads them.
 template <int W, int LV>
 __device__ __forceinline__ void ms_sweep_sparse(const MsArgs& a, int lvl, unsigned long long* Qout,
-                                                unsigned int* qcount) {
+                                                unsigned long long* qcount) {
     const int lane = threadIdx.x & 31;
     const int wpb = (int)(blockDim.x >> 5);
     const int nss = (a.n + 7) >> 3;
@@ -346,7 +346,7 @@ __device__ __forceinline__ void ms_body(const MsArgs& a) {
     const int nthreads = (int)(gridDim.x * blockDim.x);
     const int gwarp = gtid >> 5;
     const int nwarps = nthreads >> 5;
-    unsigned int gen = 0;
+    unsigned int bar = 0;   // barriers passed; the next one is number bar
     Ctrl* ctrl = a.ctrl;
     const uint64_t pol = l2_evict_first_policy();
 
@@ -354,23 +354,20 @@ __device__ __forceinline__ void ms_body(const MsArgs& a) {
         const int r = a.roots[i];
         atomicOr(&a.vnext[(size_t)r * W + (i >> 6)], 1ull << (i & 63));
     }
-    if (!grid_barrier(ctrl, gridDim.x, a.phantom, gen, a.timeout_ns)) return;
-    ms_sweep<W, LV>(a, 0, a.Q[1], &ctrl->qcount[1]);
+    if (!grid_barrier(ctrl, gridDim.x, a.phantom, bar, a.timeout_ns)) return;
+    ms_sweep<W, LV>(a, 0, a.Q[1], ring_word(ctrl, bar));
     unsigned int qn = 0;
-    if (!grid_barrier(ctrl, gridDim.x, a.phantom, gen, a.timeout_ns, &ctrl->qcount[1], &qn)) return;
+    if (!grid_barrier(ctrl, gridDim.x, a.phantom, bar, a.timeout_ns, &qn)) return;
 
     int lvl = 1;
     for (;; ++lvl) {
         if (qn > a.qcap) qn = a.qcap;   // only after an overflow, which already raised an error
         // few queued VSSs: track the touched slice sets and sweep only those
         const bool sparse = (unsigned long long)qn * 128ull <= (unsigned long long)a.n;
-        if (gtid == 0) {
-            ctrl->qcount[(lvl + 2) & 3] = 0;
-            if (a.level_sizes && lvl - 1 < a.level_cap) a.level_sizes[lvl - 1] = (int32_t)qn;
-        }
+        if (gtid == 0 && a.level_sizes && lvl - 1 < a.level_cap) a.level_sizes[lvl - 1] = (int32_t)qn;
         const unsigned long long* Qin = a.Q[lvl % 3];
         unsigned long long* Qout = a.Q[(lvl + 1) % 3];
-        unsigned int* qcount_next = &ctrl->qcount[(lvl + 1) & 3];
+        unsigned long long* qcount_next = ring_word(ctrl, bar + 1u);   // the barrier after the sweep
         if (LV == 1 && (lvl & (lvl - 1)) == 0) {
             // lvl = 2^p: this level's sweep is the first to write plane p, so it is
             // cleared now (stage 1 does not touch the planes; the barrier orders it)
@@ -394,11 +391,11 @@ __device__ __forceinline__ void ms_body(const MsArgs& a) {
             t = t_next;
             e_next = e_after;
         }
-        if (!grid_barrier(ctrl, gridDim.x, a.phantom, gen, a.timeout_ns)) return;
+        if (!grid_barrier(ctrl, gridDim.x, a.phantom, bar, a.timeout_ns)) return;
         if (sparse) ms_sweep_sparse<W, LV>(a, lvl, Qout, qcount_next);
         else ms_sweep<W, LV>(a, lvl, Qout, qcount_next);
         unsigned int qnext = 0;
-        if (!grid_barrier(ctrl, gridDim.x, a.phantom, gen, a.timeout_ns, qcount_next, &qnext)) return;
+        if (!grid_barrier(ctrl, gridDim.x, a.phantom, bar, a.timeout_ns, &qnext)) return;
         if (qnext == 0) break;
         qn = qnext;
     }
