@@ -676,10 +676,13 @@ __device__ __forceinline__ void bfs_body(const BfsArgs& a) {
         }
         const unsigned long long* Qin = a.Q[lvl % 3];
         if (UPDATE == 1) {
-            // clear the frontier bytes of level lvl-1 (read last level, rewritten at lvl+1)
+            // clear the frontier bytes of level lvl-1 (read last level, rewritten at lvl+1),
+            // counted from the last thread of the grid: on a short queue the stage-1 items
+            // go to the first warps, and a clear (a store that waits for its queue load)
+            // would delay their loads by a round trip
             const unsigned long long* Qp = a.Q[(lvl + 2) % 3];
             unsigned char* Fold = reinterpret_cast<unsigned char*>(a.F[(lvl + 2) % 3]);
-            for (unsigned int i = (unsigned int)gtid; i < qprev; i += (unsigned int)nthreads)
+            for (unsigned int i = (unsigned int)(nthreads - 1 - gtid); i < qprev; i += (unsigned int)nthreads)
                 Fold[(uint32_t)(ld_cg(&Qp[i]) >> 32)] = 0;
         }
         const uint32_t* Fcur = a.F[lvl % 3];
