@@ -74,9 +74,12 @@ def kernel_sources_sha256(sources=None):
     return d.hexdigest()
 
 
-def traffic_ratio(path=None, sources=None):
-    """(DRAM bytes per algorithmic byte, note), or (None, why) when the kernel
-    changed since the capture or no capture is committed."""
+def traffic_ratio(path=None, sources=None, workload=None, variant=None):
+    """(DRAM bytes per algorithmic byte, note) from a committed ncu capture, or
+    (None, why).  A capture file names the kernel sources' hash and holds one ratio
+    per workload and kernel variant (`<workload>/<variant>.ratio`, with its
+    `.capture` line); a ratio is used only for that workload and variant, and
+    only while the kernel sources are the ones captured."""
     try:
         kv = {}
         with open(path or TRAFFIC_FILE) as f:
@@ -86,7 +89,10 @@ def traffic_ratio(path=None, sources=None):
                     kv[k.strip()] = v.strip()
         if kv.get("kernel_sources_sha256") != kernel_sources_sha256(sources):
             return None, "kernel sources changed since the ncu capture"
-        return float(kv["dram_bytes_per_algorithmic_byte"]), kv.get("capture", "")
+        key = f"{workload}/{variant}"
+        if f"{key}.ratio" not in kv:
+            return None, f"no capture of the {variant} variant on {workload}"
+        return float(kv[f"{key}.ratio"]), kv.get(f"{key}.capture", "")
     except (OSError, KeyError, ValueError):
         return None, "no ncu capture committed"
 
@@ -437,7 +443,9 @@ def run_ours(args):
     avg_bytes = float(abytes.mean())
     hbm, peak_kind = peaks()
     achieved = avg_bytes / (avg_launch_ms / 1e3) / 1e9
-    tr_ratio, tr_note = traffic_ratio()
+    layout_run = (tune or {}).get("layout", args.layout)
+    tr_ratio, tr_note = traffic_ratio(workload=args.workload,
+                                      variant=f"{'lazy' if lazy else 'eager'}-layout{layout_run}")
 
     # end to end through the host-buffer C call
     e2e = None
@@ -564,7 +572,14 @@ def run_ours_msbfs(args, torch, blest, h, g, srcs, k, dev, stream, flush, st, t_
         cpu = cpu_baseline_parallel(g, srcs[:k], 2 * (os.cpu_count() or 1))
     hbm, peak_kind = peaks()
     achieved = ms_bytes / (ms / args.steps / 1e3) / 1e9
-    ms_ratio, ms_note = traffic_ratio(MS_TRAFFIC_FILE, MS_KERNEL_SOURCES)
+    # the variant that ran: the autotuner's choice, else the handle's defaults (CUDA-core
+    # pull, 256 sources per launch, V_next test; bit planes on a lazy-update graph)
+    msv = ms_tune or {"pull": args.ms_pull if args.ms_pull != "auto" else "popc", "chunk": 256,
+                      "visited_filter": 2, "levels": 0}
+    ms_levels = msv["levels"] or (2 if st["update"] == blest.BLEST_UPDATE_LAZY else 1)
+    ms_ratio, ms_note = traffic_ratio(MS_TRAFFIC_FILE, MS_KERNEL_SOURCES, workload=args.workload,
+                                      variant=f"{msv['pull']}-levels{ms_levels}-v{msv['visited_filter']}"
+                                              f"-c{msv['chunk']}")
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,

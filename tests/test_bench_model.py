@@ -128,3 +128,36 @@ def test_single_source_byte_model_matches_plain_definition(case, lazy, output_pa
         queues = [sum(int(nvss[s]) for s in {int(new_id[v]) // 8 for v in np.flatnonzero(levels == l)})
                   for l in range(int(levels.max()) + 1)]
         assert min(queues) <= cap < max(queues)
+
+
+def test_traffic_ratio_applies_only_to_its_workload_variant_and_sources(tmp_path):
+    """A captured DRAM ratio is reported only for the workload and kernel variant it
+    was taken on, and only while the kernel sources hash to the captured value."""
+    import bench
+    src = tmp_path / "kernel.cu"
+    src.write_text("// kernel as captured\n")
+    cap = tmp_path / "traffic.txt"
+    cap.write_text(f"# header: comment lines are skipped\n"
+                   f"kernel_sources_sha256: {bench.kernel_sources_sha256([str(src)])}\n"
+                   "wl/lazy-layout1.ratio: 0.93\n"
+                   "wl/lazy-layout1.capture: one launch\n"
+                   "wl/lazy-layout0.ratio: 1.17\n")
+    look = lambda w, v: bench.traffic_ratio(str(cap), [str(src)], workload=w, variant=v)
+    assert look("wl", "lazy-layout1") == (0.93, "one launch")
+    assert look("wl", "lazy-layout0")[0] == 1.17
+    assert look("wl", "eager-layout0")[0] is None
+    assert look("other", "lazy-layout1")[0] is None
+    src.write_text("// kernel changed\n")
+    ratio, why = look("wl", "lazy-layout1")
+    assert ratio is None and "changed" in why
+    assert bench.traffic_ratio(str(tmp_path / "absent.txt"), [str(src)], workload="wl", variant="x")[0] is None
+
+
+def test_committed_traffic_captures_match_the_kernel_sources():
+    """The committed captures are of the kernels as they are now (a kernel change
+    must come with a new capture, or the bench lines lose their traffic)."""
+    import bench
+    assert bench.traffic_ratio(workload="rmat23", variant="lazy-layout1")[0] is not None
+    assert bench.traffic_ratio(workload="rmat23", variant="lazy-layout0")[0] is not None
+    assert bench.traffic_ratio(bench.MS_TRAFFIC_FILE, bench.MS_KERNEL_SOURCES, workload="rmat22-ms64",
+                               variant="popc-levels2-v2-c256")[0] is not None
