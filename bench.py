@@ -759,7 +759,8 @@ def run_ours_serve(args, torch, blest, dev, rank, world):
             if mode == "batched":
                 srv = blest.blest_server_create(handles, memory_cap_bytes=40 << 30, max_batch_sources=64,
                                                 max_inflight=args.serve_inflight, blocks_per_sm=1,
-                                                narrow_sms=args.serve_narrow_sms, narrow_levels=256)
+                                                narrow_sms=args.serve_narrow_sms, narrow_levels=256,
+                                                long_slots=args.serve_long_slots)
             else:
                 srv = blest.blest_server_create(handles, memory_cap_bytes=40 << 30, max_batch_sources=32,
                                                 max_inflight=1, blocks_per_sm=0, max_queries_per_launch=1)
@@ -773,6 +774,18 @@ def run_ours_serve(args, torch, blest, dev, rank, world):
                          "throughput_qps": round(len(stream) / wall, 2), "launches": st["launches"],
                          "mean_sources_per_launch": round(st["sources_launched"] / max(1, st["launches"]), 2),
                          "memory_peak_gb": round(st["memory_peak"] / 2**30, 2)}
+            if mode == "batched":
+                # where the tail comes from: latency by graph kind and by graph
+                gids = np.array([q[1] for q in stream])
+                pct = lambda m, p: round(float(np.percentile(lat[m], p)) * 1e3, 3)
+                row[mode]["by_kind"] = {kind: {"queries": int(m.sum()), "p50_ms": pct(m, 50), "p99_ms": pct(m, 99)}
+                                        for kind in ("rmat", "grid")
+                                        for m in [np.isin(gids, [i for i, it in enumerate(items) if it[2] == kind])]
+                                        if m.any()}
+                row[mode]["by_graph"] = [{"graph": i, "kind": items[i][2], "n": graphs[i].n,
+                                          "queries": int((gids == i).sum()), "p50_ms": pct(gids == i, 50),
+                                          "p99_ms": pct(gids == i, 99)}
+                                         for i in range(len(graphs)) if (gids == i).any()]
         results.append(row)
     for h in handles:
         blest.blest_destroy(h)
@@ -784,7 +797,8 @@ def run_ours_serve(args, torch, blest, dev, rank, world):
                 "config": {"workload": "serving: 16 resident graphs (8 R-MAT s16..22, 8 grids 256..2048, p=0.9), "
                                        f"Poisson queries with 1..32 sources, {args.queries} per rate, 40 GB cap",
                            "server": {"max_inflight": args.serve_inflight, "max_batch_sources": 64,
-                                      "narrow_sms": args.serve_narrow_sms, "narrow_levels": 256},
+                                      "narrow_sms": args.serve_narrow_sms, "narrow_levels": 256,
+                                      "long_slots": args.serve_long_slots or max(1, args.serve_inflight - 1)},
                            "results_copied": "no (levels stay in device memory)"},
                 "serving": results, "preprocess_s": {"create_total": round(t_create, 2)}}
         print(json.dumps(line), flush=True)
@@ -1120,6 +1134,8 @@ def main():
     ap.add_argument("--queries", type=int, default=2000, help="serving: queries per arrival rate")
     ap.add_argument("--rates", default="100,400,1600", help="serving: arrival rates in queries/s")
     ap.add_argument("--serve-inflight", type=int, default=4, help="serving: launches in flight at once")
+    ap.add_argument("--serve-long-slots", type=int, default=0,
+                    help="serving: launches of long (high-diameter) graphs in flight at once; 0 = inflight - 1")
     ap.add_argument("--serve-narrow-sms", type=int, default=0,
                     help="serving: SMs of a launch on a graph whose last launch ran more than 256 levels (0 = all)")
     ap.add_argument("--oaat-queries", type=int, default=2000,

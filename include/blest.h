@@ -511,7 +511,13 @@ typedef struct {
                                     SMs, default): high-diameter graphs have small levels, and a narrow
                                     grid crosses each level barrier faster and leaves the other SMs to
                                     the launches of other graphs */
-    int32_t narrow_levels;       /* level count above which a graph's launches turn narrow (default 256) */
+    int32_t narrow_levels;       /* level count above which a graph counts as long: its launches turn
+                                    narrow (narrow_sms) and count against long_slots (default 256) */
+    int32_t long_slots;          /* launches of long graphs (the previous launch of the graph ran more
+                                    than narrow_levels levels) in flight at once; the other slots stay
+                                    free for the other graphs' launches, so that a short query does not
+                                    wait behind thousand-level traversals.  0 = max_inflight - 1, at
+                                    least 1 (default); a value >= max_inflight sets no limit */
 } blest_server_params;
 
 typedef struct {

@@ -108,7 +108,7 @@ class ServerParams(ctypes.Structure):
     _fields_ = [("memory_cap_bytes", ctypes.c_int64), ("max_batch_sources", ctypes.c_int32),
                 ("max_inflight", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("max_queries_per_launch", ctypes.c_int32), ("narrow_sms", ctypes.c_int32),
-                ("narrow_levels", ctypes.c_int32)]
+                ("narrow_levels", ctypes.c_int32), ("long_slots", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -535,10 +535,10 @@ def blest_bfs_static_scratch(n: int, num_vss: int, d_real_ptrs, d_row_ids, d_mas
 
 
 def blest_server_create(handles, memory_cap_bytes=0, max_batch_sources=0, max_inflight=0, blocks_per_sm=0,
-                        max_queries_per_launch=0, narrow_sms=0, narrow_levels=0) -> int:
+                        max_queries_per_launch=0, narrow_sms=0, narrow_levels=0, long_slots=0) -> int:
     arr = (_vp * len(handles))(*handles)
     p = ServerParams(int(memory_cap_bytes), int(max_batch_sources), int(max_inflight), int(blocks_per_sm),
-                     int(max_queries_per_launch), int(narrow_sms), int(narrow_levels))
+                     int(max_queries_per_launch), int(narrow_sms), int(narrow_levels), int(long_slots))
     s = _vp()
     _check(lib().blest_server_create(arr, len(handles), ctypes.byref(p), ctypes.byref(s)), "blest_server_create")
     return s.value

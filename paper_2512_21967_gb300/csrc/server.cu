@@ -12,7 +12,9 @@
 //     sources, and admits it only if its device memory (levels k x n, bit
 //     matrices, queues) fits under memory_cap_bytes next to the launches
 //     already in flight; the memory comes from the stream-ordered allocator and
-//     goes back when the launch retires.
+//     goes back when the launch retires.  A long graph (its previous launch ran
+//     more than narrow_levels levels) is passed over while long_slots of its kind
+//     are in flight, so that the other graphs' short launches find a slot.
 // Queries arriving while launches run join the next launch of their graph, and
 // launches of different graphs (or of the same graph) run concurrently on
 // their own streams; each launch uses a persistent grid of blocks_per_sm
@@ -80,6 +82,7 @@ struct Slot {
     unsigned int* h_status = nullptr;  // pinned: [0] the sticky status word, [1] the launch's level count
     int32_t graph = -1;                // graph of the launch in flight
     bool busy = false;
+    bool long_launch = false;          // the graph counted as long when the launch started
     std::vector<Query*> batch;
     int32_t* d_levels = nullptr;
     blest::MsbfsState ms;
@@ -235,11 +238,16 @@ bool launch_more(blest_server* sv) {
         for (Slot& s : sv->slots)
             if (!s.busy) { slot = &s; break; }
         if (!slot) return any;
-        // graph whose oldest waiting query is oldest
+        // graph whose oldest waiting query is oldest, passing over long graphs while
+        // long_slots launches of long graphs are in flight
+        int long_inflight = 0;
+        for (const Slot& s : sv->slots) long_inflight += (s.busy && s.long_launch) ? 1 : 0;
+        const bool long_full = long_inflight >= sv->p.long_slots;
         int g = -1;
-        for (size_t i = 0; i < sv->pending.size(); ++i)
-            if (!sv->pending[i].empty() && (g < 0 || sv->pending[i].front()->t_submit < sv->pending[g].front()->t_submit))
-                g = (int)i;
+        for (size_t i = 0; i < sv->pending.size(); ++i) {
+            if (sv->pending[i].empty() || (long_full && sv->last_levels[i] > sv->p.narrow_levels)) continue;
+            if (g < 0 || sv->pending[i].front()->t_submit < sv->pending[g].front()->t_submit) g = (int)i;
+        }
         if (g < 0) return any;
         const blest::HandleView& v = sv->views[g];
         std::vector<Query*> batch;
@@ -263,6 +271,7 @@ bool launch_more(blest_server* sv) {
         sv->mem_used += bytes;
         sv->mem_peak = std::max(sv->mem_peak, sv->mem_used);
         s.busy = true;
+        s.long_launch = sv->last_levels[(size_t)g] > sv->p.narrow_levels;
         sv->launches++;
         sv->sources_launched += k;
         cudaError_t e = alloc_launch(s, v, k);
@@ -354,6 +363,7 @@ blest_status blest_server_create(const blest_handle* graphs, int32_t num_graphs,
     sv->p.max_queries_per_launch = params && params->max_queries_per_launch > 0 ? params->max_queries_per_launch : 0;
     sv->p.narrow_sms = params && params->narrow_sms > 0 ? params->narrow_sms : 0;
     sv->p.narrow_levels = params && params->narrow_levels > 0 ? params->narrow_levels : 256;
+    sv->p.long_slots = params && params->long_slots > 0 ? params->long_slots : std::max(1, sv->p.max_inflight - 1);
     if (sv->p.max_batch_sources > 256) return fail(BLEST_ERR_INVALID_ARG, "max_batch_sources must be <= 256");
     if (sv->p.max_inflight > 64) return fail(BLEST_ERR_INVALID_ARG, "max_inflight must be <= 64");
     for (int32_t g = 0; g < num_graphs; ++g) {

@@ -82,6 +82,29 @@ def test_narrow_launches_keep_results(served):
         blest.blest_server_destroy(srv)
 
 
+@pytest.mark.parametrize("long_slots", [1, 2])
+def test_long_slot_cap_keeps_results(served, long_slots):
+    """With launches of long graphs (here the grids: their last launch ran more
+    than narrow_levels levels) capped below the slot count, every query still
+    completes with the oracle's levels, long and short alike."""
+    graphs, handles, queries = served
+    srv = blest.blest_server_create(handles, max_batch_sources=8, max_inflight=3, narrow_levels=10,
+                                    long_slots=long_slots)
+    try:
+        for _ in range(2):                                 # the first pass learns each graph's level count
+            outs, tickets = [], []
+            for gi, srcs, exp in queries:
+                out = np.full((len(srcs), graphs[gi].n), 99, np.int32)
+                outs.append(out)
+                tickets.append(blest.blest_server_submit(srv, gi, srcs, out))
+            for t in tickets:
+                blest.blest_server_wait(srv, t, 60.0)
+            for out, (_, _, exp) in zip(outs, queries):
+                assert np.array_equal(out, exp)
+    finally:
+        blest.blest_server_destroy(srv)
+
+
 def test_memory_cap_admits_one_launch_at_a_time(served):
     graphs, handles, queries = served
     n_max = max(g.n for g in graphs)
