@@ -1,6 +1,7 @@
 """The sharded single-source traversal's host side on CPU ranks (gloo): the
 level driver of paper_2512_21967_gb300.shard with an all-gather + OR exchange
-between 2 and 3 processes.  Each rank's device steps are replaced by a CPU
+between 2, 3 and 4 processes, on a power-law graph, a grid with several
+components, a long path and a source without edges.  Each rank's device steps are replaced by a CPU
 stand-in with the same contract (it pulls only the slice sets s with
 s mod world = rank, returns its V_next words, and finishes a level from the
 merged words), so the test checks what runs on the host: that the partition
@@ -108,12 +109,19 @@ def _graph(case):
     if case == "rmat":
         g = synth.rmat_graph(9, 8, seed=12)
         return g, int(synth.pick_sources(g, 1, seed=3)[0])
+    if case == "isolated":                          # a source with no edges: one pulled level
+        g = synth.rmat_graph(9, 8, seed=12)
+        return g, int(np.flatnonzero(np.diff(g.row_ptr) == 0)[0])
+    if case == "path":                              # 150 levels; most ranks own no frontier at a level
+        n = 150
+        a = np.arange(n - 1, dtype=np.int32)
+        return synth.csr_from_edges(n, a, a + 1), 0
     g, _ = synth.grid_graph(23, 0.85, seed=5)       # n = 529, many levels, several components
     return g, 0
 
 
-@pytest.mark.parametrize("world", [2, 3])
-@pytest.mark.parametrize("case", ["rmat", "grid"])
+@pytest.mark.parametrize("world", [2, 3, 4])
+@pytest.mark.parametrize("case", ["rmat", "grid", "isolated", "path"])
 def test_sharded_levels_on_gloo_ranks(world, case):
     import oracle
     ctx = mp.get_context("spawn")
