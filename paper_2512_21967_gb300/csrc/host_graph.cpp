@@ -579,6 +579,7 @@ struct JaccardWorker {
     const int32_t* row_at;   // window position -> row of g (NULL: the identity)
     int sigma;
     std::vector<int32_t> c, cstamp;
+    std::vector<int32_t> wdeg;   // degree of each window row (read at every pick)
     std::vector<uint8_t> inq;
     std::vector<int32_t> touched;
     // Reverse index of the window: neighbour x -> the window rows that hold x.
@@ -650,6 +651,8 @@ struct JaccardWorker {
         int32_t L = e_k - s_k;
         s_k_ = s_k;
         build_index(s_k, L);
+        wdeg.resize((size_t)L);
+        for (int32_t jl = 0; jl < L; ++jl) wdeg[(size_t)jl] = deg(s_k + jl);
         c.assign((size_t)L, 0);
         cstamp.assign((size_t)L, 0);
         inq.assign((size_t)L, 1);
@@ -677,7 +680,7 @@ struct JaccardWorker {
                 for (int32_t jl : touched) {
                     if (!inq[jl]) continue;
                     int64_t num = c[jl];
-                    int64_t den = (int64_t)deg(s_k + jl) + usize - num;
+                    int64_t den = (int64_t)wdeg[(size_t)jl] + usize - num;
                     // num > 0 here, so den >= 1
                     bool better = best < 0 || num * bden > bnum * den || (num * bden == bnum * den && jl < best);
                     if (better) { best = jl; bnum = num; bden = den; }
