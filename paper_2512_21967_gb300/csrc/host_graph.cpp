@@ -578,7 +578,10 @@ struct JaccardWorker {
     const Csr& g;
     const int32_t* row_at;   // window position -> row of g (NULL: the identity)
     int sigma;
-    std::vector<int32_t> c, cstamp;
+    std::vector<int32_t> c;        // scratch of build_index
+    // per window row: (cluster stamp << 32) | |N(j) & U|, one word per row so that a
+    // list walk reads and writes one array; the count is current iff the stamp is
+    std::vector<uint64_t> cs;
     std::vector<int32_t> wdeg;   // degree of each window row (read at every pick)
     std::vector<uint8_t> inq;
     std::vector<int32_t> touched;
@@ -636,7 +639,7 @@ struct JaccardWorker {
         int32_t run = 0;
         for (size_t h = 0; h < cap; ++h) { hoff[h] = run; run += hlen[h]; }
         revj.resize((size_t)nnz);
-        std::vector<int32_t>& fill = c;   // scratch: per-slot fill position (c is reset by window())
+        std::vector<int32_t>& fill = c;   // scratch: per-slot fill position
         fill.assign(cap, 0);
         for (int32_t jl = 0; jl < L; ++jl)
             for (int64_t i = eoff[(size_t)jl]; i < eoff[(size_t)jl + 1]; ++i) {
@@ -653,8 +656,7 @@ struct JaccardWorker {
         build_index(s_k, L);
         wdeg.resize((size_t)L);
         for (int32_t jl = 0; jl < L; ++jl) wdeg[(size_t)jl] = deg(s_k + jl);
-        c.assign((size_t)L, 0);
-        cstamp.assign((size_t)L, 0);
+        cs.assign((size_t)L, 0);
         inq.assign((size_t)L, 1);
 
         int32_t qptr = 0, remaining = L;
@@ -667,7 +669,7 @@ struct JaccardWorker {
             ++stamp;
             if (stamp == 0x7fffffff) {  // stamp wrap: reset the marks
                 std::fill(ustamp.begin(), ustamp.end(), 0);
-                std::fill(cstamp.begin(), cstamp.end(), 0);
+                std::fill(cs.begin(), cs.end(), 0);
                 stamp = 1;
             }
             int64_t usize = 0;
@@ -679,7 +681,7 @@ struct JaccardWorker {
                 int64_t bnum = 0, bden = 1;
                 for (int32_t jl : touched) {
                     if (!inq[jl]) continue;
-                    int64_t num = c[jl];
+                    int64_t num = (int64_t)(uint32_t)cs[(size_t)jl];
                     int64_t den = (int64_t)wdeg[(size_t)jl] + usize - num;
                     // num > 0 here, so den >= 1
                     bool better = best < 0 || num * bden > bnum * den || (num * bden == bnum * den && jl < best);
@@ -711,8 +713,13 @@ struct JaccardWorker {
                 const int32_t jl = revj[i];
                 if (!inq[jl]) continue;   // placed rows leave the list
                 revj[w++] = (Pos)jl;
-                if (cstamp[jl] != stamp) { cstamp[jl] = stamp; c[jl] = 0; touched.push_back(jl); }
-                ++c[jl];
+                const uint64_t x = cs[jl];
+                if ((uint32_t)(x >> 32) != (uint32_t)stamp) {
+                    cs[jl] = ((uint64_t)(uint32_t)stamp << 32) | 1u;
+                    touched.push_back(jl);
+                } else {
+                    cs[jl] = x + 1u;
+                }
             }
             hlen[h] = w - hoff[h];
         }
