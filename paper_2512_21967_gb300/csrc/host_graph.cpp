@@ -112,27 +112,67 @@ bool is_symmetric(const Csr& g, int threads, int64_t* bad_u, int64_t* bad_v) {
     // the edges (u, v) with v > u one-to-one onto edges with v < u, so the graph
     // is symmetric iff every such upper edge has its reverse and there are as
     // many upper as lower edges.  The reverse of (u, v) lies in row v below v.
+    //
+    // Workers take chunks of consecutive rows u in ascending order, so within a
+    // chunk the reverses sought in one row v come in ascending order too.  In a
+    // long row (a hub, where a binary search misses the cache at most steps) the
+    // worker keeps a cursor per chunk: placed by one binary search at the chunk's
+    // first visit, then moved forward only.  Short rows are binary-searched.
+    constexpr int32_t kHubDeg = 256;
+    constexpr int64_t kChunk = 4096;
+    std::vector<int32_t> hub_of((size_t)g.n, -1);
+    int32_t nhub = 0;
+    for (int32_t v = 0; v < g.n; ++v)
+        if (g.rp[v + 1] - g.rp[v] >= kHubDeg) hub_of[(size_t)v] = nhub++;
     std::atomic<int64_t> found(-1);
     std::atomic<int64_t> found_v(-1);
     std::atomic<int64_t> upper(0), lower(0);
-    parallel_chunks(threads, g.n, 4096, [&](int64_t lo, int64_t hi) {
+    std::atomic<int64_t> next(0);
+    auto worker = [&]() {
+        std::vector<int64_t> cur((size_t)nhub), tag((size_t)nhub, -1);   // cursor and its chunk
         int64_t up = 0, low = 0;
-        for (int64_t u = lo; u < hi && found.load(std::memory_order_relaxed) < 0; ++u) {
-            const int32_t* rb = g.ci.data() + g.rp[u];
-            const int32_t* re = g.ci.data() + g.rp[u + 1];
-            const int32_t* mid = std::upper_bound(rb, re, (int32_t)u);   // first neighbour above u
-            low += mid - rb;
-            up += re - mid;
-            for (const int32_t* p = mid; p < re; ++p) {
-                const int32_t v = *p;
-                const int32_t* b = g.ci.data() + g.rp[v];
-                const int32_t* en = g.ci.data() + g.rp[v + 1];
-                if (!std::binary_search(b, en, (int32_t)u)) { found.store(u); found_v.store(v); break; }
+        for (;;) {
+            const int64_t lo = next.fetch_add(kChunk);
+            if (lo >= g.n || found.load(std::memory_order_relaxed) >= 0) break;
+            const int64_t hi = std::min<int64_t>(g.n, lo + kChunk);
+            for (int64_t u = lo; u < hi && found.load(std::memory_order_relaxed) < 0; ++u) {
+                const int32_t* rb = g.ci.data() + g.rp[u];
+                const int32_t* re = g.ci.data() + g.rp[u + 1];
+                const int32_t* mid = std::upper_bound(rb, re, (int32_t)u);   // first neighbour above u
+                low += mid - rb;
+                up += re - mid;
+                for (const int32_t* p = mid; p < re; ++p) {
+                    const int32_t v = *p;
+                    const int32_t* b = g.ci.data() + g.rp[v];
+                    const int32_t* en = g.ci.data() + g.rp[v + 1];
+                    bool ok;
+                    const int32_t h = hub_of[(size_t)v];
+                    if (h >= 0) {
+                        int64_t c = cur[(size_t)h];
+                        if (tag[(size_t)h] != lo) {
+                            c = std::lower_bound(b, en, (int32_t)u) - b;
+                            tag[(size_t)h] = lo;
+                        }
+                        while (b + c < en && b[c] < (int32_t)u) ++c;
+                        cur[(size_t)h] = c;
+                        ok = b + c < en && b[c] == (int32_t)u;
+                    } else {
+                        ok = std::binary_search(b, en, (int32_t)u);
+                    }
+                    if (!ok) { found.store(u); found_v.store(v); break; }
+                }
             }
         }
         upper += up;
         lower += low;
-    });
+    };
+    {
+        const int nt = (int)std::max<int64_t>(1, std::min<int64_t>(threads, (g.n + kChunk - 1) / kChunk));
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+        worker();
+        for (auto& th : pool) th.join();
+    }
     if (found.load() < 0 && upper.load() != lower.load()) {
         // some lower edge (u, v) has no reverse: find one for the message
         parallel_chunks(threads, g.n, 4096, [&](int64_t lo, int64_t hi) {

@@ -202,3 +202,43 @@ def test_batch_preparation_runs_to_the_device_step():
         assert e.name == "BLEST_ERR_CUDA", str(e)
     else:
         blest.blest_destroy(h)
+
+
+def _drop_entries(g, drops):
+    """g's CSR without the entries (row, col) in drops."""
+    drops = set(drops)
+    rows = [[int(x) for x in g.col_idx[g.row_ptr[u]:g.row_ptr[u + 1]] if (u, int(x)) not in drops]
+            for u in range(g.n)]
+    rp = np.zeros(g.n + 1, np.int32)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    return rp, np.array([x for r in rows for x in r], np.int32)
+
+
+@pytest.mark.parametrize("threads", [1, 4])
+def test_symmetry_check_in_long_rows(threads):
+    """Rows of 256 entries or more are searched with a forward-only cursor per
+    chunk of rows; a reverse missing there, alone or several in one row, in
+    either direction, must be reported with an edge whose reverse is absent."""
+    from paper_2512_21967_gb300 import synth
+    g = synth.rmat_graph(12, 16, seed=3)
+    deg = np.diff(g.row_ptr)
+    hubs = np.flatnonzero(deg >= 256)
+    assert len(hubs) >= 3
+    blest.blest_compute_order(g.n, g.row_ptr, g.col_idx, blest.BLEST_ORDER_NONE, threads=threads)   # symmetric
+    rng = np.random.default_rng(11)
+    edges = {(u, int(x)) for u in range(g.n) for x in g.col_idx[g.row_ptr[u]:g.row_ptr[u + 1]]}
+    for trial in range(12):
+        v = int(rng.choice(hubs))
+        row = g.col_idx[g.row_ptr[v]:g.row_ptr[v + 1]]
+        below = row[row < v]
+        us = [int(x) for x in rng.choice(below, size=min(len(below), 1 + trial % 3), replace=False)]
+        # trial even: drop (v, u) from the long row v, so the upper edges (u, v) lose their
+        # reverses; odd: drop (u, v) from the rows u, so the lower edges (v, u) of row v do
+        drops = [(v, u) for u in us] if trial % 2 == 0 else [(u, v) for u in us]
+        rp, ci = _drop_entries(g, drops)
+        with pytest.raises(blest.BlestError) as e:
+            blest.blest_compute_order(g.n, rp, ci, blest.BLEST_ORDER_NONE, threads=threads)
+        assert e.value.name == "BLEST_ERR_NOT_SYMMETRIC"
+        a, b = (int(t) for t in str(e.value).split("edge (")[1].split(")")[0].split(", "))
+        kept = edges - set(drops)
+        assert (a, b) in kept and (b, a) not in kept, (drops, (a, b))
