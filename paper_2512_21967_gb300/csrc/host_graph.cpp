@@ -355,70 +355,137 @@ struct LevelBfs {
 // One level of a FIFO-order BFS: appends to queue[tail..), for i = fs .. fe-1 in
 // order, the neighbours of queue[i] that are not yet seen and not taken by an
 // earlier position, each group in the order arrange(u, first, last) leaves it,
-// and marks them seen.  Returns the new tail.  Large levels run on `threads`
-// threads with the same result: every such neighbour belongs to the smallest
-// position that reaches it (an atomic minimum in owner[], which must hold
-// INT32_MAX for unseen vertices), and each position writes its group at an
-// offset from a prefix sum of group sizes.
+// and marks them seen.  Returns the new tail.
 template <class Arrange>
 static int64_t expand_level_fifo(const Csr& g, int32_t* queue, int64_t fs, int64_t fe, int64_t tail,
-                                 std::vector<uint8_t>& seen, std::vector<int32_t>& owner, int threads,
-                                 Arrange arrange) {
-    constexpr int64_t kParallelLevel = 65536;   // three thread launches per level must pay off
-    if (threads <= 1 || fe - fs < kParallelLevel) {
-        for (int64_t i = fs; i < fe; ++i) {
-            const int32_t u = queue[i];
-            const int64_t first = tail;
-            for (int32_t e = g.rp[u]; e < g.rp[u + 1]; ++e) {
-                const int32_t v = g.ci[e];
-                if (!seen[(size_t)v]) { seen[(size_t)v] = 1; queue[tail++] = v; }
-            }
-            arrange(u, queue + first, queue + tail);
+                                 std::vector<uint8_t>& seen, Arrange arrange) {
+    for (int64_t i = fs; i < fe; ++i) {
+        const int32_t u = queue[i];
+        const int64_t first = tail;
+        for (int32_t e = g.rp[u]; e < g.rp[u + 1]; ++e) {
+            const int32_t v = g.ci[e];
+            if (!seen[(size_t)v]) { seen[(size_t)v] = 1; queue[tail++] = v; }
         }
-        return tail;
+        arrange(u, queue + first, queue + tail);
     }
-    // owners: the smallest frontier position with an edge to each unseen neighbour
-    parallel_chunks(threads, fe - fs, 256, [&](int64_t lo, int64_t hi) {
-        for (int64_t i = fs + lo; i < fs + hi; ++i) {
-            const int32_t u = queue[i];
-            for (int32_t e = g.rp[u]; e < g.rp[u + 1]; ++e) {
-                const int32_t v = g.ci[e];
-                if (seen[(size_t)v]) continue;
-                int32_t cur = __atomic_load_n(&owner[(size_t)v], __ATOMIC_RELAXED);
-                while ((int32_t)i < cur && !__atomic_compare_exchange_n(&owner[(size_t)v], &cur, (int32_t)i, true,
-                                                                          __ATOMIC_RELAXED, __ATOMIC_RELAXED)) {
+    return tail;
+}
+
+// Every remaining level of one component's FIFO-order BFS, queue[fs, tail) being
+// the current frontier: the same result as expand_level_fifo level after level.
+// Levels run sequentially until one holds kPoolLevel positions; from then on
+// `threads` host threads stay alive for the rest of the component and meet at
+// spin barriers, so that a high-diameter graph's thousands of mid-sized levels
+// do not each pay thread launches.  A pooled level of kPoolLevel positions or
+// more is expanded by all threads: every unseen neighbour belongs to the
+// smallest position that reaches it (an atomic minimum in owner[], which holds
+// INT32_MAX for every vertex not yet owned), and each position writes its group
+// at an offset from a prefix sum of group sizes; smaller levels run on thread 0.
+// Returns the new tail.
+template <class Arrange>
+static int64_t fifo_component(const Csr& g, int32_t* queue, int64_t fs, int64_t tail, std::vector<uint8_t>& seen,
+                              std::vector<int32_t>& owner, int threads, Arrange arrange) {
+    constexpr int64_t kPoolLevel = 1024;
+    constexpr int64_t kChunk = 256;
+    while (fs < tail && (threads <= 1 || tail - fs < kPoolLevel)) {
+        const int64_t fe = tail;
+        tail = expand_level_fifo(g, queue, fs, fe, tail, seen, arrange);
+        fs = fe;
+    }
+    if (fs >= tail) return tail;
+    const int T = threads;
+    SpinBarrier bar(T);
+    std::atomic<int64_t> next_own(0), next_count(0), next_place(0), next_seen(0);
+    std::vector<int64_t> off;                // group offsets of the current level's positions
+    int64_t lvl_fs = fs, lvl_fe = tail;      // the current level; written by thread 0 between barriers
+    int64_t new_tail = tail;
+    bool done = false;
+    auto worker = [&](int t) {
+        for (;;) {
+            const int64_t s = lvl_fs, e = lvl_fe, L = e - s;
+            if (L < kPoolLevel) {
+                if (t == 0) new_tail = expand_level_fifo(g, queue, s, e, e, seen, arrange);
+            } else {
+                for (;;) {   // owners
+                    const int64_t c = s + next_own.fetch_add(kChunk, std::memory_order_relaxed);
+                    if (c >= e) break;
+                    for (int64_t i = c, ce = std::min(c + kChunk, e); i < ce; ++i) {
+                        const int32_t u = queue[i];
+                        for (int32_t x = g.rp[u]; x < g.rp[u + 1]; ++x) {
+                            const int32_t v = g.ci[x];
+                            if (seen[(size_t)v]) continue;
+                            int32_t cur = __atomic_load_n(&owner[(size_t)v], __ATOMIC_RELAXED);
+                            while ((int32_t)i < cur &&
+                                   !__atomic_compare_exchange_n(&owner[(size_t)v], &cur, (int32_t)i, true,
+                                                                __ATOMIC_RELAXED, __ATOMIC_RELAXED)) {
+                            }
+                        }
+                    }
+                }
+                bar.wait();
+                for (;;) {   // group sizes
+                    const int64_t c = s + next_count.fetch_add(kChunk, std::memory_order_relaxed);
+                    if (c >= e) break;
+                    for (int64_t i = c, ce = std::min(c + kChunk, e); i < ce; ++i) {
+                        const int32_t u = queue[i];
+                        int64_t k = 0;
+                        for (int32_t x = g.rp[u]; x < g.rp[u + 1]; ++x) {
+                            const int32_t v = g.ci[x];
+                            k += !seen[(size_t)v] && owner[(size_t)v] == (int32_t)i;
+                        }
+                        off[(size_t)(i - s) + 1] = k;
+                    }
+                }
+                bar.wait();
+                if (t == 0) {
+                    off[0] = 0;
+                    for (int64_t k = 1; k <= L; ++k) off[(size_t)k] += off[(size_t)k - 1];
+                    new_tail = e + off[(size_t)L];
+                }
+                bar.wait();
+                for (;;) {   // groups, each arranged
+                    const int64_t c = s + next_place.fetch_add(kChunk, std::memory_order_relaxed);
+                    if (c >= e) break;
+                    for (int64_t i = c, ce = std::min(c + kChunk, e); i < ce; ++i) {
+                        const int32_t u = queue[i];
+                        int32_t* first = queue + e + off[(size_t)(i - s)];
+                        int32_t* w = first;
+                        for (int32_t x = g.rp[u]; x < g.rp[u + 1]; ++x) {
+                            const int32_t v = g.ci[x];
+                            if (!seen[(size_t)v] && owner[(size_t)v] == (int32_t)i) *w++ = v;
+                        }
+                        arrange(u, first, w);
+                    }
+                }
+                bar.wait();
+                for (;;) {   // the new level is seen
+                    const int64_t c = e + next_seen.fetch_add(kChunk, std::memory_order_relaxed);
+                    if (c >= new_tail) break;
+                    for (int64_t k = c, ce = std::min(c + kChunk, new_tail); k < ce; ++k)
+                        seen[(size_t)queue[k]] = 1;
                 }
             }
-        }
-    });
-    std::vector<int64_t> off((size_t)(fe - fs) + 1, 0);
-    parallel_chunks(threads, fe - fs, 256, [&](int64_t lo, int64_t hi) {
-        for (int64_t i = fs + lo; i < fs + hi; ++i) {
-            const int32_t u = queue[i];
-            int64_t c = 0;
-            for (int32_t e = g.rp[u]; e < g.rp[u + 1]; ++e) {
-                const int32_t v = g.ci[e];
-                c += !seen[(size_t)v] && owner[(size_t)v] == (int32_t)i;
+            bar.wait();
+            if (t == 0) {   // the next level
+                next_own.store(0, std::memory_order_relaxed);
+                next_count.store(0, std::memory_order_relaxed);
+                next_place.store(0, std::memory_order_relaxed);
+                next_seen.store(0, std::memory_order_relaxed);
+                lvl_fs = e;
+                lvl_fe = new_tail;
+                done = new_tail == e;
+                if ((int64_t)off.size() < new_tail - e + 1) off.resize((size_t)(new_tail - e + 1));
             }
-            off[(size_t)(i - fs) + 1] = c;
+            bar.wait();
+            if (done) return;
         }
-    });
-    for (size_t k = 1; k < off.size(); ++k) off[k] += off[k - 1];
-    parallel_chunks(threads, fe - fs, 256, [&](int64_t lo, int64_t hi) {
-        for (int64_t i = fs + lo; i < fs + hi; ++i) {
-            const int32_t u = queue[i];
-            int32_t* first = queue + tail + off[(size_t)(i - fs)];
-            int32_t* w = first;
-            for (int32_t e = g.rp[u]; e < g.rp[u + 1]; ++e) {
-                const int32_t v = g.ci[e];
-                if (!seen[(size_t)v] && owner[(size_t)v] == (int32_t)i) *w++ = v;
-            }
-            arrange(u, first, w);
-        }
-    });
-    const int64_t new_tail = tail + off.back();
-    for (int64_t k = tail; k < new_tail; ++k) seen[(size_t)queue[k]] = 1;
-    return new_tail;
+    };
+    if ((int64_t)off.size() < tail - fs + 1) off.resize((size_t)(tail - fs + 1));
+    std::vector<std::thread> pool;
+    for (int t = 1; t < T; ++t) pool.emplace_back(worker, t);
+    worker(0);
+    for (auto& th : pool) th.join();
+    return lvl_fe;
 }
 
 static int32_t pseudo_peripheral(const Csr& g, LevelBfs& bfs, int32_t start) {
@@ -468,13 +535,10 @@ void order_rcm(const Csr& g, std::vector<int32_t>& new_id, int threads) {
         }
         int32_t r = pseudo_peripheral(g, bfs, v0);
         seen[r] = 1;
-        int64_t fs = tail;
+        const int64_t fs = tail;
         order[(size_t)tail++] = r;
-        while (fs < tail) {   // one BFS level at a time, in the FIFO order of the sequential method
-            const int64_t fe = tail;
-            tail = expand_level_fifo(g, order.data(), fs, fe, tail, seen, owner, threads, by_degree);
-            fs = fe;
-        }
+        // level by level, in the FIFO order of the sequential method
+        tail = fifo_component(g, order.data(), fs, tail, seen, owner, threads, by_degree);
     }
     for (int64_t pos = 0; pos < n; ++pos) new_id[order[pos]] = (int32_t)(n - 1 - pos);
 }
@@ -503,13 +567,9 @@ void order_hub_prepass(const Csr& g, std::vector<int32_t>& new_id, int threads) 
     for (int32_t r : cand) {
         if (seen[r]) continue;
         seen[r] = 1;
-        int64_t fs = tail;
+        const int64_t fs = tail;
         order[(size_t)tail++] = r;
-        while (fs < tail) {
-            const int64_t fe = tail;
-            tail = expand_level_fifo(g, order.data(), fs, fe, tail, seen, owner, threads, as_listed);
-            fs = fe;
-        }
+        tail = fifo_component(g, order.data(), fs, tail, seen, owner, threads, as_listed);
     }
     for (int32_t pos = 0; pos < n; ++pos) new_id[order[pos]] = pos;
 }

@@ -156,6 +156,41 @@ int main() {
             if (!sorted || longest <= 1024) { std::printf("relabelled rows: sorted %d longest %lld\n", sorted, (long long)longest); ++failures; }
         }
     }
+    // a high-diameter layered graph: 120 layers of 1100 vertices, vertex i of a layer
+    // joined to vertices 7i+3 and 11i+4 (mod 1100) of the next (one connected graph), so
+    // that after a few levels a BFS level spans about a layer: 113 of its 122 levels
+    // reach the size at which the FIFO levels of RCM and the pre-pass use the thread pool
+    {
+        const int32_t W = 1100, H = 120, n = W * H;
+        std::vector<std::vector<int32_t>> adj((size_t)n);
+        for (int32_t k = 0; k + 1 < H; ++k)
+            for (int32_t i = 0; i < W; ++i) {
+                const int32_t u = k * W + i;
+                for (int32_t j : {(7 * i + 3) % W, (11 * i + 4) % W}) {
+                    const int32_t v = (k + 1) * W + j;
+                    adj[(size_t)u].push_back(v);
+                    adj[(size_t)v].push_back(u);
+                }
+            }
+        std::vector<int32_t> rp((size_t)n + 1, 0), ci;
+        for (int32_t u = 0; u < n; ++u) {
+            for (int32_t v : adj[(size_t)u]) ci.push_back(v);
+            rp[(size_t)u + 1] = (int32_t)ci.size();
+        }
+        blest::Csr g;
+        std::string err;
+        if (blest::clean_csr(n, rp.data(), ci.data(), 4, g, err) != 0) {
+            ++failures;
+        } else {
+            std::vector<int32_t> one, four;
+            blest::order_rcm(g, one, 1);
+            blest::order_rcm(g, four, 4);
+            if (!is_perm(one, n) || one != four) { std::printf("layered RCM differs across thread counts\n"); ++failures; }
+            blest::order_hub_prepass(g, one, 1);
+            blest::order_hub_prepass(g, four, 4);
+            if (!is_perm(one, n) || one != four) { std::printf("layered pre-pass differs across thread counts\n"); ++failures; }
+        }
+    }
     // a long row whose relabelled ids fill all three 10-bit radix digits (ids up to 2^23)
     {
         const int32_t n = 1 << 23, hub = 12345, deg = 5000;
