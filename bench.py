@@ -151,25 +151,34 @@ class ClockSampler:
         except Exception:
             self.p.kill()
             out = ""
-        sm, smax, reasons, power = [], [], set(), []
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.strip().splitlines():
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
-                power.append(float(f[3]))
-            except ValueError:
-                continue
-            for nm, val in zip(names, f[5:9]):
-                if val.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
-                "samples": len(sm), "power_w_max": float(max(power)) if power else None}
+        return parse_clock_samples(out)
+
+
+def parse_clock_samples(text):
+    """The clock record of a timed region from nvidia-smi's CSV samples (the
+    fields of ClockSampler.FIELDS, no header, no units): median SM clock, the
+    maximum SM clock, every throttle reason seen active in any sample, the sample
+    count and the highest power draw.  Lines with unreadable numbers are skipped."""
+    sm, smax, reasons, power = [], [], set(), []
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in text.strip().splitlines():
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm_v, smax_v, power_v = float(f[1]), float(f[2]), float(f[3])
+        except ValueError:
+            continue
+        sm.append(sm_v)
+        smax.append(smax_v)
+        power.append(power_v)
+        for nm, val in zip(names, f[5:9]):
+            if val.lower().startswith("active"):
+                reasons.add(nm)
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+    return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+            "samples": len(sm), "power_w_max": float(max(power))}
 
 
 # ------------------------------------------------------------- byte model

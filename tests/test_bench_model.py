@@ -161,3 +161,19 @@ def test_committed_traffic_captures_match_the_kernel_sources():
     assert bench.traffic_ratio(workload="rmat23", variant="lazy-layout0")[0] is not None
     assert bench.traffic_ratio(bench.MS_TRAFFIC_FILE, bench.MS_KERNEL_SOURCES, workload="rmat22-ms64",
                                variant="popc-levels2-v2-c256")[0] is not None
+
+
+def test_clock_record_from_nvidia_smi_samples():
+    """The clock record that decides whether a timed run is kept: median SM clock,
+    every throttle reason active in any sample, unreadable lines skipped."""
+    import bench
+    idle = "0, 2070, 2070, 210.50, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active"
+    capped = "0, 1965, 2070, 1398.10, 0x0000000000000004, Not Active, Not Active, Not Active, Active"
+    hot = "0, 1800, 2070, 1200.00, 0x0000000000000008, Active, Not Active, Not Active, Not Active"
+    r = bench.parse_clock_samples("\n".join([idle, idle, capped]))
+    assert r["sm_mhz"] == 2070.0 and r["sm_max_mhz"] == 2070.0 and r["samples"] == 3
+    assert r["reasons"] == ["sw_power_cap"] and r["power_w_max"] == 1398.1
+    r = bench.parse_clock_samples("\n".join([hot, capped, "0, [N/A], 2070, 5, x, a, b, c, d", "short, line"]))
+    assert r["samples"] == 2 and r["sm_mhz"] == (1800.0 + 1965.0) / 2
+    assert r["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert bench.parse_clock_samples("")["reasons"] == ["no samples"]
